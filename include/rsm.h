@@ -1,0 +1,206 @@
+/*
+ * rsm.h - C ABI of the GB300 Random SubMatrix (RSM) library (librsm.so).
+ *
+ * RSM (Y. Liu, arXiv 1411.0814) computes a rank-r decomposition Y ~ U V^T of an
+ * m x n matrix Y with missing entries (eq. problem, Section I):
+ *   step 2 (Section IV-A): repeatedly draw l columns (method M1, Section III),
+ *          keep the rows known in all of them, and take the l - r right singular
+ *          vectors of the smallest singular values of that submatrix;
+ *   step 3: accumulate M = Xi Xi^T = sum xi xi^T (eq. XI and the text after
+ *          eq. solve.barV_L2_norm), take V = the r smallest eigenvectors of M,
+ *          then solve U row by row by least squares (eq. solve.barU).
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are column-major.  "device" pointers are CUDA device memory of
+ *     the handle's (or the current) device; "host" pointers are ordinary host
+ *     memory.  The caller owns every pointer it passes; the library never frees
+ *     or retains one past the call (rsm_submit: past completion, see there).
+ *   - No C++ exception crosses this boundary; every failure is a status code.
+ *   - Arguments are validated before any launch; on RSM_ERR_INVALID_ARG nothing
+ *     was launched and no output was written.
+ *   - A "stream" argument is a cudaStream_t passed as void* (NULL = legacy
+ *     default stream).  Stage entry points are asynchronous on that stream.
+ */
+#ifndef RSM_H_
+#define RSM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rsm_status {
+  RSM_OK = 0,
+  RSM_ERR_INVALID_ARG = 1,          /* a size, pointer, leading dimension or enum is out of range */
+  RSM_ERR_NO_MEMORY = 2,            /* footprint above the handle's HBM budget, or cudaMalloc failed */
+  RSM_ERR_UNDERDETERMINED = 3,      /* no accepted trial, or M has more than r numerically zero
+                                       eigenvalues (rank(Xi) < n - r, Section III before eq.
+                                       solve.barV); V and U are not written */
+  RSM_ERR_ROWS_UNDERDETERMINED = 4, /* V and U are written, but some rows of Y have fewer than r
+                                       known entries; those rows got the minimum-norm solution */
+  RSM_ERR_TIMEOUT = 5,              /* a bounded device-side or host-side wait ran out */
+  RSM_ERR_CANCELLED = 6,            /* the request was cancelled before it ran */
+  RSM_ERR_CUDA = 7,                 /* a CUDA runtime call failed (message: rsm_last_error) */
+  RSM_ERR_NOT_IMPLEMENTED = 8,      /* the requested option exists in the ABI but not in this build */
+  RSM_PENDING = 9,                  /* rsm_poll: the request has not finished */
+  RSM_ERR_QUEUE_FULL = 10           /* rsm_submit: the admission queue is full; retry later */
+} rsm_status;
+
+/* Element type of Y. */
+typedef enum rsm_dtype { RSM_F64 = 0, RSM_F32 = 1 } rsm_dtype;
+
+/* Arithmetic of the two bulk contractions: the per-trial Gram A^T A of step 2
+ * and the per-row normal equations of step 3.
+ *   RSM_PREC_F64:   FP64 multiply-add throughout.
+ *   RSM_PREC_F32X2: products and sums carried as unevaluated pairs of FP32
+ *                   values (about 48 significant bits) on the FP32 pipes.
+ *   RSM_PREC_F32:   FP32 multiply-add (the reduced-precision form).
+ * The l x l eigenproblems, the accumulation of M, the eigensolve of M and the
+ * r x r solves are FP64 in every mode. */
+typedef enum rsm_prec { RSM_PREC_F64 = 0, RSM_PREC_F32X2 = 1, RSM_PREC_F32 = 2 } rsm_prec;
+
+/* Column sampler (Section III, method M1). */
+typedef enum rsm_variant {
+  RSM_COLS_RANDOM = 0,   /* l distinct columns, uniform without replacement (Floyd's algorithm) */
+  RSM_COLS_ADJACENT = 1  /* l contiguous columns s..s+l-1, s uniform in [0, n-l] */
+} rsm_variant;
+
+typedef struct rsm_config {
+  int32_t device;            /* CUDA device ordinal */
+  int32_t max_slots;         /* requests the serving loop runs concurrently (0 -> 4) */
+  size_t hbm_budget_bytes;   /* library-owned device memory the handle may hold (0 -> 80% of free) */
+  uint64_t wait_timeout_ns;  /* bound on every blocking wait of the serving loop (0 -> 10 s) */
+  void* stream;              /* cudaStream_t used by rsm_decompose (NULL -> a stream the handle creates) */
+  uint32_t fault_inject;     /* host-side fault injection for tests (RSM_FAULT_* bits); 0 in production */
+  uint32_t reserved;
+} rsm_config;
+
+/* Host-side fault injection bits (rsm_config.fault_inject).  They act on the
+ * host only: no kernel is ever made to fault, trap or hang. */
+#define RSM_FAULT_ADMISSION 0x1u  /* every admission check reports the budget exhausted */
+#define RSM_FAULT_ALLOC 0x2u      /* the next workspace allocation reports failure */
+#define RSM_FAULT_STALL 0x4u      /* the scheduler withholds work, so waits run out (TIMEOUT) */
+
+typedef struct rsm_problem {
+  int64_t m, n;          /* Y is m x n; the paper assumes m >= n (Section II) */
+  int32_t r;             /* target rank, 1 <= r < n */
+  int32_t l;             /* columns per submatrix, r < l <= n; 0 -> r + 1 (Section IV-A step 1) */
+  int32_t n_minor;       /* minor vectors kept per submatrix, 1..l-r; 0 -> l - r (Section III) */
+  int32_t variant;       /* rsm_variant */
+  int64_t trials;        /* number of submatrix draws I >= 1 (rejected draws count) */
+  uint64_t seed;         /* Philox key of the column sampler */
+  uint32_t problem_id;   /* second counter word of the sampler, distinguishes problems */
+  int32_t y_dtype;       /* rsm_dtype of Y */
+  int32_t gram_prec;     /* rsm_prec of the per-trial Gram */
+  int32_t solve_prec;    /* rsm_prec of the per-row normal equations */
+  const void* Y;         /* device, m x n column-major, leading dimension ldy >= m; read only */
+  int64_t ldy;
+  const uint8_t* W;      /* device, m x n column-major bytes, 1 = known (eq. problem); read only */
+  int64_t ldw;
+  double* U;             /* device output m x r (ldu >= m), or NULL to stop after V */
+  int64_t ldu;
+  double* V;             /* device output n x r (ldv >= n), orthonormal columns */
+  int64_t ldv;
+  /* Optional device outputs for inspection (NULL = not written). */
+  int32_t* debug_cols;       /* trials x l, row-major: the sorted column set of each trial */
+  int32_t* debug_row_counts; /* trials: rows kept by each trial (p_t), rejected trials included */
+  double* debug_Z;           /* trials x l x n_minor: minor vectors (zero for rejected trials) */
+  double* debug_M;           /* n x n: the accumulated M */
+} rsm_problem;
+
+typedef struct rsm_result {
+  int32_t status;                /* rsm_status of the decomposition */
+  int32_t n_eig;                 /* eigenvalues of M reported in eig_M */
+  int64_t accepted_trials;       /* trials that kept at least l rows */
+  int64_t rows_underdetermined;  /* rows with fewer than r known entries */
+  double eig_M[32];              /* smallest eigenvalues of M, ascending */
+  double e_known_rms;            /* eq. (ep): RMS residual over the known entries (NaN if U is NULL) */
+  float stage_ms[8];             /* pack, sample+select+gram, minor+scatter, eig M, solve U, residual, -, total */
+  double queue_ms;               /* serving: submit -> start */
+  double run_ms;                 /* serving: start -> finish */
+} rsm_result;
+
+typedef struct rsm_handle rsm_handle;
+
+/* Library version string (static storage). */
+const char* rsm_version(void);
+/* Text for a status code (static storage). */
+const char* rsm_status_string(int32_t status);
+/* Message of the last failure on the calling thread (thread-local storage). */
+const char* rsm_last_error(void);
+
+/* Create a handle bound to config->device (config may be NULL for defaults).
+ * On success *out owns the device workspace and the serving threads. */
+int32_t rsm_create(const rsm_config* config, rsm_handle** out);
+/* Wait for in-flight work (bounded by the wait timeout), then free everything
+ * the handle owns.  NULL is ignored. */
+void rsm_destroy(rsm_handle* h);
+
+/* Device bytes a problem needs beyond the caller's Y, W, U and V: the packed
+ * mask, the sampled columns, per-trial Grams and minor vectors, M and the
+ * eigensolver workspace.  0 if the problem is invalid.  Pure host arithmetic. */
+size_t rsm_footprint_bytes(const rsm_problem* p);
+
+/* Synchronous decomposition (Section IV-A steps 1-3).  Runs every stage on the
+ * handle's stream and returns after the stream is synchronised.  res (host)
+ * may be NULL.  Returns the same status as res->status. */
+int32_t rsm_decompose(rsm_handle* h, const rsm_problem* p, rsm_result* res);
+
+/* Batched decomposition of count independent problems (host array ps).  The
+ * problems share the launches of every stage (one launch covers all trials of
+ * all problems).  res (host) holds count results or is NULL.  Returns RSM_OK if
+ * every problem succeeded, else the first failing status. */
+int32_t rsm_decompose_batch(rsm_handle* h, const rsm_problem* ps, int32_t count, rsm_result* res);
+
+/* Serving: enqueue a problem.  The problem struct is copied; Y, W, U, V and the
+ * debug buffers must stay valid until rsm_poll reports a final status.  A
+ * request is admitted when a slot is free and its footprint fits the budget;
+ * requests run concurrently on separate streams.  *ticket identifies it. */
+int32_t rsm_submit(rsm_handle* h, const rsm_problem* p, uint64_t* ticket);
+/* Non-blocking: RSM_PENDING while queued or running, else the final status
+ * (res filled).  A finished ticket can be polled again until rsm_release. */
+int32_t rsm_poll(rsm_handle* h, uint64_t ticket, rsm_result* res);
+/* Blocking form of rsm_poll, bounded by timeout_ns (0 -> the handle's wait
+ * timeout); returns RSM_ERR_TIMEOUT if the request is still pending then. */
+int32_t rsm_wait(rsm_handle* h, uint64_t ticket, uint64_t timeout_ns, rsm_result* res);
+/* Cancel a request that has not started (RSM_ERR_CANCELLED becomes its status);
+ * a running request is not interrupted and RSM_ERR_INVALID_ARG is returned. */
+int32_t rsm_cancel(rsm_handle* h, uint64_t ticket);
+/* Forget a finished ticket. */
+int32_t rsm_release(rsm_handle* h, uint64_t ticket);
+
+/* ---- Stage entry points: one hot-path kernel each, asynchronous on stream ---- */
+
+/* Pack the mask (Section IV-A: submatrix extraction needs only logical tests on
+ * W).  W: device m x n bytes (ldw >= m), nonzero = known.  bits: device
+ * n x ldb uint32 words, column c at bits + c*ldb, bit (i mod 32) of word i/32 is
+ * W[i, c] != 0; ldb >= ceil(m/32); words past the last row are zero. */
+int32_t rsm_pack_mask(const uint8_t* W, int64_t ldw, int64_t m, int64_t n, uint32_t* bits, int64_t ldb,
+                      void* stream);
+
+/* Draw the column sets of trials t0..t0+count-1 (Section III, M1; Section II:
+ * the indices of a list are distinct).  Word w of trial t is lane (w mod 4) of
+ * Philox4x32-10 with key (seed mod 2^32, seed >> 32) and counter
+ * (t mod 2^32, problem_id, w div 4, t >> 32); a draw in [0, k) is
+ * (word * k) >> 32.  RANDOM: Floyd's algorithm, draw number d = 0..l-1 picks x
+ * in [0, n-l+d] from word d and inserts n-l+d if x is already taken; ADJACENT:
+ * s from word 0 in [0, n-l].  cols: device count x l int32, each row ascending. */
+int32_t rsm_sample_columns(int64_t n, int32_t l, int64_t t0, int64_t count, uint64_t seed, uint32_t problem_id,
+                           int32_t variant, int32_t* cols, void* stream);
+
+/* Row lists R_t (Section III, M1: the rows whose entries in all chosen columns
+ * are known) for count trials.  bits/ldb: packed mask (rsm_pack_mask).  cols:
+ * device count x l.  row_offsets: device count+1 int64, exclusive prefix of the
+ * caller's capacity per trial; rows: device int32 array of row_offsets[count]
+ * entries.  row_counts: device count int32, receives p_t; a trial whose p_t
+ * exceeds its capacity writes only the first rows (ascending). */
+int32_t rsm_select_rows(const uint32_t* bits, int64_t ldb, int64_t m, const int32_t* cols, int32_t l, int64_t count,
+                        const int64_t* row_offsets, int32_t* rows, int32_t* row_counts, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSM_H_ */
