@@ -126,6 +126,9 @@ typedef struct rsm_handle rsm_handle;
 
 /* Library version string (static storage). */
 const char* rsm_version(void);
+/* sizeof of the ABI structs, for bindings to check their layout:
+ * which = 0 rsm_config, 1 rsm_problem, 2 rsm_result; 0 for other values. */
+size_t rsm_struct_size(int32_t which);
 /* Text for a status code (static storage). */
 const char* rsm_status_string(int32_t status);
 /* Message of the last failure on the calling thread (thread-local storage). */

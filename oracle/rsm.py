@@ -25,7 +25,8 @@ Readings of points the paper leaves open (each applied below):
     orthonormal (eq. solve.barV_L2_norm; the norm constraint read as V^T V = I);
   * the problem is underdetermined when M has more than r numerically zero
     eigenvalues (rank(Xi) < n - r, Section III before eq. solve.barV) or when no
-    trial is accepted;
+    trial is accepted; "numerically zero" means lambda_{r+1} <= 1e-12 trace(M),
+    the numerical rank of Xi relative to ||Xi||_F^2 = trace(M);
   * U-hat: per row, least squares over the known entries (eq. solve.barU with
     the L2 norm); a row with fewer than r known entries gets the minimum-norm
     solution and is counted.
@@ -43,7 +44,7 @@ STATUS_OK = 0
 STATUS_UNDERDETERMINED = 3
 STATUS_ROWS_UNDERDETERMINED = 4
 
-# Numerical-zero threshold for lambda_{r+1}(M) relative to lambda_max(M).
+# Numerical-zero threshold for lambda_{r+1}(M) relative to trace(M) = ||Xi||_F^2.
 RANK_TOL = 1e-12
 
 
@@ -216,9 +217,9 @@ def decompose(Y: np.ndarray, W: np.ndarray, r: int, l: Optional[int] = None, tri
         Z_list.append(minor_vectors(A, n_minor))
     M = accumulate_M(n, cols, Z_list)
     V, evals = eig_smallest(M, r)
-    lam_max = max(float(evals[-1]), 0.0)
+    trace = max(float(np.trace(M)), 0.0)
     status = STATUS_OK
-    if accepted.sum() == 0 or evals[r] <= RANK_TOL * lam_max:
+    if accepted.sum() == 0 or evals[r] <= RANK_TOL * trace:
         status = STATUS_UNDERDETERMINED
     U, under, e = None, 0, float("nan")
     if solve_u and status == STATUS_OK:

@@ -1,0 +1,140 @@
+// Shared device-side definitions of the RSM library: the per-problem
+// descriptor every batched kernel reads, the Philox4x32-10 generator and a few
+// block-level helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rsm {
+
+constexpr int kMaxL = 32;  // columns per submatrix supported by the kernels
+constexpr int kMaxR = 32;  // rank supported by the kernels (r < l <= 32)
+
+// Everything a kernel needs to know about one problem of a batch.  Lives in
+// device memory (an array with one entry per problem).
+struct ProbDesc {
+  int64_t m, n, trials;
+  int32_t r, l, n_minor, variant;
+  uint64_t seed;
+  uint32_t pid;
+  int32_t y_dtype;  // 0 = FP64, 1 = FP32
+  // caller inputs
+  const void* Y;
+  int64_t ldy;
+  const uint8_t* W;
+  int64_t ldw;
+  // library workspace
+  uint32_t* bits;  // packed mask, n columns of ldb words
+  int64_t ldb;
+  int32_t* cols;        // trials x l
+  int32_t* row_counts;  // trials
+  double* gram;         // trials x l(l+1)/2, packed upper triangle (a <= b), row-major by a
+  unsigned long long* macc;  // n x n fixed-point accumulator of M
+  double* M;                 // n x n
+  void* F1;                  // npad x npad work (Cholesky factor, then A^-1), FP32 or FP64
+  void* F2;                  // npad x npad work (inverse factor)
+  void* Dinv;                // nblk diagonal-block inverses, 32 x 32 each
+  double* X;                 // n x kx  subspace
+  double* MX;                // n x kx
+  double* R;                 // n x kx
+  double* small;             // per-problem small matrices (k x k blocks)
+  double* Kmat;              // n x q_pad products of V for the normal equations
+  double* NB;                // m x q_pad normal-equation data (N_i packed, b_i)
+  unsigned long long* counters;  // [0] accepted trials, [1] known entries, [2] max column count, [3] chol fail
+  int32_t* colcount;             // n: how many trials drew each column
+  double* stats;                 // [0..31] eigenvalues, [32] residual num, [33] e, [34] eig residual
+  // outputs
+  double* U;
+  int64_t ldu;
+  double* V;
+  int64_t ldv;
+  double* debug_Z;
+  double* debug_M;
+  int32_t* debug_cols;
+  int32_t* debug_row_counts;
+  // sizes of the eigen stage
+  int32_t kx;    // subspace dimension (r + extra, <= n)
+  int32_t nblk;  // ceil(n / 32)
+  int32_t q;     // number of normal-equation columns: r(r+1)/2 + r
+  int32_t q_pad;
+  int32_t status;  // device-written status of this problem
+  int32_t pad_;
+};
+
+// ------------------------------------------------------------------ Philox4x32-10
+// J. K. Salmon et al., "Parallel random numbers: as easy as 1, 2, 3" (SC'11):
+// ten rounds of the Philox S-box with multipliers 0xD2511F53 / 0xCD9E8D57 and
+// Weyl key increments 0x9E3779B9 / 0xBB67AE85.
+__device__ __forceinline__ uint4 philox_round(uint4 x, uint32_t k0, uint32_t k1) {
+  const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+  uint32_t hi0 = __umulhi(m0, x.x), lo0 = m0 * x.x;
+  uint32_t hi1 = __umulhi(m1, x.z), lo1 = m1 * x.z;
+  return make_uint4(hi1 ^ x.y ^ k0, lo1, hi0 ^ x.w ^ k1, lo0);
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    if (i) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    ctr = philox_round(ctr, k0, k1);
+  }
+  return ctr;
+}
+
+// Index of the problem owning flat item g, given exclusive prefix sums
+// offsets[0..nprob] (offsets[nprob] = total).  Binary search.
+__device__ __forceinline__ int find_problem(const int64_t* offsets, int nprob, int64_t g) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (offsets[mid] <= g)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// Exclusive prefix sum of one int per thread over a block of NT threads.
+// Returns the exclusive prefix; *total receives the block total.  Needs
+// NT/32 ints of shared memory in warp_sums.  Contains __syncthreads().
+template <int NT>
+__device__ __forceinline__ int block_exclusive_scan(int v, int* warp_sums, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int s = (lane < NT / 32) ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < NT / 32) warp_sums[lane] = s;  // inclusive
+  }
+  __syncthreads();
+  int base = warp ? warp_sums[warp - 1] : 0;
+  *total = warp_sums[NT / 32 - 1];
+  return base + x - v;
+}
+
+// Fixed-point scale of the M accumulator: the largest f with
+// (max column count + 1) * 2^f <= 2^61, so no sum of rounded contributions of
+// magnitude <= 1 can overflow a signed 64-bit word.
+__device__ __forceinline__ int macc_frac_bits(unsigned long long max_count) {
+  int bits = 64 - __clzll((long long)(max_count + 1));  // ceil(log2(count + 2))
+  int f = 61 - bits;
+  return f > 52 ? 52 : f;
+}
+
+}  // namespace rsm

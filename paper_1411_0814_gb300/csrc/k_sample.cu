@@ -1,0 +1,180 @@
+// Stage a1 (mask packing), a2 (column sampling) and the stand-alone row-list
+// stage of a3 (the fused selection lives in k_gram.cu).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rsm {
+
+// ------------------------------------------------------------------ a1 pack_mask
+// Section IV-A: extracting a submatrix needs only logical tests on W, so W is
+// packed once into bit words: bit (i mod 32) of word i/32 of column c is
+// W[i, c] != 0.  One thread per output word; a CTA covers 256 consecutive words
+// of one column.  Blocks are flattened over the problems of the batch.
+__global__ void __launch_bounds__(256) k_pack_mask(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ blk_off,
+                                                   int nprob) {
+  const int p = find_problem(blk_off, nprob, blockIdx.x);
+  const ProbDesc& d = descs[p];
+  const int64_t local = blockIdx.x - blk_off[p];
+  const int64_t chunks = (d.ldb + 255) / 256;
+  const int64_t c = local / chunks;
+  const int64_t w = (local % chunks) * 256 + threadIdx.x;
+  uint32_t word = 0;
+  if (w < d.ldb) {
+    const uint8_t* col = d.W + c * d.ldw;
+    const int64_t r0 = w * 32;
+    if (r0 + 32 <= d.m && ((reinterpret_cast<uintptr_t>(col + r0) & 15) == 0)) {
+      const uint4* q = reinterpret_cast<const uint4*>(col + r0);
+      uint4 a = __ldg(q), b = __ldg(q + 1);
+      uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int by = 0; by < 4; ++by)
+          if ((v[k] >> (8 * by)) & 0xffu) word |= 1u << (4 * k + by);
+    } else {
+      for (int k = 0; k < 32; ++k)
+        if (r0 + k < d.m && col[r0 + k]) word |= 1u << k;
+    }
+    d.bits[c * d.ldb + w] = word;
+  }
+  // known-entry count of the problem (eq. def.rho numerator), exact integer sum
+  unsigned cnt = __popc(word);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&d.counters[1], (unsigned long long)cnt);
+}
+
+// ------------------------------------------------------------------ a2 sample_cols
+// Section III, method M1: choose l distinct columns (Section II: a list <k> has
+// distinct entries).  Word w of trial t is lane (w mod 4) of Philox4x32-10 with
+// key (seed lo, seed hi) and counter (t lo, problem id, w / 4, t hi).  A draw in
+// [0, k) is (word * k) >> 32.  RANDOM: Floyd's algorithm, draw d picks x in
+// [0, n-l+d] and takes n-l+d instead when x is already chosen.  ADJACENT: a
+// start s in [0, n-l] and columns s..s+l-1.  The set is sorted ascending.
+__device__ __forceinline__ void draw_columns(const ProbDesc& d, int64_t t, int32_t* out) {
+  const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+  const int l = d.l;
+  const int64_t n = d.n;
+  int32_t c[kMaxL];
+  if (d.variant == 1) {
+    uint4 w = philox4x32_10(make_uint4((uint32_t)t, d.pid, 0u, (uint32_t)(t >> 32)), k0, k1);
+    const int64_t s = (int64_t)(((uint64_t)w.x * (uint64_t)(n - l + 1)) >> 32);
+    for (int k = 0; k < l; ++k) out[k] = (int32_t)(s + k);
+    return;
+  }
+  uint4 blk = make_uint4(0, 0, 0, 0);
+  for (int dd = 0; dd < l; ++dd) {
+    if ((dd & 3) == 0)
+      blk = philox4x32_10(make_uint4((uint32_t)t, d.pid, (uint32_t)(dd >> 2), (uint32_t)(t >> 32)), k0, k1);
+    const uint32_t word = (dd & 3) == 0 ? blk.x : (dd & 3) == 1 ? blk.y : (dd & 3) == 2 ? blk.z : blk.w;
+    const int64_t j = n - l + dd;
+    int32_t x = (int32_t)(((uint64_t)word * (uint64_t)(j + 1)) >> 32);
+    bool taken = false;
+    for (int e = 0; e < dd; ++e) taken |= (c[e] == x);
+    c[dd] = taken ? (int32_t)j : x;
+  }
+  for (int a = 1; a < l; ++a) {  // insertion sort, l <= 32
+    int32_t v = c[a];
+    int b = a - 1;
+    while (b >= 0 && c[b] > v) {
+      c[b + 1] = c[b];
+      --b;
+    }
+    c[b + 1] = v;
+  }
+  for (int k = 0; k < l; ++k) out[k] = c[k];
+}
+
+// One thread per trial, flattened over the problems of the batch.  Also counts
+// how many trials drew each column (an upper bound of every entry of M, used to
+// size the fixed-point accumulator).
+__global__ void __launch_bounds__(256) k_sample(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ trial_off,
+                                                int nprob) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= trial_off[nprob]) return;
+  const int p = find_problem(trial_off, nprob, g);
+  const ProbDesc& d = descs[p];
+  const int64_t t = g - trial_off[p];
+  int32_t* out = d.cols + t * d.l;
+  draw_columns(d, t, out);
+  for (int k = 0; k < d.l; ++k) {
+    int v = atomicAdd(&d.colcount[out[k]], 1) + 1;
+    atomicMax(&d.counters[2], (unsigned long long)v);
+  }
+  if (d.debug_cols)
+    for (int k = 0; k < d.l; ++k) d.debug_cols[t * d.l + k] = out[k];
+}
+
+// Stand-alone sampler for the stage entry point: trials t0 .. t0+count-1 of one problem.
+__global__ void __launch_bounds__(256) k_sample_range(ProbDesc d, int64_t t0, int64_t count, int32_t* cols) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  draw_columns(d, t0 + i, cols + i * d.l);
+}
+
+// ------------------------------------------------------------------ a3 row lists (stage entry)
+// Section III, M1: R_t = rows known in every chosen column, ascending.  One CTA
+// per trial; each thread ANDs the l mask words of one 32-row group, and a block
+// scan places the rows in order.
+__global__ void __launch_bounds__(256) k_select_rows(const uint32_t* __restrict__ bits, int64_t ldb, int64_t m,
+                                                     const int32_t* __restrict__ cols, int l,
+                                                     const int64_t* __restrict__ row_off, int32_t* __restrict__ rows,
+                                                     int32_t* __restrict__ row_counts) {
+  __shared__ int warp_sums[8];
+  __shared__ int32_t cidx[kMaxL];
+  const int64_t t = blockIdx.x;
+  if (threadIdx.x < l) cidx[threadIdx.x] = cols[t * l + threadIdx.x];
+  __syncthreads();
+  const int64_t nwords = (m + 31) / 32;
+  const int64_t cap = row_off[t + 1] - row_off[t];
+  int32_t* out = rows + row_off[t];
+  int64_t done = 0;
+  for (int64_t w0 = 0; w0 < nwords; w0 += 256) {
+    const int64_t w = w0 + threadIdx.x;
+    uint32_t mask = 0;
+    if (w < nwords) {
+      mask = 0xffffffffu;
+      for (int k = 0; k < l; ++k) mask &= bits[(int64_t)cidx[k] * ldb + w];
+    }
+    int total;
+    int off = block_exclusive_scan<256>(__popc(mask), warp_sums, &total);
+    int64_t rank = done + off;
+    while (mask) {
+      int b = __ffs(mask) - 1;
+      mask &= mask - 1;
+      if (rank < cap) out[rank] = (int32_t)(w * 32 + b);
+      ++rank;
+    }
+    done += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) row_counts[t] = (int32_t)done;
+}
+
+// ------------------------------------------------------------------ launchers
+cudaError_t launch_pack_mask(const ProbDesc* descs, const int64_t* blk_off, int nprob, int64_t nblocks, cudaStream_t s) {
+  if (nblocks <= 0) return cudaSuccess;
+  k_pack_mask<<<(unsigned)nblocks, 256, 0, s>>>(descs, blk_off, nprob);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample(const ProbDesc* descs, const int64_t* trial_off, int nprob, int64_t total, cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+  k_sample<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(descs, trial_off, nprob);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample_range(const ProbDesc& d, int64_t t0, int64_t count, int32_t* cols, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_sample_range<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(d, t0, count, cols);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_select_rows(const uint32_t* bits, int64_t ldb, int64_t m, const int32_t* cols, int l, int64_t count,
+                               const int64_t* row_off, int32_t* rows, int32_t* row_counts, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_select_rows<<<(unsigned)count, 256, 0, s>>>(bits, ldb, m, cols, l, row_off, rows, row_counts);
+  return cudaGetLastError();
+}
+
+}  // namespace rsm

@@ -1,0 +1,367 @@
+// Stages a8 (U-hat) and a9 (the error e).
+//
+// a8, eq. (solve.barU) with the L2 norm: for every row i, with
+// K_i = {j : w_ij = 1}, u_i solves N_i u_i = b_i where N_i = sum_{j in K_i} v_j v_j^T
+// and b_i = sum_{j in K_i} y_ij v_j.  For all rows at once this is a product:
+//   [N_flat | b | |K_i|] (m x q) = [W | W o Y | W] (per output column) x Kmat (n x q)
+// with Kmat[j] = (v_ja v_jb for a <= b, v_j, 1).  k_normal computes it as a tiled
+// product (64 rows x 64 outputs per CTA); k_row_solve then solves each r x r
+// system by Cholesky in FP64, falling back to the minimum-norm solution (a
+// pseudo-inverse from a Jacobi eigendecomposition) for rank-deficient rows.
+//
+// a9, eq. (ep): e = (sum w_ij)^-1/2 || W o (Y - U V^T) ||_F, one thread per row,
+// per-CTA partial sums reduced in a fixed order.
+#include <cfloat>
+
+#include "common.cuh"
+#include "jacobi.cuh"
+#include "kernels.h"
+
+namespace rsm {
+
+__device__ __forceinline__ void pair_of(int q, int r, int& a, int& b) {
+  a = 0;
+  int rem = q;
+  while (rem >= r - a) {
+    rem -= r - a;
+    ++a;
+  }
+  b = a + rem;
+}
+
+__global__ void __launch_bounds__(256) k_build_K(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
+                                                int nprob) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= off[nprob]) return;
+  const int p = find_problem(off, nprob, g);
+  const ProbDesc& d = descs[p];
+  const int64_t e = g - off[p];
+  const int64_t j = e / d.q_pad;
+  const int qq = (int)(e % d.q_pad);
+  const int r = d.r, P = r * (r + 1) / 2;
+  double v = 0.0;
+  if (qq < P) {
+    int a, b;
+    pair_of(qq, r, a, b);
+    v = d.V[(int64_t)a * d.ldv + j] * d.V[(int64_t)b * d.ldv + j];
+  } else if (qq < P + r) {
+    v = d.V[(int64_t)(qq - P) * d.ldv + j];
+  } else if (qq == P + r) {
+    v = 1.0;
+  }
+  d.Kmat[e] = v;
+}
+
+template <typename T>
+__device__ __forceinline__ T load_y(const ProbDesc& d, int64_t idx) {
+  if (d.y_dtype == 0) return (T)__ldg(static_cast<const double*>(d.Y) + idx);
+  return (T)__ldg(static_cast<const float*>(d.Y) + idx);
+}
+
+constexpr int kNT = 64;  // rows per tile
+constexpr int kQT = 64;  // outputs per tile
+constexpr int kJT = 16;  // inner chunk
+
+// MODE 0: FP64 multiply-add; MODE 2: FP32 multiply-add (output stored as FP64).
+template <int MODE>
+__global__ void __launch_bounds__(256) k_normal(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
+                                               int nprob) {
+  using T = typename std::conditional<MODE == 0, double, float>::type;
+  __shared__ T ys[kJT][kNT], ws[kJT][kNT], ks[kJT][kQT];
+  const int p = find_problem(off, nprob, blockIdx.x);
+  const ProbDesc& d = descs[p];
+  const int64_t local = blockIdx.x - off[p];
+  const int nqt = d.q_pad / kQT;
+  const int64_t i0 = (local / nqt) * kNT;
+  const int q0 = (int)(local % nqt) * kQT;
+  const int P = d.r * (d.r + 1) / 2;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  bool isy[4];
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    const int qq = q0 + tx + 16 * o;
+    isy[o] = qq >= P && qq < P + d.r;
+  }
+  T acc[4][4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int o = 0; o < 4; ++o) acc[s][o] = (T)0;
+  const int64_t m = d.m, n = d.n;
+  for (int64_t j0 = 0; j0 < n; j0 += kJT) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < kJT * kNT; e += 256) {
+      const int jj = e / kNT, rr = e % kNT;
+      const int64_t i = i0 + rr, j = j0 + jj;
+      T yv = (T)0, wv = (T)0;
+      if (i < m && j < n) {
+        const uint32_t word = __ldg(d.bits + j * d.ldb + (i >> 5));
+        if ((word >> (i & 31)) & 1u) {
+          wv = (T)1;
+          yv = load_y<T>(d, j * d.ldy + i);
+        }
+      }
+      ys[jj][rr] = yv;
+      ws[jj][rr] = wv;
+    }
+    for (int e = threadIdx.x; e < kJT * kQT; e += 256) {
+      const int jj = e / kQT, qq = e % kQT;
+      const int64_t j = j0 + jj;
+      ks[jj][qq] = (j < n) ? (T)d.Kmat[j * d.q_pad + q0 + qq] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < kJT; ++jj) {
+      T kv[4], wv[4], yv[4];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) kv[o] = ks[jj][tx + 16 * o];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        wv[s] = ws[jj][ty + 16 * s];
+        yv[s] = ys[jj][ty + 16 * s];
+      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int o = 0; o < 4; ++o) acc[s][o] = fma(isy[o] ? yv[s] : wv[s], kv[o], acc[s][o]);
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int64_t i = i0 + ty + 16 * s;
+    if (i < m)
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const int qq = q0 + tx + 16 * o;
+        if (qq < d.q) d.NB[i * d.q_pad + qq] = (double)acc[s][o];
+      }
+  }
+}
+
+// Cholesky solve of one row's r x r system (FP64), r <= RM, packed lower factor
+// in registers.  A row with fewer than r known entries, or whose pivot falls
+// below 1e-13 trace(N_i), is appended to the batch's fail list for the
+// minimum-norm path (k_row_pinv).
+template <int RM>
+__global__ void __launch_bounds__(128) k_row_solve(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
+                                                  int nprob, unsigned long long* __restrict__ fail_list,
+                                                  unsigned long long* __restrict__ fail_count) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= off[nprob]) return;
+  const int p = find_problem(off, nprob, g);
+  const ProbDesc& d = descs[p];
+  const int64_t i = g - off[p];
+  const int r = d.r, P = r * (r + 1) / 2;
+  const double* row = d.NB + i * d.q_pad;
+  double L[RM * (RM + 1) / 2];  // packed lower triangle, row-major: (a, b<=a) -> a(a+1)/2 + b
+  double u[RM];
+  double tr = 0.0;
+#pragma unroll
+  for (int a = 0; a < RM; ++a) {
+    if (a >= r) break;
+#pragma unroll
+    for (int b = 0; b <= a; ++b) {
+      // N[a][b] = N[b][a]: packed upper index of (b, a) with b <= a
+      const int qq = b * r - b * (b - 1) / 2 + (a - b);
+      L[a * (a + 1) / 2 + b] = row[qq];
+    }
+    tr += L[a * (a + 1) / 2 + a];
+  }
+  const double known = row[P + r];
+  bool ok = known >= (double)r;
+#pragma unroll
+  for (int j = 0; j < RM; ++j) {
+    if (j >= r || !ok) break;
+    double v = L[j * (j + 1) / 2 + j];
+#pragma unroll
+    for (int t = 0; t < j; ++t) v -= L[j * (j + 1) / 2 + t] * L[j * (j + 1) / 2 + t];
+    if (!(v > 1e-13 * tr)) {
+      ok = false;
+      break;
+    }
+    v = sqrt(v);
+    L[j * (j + 1) / 2 + j] = v;
+#pragma unroll
+    for (int k = j + 1; k < RM; ++k) {
+      if (k >= r) break;
+      double w = L[k * (k + 1) / 2 + j];
+#pragma unroll
+      for (int t = 0; t < j; ++t) w -= L[k * (k + 1) / 2 + t] * L[j * (j + 1) / 2 + t];
+      L[k * (k + 1) / 2 + j] = w / v;
+    }
+  }
+  if (!ok) {
+    if (known < (double)r) atomicAdd(&d.counters[4], 1ull);
+    const unsigned long long slot = atomicAdd(fail_count, 1ull);
+    fail_list[slot] = ((unsigned long long)p << 32) | (unsigned long long)i;
+    return;
+  }
+#pragma unroll
+  for (int a = 0; a < RM; ++a) {  // C y = b
+    if (a >= r) break;
+    double v = row[P + a];
+#pragma unroll
+    for (int t = 0; t < a; ++t) v -= L[a * (a + 1) / 2 + t] * u[t];
+    u[a] = v / L[a * (a + 1) / 2 + a];
+  }
+#pragma unroll
+  for (int a = RM - 1; a >= 0; --a) {  // C^T u = y
+    if (a >= r) continue;
+    double v = u[a];
+#pragma unroll
+    for (int t = a + 1; t < RM; ++t)
+      if (t < r) v -= L[t * (t + 1) / 2 + a] * u[t];
+    u[a] = v / L[a * (a + 1) / 2 + a];
+  }
+  for (int a = 0; a < r; ++a) d.U[(int64_t)a * d.ldu + i] = u[a];
+}
+
+// Minimum-norm solution u = N^+ b for the rows of the fail list: one warp per
+// row, eigendecomposition of N by the warp Jacobi solver, eigenvalues below
+// 1e-12 of the largest treated as zero.
+constexpr int kPinvWarps = 2;
+__global__ void __launch_bounds__(32 * kPinvWarps) k_row_pinv(const ProbDesc* __restrict__ descs,
+                                                             const unsigned long long* __restrict__ fail_list,
+                                                             const unsigned long long* __restrict__ fail_count) {
+  __shared__ double S[kPinvWarps][kMaxR][kMaxR + 1], Q[kPinvWarps][kMaxR][kMaxR + 1];
+  __shared__ JacobiScratch js[kPinvWarps];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned long long total = *fail_count;
+  for (unsigned long long f = (unsigned long long)blockIdx.x * kPinvWarps + wid; f < total;
+       f += (unsigned long long)gridDim.x * kPinvWarps) {
+    const unsigned long long code = fail_list[f];
+    const ProbDesc& d = descs[code >> 32];
+    const int64_t i = (int64_t)(code & 0xffffffffull);
+    const int r = d.r, P = r * (r + 1) / 2;
+    const double* row = d.NB + i * d.q_pad;
+    for (int qq = lane; qq < P; qq += 32) {
+      int a, b;
+      pair_of(qq, r, a, b);
+      S[wid][a][b] = row[qq];
+      S[wid][b][a] = row[qq];
+    }
+    __syncwarp();
+    warp_jacobi(&S[wid][0][0], &Q[wid][0][0], r, kMaxR + 1, js[wid]);
+    double lmax = 0.0;
+    for (int k = 0; k < r; ++k) lmax = fmax(lmax, S[wid][k][k]);
+    // u_a = sum_k [lambda_k > tol] q_ak (q_k . b) / lambda_k, one output per lane
+    for (int a = lane; a < r; a += 32) {
+      double ua = 0.0;
+      for (int k = 0; k < r; ++k) {
+        const double lam = S[wid][k][k];
+        if (!(lam > 1e-12 * lmax)) continue;
+        double qb = 0.0;
+        for (int t = 0; t < r; ++t) qb += Q[wid][t][k] * row[P + t];
+        ua += Q[wid][a][k] * qb / lam;
+      }
+      d.U[(int64_t)a * d.ldu + i] = ua;
+    }
+    __syncwarp();
+  }
+}
+
+// e numerator: sum over known entries of (y_ij - u_i . v_j)^2.  One thread per row,
+// columns of V staged in shared memory; one partial per CTA.
+template <typename T>
+__global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
+                                                 int nprob, double* __restrict__ partial) {
+  __shared__ T vs[32][kMaxR + 1];
+  __shared__ double red[256];
+  const int p = find_problem(off, nprob, blockIdx.x);
+  const ProbDesc& d = descs[p];
+  const int64_t i = (blockIdx.x - off[p]) * 256 + threadIdx.x;
+  const int r = d.r;
+  T u[kMaxR];
+  for (int a = 0; a < kMaxR; ++a) u[a] = (T)0;
+  if (i < d.m)
+    for (int a = 0; a < r; ++a) u[a] = (T)d.U[(int64_t)a * d.ldu + i];
+  double acc = 0.0;
+  for (int64_t j0 = 0; j0 < d.n; j0 += 32) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * r; e += 256) {
+      const int jj = e / r, a = e % r;
+      const int64_t j = j0 + jj;
+      vs[jj][a] = j < d.n ? (T)d.V[(int64_t)a * d.ldv + j] : (T)0;
+    }
+    __syncthreads();
+    if (i < d.m) {
+      const int64_t jn = d.n - j0 < 32 ? d.n - j0 : 32;
+      for (int jj = 0; jj < jn; ++jj) {
+        const int64_t j = j0 + jj;
+        const uint32_t word = __ldg(d.bits + j * d.ldb + (i >> 5));
+        if (!((word >> (i & 31)) & 1u)) continue;
+        T pred = (T)0;
+#pragma unroll 8
+        for (int a = 0; a < kMaxR; ++a)
+          if (a < r) pred = fma(u[a], vs[jj][a], pred);
+        const T diff = load_y<T>(d, j * d.ldy + i) - pred;
+        acc += (double)(diff * diff);
+      }
+    }
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(32) k_residual_final(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
+                                                      int nprob, const double* __restrict__ partial) {
+  const int p = blockIdx.x;
+  if (p >= nprob || threadIdx.x) return;
+  const ProbDesc& d = descs[p];
+  double s = 0.0;
+  for (int64_t b = off[p]; b < off[p + 1]; ++b) s += partial[b];
+  const double known = (double)d.counters[1];
+  d.stats[32] = s;
+  d.stats[33] = known > 0.0 ? sqrt(s / known) : 0.0;
+}
+
+cudaError_t launch_solve_u(const SolvePlan& S, int mode, cudaStream_t s) {
+  const ProbDesc* D = S.descs;
+  const int np = S.nprob;
+  if (S.k_total > 0) k_build_K<<<(unsigned)((S.k_total + 255) / 256), 256, 0, s>>>(D, S.k_off, np);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (S.tile_off_host_total > 0) {
+    if (mode == 0)
+      k_normal<0><<<(unsigned)S.tile_off_host_total, 256, 0, s>>>(D, S.tile_off, np);
+    else
+      k_normal<2><<<(unsigned)S.tile_off_host_total, 256, 0, s>>>(D, S.tile_off, np);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (S.row_total > 0) {
+    const unsigned blocks = (unsigned)((S.row_total + 127) / 128);
+    if (S.rmax <= 4)
+      k_row_solve<4><<<blocks, 128, 0, s>>>(D, S.row_off, np, S.fail_list, S.fail_count);
+    else if (S.rmax <= 8)
+      k_row_solve<8><<<blocks, 128, 0, s>>>(D, S.row_off, np, S.fail_list, S.fail_count);
+    else if (S.rmax <= 16)
+      k_row_solve<16><<<blocks, 128, 0, s>>>(D, S.row_off, np, S.fail_list, S.fail_count);
+    else
+      k_row_solve<32><<<blocks, 128, 0, s>>>(D, S.row_off, np, S.fail_list, S.fail_count);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_row_pinv<<<152, 32 * kPinvWarps, 0, s>>>(D, S.fail_list, S.fail_count);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const SolvePlan& S, int mode, double* partial, cudaStream_t s) {
+  const ProbDesc* D = S.descs;
+  const int np = S.nprob;
+  if (S.res_blocks > 0) {
+    if (mode == 0)
+      k_residual<double><<<(unsigned)S.res_blocks, 256, 0, s>>>(D, S.res_off, np, partial);
+    else
+      k_residual<float><<<(unsigned)S.res_blocks, 256, 0, s>>>(D, S.res_off, np, partial);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_residual_final<<<np, 32, 0, s>>>(D, S.res_off, np, partial);
+  return cudaGetLastError();
+}
+
+}  // namespace rsm

@@ -1,0 +1,57 @@
+// Host-side declarations of the kernel launchers (internal to librsm.so).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+namespace rsm {
+
+struct ProbDesc;
+
+// Offsets of the eigen stage.  Every table is an exclusive prefix sum of
+// nprob + 1 int64 values; dT is the device copy (read by kernels), hT the host
+// copy (read by the launcher for grid sizes); both hold the same tables at the
+// same positions.
+struct EigPlan {
+  const ProbDesc* descs;
+  int nprob;
+  int max_nblk;
+  const int64_t* dT;
+  const int64_t* hT;
+  size_t pad2, step, blk, linv, tri, nk, mx, chunk, part_off, rot, row_tile;  // table positions
+  double* part;  // partial Gram sums of the block iteration
+};
+
+struct SolvePlan {
+  const ProbDesc* descs;
+  int nprob;
+  int64_t k_total;
+  const int64_t* k_off;      // n * q_pad per problem
+  int64_t tile_off_host_total;
+  const int64_t* tile_off;   // ceil(m / 64) * q_pad / 64 per problem
+  int64_t row_total;
+  const int64_t* row_off;    // m per problem
+  int64_t res_blocks;
+  const int64_t* res_off;    // ceil(m / 256) per problem
+  int rmax;                  // largest r of the batch
+  unsigned long long* fail_list;   // row_total entries: (problem << 32) | row
+  unsigned long long* fail_count;  // zero before the launch
+};
+
+cudaError_t launch_pack_mask(const ProbDesc* descs, const int64_t* blk_off, int nprob, int64_t nblocks, cudaStream_t s);
+cudaError_t launch_sample(const ProbDesc* descs, const int64_t* trial_off, int nprob, int64_t total, cudaStream_t s);
+cudaError_t launch_sample_range(const ProbDesc& d, int64_t t0, int64_t count, int32_t* cols, cudaStream_t s);
+cudaError_t launch_select_rows(const uint32_t* bits, int64_t ldb, int64_t m, const int32_t* cols, int l, int64_t count,
+                               const int64_t* row_off, int32_t* rows, int32_t* row_counts, cudaStream_t s);
+cudaError_t launch_select_gram(int mode, const ProbDesc* descs, const int64_t* trial_off, int nprob, int64_t total,
+                               int lmax, cudaStream_t s);
+cudaError_t launch_minor_scatter(const ProbDesc* descs, const int64_t* trial_off, int nprob, int64_t total, int lmax,
+                                 cudaStream_t s);
+cudaError_t launch_finalize_M(const ProbDesc* descs, const int64_t* ent_off, int nprob, int64_t total, cudaStream_t s);
+cudaError_t launch_eig(const EigPlan& P, bool fp64_factor, double shift_rel, int iters, cudaStream_t s);
+cudaError_t launch_solve_u(const SolvePlan& S, int mode, cudaStream_t s);
+cudaError_t launch_residual(const SolvePlan& S, int mode, double* partial, cudaStream_t s);
+
+}  // namespace rsm

@@ -1,0 +1,259 @@
+// Host-side planning of a batch of problems (see plan.h).
+#include "plan.h"
+
+#include <algorithm>
+
+namespace rsm {
+
+namespace {
+constexpr int kEigSplit = 4;  // must equal kSplit in k_eig.cu
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Sizes {
+  size_t macc, counters, colcount, stats;                    // zero region
+  size_t bits, cols, rowc, gram, M, F1, F2, Dinv, X, MX, R, small, Kmat, NB;  // data region
+};
+
+Sizes sizes_of(const rsm_problem& p, const Derived& dv) {
+  Sizes s{};
+  const size_t n = (size_t)p.n, m = (size_t)p.m, I = (size_t)p.trials;
+  s.macc = align_up(n * n * 8);
+  s.counters = align_up(8 * 8);
+  s.colcount = align_up(n * 4);
+  s.stats = align_up(64 * 8);
+  s.bits = align_up(n * (size_t)dv.ldb * 4);
+  s.cols = align_up(I * dv.l * 4);
+  s.rowc = align_up(I * 4);
+  s.gram = align_up(I * dv.P_l * 8);
+  s.M = align_up(n * n * 8);
+  s.F1 = align_up((size_t)dv.npad * dv.npad * 8);
+  s.F2 = s.F1;
+  s.Dinv = align_up((size_t)dv.nblk * 32 * 32 * 8);
+  s.X = align_up(n * dv.kx * 8);
+  s.MX = s.X;
+  s.R = align_up((size_t)kEigSplit * n * dv.kx * 8);
+  s.small = align_up((32 * 32 + 32) * 8);
+  s.Kmat = dv.solve_u ? align_up(n * dv.q_pad * 8) : 0;
+  s.NB = dv.solve_u ? align_up(m * dv.q_pad * 8) : 0;
+  return s;
+}
+
+size_t zero_sum(const Sizes& s) { return s.macc + s.counters + s.colcount + s.stats; }
+size_t data_sum(const Sizes& s) {
+  return s.bits + s.cols + s.rowc + s.gram + s.M + s.F1 + s.F2 + s.Dinv + s.X + s.MX + s.R + s.small + s.Kmat + s.NB;
+}
+size_t part_doubles(const rsm_problem& p, const Derived& dv) {
+  return (size_t)((p.n + 63) / 64) * 2 * dv.kx * dv.kx;
+}
+size_t res_blocks_of(const rsm_problem& p, const Derived& dv) { return dv.solve_u ? (size_t)((p.m + 255) / 256) : 0; }
+}  // namespace
+
+int validate_problem(const rsm_problem& p, Derived& dv, std::string* why) {
+  auto bad = [&](const char* msg) {
+    if (why) *why = msg;
+    return (int)RSM_ERR_INVALID_ARG;
+  };
+  if (!p.Y || !p.W || !p.V) return bad("Y, W and V must be device pointers");
+  if (p.n < 2 || p.m < p.n) return bad("need 2 <= n <= m");
+  if (p.m > 0x7fffffffLL) return bad("m must fit in int32");
+  if (p.r < 1 || p.r >= p.n) return bad("need 1 <= r < n");
+  dv.l = p.l ? p.l : p.r + 1;
+  if (dv.l <= p.r || dv.l > p.n || dv.l > kMaxL) return bad("need r < l <= min(n, 32)");
+  dv.nm = p.n_minor ? p.n_minor : dv.l - p.r;
+  if (dv.nm < 1 || dv.nm > dv.l - p.r) return bad("need 1 <= n_minor <= l - r");
+  if (p.trials < 1 || p.trials > (int64_t)1 << 36) return bad("need 1 <= trials <= 2^36");
+  if (p.ldy < p.m || p.ldw < p.m || p.ldv < p.n) return bad("leading dimensions too small");
+  if (p.U && p.ldu < p.m) return bad("ldu < m");
+  if (p.y_dtype != RSM_F64 && p.y_dtype != RSM_F32) return bad("y_dtype");
+  if (p.variant != RSM_COLS_RANDOM && p.variant != RSM_COLS_ADJACENT) return bad("variant");
+  if (p.gram_prec < RSM_PREC_F64 || p.gram_prec > RSM_PREC_F32) return bad("gram_prec");
+  if (p.solve_prec != RSM_PREC_F64 && p.solve_prec != RSM_PREC_F32) {
+    if (p.solve_prec == RSM_PREC_F32X2) {
+      if (why) *why = "solve_prec F32X2 is not implemented";
+      return (int)RSM_ERR_NOT_IMPLEMENTED;
+    }
+    return bad("solve_prec");
+  }
+  dv.P_l = dv.l * (dv.l + 1) / 2;
+  dv.ldb = (((p.m + 31) / 32) + 3) / 4 * 4;
+  dv.nblk = (int)((p.n + 31) / 32);
+  dv.npad = (int64_t)dv.nblk * 32;
+  dv.kx = (int)std::min<int64_t>(std::min<int64_t>(p.n, 32), p.r + 8);
+  dv.q = p.r * (p.r + 1) / 2 + p.r + 1;
+  dv.q_pad = (dv.q + 63) / 64 * 64;
+  dv.solve_u = p.U != nullptr;
+  return RSM_OK;
+}
+
+size_t problem_footprint(const rsm_problem& p, const Derived& dv) {
+  Sizes s = sizes_of(p, dv);
+  return zero_sum(s) + data_sum(s) + align_up(part_doubles(p, dv) * 8) + align_up(res_blocks_of(p, dv) * 8) +
+         align_up(dv.solve_u ? (size_t)p.m * 8 : 0) + kAlign;
+}
+
+void build_batch(const rsm_problem* ps, int count, Batch& b) {
+  b.nprob = count;
+  b.dv.resize(count);
+  b.descs.assign(count, ProbDesc{});
+  b.lmax = 0;
+  b.max_nblk = 0;
+  b.rmax = 0;
+  b.any_solve = false;
+  for (int i = 0; i < count; ++i) {
+    validate_problem(ps[i], b.dv[i], nullptr);
+    b.lmax = std::max(b.lmax, b.dv[i].l);
+    b.max_nblk = std::max(b.max_nblk, b.dv[i].nblk);
+    b.any_solve |= b.dv[i].solve_u;
+    b.rmax = std::max(b.rmax, ps[i].r);
+  }
+  std::vector<int64_t>& T = b.tables;
+  T.clear();
+  auto prefix = [&](auto per) -> size_t {  // append an exclusive prefix table, return its position
+    size_t pos = T.size();
+    int64_t acc = 0;
+    for (int i = 0; i < count; ++i) {
+      T.push_back(acc);
+      acc += per(i);
+    }
+    T.push_back(acc);
+    return pos;
+  };
+  auto total = [&](size_t pos) { return T[pos + count]; };
+  b.o_pack = prefix([&](int i) { return ps[i].n * ((b.dv[i].ldb + 255) / 256); });
+  b.pack_blocks = total(b.o_pack);
+  b.o_trial = prefix([&](int i) { return ps[i].trials; });
+  b.trials_total = total(b.o_trial);
+  b.o_ent = prefix([&](int i) { return ps[i].n * ps[i].n; });
+  b.ent_total = total(b.o_ent);
+  b.o_pad2 = prefix([&](int i) { return b.dv[i].npad * b.dv[i].npad; });
+  b.pad2_total = total(b.o_pad2);
+  b.o_step = T.size();
+  for (int k = 0; k < b.max_nblk; ++k) {
+    prefix([&](int i) { return (int64_t)(k < b.dv[i].nblk ? 1 : 0); });
+    prefix([&](int i) { return (int64_t)std::max(0, b.dv[i].nblk - k - 1); });
+    prefix([&](int i) {
+      const int64_t t = std::max(0, b.dv[i].nblk - k - 1);
+      return t * (t + 1) / 2;
+    });
+  }
+  b.o_blk = prefix([&](int i) { return (int64_t)b.dv[i].nblk; });
+  b.o_linv = T.size();
+  for (int k = 0; k < b.max_nblk; ++k) prefix([&](int i) { return (int64_t)(k < b.dv[i].nblk ? k : 0); });
+  b.o_tri = prefix([&](int i) { return (int64_t)b.dv[i].nblk * (b.dv[i].nblk + 1) / 2; });
+  b.o_nk = prefix([&](int i) { return ps[i].n * b.dv[i].kx; });
+  b.nk_total = total(b.o_nk);
+  b.o_mx = prefix([&](int i) { return (int64_t)kEigSplit * ((ps[i].n + 31) / 32); });
+  b.o_chunk = prefix([&](int i) { return (ps[i].n + 63) / 64; });
+  b.o_part = prefix([&](int i) { return (int64_t)part_doubles(ps[i], b.dv[i]); });
+  b.part_total = total(b.o_part);
+  b.o_rot = prefix([&](int i) { return (ps[i].n + 127) / 128; });
+  b.o_rowtile = prefix([&](int i) { return (ps[i].n + 31) / 32; });
+  b.o_k = prefix([&](int i) { return b.dv[i].solve_u ? ps[i].n * b.dv[i].q_pad : 0; });
+  b.k_total = total(b.o_k);
+  b.o_tile = prefix([&](int i) { return b.dv[i].solve_u ? ((ps[i].m + 63) / 64) * (b.dv[i].q_pad / 64) : 0; });
+  b.tile_total = total(b.o_tile);
+  b.o_row = prefix([&](int i) { return b.dv[i].solve_u ? ps[i].m : 0; });
+  b.row_total = total(b.o_row);
+  b.o_res = prefix([&](int i) { return (int64_t)res_blocks_of(ps[i], b.dv[i]); });
+  b.res_blocks = total(b.o_res);
+
+  // workspace: all zero regions first, then all data regions, then shared partial buffers
+  b.zero_off.resize(count);
+  b.data_off.resize(count);
+  b.zero_size.resize(count);
+  b.data_size.resize(count);
+  size_t off = kAlign;  // batch header: the fail-list counter
+  b.fail_count_off = 0;
+  for (int i = 0; i < count; ++i) {
+    Sizes s = sizes_of(ps[i], b.dv[i]);
+    b.zero_off[i] = off;
+    b.zero_size[i] = zero_sum(s);
+    off += b.zero_size[i];
+  }
+  b.layout.zero_bytes = off;
+  for (int i = 0; i < count; ++i) {
+    Sizes s = sizes_of(ps[i], b.dv[i]);
+    b.data_off[i] = off;
+    b.data_size[i] = data_sum(s);
+    off += b.data_size[i];
+  }
+  b.part_bytes_off = off;
+  off += align_up((size_t)b.part_total * 8);
+  b.res_bytes_off = off;
+  off += align_up((size_t)b.res_blocks * 8);
+  b.fail_list_off = off;
+  off += align_up((size_t)b.row_total * 8);
+  b.layout.total_bytes = off;
+  b.layout.plan_bytes = align_up(sizeof(ProbDesc) * count) + align_up(T.size() * 8);
+  b.gram_mode = ps[0].gram_prec == RSM_PREC_F64 ? 0 : ps[0].gram_prec == RSM_PREC_F32X2 ? 1 : 2;
+  b.solve_mode = ps[0].solve_prec == RSM_PREC_F64 ? 0 : 2;
+}
+
+void bind_batch(Batch& b, const rsm_problem* ps, unsigned char* ws) {
+  for (int i = 0; i < b.nprob; ++i) {
+    const rsm_problem& p = ps[i];
+    const Derived& dv = b.dv[i];
+    Sizes s = sizes_of(p, dv);
+    ProbDesc& d = b.descs[i];
+    d = ProbDesc{};
+    d.m = p.m;
+    d.n = p.n;
+    d.trials = p.trials;
+    d.r = p.r;
+    d.l = dv.l;
+    d.n_minor = dv.nm;
+    d.variant = p.variant;
+    d.seed = p.seed;
+    d.pid = p.problem_id;
+    d.y_dtype = p.y_dtype;
+    d.Y = p.Y;
+    d.ldy = p.ldy;
+    d.W = p.W;
+    d.ldw = p.ldw;
+    d.ldb = dv.ldb;
+    d.U = p.U;
+    d.ldu = p.ldu;
+    d.V = p.V;
+    d.ldv = p.ldv;
+    d.debug_Z = p.debug_Z;
+    d.debug_M = p.debug_M;
+    d.debug_cols = p.debug_cols;
+    d.debug_row_counts = p.debug_row_counts;
+    d.kx = dv.kx;
+    d.nblk = dv.nblk;
+    d.q = dv.q;
+    d.q_pad = dv.q_pad;
+    unsigned char* z = ws + b.zero_off[i];
+    d.macc = reinterpret_cast<unsigned long long*>(z);
+    z += s.macc;
+    d.counters = reinterpret_cast<unsigned long long*>(z);
+    z += s.counters;
+    d.colcount = reinterpret_cast<int32_t*>(z);
+    z += s.colcount;
+    d.stats = reinterpret_cast<double*>(z);
+    unsigned char* q = ws + b.data_off[i];
+    auto take = [&](size_t bytes) {
+      unsigned char* r = q;
+      q += bytes;
+      return r;
+    };
+    d.bits = reinterpret_cast<uint32_t*>(take(s.bits));
+    d.cols = reinterpret_cast<int32_t*>(take(s.cols));
+    d.row_counts = reinterpret_cast<int32_t*>(take(s.rowc));
+    d.gram = reinterpret_cast<double*>(take(s.gram));
+    d.M = reinterpret_cast<double*>(take(s.M));
+    d.F1 = take(s.F1);
+    d.F2 = take(s.F2);
+    d.Dinv = take(s.Dinv);
+    d.X = reinterpret_cast<double*>(take(s.X));
+    d.MX = reinterpret_cast<double*>(take(s.MX));
+    d.R = reinterpret_cast<double*>(take(s.R));
+    d.small = reinterpret_cast<double*>(take(s.small));
+    d.Kmat = s.Kmat ? reinterpret_cast<double*>(take(s.Kmat)) : nullptr;
+    d.NB = s.NB ? reinterpret_cast<double*>(take(s.NB)) : nullptr;
+  }
+}
+
+}  // namespace rsm

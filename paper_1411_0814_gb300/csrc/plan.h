@@ -1,0 +1,65 @@
+// Host-side planning of a batch of problems: validation, derived sizes,
+// workspace layout and the offset tables the batched kernels read.
+#pragma once
+
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rsm.h"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rsm {
+
+struct Derived {
+  int l = 0, nm = 0, P_l = 0, nblk = 0, kx = 0, q = 0, q_pad = 0;
+  int64_t ldb = 0, npad = 0;
+  bool solve_u = false;
+};
+
+// Validate a problem and fill its derived sizes.  Returns RSM_OK or
+// RSM_ERR_INVALID_ARG / RSM_ERR_NOT_IMPLEMENTED with a message in *why.
+int validate_problem(const rsm_problem& p, Derived& dv, std::string* why);
+
+// Byte layout of one batch inside a workspace buffer.
+struct BatchLayout {
+  size_t zero_bytes = 0;   // [0, zero_bytes) must be zeroed before the launch
+  size_t total_bytes = 0;  // workspace bytes
+  size_t plan_bytes = 0;   // descriptor + offset tables (uploaded to the start of the plan buffer)
+};
+
+// Everything needed to launch one batch, built on the host.
+struct Batch {
+  int nprob = 0;
+  int lmax = 0;
+  int gram_mode = 0;
+  int solve_mode = 0;
+  bool any_solve = false;
+  std::vector<Derived> dv;
+  std::vector<ProbDesc> descs;  // host copies (device pointers filled by bind())
+  std::vector<int64_t> tables;  // all int64 offset tables, concatenated
+  // positions (in int64 elements) of each table inside `tables`
+  size_t o_pack = 0, o_trial = 0, o_ent = 0, o_pad2 = 0, o_step = 0, o_blk = 0, o_linv = 0, o_tri = 0, o_nk = 0,
+         o_mx = 0, o_chunk = 0, o_part = 0, o_rot = 0, o_rowtile = 0, o_k = 0, o_tile = 0, o_row = 0, o_res = 0;
+  int64_t pack_blocks = 0, trials_total = 0, ent_total = 0, pad2_total = 0, nk_total = 0, part_total = 0,
+          k_total = 0, tile_total = 0, row_total = 0, res_blocks = 0;
+  int max_nblk = 0;
+  // per-problem byte offsets inside the workspace
+  std::vector<size_t> zero_off, data_off;
+  std::vector<size_t> zero_size, data_size;
+  size_t part_bytes_off = 0, res_bytes_off = 0, fail_list_off = 0, fail_count_off = 0;
+  int rmax = 0;
+  BatchLayout layout;
+};
+
+// Build the batch (sizes, tables, layout).  Problems must be validated first.
+void build_batch(const rsm_problem* ps, int count, Batch& b);
+// Fill the device pointers of b.descs for a workspace at `ws`.
+void bind_batch(Batch& b, const rsm_problem* ps, unsigned char* ws);
+
+// Device bytes of one problem's workspace (what rsm_footprint_bytes reports).
+size_t problem_footprint(const rsm_problem& p, const Derived& dv);
+
+}  // namespace rsm

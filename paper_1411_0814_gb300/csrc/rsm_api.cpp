@@ -1,0 +1,638 @@
+// C ABI of librsm.so (include/rsm.h): handles, the synchronous and batched
+// decompositions, the serving loop and the stage entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/rsm.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "plan.h"
+
+using namespace rsm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int status, const std::string& msg) {
+  g_last_error = msg;
+  return status;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return RSM_ERR_CUDA;
+}
+
+#define RSM_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+constexpr double kShiftRel32 = 1e-3;   // tau / (trace(M) / n) with the FP32 factor
+constexpr double kShiftRel64 = 1e-11;  // tau / (trace(M) / n) with the FP64 factor
+constexpr int kEigIters32 = 10;        // preconditioned iterations with the FP32 factor
+constexpr int kEigIters64 = 5;         // iterations with the FP64 factor (near-exact shift-invert)
+constexpr int64_t kSmallN = 256;       // at or below this n the FP64 factor is cheap: use it directly
+constexpr double kEigErrTol = 1e-11;   // a-posteriori bound that accepts the FP32-factor result
+constexpr double kRankTol = 1e-12;  // lambda_{r+1} <= kRankTol * trace(M): underdetermined
+
+// A device buffer that only grows.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t size = 0;
+  int reserve(size_t bytes) {
+    if (bytes <= size) return RSM_OK;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    size = 0;
+    cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(RSM_ERR_NO_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    size = bytes;
+    return RSM_OK;
+  }
+  void release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    size = 0;
+  }
+};
+
+struct PinBuf {
+  void* ptr = nullptr;
+  size_t size = 0;
+  int reserve(size_t bytes) {
+    if (bytes <= size) return RSM_OK;
+    if (ptr) cudaFreeHost(ptr);
+    ptr = nullptr;
+    size = 0;
+    cudaError_t e = cudaMallocHost(&ptr, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+    size = bytes;
+    return RSM_OK;
+  }
+  void release() {
+    if (ptr) cudaFreeHost(ptr);
+    ptr = nullptr;
+    size = 0;
+  }
+};
+
+// Everything one in-flight decomposition (or batch) uses: a stream, a
+// workspace, a plan buffer, pinned readback space and stage events.
+struct Slot {
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  DevBuf ws, plan;
+  PinBuf host;
+  cudaEvent_t ev[8] = {};
+  int init(cudaStream_t external) {
+    if (external) {
+      stream = external;
+    } else {
+      RSM_CUDA(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+      own_stream = true;
+    }
+    for (auto& e : ev) RSM_CUDA(cudaEventCreate(&e));
+    return RSM_OK;
+  }
+  void destroy() {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+    ws.release();
+    plan.release();
+    host.release();
+    if (own_stream && stream) cudaStreamDestroy(stream);
+    stream = nullptr;
+  }
+};
+
+struct Request {
+  uint64_t ticket = 0;
+  rsm_problem prob{};
+  size_t footprint = 0;
+  int state = 0;  // 0 queued, 1 running, 2 done
+  rsm_result res{};
+  std::chrono::steady_clock::time_point t_submit, t_start, t_end;
+};
+
+}  // namespace
+
+struct rsm_handle {
+  rsm_config cfg{};
+  int device = 0;
+  Slot main;  // rsm_decompose / rsm_decompose_batch
+  std::mutex api_mu;  // serialises the synchronous entry points
+  // serving
+  std::mutex mu;
+  std::condition_variable cv, done_cv;
+  std::deque<uint64_t> queue;
+  std::map<uint64_t, std::shared_ptr<Request>> reqs;
+  std::vector<Slot> slots;
+  std::vector<std::thread> workers;
+  size_t budget = 0, in_use = 0;
+  uint64_t next_ticket = 1;
+  bool stopping = false;
+  uint32_t fault = 0;
+};
+
+namespace {
+
+// Launch every stage of one batch on slot.stream.  The workspace and plan
+// buffers of the slot must already hold the batch.  Does not synchronise.
+int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool do_front) {
+  cudaStream_t s = slot.stream;
+  unsigned char* plan = static_cast<unsigned char*>(slot.plan.ptr);
+  const ProbDesc* D = reinterpret_cast<const ProbDesc*>(plan);
+  const int64_t* T = reinterpret_cast<const int64_t*>(plan + ((sizeof(ProbDesc) * b.nprob + 255) / 256 * 256));
+  const int np = b.nprob;
+  cudaError_t e;
+  if (do_front) {
+    RSM_CUDA(cudaEventRecord(slot.ev[0], s));
+    if ((e = launch_pack_mask(D, T + b.o_pack, np, b.pack_blocks, s)) != cudaSuccess) return cuda_fail(e, "pack_mask");
+    RSM_CUDA(cudaEventRecord(slot.ev[1], s));
+    if ((e = launch_sample(D, T + b.o_trial, np, b.trials_total, s)) != cudaSuccess) return cuda_fail(e, "sample");
+    if ((e = launch_select_gram(b.gram_mode, D, T + b.o_trial, np, b.trials_total, b.lmax, s)) != cudaSuccess)
+      return cuda_fail(e, "select_gram");
+    RSM_CUDA(cudaEventRecord(slot.ev[2], s));
+    if ((e = launch_minor_scatter(D, T + b.o_trial, np, b.trials_total, b.lmax, s)) != cudaSuccess)
+      return cuda_fail(e, "minor_scatter");
+    if ((e = launch_finalize_M(D, T + b.o_ent, np, b.ent_total, s)) != cudaSuccess) return cuda_fail(e, "finalize_M");
+    RSM_CUDA(cudaEventRecord(slot.ev[3], s));
+  }
+  EigPlan ep{};
+  ep.descs = D;
+  ep.nprob = np;
+  ep.max_nblk = b.max_nblk;
+  ep.dT = T;
+  ep.hT = b.tables.data();
+  ep.pad2 = b.o_pad2;
+  ep.step = b.o_step;
+  ep.blk = b.o_blk;
+  ep.linv = b.o_linv;
+  ep.tri = b.o_tri;
+  ep.nk = b.o_nk;
+  ep.mx = b.o_mx;
+  ep.chunk = b.o_chunk;
+  ep.part_off = b.o_part;
+  ep.rot = b.o_rot;
+  ep.row_tile = b.o_rowtile;
+  ep.part = reinterpret_cast<double*>(static_cast<unsigned char*>(slot.ws.ptr) + b.part_bytes_off);
+  if ((e = launch_eig(ep, fp64_factor, shift_rel, fp64_factor ? kEigIters64 : kEigIters32, s)) != cudaSuccess) return cuda_fail(e, "eig");
+  RSM_CUDA(cudaEventRecord(slot.ev[4], s));
+  if (b.any_solve) {
+    SolvePlan sp{};
+    sp.descs = D;
+    sp.nprob = np;
+    sp.k_total = b.k_total;
+    sp.k_off = T + b.o_k;
+    sp.tile_off_host_total = b.tile_total;
+    sp.tile_off = T + b.o_tile;
+    sp.row_total = b.row_total;
+    sp.row_off = T + b.o_row;
+    sp.res_blocks = b.res_blocks;
+    sp.res_off = T + b.o_res;
+    sp.rmax = b.rmax;
+    sp.fail_list = reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(slot.ws.ptr) + b.fail_list_off);
+    sp.fail_count = reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(slot.ws.ptr) + b.fail_count_off);
+    if ((e = launch_solve_u(sp, b.solve_mode, s)) != cudaSuccess) return cuda_fail(e, "solve_u");
+    RSM_CUDA(cudaEventRecord(slot.ev[5], s));
+    double* partial = reinterpret_cast<double*>(static_cast<unsigned char*>(slot.ws.ptr) + b.res_bytes_off);
+    if ((e = launch_residual(sp, b.solve_mode, partial, s)) != cudaSuccess) return cuda_fail(e, "residual");
+  } else {
+    RSM_CUDA(cudaEventRecord(slot.ev[5], s));
+  }
+  RSM_CUDA(cudaEventRecord(slot.ev[6], s));
+  return RSM_OK;
+}
+
+// Host readback area per problem: counters (8 x u64) + stats (64 doubles).
+constexpr size_t kReadback = 8 * 8 + 64 * 8;
+
+int enqueue_readback(Batch& b, Slot& slot) {
+  for (int i = 0; i < b.nprob; ++i) {
+    unsigned char* dst = static_cast<unsigned char*>(slot.host.ptr) + (size_t)i * kReadback;
+    RSM_CUDA(cudaMemcpyAsync(dst, b.descs[i].counters, 64, cudaMemcpyDeviceToHost, slot.stream));
+    RSM_CUDA(cudaMemcpyAsync(dst + 64, b.descs[i].stats, 64 * 8, cudaMemcpyDeviceToHost, slot.stream));
+  }
+  return RSM_OK;
+}
+
+// Prepare slot buffers, upload the plan, zero the accumulators, launch, read
+// back and fill results.  Synchronises slot.stream.
+int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_result* res) {
+  Batch b;
+  build_batch(ps, count, b);
+  int st = slot.ws.reserve(b.layout.total_bytes);
+  if (st != RSM_OK) return st;
+  if ((st = slot.plan.reserve(b.layout.plan_bytes)) != RSM_OK) return st;
+  if ((st = slot.host.reserve(std::max(b.layout.plan_bytes, (size_t)count * kReadback))) != RSM_OK) return st;
+  bind_batch(b, ps, static_cast<unsigned char*>(slot.ws.ptr));
+  // plan upload through the pinned buffer
+  unsigned char* hp = static_cast<unsigned char*>(slot.host.ptr);
+  const size_t dsz = (sizeof(ProbDesc) * count + 255) / 256 * 256;
+  std::memcpy(hp, b.descs.data(), sizeof(ProbDesc) * count);
+  std::memcpy(hp + dsz, b.tables.data(), b.tables.size() * 8);
+  RSM_CUDA(cudaMemcpyAsync(slot.plan.ptr, hp, dsz + b.tables.size() * 8, cudaMemcpyHostToDevice, slot.stream));
+  RSM_CUDA(cudaMemsetAsync(slot.ws.ptr, 0, b.layout.zero_bytes, slot.stream));
+  int64_t max_n = 0;
+  for (int i = 0; i < count; ++i) max_n = std::max<int64_t>(max_n, ps[i].n);
+  bool fp64 = max_n <= kSmallN;
+  double shift = fp64 ? kShiftRel64 : kShiftRel32;
+  if ((st = launch_batch(b, slot, fp64, shift, true)) != RSM_OK) return st;
+  if ((st = enqueue_readback(b, slot)) != RSM_OK) return st;
+  RSM_CUDA(cudaStreamSynchronize(slot.stream));
+  // Accept the result when the factorisation succeeded and the a-posteriori
+  // eigenvector bound (residual norm over the eigen-gap) is small; otherwise
+  // redo the eigen stage with the FP64 factor (and then larger shifts).
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    bool redo = false;
+    for (int i = 0; i < count; ++i) {
+      const unsigned long long* c = reinterpret_cast<const unsigned long long*>(hp + (size_t)i * kReadback);
+      const double* stats = reinterpret_cast<const double*>(hp + (size_t)i * kReadback + 64);
+      const int r = ps[i].r;
+      const double gap = stats[r] - stats[r - 1];
+      const double trace = (double)c[0] * b.dv[i].nm;
+      const bool determined = c[0] > 0 && stats[r] > kRankTol * trace;
+      const double est = stats[34] / (gap > 0.0 ? gap : 1e-300);
+      if (c[3] != 0 || (!fp64 && determined && !(est <= kEigErrTol))) redo = true;
+    }
+    if (!redo) break;
+    if (fp64)
+      shift *= 100.0;
+    else {
+      fp64 = true;
+      shift = kShiftRel64;
+    }
+    for (int i = 0; i < count; ++i) RSM_CUDA(cudaMemsetAsync(b.descs[i].counters + 3, 0, 16, slot.stream));
+    RSM_CUDA(cudaMemsetAsync(static_cast<unsigned char*>(slot.ws.ptr) + b.fail_count_off, 0, 8, slot.stream));
+    if ((st = launch_batch(b, slot, fp64, shift, false)) != RSM_OK) return st;
+    if ((st = enqueue_readback(b, slot)) != RSM_OK) return st;
+    RSM_CUDA(cudaStreamSynchronize(slot.stream));
+  }
+  float ms[7] = {0};
+  for (int k = 0; k < 6; ++k) cudaEventElapsedTime(&ms[k], slot.ev[k], slot.ev[k + 1]);
+  float total_ms = 0;
+  cudaEventElapsedTime(&total_ms, slot.ev[0], slot.ev[6]);
+  int first_bad = RSM_OK;
+  for (int i = 0; i < count; ++i) {
+    const unsigned long long* c = reinterpret_cast<const unsigned long long*>(hp + (size_t)i * kReadback);
+    const double* stats = reinterpret_cast<const double*>(hp + (size_t)i * kReadback + 64);
+    rsm_result r{};
+    r.accepted_trials = (int64_t)c[0];
+    r.rows_underdetermined = (int64_t)c[4];
+    r.n_eig = b.dv[i].kx;
+    for (int k = 0; k < 32; ++k) r.eig_M[k] = k < r.n_eig ? stats[k] : 0.0;
+    const double trace = (double)c[0] * b.dv[i].nm;
+    r.e_known_rms = b.dv[i].solve_u ? stats[33] : NAN;
+    int status = RSM_OK;
+    if (c[0] == 0 || !(r.eig_M[ps[i].r] > kRankTol * trace))
+      status = RSM_ERR_UNDERDETERMINED;
+    else if (c[3] != 0)
+      status = RSM_ERR_UNDERDETERMINED;
+    else if (c[4] > 0)
+      status = RSM_ERR_ROWS_UNDERDETERMINED;
+    r.status = status;
+    for (int k = 0; k < 6; ++k) r.stage_ms[k] = ms[k];
+    r.stage_ms[7] = total_ms;
+    if (res) res[i] = r;
+    if (status != RSM_OK && first_bad == RSM_OK) first_bad = status;
+  }
+  (void)h;
+  return first_bad;
+}
+
+int validate_all(const rsm_problem* ps, int count) {
+  for (int i = 0; i < count; ++i) {
+    Derived dv;
+    std::string why;
+    int st = validate_problem(ps[i], dv, &why);
+    if (st != RSM_OK) return fail(st, "problem " + std::to_string(i) + ": " + why);
+    if (ps[i].gram_prec != ps[0].gram_prec || ps[i].solve_prec != ps[0].solve_prec)
+      return fail(RSM_ERR_INVALID_ARG, "all problems of a batch must share gram_prec and solve_prec");
+  }
+  return RSM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rsm_version(void) { return "rsm-gb300 0.1.0 (sm_103a)"; }
+
+size_t rsm_struct_size(int32_t which) {
+  switch (which) {
+    case 0: return sizeof(rsm_config);
+    case 1: return sizeof(rsm_problem);
+    case 2: return sizeof(rsm_result);
+    default: return 0;
+  }
+}
+
+const char* rsm_status_string(int32_t s) {
+  switch (s) {
+    case RSM_OK: return "ok";
+    case RSM_ERR_INVALID_ARG: return "invalid argument";
+    case RSM_ERR_NO_MEMORY: return "out of device memory or above the HBM budget";
+    case RSM_ERR_UNDERDETERMINED: return "underdetermined: M has more than r null directions";
+    case RSM_ERR_ROWS_UNDERDETERMINED: return "some rows have fewer than r known entries";
+    case RSM_ERR_TIMEOUT: return "timed out";
+    case RSM_ERR_CANCELLED: return "cancelled";
+    case RSM_ERR_CUDA: return "CUDA error";
+    case RSM_ERR_NOT_IMPLEMENTED: return "not implemented";
+    case RSM_PENDING: return "pending";
+    case RSM_ERR_QUEUE_FULL: return "admission queue full";
+    default: return "unknown status";
+  }
+}
+
+const char* rsm_last_error(void) { return g_last_error.c_str(); }
+
+size_t rsm_footprint_bytes(const rsm_problem* p) {
+  if (!p) return 0;
+  Derived dv;
+  if (validate_problem(*p, dv, nullptr) != RSM_OK) return 0;
+  return problem_footprint(*p, dv);
+}
+
+int32_t rsm_create(const rsm_config* config, rsm_handle** out) {
+  if (!out) return fail(RSM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  rsm_config cfg{};
+  if (config) cfg = *config;
+  int ndev = 0;
+  RSM_CUDA(cudaGetDeviceCount(&ndev));
+  if (cfg.device < 0 || cfg.device >= ndev) return fail(RSM_ERR_INVALID_ARG, "device ordinal out of range");
+  RSM_CUDA(cudaSetDevice(cfg.device));
+  if (cfg.max_slots <= 0) cfg.max_slots = 4;
+  if (cfg.max_slots > 64) return fail(RSM_ERR_INVALID_ARG, "max_slots > 64");
+  if (cfg.wait_timeout_ns == 0) cfg.wait_timeout_ns = 10ull * 1000 * 1000 * 1000;
+  auto h = std::make_unique<rsm_handle>();
+  h->cfg = cfg;
+  h->device = cfg.device;
+  h->fault = cfg.fault_inject;
+  size_t free_b = 0, total_b = 0;
+  RSM_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  h->budget = cfg.hbm_budget_bytes ? cfg.hbm_budget_bytes : (size_t)(0.8 * (double)free_b);
+  int st = h->main.init(static_cast<cudaStream_t>(cfg.stream));
+  if (st != RSM_OK) return st;
+  *out = h.release();
+  return RSM_OK;
+}
+
+int32_t rsm_decompose_batch(rsm_handle* h, const rsm_problem* ps, int32_t count, rsm_result* res) {
+  if (!h || !ps || count < 1) return fail(RSM_ERR_INVALID_ARG, "handle, problems and count >= 1 are required");
+  int st = validate_all(ps, count);
+  if (st != RSM_OK) return st;
+  std::lock_guard<std::mutex> lk(h->api_mu);
+  RSM_CUDA(cudaSetDevice(h->device));
+  size_t need = 0;
+  for (int i = 0; i < count; ++i) need += rsm_footprint_bytes(&ps[i]);
+  if (need > h->budget) return fail(RSM_ERR_NO_MEMORY, "batch footprint above the handle's HBM budget");
+  if (h->fault & RSM_FAULT_ALLOC) {
+    h->fault &= ~RSM_FAULT_ALLOC;
+    return fail(RSM_ERR_NO_MEMORY, "injected allocation failure");
+  }
+  return run_batch(h, h->main, ps, count, res);
+}
+
+int32_t rsm_decompose(rsm_handle* h, const rsm_problem* p, rsm_result* res) {
+  rsm_result tmp{};
+  int st = rsm_decompose_batch(h, p, 1, &tmp);
+  if (res) *res = tmp;
+  if (st == RSM_OK || st == RSM_ERR_UNDERDETERMINED || st == RSM_ERR_ROWS_UNDERDETERMINED) return tmp.status;
+  if (res) res->status = st;
+  return st;
+}
+
+// ---------------------------------------------------------------- serving
+
+namespace {
+
+void worker_loop(rsm_handle* h, int slot_id) {
+  cudaSetDevice(h->device);
+  Slot& slot = h->slots[slot_id];
+  for (;;) {
+    std::shared_ptr<Request> req;
+    {
+      std::unique_lock<std::mutex> lk(h->mu);
+      for (;;) {
+        if (h->stopping) return;
+        if (!(h->fault & RSM_FAULT_STALL) && !h->queue.empty()) {
+          // admit the oldest request whose footprint fits the free budget
+          auto it = h->queue.begin();
+          for (; it != h->queue.end(); ++it) {
+            auto& r = h->reqs[*it];
+            if (r->footprint + h->in_use <= h->budget) break;
+          }
+          if (it != h->queue.end()) {
+            req = h->reqs[*it];
+            h->queue.erase(it);
+            h->in_use += req->footprint;
+            req->state = 1;
+            req->t_start = std::chrono::steady_clock::now();
+            break;
+          }
+        }
+        h->cv.wait(lk);
+      }
+    }
+    rsm_result res{};
+    int st = run_batch(h, slot, &req->prob, 1, &res);
+    if (st != RSM_OK && st != RSM_ERR_UNDERDETERMINED && st != RSM_ERR_ROWS_UNDERDETERMINED) res.status = st;
+    {
+      std::lock_guard<std::mutex> lk(h->mu);
+      req->t_end = std::chrono::steady_clock::now();
+      res.queue_ms = std::chrono::duration<double, std::milli>(req->t_start - req->t_submit).count();
+      res.run_ms = std::chrono::duration<double, std::milli>(req->t_end - req->t_start).count();
+      req->res = res;
+      req->state = 2;
+      h->in_use -= req->footprint;
+    }
+    h->cv.notify_all();
+    h->done_cv.notify_all();
+  }
+}
+
+int ensure_workers(rsm_handle* h) {
+  if (!h->workers.empty()) return RSM_OK;
+  h->slots.resize(h->cfg.max_slots);
+  for (auto& s : h->slots) {
+    int st = s.init(nullptr);
+    if (st != RSM_OK) return st;
+  }
+  for (int i = 0; i < h->cfg.max_slots; ++i) h->workers.emplace_back(worker_loop, h, i);
+  return RSM_OK;
+}
+
+}  // namespace
+
+int32_t rsm_submit(rsm_handle* h, const rsm_problem* p, uint64_t* ticket) {
+  if (!h || !p || !ticket) return fail(RSM_ERR_INVALID_ARG, "handle, problem and ticket are required");
+  int st = validate_all(p, 1);
+  if (st != RSM_OK) return st;
+  const size_t fp = rsm_footprint_bytes(p);
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (fp > h->budget || (h->fault & RSM_FAULT_ADMISSION))
+    return fail(RSM_ERR_NO_MEMORY, "footprint above the handle's HBM budget: never admissible");
+  if (h->queue.size() >= 4096) return fail(RSM_ERR_QUEUE_FULL, "admission queue full");
+  st = ensure_workers(h);
+  if (st != RSM_OK) return st;
+  auto r = std::make_shared<Request>();
+  r->ticket = h->next_ticket++;
+  r->prob = *p;
+  r->footprint = fp;
+  r->t_submit = std::chrono::steady_clock::now();
+  h->reqs[r->ticket] = r;
+  h->queue.push_back(r->ticket);
+  *ticket = r->ticket;
+  h->cv.notify_all();
+  return RSM_OK;
+}
+
+int32_t rsm_poll(rsm_handle* h, uint64_t ticket, rsm_result* res) {
+  if (!h) return fail(RSM_ERR_INVALID_ARG, "handle is NULL");
+  std::lock_guard<std::mutex> lk(h->mu);
+  auto it = h->reqs.find(ticket);
+  if (it == h->reqs.end()) return fail(RSM_ERR_INVALID_ARG, "unknown ticket");
+  if (it->second->state != 2) return RSM_PENDING;
+  if (res) *res = it->second->res;
+  return it->second->res.status;
+}
+
+int32_t rsm_wait(rsm_handle* h, uint64_t ticket, uint64_t timeout_ns, rsm_result* res) {
+  if (!h) return fail(RSM_ERR_INVALID_ARG, "handle is NULL");
+  if (timeout_ns == 0) timeout_ns = h->cfg.wait_timeout_ns;
+  std::unique_lock<std::mutex> lk(h->mu);
+  auto it = h->reqs.find(ticket);
+  if (it == h->reqs.end()) return fail(RSM_ERR_INVALID_ARG, "unknown ticket");
+  auto req = it->second;
+  const bool done = h->done_cv.wait_for(lk, std::chrono::nanoseconds(timeout_ns), [&] { return req->state == 2; });
+  if (!done) return fail(RSM_ERR_TIMEOUT, "request still pending after the wait limit");
+  if (res) *res = req->res;
+  return req->res.status;
+}
+
+int32_t rsm_cancel(rsm_handle* h, uint64_t ticket) {
+  if (!h) return fail(RSM_ERR_INVALID_ARG, "handle is NULL");
+  std::lock_guard<std::mutex> lk(h->mu);
+  auto it = h->reqs.find(ticket);
+  if (it == h->reqs.end()) return fail(RSM_ERR_INVALID_ARG, "unknown ticket");
+  auto& r = it->second;
+  if (r->state != 0) return fail(RSM_ERR_INVALID_ARG, "request already started");
+  h->queue.erase(std::remove(h->queue.begin(), h->queue.end(), ticket), h->queue.end());
+  r->state = 2;
+  r->res = rsm_result{};
+  r->res.status = RSM_ERR_CANCELLED;
+  h->done_cv.notify_all();
+  return RSM_OK;
+}
+
+int32_t rsm_release(rsm_handle* h, uint64_t ticket) {
+  if (!h) return fail(RSM_ERR_INVALID_ARG, "handle is NULL");
+  std::lock_guard<std::mutex> lk(h->mu);
+  auto it = h->reqs.find(ticket);
+  if (it == h->reqs.end()) return fail(RSM_ERR_INVALID_ARG, "unknown ticket");
+  if (it->second->state != 2) return fail(RSM_ERR_INVALID_ARG, "request not finished");
+  h->reqs.erase(it);
+  return RSM_OK;
+}
+
+void rsm_destroy(rsm_handle* h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  {
+    std::unique_lock<std::mutex> lk(h->mu);
+    // let running requests finish (bounded by the wait limit), drop queued ones
+    h->queue.clear();
+    h->done_cv.wait_for(lk, std::chrono::nanoseconds(h->cfg.wait_timeout_ns), [&] {
+      for (auto& kv : h->reqs)
+        if (kv.second->state == 1) return false;
+      return true;
+    });
+    h->stopping = true;
+  }
+  h->cv.notify_all();
+  for (auto& t : h->workers) t.join();
+  for (auto& s : h->slots) s.destroy();
+  h->main.destroy();
+  delete h;
+}
+
+// ---------------------------------------------------------------- stage entry points
+
+int32_t rsm_pack_mask(const uint8_t* W, int64_t ldw, int64_t m, int64_t n, uint32_t* bits, int64_t ldb, void* stream) {
+  if (!W || !bits || m < 1 || n < 1 || ldw < m || ldb < (m + 31) / 32)
+    return fail(RSM_ERR_INVALID_ARG, "pack_mask: bad pointer or size");
+  ProbDesc d{};
+  d.m = m;
+  d.n = n;
+  d.W = W;
+  d.ldw = ldw;
+  d.bits = bits;
+  d.ldb = ldb;
+  unsigned long long* cnt = nullptr;
+  int64_t* offs = nullptr;
+  ProbDesc* dd = nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // small transient device copies of the descriptor and offsets
+  RSM_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&dd), sizeof(ProbDesc) + 64, s));
+  offs = reinterpret_cast<int64_t*>(reinterpret_cast<unsigned char*>(dd) + sizeof(ProbDesc));
+  cnt = reinterpret_cast<unsigned long long*>(offs + 2);
+  d.counters = cnt - 1;  // counters[1] is the known-entry count
+  const int64_t nblocks = n * ((ldb + 255) / 256);
+  int64_t h_off[2] = {0, nblocks};
+  RSM_CUDA(cudaMemcpyAsync(dd, &d, sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
+  RSM_CUDA(cudaMemcpyAsync(offs, h_off, sizeof(h_off), cudaMemcpyHostToDevice, s));
+  RSM_CUDA(cudaMemsetAsync(cnt, 0, 8, s));
+  cudaError_t e = launch_pack_mask(dd, offs, 1, nblocks, s);
+  RSM_CUDA(cudaFreeAsync(dd, s));
+  if (e != cudaSuccess) return cuda_fail(e, "pack_mask");
+  return RSM_OK;
+}
+
+int32_t rsm_sample_columns(int64_t n, int32_t l, int64_t t0, int64_t count, uint64_t seed, uint32_t problem_id,
+                           int32_t variant, int32_t* cols, void* stream) {
+  if (!cols || n < 1 || l < 1 || l > n || l > kMaxL || t0 < 0 || count < 0 ||
+      (variant != RSM_COLS_RANDOM && variant != RSM_COLS_ADJACENT))
+    return fail(RSM_ERR_INVALID_ARG, "sample_columns: bad argument");
+  ProbDesc d{};
+  d.n = n;
+  d.l = l;
+  d.seed = seed;
+  d.pid = problem_id;
+  d.variant = variant;
+  cudaError_t e = launch_sample_range(d, t0, count, cols, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "sample_columns");
+  return RSM_OK;
+}
+
+int32_t rsm_select_rows(const uint32_t* bits, int64_t ldb, int64_t m, const int32_t* cols, int32_t l, int64_t count,
+                        const int64_t* row_offsets, int32_t* rows, int32_t* row_counts, void* stream) {
+  if (!bits || !cols || !row_offsets || !rows || !row_counts || m < 1 || l < 1 || l > kMaxL || count < 0 ||
+      ldb < (m + 31) / 32)
+    return fail(RSM_ERR_INVALID_ARG, "select_rows: bad argument");
+  cudaError_t e = launch_select_rows(bits, ldb, m, cols, l, count, row_offsets, rows, row_counts,
+                                     static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "select_rows");
+  return RSM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,251 @@
+"""Python binding of librsm.so: torch tensors in, torch tensors out.
+
+The binding only marshals arguments (device pointers, sizes, enums) into the C
+ABI of include/rsm.h; every stage of the RSM path runs in the library's CUDA
+kernels.  PyTorch provides device memory and streams.
+
+Layout: every matrix is column-major.  A column-major m x n torch tensor is a
+tensor of shape (m, n) with stride (1, ld), e.g. ``t.t().contiguous().t()``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+from typing import List, Optional, Sequence
+
+import torch
+
+from . import _abi
+from ._abi import rsm_config, rsm_problem, rsm_result
+
+_VARIANT = {"random": _abi.RSM_COLS_RANDOM, "adjacent": _abi.RSM_COLS_ADJACENT}
+_PREC = {"f64": _abi.RSM_PREC_F64, "f32x2": _abi.RSM_PREC_F32X2, "f32": _abi.RSM_PREC_F32}
+
+
+class RSMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def lib():
+    return _abi.load()
+
+
+def status_string(status: int) -> str:
+    return lib().rsm_status_string(status).decode()
+
+
+def _check(status: int, what: str, ok=(_abi.RSM_OK,)):
+    if status not in ok:
+        raise RSMError(status, f"{what}: {status_string(status)}: {lib().rsm_last_error().decode()}")
+    return status
+
+
+def colmajor(t: torch.Tensor) -> torch.Tensor:
+    """Column-major copy (or view) of a 2-D tensor."""
+    if t.dim() != 2:
+        raise ValueError("expected a 2-D tensor")
+    if t.stride(0) == 1 and t.stride(1) >= max(1, t.shape[0]):
+        return t
+    return t.t().contiguous().t()
+
+
+def _ld(t: torch.Tensor) -> int:
+    if t.stride(0) != 1:
+        raise ValueError("matrix must be column-major (stride(0) == 1)")
+    return max(int(t.stride(1)), int(t.shape[0]))
+
+
+@dataclasses.dataclass
+class Result:
+    status: int
+    accepted_trials: int
+    rows_underdetermined: int
+    eig_M: List[float]
+    e: float
+    stage_ms: List[float]
+    queue_ms: float
+    run_ms: float
+    V: Optional[torch.Tensor] = None
+    U: Optional[torch.Tensor] = None
+    cols: Optional[torch.Tensor] = None
+    row_counts: Optional[torch.Tensor] = None
+    Z: Optional[torch.Tensor] = None
+    M: Optional[torch.Tensor] = None
+
+    @property
+    def ok(self) -> bool:
+        return self.status in (_abi.RSM_OK, _abi.RSM_ERR_ROWS_UNDERDETERMINED)
+
+
+def _result(res: rsm_result, outs: dict) -> Result:
+    return Result(status=res.status, accepted_trials=res.accepted_trials, rows_underdetermined=res.rows_underdetermined,
+                  eig_M=[res.eig_M[i] for i in range(res.n_eig)], e=res.e_known_rms,
+                  stage_ms=[res.stage_ms[i] for i in range(8)], queue_ms=res.queue_ms, run_ms=res.run_ms, **outs)
+
+
+class Problem:
+    """Arguments of one decomposition with the output tensors it owns.
+
+    Y: (m, n) float64/float32 CUDA tensor, W: (m, n) uint8 CUDA tensor (1 = known);
+    both column-major.  U (m x r) and V (n x r) are allocated here (FP64,
+    column-major) unless given.
+    """
+
+    def __init__(self, Y: torch.Tensor, W: torch.Tensor, r: int, *, trials: int, l: int = 0, n_minor: int = 0,
+                 seed: int = 0, problem_id: int = 0, variant: str = "random", gram: str = "f64", solve: str = "f64",
+                 want_U: bool = True, debug: bool = False, U: Optional[torch.Tensor] = None,
+                 V: Optional[torch.Tensor] = None):
+        if not (Y.is_cuda and W.is_cuda):
+            raise ValueError("Y and W must be CUDA tensors")
+        if Y.dtype not in (torch.float64, torch.float32) or W.dtype != torch.uint8:
+            raise ValueError("Y must be float64/float32 and W uint8")
+        self.Y, self.W = Y, W
+        m, n = Y.shape
+        dev = Y.device
+        self.V = V if V is not None else torch.empty((r, n), dtype=torch.float64, device=dev).t()
+        self.U = (U if U is not None else torch.empty((r, m), dtype=torch.float64, device=dev).t()) if want_U else None
+        ll = l if l else r + 1
+        nm = n_minor if n_minor else ll - r
+        self.cols = self.row_counts = self.Z = self.M = None
+        if debug:
+            self.cols = torch.empty((trials, ll), dtype=torch.int32, device=dev)
+            self.row_counts = torch.empty(trials, dtype=torch.int32, device=dev)
+            self.Z = torch.empty((trials, ll, nm), dtype=torch.float64, device=dev)
+            self.M = torch.empty((n, n), dtype=torch.float64, device=dev)
+        p = rsm_problem()
+        p.m, p.n, p.r, p.l, p.n_minor = m, n, r, l, n_minor
+        p.variant = _VARIANT[variant]
+        p.trials, p.seed, p.problem_id = trials, seed, problem_id
+        p.y_dtype = _abi.RSM_F64 if Y.dtype == torch.float64 else _abi.RSM_F32
+        p.gram_prec, p.solve_prec = _PREC[gram], _PREC[solve]
+        p.Y, p.ldy = Y.data_ptr(), _ld(Y)
+        p.W, p.ldw = W.data_ptr(), _ld(W)
+        p.V, p.ldv = self.V.data_ptr(), _ld(self.V)
+        if self.U is not None:
+            p.U, p.ldu = self.U.data_ptr(), _ld(self.U)
+        if debug:
+            p.debug_cols = self.cols.data_ptr()
+            p.debug_row_counts = self.row_counts.data_ptr()
+            p.debug_Z = self.Z.data_ptr()
+            p.debug_M = self.M.data_ptr()
+        self.c = p
+
+    def outputs(self) -> dict:
+        return dict(V=self.V, U=self.U, cols=self.cols, row_counts=self.row_counts, Z=self.Z, M=self.M)
+
+    def footprint_bytes(self) -> int:
+        return int(lib().rsm_footprint_bytes(C.byref(self.c)))
+
+
+class RSM:
+    """A library handle (rsm_create / rsm_destroy) bound to one CUDA device."""
+
+    def __init__(self, device: int = 0, *, max_slots: int = 0, hbm_budget_bytes: int = 0, wait_timeout_ns: int = 0,
+                 stream: Optional[torch.cuda.Stream] = None, fault_inject: int = 0):
+        cfg = rsm_config()
+        cfg.device = device
+        cfg.max_slots = max_slots
+        cfg.hbm_budget_bytes = hbm_budget_bytes
+        cfg.wait_timeout_ns = wait_timeout_ns
+        cfg.stream = stream.cuda_stream if stream is not None else None
+        cfg.fault_inject = fault_inject
+        h = C.c_void_p()
+        _check(lib().rsm_create(C.byref(cfg), C.byref(h)), "rsm_create")
+        self._h = h
+        self._pending = {}
+
+    def close(self):
+        if self._h:
+            lib().rsm_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    _SOFT = (_abi.RSM_OK, _abi.RSM_ERR_UNDERDETERMINED, _abi.RSM_ERR_ROWS_UNDERDETERMINED)
+
+    def decompose(self, prob: Problem) -> Result:
+        res = rsm_result()
+        st = lib().rsm_decompose(self._h, C.byref(prob.c), C.byref(res))
+        _check(st, "rsm_decompose", self._SOFT)
+        return _result(res, prob.outputs())
+
+    def decompose_batch(self, probs: Sequence[Problem]) -> List[Result]:
+        arr = (rsm_problem * len(probs))(*[p.c for p in probs])
+        res = (rsm_result * len(probs))()
+        st = lib().rsm_decompose_batch(self._h, arr, len(probs), res)
+        _check(st, "rsm_decompose_batch", self._SOFT)
+        return [_result(res[i], probs[i].outputs()) for i in range(len(probs))]
+
+    def submit(self, prob: Problem) -> int:
+        t = C.c_uint64()
+        _check(lib().rsm_submit(self._h, C.byref(prob.c), C.byref(t)), "rsm_submit")
+        self._pending[t.value] = prob
+        return t.value
+
+    def poll(self, ticket: int) -> Optional[Result]:
+        res = rsm_result()
+        st = lib().rsm_poll(self._h, ticket, C.byref(res))
+        if st == _abi.RSM_PENDING:
+            return None
+        _check(st, "rsm_poll", self._SOFT + (_abi.RSM_ERR_CANCELLED,))
+        return _result(res, self._pending[ticket].outputs())
+
+    def wait(self, ticket: int, timeout_ns: int = 0) -> Result:
+        res = rsm_result()
+        st = lib().rsm_wait(self._h, ticket, timeout_ns, C.byref(res))
+        _check(st, "rsm_wait", self._SOFT + (_abi.RSM_ERR_CANCELLED,))
+        return _result(res, self._pending[ticket].outputs())
+
+    def cancel(self, ticket: int) -> int:
+        return lib().rsm_cancel(self._h, ticket)
+
+    def release(self, ticket: int):
+        _check(lib().rsm_release(self._h, ticket), "rsm_release")
+        self._pending.pop(ticket, None)
+
+
+# ------------------------------------------------------------------ stage entry points
+
+def pack_mask(W: torch.Tensor, stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    """Bit-packed mask (n columns of ldb uint32 words) of a column-major uint8 W."""
+    m, n = W.shape
+    ldb = ((m + 31) // 32 + 3) // 4 * 4
+    bits = torch.empty((n, ldb), dtype=torch.int32, device=W.device)
+    s = (stream or torch.cuda.current_stream(W.device)).cuda_stream
+    _check(lib().rsm_pack_mask(W.data_ptr(), _ld(W), m, n, bits.data_ptr(), ldb, s), "rsm_pack_mask")
+    return bits
+
+
+def sample_columns(n: int, l: int, t0: int, count: int, seed: int, problem_id: int = 0, variant: str = "random",
+                   device="cuda", stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    cols = torch.empty((count, l), dtype=torch.int32, device=device)
+    s = (stream or torch.cuda.current_stream(cols.device)).cuda_stream
+    _check(lib().rsm_sample_columns(n, l, t0, count, seed, problem_id, _VARIANT[variant], cols.data_ptr(), s),
+           "rsm_sample_columns")
+    return cols
+
+
+def select_rows(bits: torch.Tensor, m: int, cols: torch.Tensor, capacity: int,
+                stream: Optional[torch.cuda.Stream] = None):
+    """Row lists of the trials in ``cols`` (count x l); returns (rows, offsets, counts)."""
+    count, l = cols.shape
+    dev = cols.device
+    offsets = torch.arange(count + 1, dtype=torch.int64, device=dev) * capacity
+    rows = torch.empty(max(1, count * capacity), dtype=torch.int32, device=dev)
+    counts = torch.empty(count, dtype=torch.int32, device=dev)
+    s = (stream or torch.cuda.current_stream(dev)).cuda_stream
+    _check(lib().rsm_select_rows(bits.data_ptr(), bits.shape[1], m, cols.data_ptr(), l, count, offsets.data_ptr(),
+                                 rows.data_ptr(), counts.data_ptr(), s), "rsm_select_rows")
+    return rows, offsets, counts
