@@ -115,9 +115,18 @@ typedef struct rsm_result {
   int32_t n_eig;                 /* eigenvalues of M reported in eig_M */
   int64_t accepted_trials;       /* trials that kept at least l rows */
   int64_t rows_underdetermined;  /* rows with fewer than r known entries */
+  int64_t rows_selected;         /* sum over all trials of the rows kept (p_t) */
+  int64_t kernel_launches;       /* CUDA kernels this call launched (whole batch) */
+  int32_t eig_factor_bits;       /* 32 or 64: precision of the Cholesky preconditioner used for M */
+  int32_t reserved;
   double eig_M[32];              /* smallest eigenvalues of M, ascending */
+  double eig_residual;           /* largest ||M v - lambda v|| over the r returned vectors */
   double e_known_rms;            /* eq. (ep): RMS residual over the known entries (NaN if U is NULL) */
-  float stage_ms[8];             /* pack, sample+select+gram, minor+scatter, eig M, solve U, residual, -, total */
+  float stage_ms[12];            /* device time per stage (CUDA events on the launching stream):
+                                    0 setup (plan upload, zeroing), 1 pack_mask, 2 sample_cols,
+                                    3 select+Gram, 4 minor vectors + scatter into M, 5 eigensolve of M,
+                                    6 solve U, 7 residual e, 8 total; 9-11 reserved.  A batch reports
+                                    the batch's times in every result. */
   double queue_ms;               /* serving: submit -> start */
   double run_ms;                 /* serving: start -> finish */
 } rsm_result;

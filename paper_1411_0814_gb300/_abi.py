@@ -76,12 +76,20 @@ class rsm_result(C.Structure):
         ("n_eig", C.c_int32),
         ("accepted_trials", C.c_int64),
         ("rows_underdetermined", C.c_int64),
+        ("rows_selected", C.c_int64),
+        ("kernel_launches", C.c_int64),
+        ("eig_factor_bits", C.c_int32),
+        ("reserved", C.c_int32),
         ("eig_M", C.c_double * 32),
+        ("eig_residual", C.c_double),
         ("e_known_rms", C.c_double),
-        ("stage_ms", C.c_float * 8),
+        ("stage_ms", C.c_float * 12),
         ("queue_ms", C.c_double),
         ("run_ms", C.c_double),
     ]
+
+
+STAGES = ["setup", "pack_mask", "sample_cols", "select_gram", "minor_scatter", "eig_M", "solve_U", "residual", "total"]
 
 
 # every symbol include/rsm.h declares, with (restype, argtypes)

@@ -594,6 +594,7 @@ __global__ void __launch_bounds__(256) k_eig_finish(const ProbDesc* __restrict__
   do {                                                             \
     if ((blocks) > 0) {                                            \
       kernel<<<(unsigned)(blocks), threads, 0, s>>>(__VA_ARGS__);  \
+      ++g_kernel_launches;                                         \
       cudaError_t e_ = cudaGetLastError();                         \
       if (e_ != cudaSuccess) return e_;                            \
     }                                                              \

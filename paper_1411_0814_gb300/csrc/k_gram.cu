@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(kGramThreads) k_select_gram(const ProbDesc* __
   }
   if (tid == 0) {
     d.row_counts[t] = (int32_t)count;
+    if (count) atomicAdd(&d.counters[5], (unsigned long long)count);
     if (d.debug_row_counts) d.debug_row_counts[t] = (int32_t)count;
   }
 }
@@ -243,16 +244,19 @@ cudaError_t launch_select_gram(int mode, const ProbDesc* descs, const int64_t* t
       e = cudaFuncSetAttribute(k_select_gram<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
       if (e != cudaSuccess) return e;
       k_select_gram<0><<<(unsigned)total, kGramThreads, dyn, s>>>(descs, trial_off, nprob, cap);
+      ++g_kernel_launches;
       break;
     case 1:
       e = cudaFuncSetAttribute(k_select_gram<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
       if (e != cudaSuccess) return e;
       k_select_gram<1><<<(unsigned)total, kGramThreads, dyn, s>>>(descs, trial_off, nprob, cap);
+      ++g_kernel_launches;
       break;
     default:
       e = cudaFuncSetAttribute(k_select_gram<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
       if (e != cudaSuccess) return e;
       k_select_gram<2><<<(unsigned)total, kGramThreads, dyn, s>>>(descs, trial_off, nprob, cap);
+      ++g_kernel_launches;
       break;
   }
   return cudaGetLastError();

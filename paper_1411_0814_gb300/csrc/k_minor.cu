@@ -126,6 +126,7 @@ cudaError_t launch_minor_scatter(const ProbDesc* descs, const int64_t* trial_off
 cudaError_t launch_finalize_M(const ProbDesc* descs, const int64_t* ent_off, int nprob, int64_t total, cudaStream_t s) {
   if (total <= 0) return cudaSuccess;
   k_finalize_M<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(descs, ent_off, nprob);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 

@@ -155,18 +155,21 @@ __global__ void __launch_bounds__(256) k_select_rows(const uint32_t* __restrict_
 cudaError_t launch_pack_mask(const ProbDesc* descs, const int64_t* blk_off, int nprob, int64_t nblocks, cudaStream_t s) {
   if (nblocks <= 0) return cudaSuccess;
   k_pack_mask<<<(unsigned)nblocks, 256, 0, s>>>(descs, blk_off, nprob);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_sample(const ProbDesc* descs, const int64_t* trial_off, int nprob, int64_t total, cudaStream_t s) {
   if (total <= 0) return cudaSuccess;
   k_sample<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(descs, trial_off, nprob);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_sample_range(const ProbDesc& d, int64_t t0, int64_t count, int32_t* cols, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   k_sample_range<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(d, t0, count, cols);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
@@ -174,6 +177,7 @@ cudaError_t launch_select_rows(const uint32_t* bits, int64_t ldb, int64_t m, con
                                const int64_t* row_off, int32_t* rows, int32_t* row_counts, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   k_select_rows<<<(unsigned)count, 256, 0, s>>>(bits, ldb, m, cols, l, row_off, rows, row_counts);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 

@@ -323,28 +323,36 @@ __global__ void __launch_bounds__(32) k_residual_final(const ProbDesc* __restric
 cudaError_t launch_solve_u(const SolvePlan& S, int mode, cudaStream_t s) {
   const ProbDesc* D = S.descs;
   const int np = S.nprob;
-  if (S.k_total > 0) k_build_K<<<(unsigned)((S.k_total + 255) / 256), 256, 0, s>>>(D, S.k_off, np);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  if (S.tile_off_host_total > 0) {
-    if (mode == 0)
-      k_normal<0><<<(unsigned)S.tile_off_host_total, 256, 0, s>>>(D, S.tile_off, np);
-    else
-      k_normal<2><<<(unsigned)S.tile_off_host_total, 256, 0, s>>>(D, S.tile_off, np);
+  cudaError_t e;
+  if (S.k_total > 0) {
+    k_build_K<<<(unsigned)((S.k_total + 255) / 256), 256, 0, s>>>(D, S.k_off, np);
+    ++g_kernel_launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (S.tile_off_host_total > 0) {
+    if (mode == 0) {
+      k_normal<0><<<(unsigned)S.tile_off_host_total, 256, 0, s>>>(D, S.tile_off, np);
+    } else {
+      k_normal<2><<<(unsigned)S.tile_off_host_total, 256, 0, s>>>(D, S.tile_off, np);
+    }
+    ++g_kernel_launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   if (S.row_total > 0) {
     const unsigned blocks = (unsigned)((S.row_total + 127) / 128);
-    if (S.rmax <= 4)
+    if (S.rmax <= 4) {
       k_row_solve<4><<<blocks, 128, 0, s>>>(D, S.row_off, np, S.fail_list, S.fail_count);
-    else if (S.rmax <= 8)
+    } else if (S.rmax <= 8) {
       k_row_solve<8><<<blocks, 128, 0, s>>>(D, S.row_off, np, S.fail_list, S.fail_count);
-    else if (S.rmax <= 16)
+    } else if (S.rmax <= 16) {
       k_row_solve<16><<<blocks, 128, 0, s>>>(D, S.row_off, np, S.fail_list, S.fail_count);
-    else
+    } else {
       k_row_solve<32><<<blocks, 128, 0, s>>>(D, S.row_off, np, S.fail_list, S.fail_count);
+    }
+    ++g_kernel_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_row_pinv<<<152, 32 * kPinvWarps, 0, s>>>(D, S.fail_list, S.fail_count);
+    ++g_kernel_launches;
   }
   return cudaGetLastError();
 }
@@ -353,14 +361,17 @@ cudaError_t launch_residual(const SolvePlan& S, int mode, double* partial, cudaS
   const ProbDesc* D = S.descs;
   const int np = S.nprob;
   if (S.res_blocks > 0) {
-    if (mode == 0)
+    if (mode == 0) {
       k_residual<double><<<(unsigned)S.res_blocks, 256, 0, s>>>(D, S.res_off, np, partial);
-    else
+    } else {
       k_residual<float><<<(unsigned)S.res_blocks, 256, 0, s>>>(D, S.res_off, np, partial);
+    }
+    ++g_kernel_launches;
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_residual_final<<<np, 32, 0, s>>>(D, S.res_off, np, partial);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 

@@ -10,6 +10,9 @@ namespace rsm {
 
 struct ProbDesc;
 
+// Kernels launched by the calling thread (incremented by every launcher).
+extern thread_local int64_t g_kernel_launches;
+
 // Offsets of the eigen stage.  Every table is an exclusive prefix sum of
 // nprob + 1 int64 values; dT is the device copy (read by kernels), hT the host
 // copy (read by the launcher for grid sizes); both hold the same tables at the

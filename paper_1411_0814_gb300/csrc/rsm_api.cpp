@@ -27,6 +27,14 @@ namespace {
 
 thread_local std::string g_last_error;
 
+}  // namespace
+
+namespace rsm {
+thread_local int64_t g_kernel_launches = 0;
+}
+
+namespace {
+
 int fail(int status, const std::string& msg) {
   g_last_error = msg;
   return status;
@@ -102,7 +110,7 @@ struct Slot {
   bool own_stream = false;
   DevBuf ws, plan;
   PinBuf host;
-  cudaEvent_t ev[8] = {};
+  cudaEvent_t ev[10] = {};
   int init(cudaStream_t external) {
     if (external) {
       stream = external;
@@ -165,17 +173,17 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
   const int np = b.nprob;
   cudaError_t e;
   if (do_front) {
-    RSM_CUDA(cudaEventRecord(slot.ev[0], s));
     if ((e = launch_pack_mask(D, T + b.o_pack, np, b.pack_blocks, s)) != cudaSuccess) return cuda_fail(e, "pack_mask");
-    RSM_CUDA(cudaEventRecord(slot.ev[1], s));
+    RSM_CUDA(cudaEventRecord(slot.ev[2], s));
     if ((e = launch_sample(D, T + b.o_trial, np, b.trials_total, s)) != cudaSuccess) return cuda_fail(e, "sample");
+    RSM_CUDA(cudaEventRecord(slot.ev[3], s));
     if ((e = launch_select_gram(b.gram_mode, D, T + b.o_trial, np, b.trials_total, b.lmax, s)) != cudaSuccess)
       return cuda_fail(e, "select_gram");
-    RSM_CUDA(cudaEventRecord(slot.ev[2], s));
+    RSM_CUDA(cudaEventRecord(slot.ev[4], s));
     if ((e = launch_minor_scatter(D, T + b.o_trial, np, b.trials_total, b.lmax, s)) != cudaSuccess)
       return cuda_fail(e, "minor_scatter");
     if ((e = launch_finalize_M(D, T + b.o_ent, np, b.ent_total, s)) != cudaSuccess) return cuda_fail(e, "finalize_M");
-    RSM_CUDA(cudaEventRecord(slot.ev[3], s));
+    RSM_CUDA(cudaEventRecord(slot.ev[5], s));
   }
   EigPlan ep{};
   ep.descs = D;
@@ -195,8 +203,9 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
   ep.rot = b.o_rot;
   ep.row_tile = b.o_rowtile;
   ep.part = reinterpret_cast<double*>(static_cast<unsigned char*>(slot.ws.ptr) + b.part_bytes_off);
-  if ((e = launch_eig(ep, fp64_factor, shift_rel, fp64_factor ? kEigIters64 : kEigIters32, s)) != cudaSuccess) return cuda_fail(e, "eig");
-  RSM_CUDA(cudaEventRecord(slot.ev[4], s));
+  if ((e = launch_eig(ep, fp64_factor, shift_rel, fp64_factor ? kEigIters64 : kEigIters32, s)) != cudaSuccess)
+    return cuda_fail(e, "eig");
+  RSM_CUDA(cudaEventRecord(slot.ev[6], s));
   if (b.any_solve) {
     SolvePlan sp{};
     sp.descs = D;
@@ -213,13 +222,13 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
     sp.fail_list = reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(slot.ws.ptr) + b.fail_list_off);
     sp.fail_count = reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(slot.ws.ptr) + b.fail_count_off);
     if ((e = launch_solve_u(sp, b.solve_mode, s)) != cudaSuccess) return cuda_fail(e, "solve_u");
-    RSM_CUDA(cudaEventRecord(slot.ev[5], s));
+    RSM_CUDA(cudaEventRecord(slot.ev[7], s));
     double* partial = reinterpret_cast<double*>(static_cast<unsigned char*>(slot.ws.ptr) + b.res_bytes_off);
     if ((e = launch_residual(sp, b.solve_mode, partial, s)) != cudaSuccess) return cuda_fail(e, "residual");
   } else {
-    RSM_CUDA(cudaEventRecord(slot.ev[5], s));
+    RSM_CUDA(cudaEventRecord(slot.ev[7], s));
   }
-  RSM_CUDA(cudaEventRecord(slot.ev[6], s));
+  RSM_CUDA(cudaEventRecord(slot.ev[8], s));
   return RSM_OK;
 }
 
@@ -250,8 +259,11 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
   const size_t dsz = (sizeof(ProbDesc) * count + 255) / 256 * 256;
   std::memcpy(hp, b.descs.data(), sizeof(ProbDesc) * count);
   std::memcpy(hp + dsz, b.tables.data(), b.tables.size() * 8);
+  const int64_t launches0 = g_kernel_launches;
+  RSM_CUDA(cudaEventRecord(slot.ev[0], slot.stream));
   RSM_CUDA(cudaMemcpyAsync(slot.plan.ptr, hp, dsz + b.tables.size() * 8, cudaMemcpyHostToDevice, slot.stream));
   RSM_CUDA(cudaMemsetAsync(slot.ws.ptr, 0, b.layout.zero_bytes, slot.stream));
+  RSM_CUDA(cudaEventRecord(slot.ev[1], slot.stream));
   int64_t max_n = 0;
   for (int i = 0; i < count; ++i) max_n = std::max<int64_t>(max_n, ps[i].n);
   bool fp64 = max_n <= kSmallN;
@@ -287,10 +299,10 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
     if ((st = enqueue_readback(b, slot)) != RSM_OK) return st;
     RSM_CUDA(cudaStreamSynchronize(slot.stream));
   }
-  float ms[7] = {0};
-  for (int k = 0; k < 6; ++k) cudaEventElapsedTime(&ms[k], slot.ev[k], slot.ev[k + 1]);
-  float total_ms = 0;
-  cudaEventElapsedTime(&total_ms, slot.ev[0], slot.ev[6]);
+  float ms[9] = {0};
+  for (int k = 0; k < 8; ++k) cudaEventElapsedTime(&ms[k], slot.ev[k], slot.ev[k + 1]);
+  cudaEventElapsedTime(&ms[8], slot.ev[0], slot.ev[8]);
+  const int64_t launches = g_kernel_launches - launches0;
   int first_bad = RSM_OK;
   for (int i = 0; i < count; ++i) {
     const unsigned long long* c = reinterpret_cast<const unsigned long long*>(hp + (size_t)i * kReadback);
@@ -298,8 +310,12 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
     rsm_result r{};
     r.accepted_trials = (int64_t)c[0];
     r.rows_underdetermined = (int64_t)c[4];
+    r.rows_selected = (int64_t)c[5];
+    r.kernel_launches = launches;
+    r.eig_factor_bits = fp64 ? 64 : 32;
     r.n_eig = b.dv[i].kx;
     for (int k = 0; k < 32; ++k) r.eig_M[k] = k < r.n_eig ? stats[k] : 0.0;
+    r.eig_residual = stats[34];
     const double trace = (double)c[0] * b.dv[i].nm;
     r.e_known_rms = b.dv[i].solve_u ? stats[33] : NAN;
     int status = RSM_OK;
@@ -310,8 +326,7 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
     else if (c[4] > 0)
       status = RSM_ERR_ROWS_UNDERDETERMINED;
     r.status = status;
-    for (int k = 0; k < 6; ++k) r.stage_ms[k] = ms[k];
-    r.stage_ms[7] = total_ms;
+    for (int k = 0; k < 9; ++k) r.stage_ms[k] = ms[k];
     if (res) res[i] = r;
     if (status != RSM_OK && first_bad == RSM_OK) first_bad = status;
   }
