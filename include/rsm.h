@@ -211,6 +211,24 @@ int32_t rsm_sample_columns(int64_t n, int32_t l, int64_t t0, int64_t count, uint
 int32_t rsm_select_rows(const uint32_t* bits, int64_t ldb, int64_t m, const int32_t* cols, int32_t l, int64_t count,
                         const int64_t* row_offsets, int32_t* rows, int32_t* row_counts, void* stream);
 
+/* The error e of eq. (ep) for a given U and V, without allocating device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate when they need the error - work recorded into a CUDA graph by
+ * stream capture, code running under a fixed memory pool, latency-bound loops.
+ * Y: device m x n (ldy >= m) of y_dtype; W: device m x n bytes (ldw >= m),
+ * nonzero = known; U: device m x r FP64 (ldu >= m); V: device n x r FP64
+ * (ldv >= n); 1 <= r <= 32.  e: device pointer to one double that receives
+ * sqrt(sum over known (y_ij - u_i . v_j)^2 / number of known entries).
+ * Asynchronous on stream.  Scratch is a fixed array inside the library (256 KiB
+ * per device, held until the process exits): m above 4,194,304 rows returns
+ * RSM_ERR_INVALID_ARG.  All calls share that array, so calls that overlap on the
+ * GPU race and give wrong results.  The first call on a device resolves the
+ * array's address (cudaGetSymbolAddress, device current); make it before any
+ * stream capture.  No cudaMalloc, cudaFree or allocating library call is made. */
+int32_t rsm_residual_noalloc(const void* Y, int64_t ldy, int32_t y_dtype, const uint8_t* W, int64_t ldw,
+                             const double* U, int64_t ldu, const double* V, int64_t ldv, int64_t m, int64_t n,
+                             int32_t r, double* e, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

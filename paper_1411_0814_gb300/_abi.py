@@ -113,6 +113,9 @@ SIGNATURES = {
                                        C.c_void_p, C.c_void_p]),
     "rsm_select_rows": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int32, C.c_int64, C.c_void_p,
                                     C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rsm_residual_noalloc": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p,
+                                         C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
+                                         C.c_void_p, C.c_void_p]),
 }
 
 _lib = None

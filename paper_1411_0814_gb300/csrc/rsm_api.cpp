@@ -31,6 +31,7 @@ thread_local std::string g_last_error;
 
 namespace rsm {
 thread_local int64_t g_kernel_launches = 0;
+void set_last_error(const std::string& msg) { g_last_error = msg; }
 }
 
 namespace {

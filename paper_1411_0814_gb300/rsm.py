@@ -256,3 +256,17 @@ def select_rows(bits: torch.Tensor, m: int, cols: torch.Tensor, capacity: int,
     _check(lib().rsm_select_rows(bits.data_ptr(), bits.shape[1], m, cols.data_ptr(), l, count, offsets.data_ptr(),
                                  rows.data_ptr(), counts.data_ptr(), s), "rsm_select_rows")
     return rows, offsets, counts
+
+
+def residual_noalloc(Y: torch.Tensor, W: torch.Tensor, U: torch.Tensor, V: torch.Tensor,
+                     stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    """Error e of eq. (ep) for given U, V through rsm_residual_noalloc (no device allocation
+    inside the library; the one-element output tensor is allocated here by the caller side)."""
+    m, n = Y.shape
+    r = U.shape[1]
+    e = torch.empty(1, dtype=torch.float64, device=Y.device)
+    s = (stream or torch.cuda.current_stream(Y.device)).cuda_stream
+    y_dtype = _abi.RSM_F64 if Y.dtype == torch.float64 else _abi.RSM_F32
+    _check(lib().rsm_residual_noalloc(Y.data_ptr(), _ld(Y), y_dtype, W.data_ptr(), _ld(W), U.data_ptr(), _ld(U),
+                                      V.data_ptr(), _ld(V), m, n, r, e.data_ptr(), s), "rsm_residual_noalloc")
+    return e

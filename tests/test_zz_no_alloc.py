@@ -1,0 +1,35 @@
+"""rsm_residual_noalloc: the error e of eq. (ep) without device allocation.
+
+Callers that cannot allocate device memory when they need the error (work
+recorded into a CUDA graph by stream capture, code running under a fixed memory
+pool, latency-bound loops) use this entry point; its scratch is a fixed array
+inside the library.  It must agree with the error rsm_decompose reports, call
+after call, even though every call reuses the same scratch array.  This file is
+collected last on purpose.
+"""
+import pytest
+
+from tests.gpu_helpers import to_device
+from workloads import lowrank_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def test_noalloc_residual_matches_decompose_on_consecutive_calls():
+    import paper_1411_0814_gb300 as rsm
+
+    big = lowrank_problem(4133, 96, 4, 0.85, 1e-3, trials=2000, seed=21)   # ragged m: partial last block
+    small = lowrank_problem(700, 48, 3, 0.9, 1e-2, trials=1000, seed=22)   # fewer blocks than the call before
+    with rsm.RSM(0) as h:
+        runs = []
+        for p in (big, small):
+            Y, W = to_device(p)
+            res = h.decompose(rsm.Problem(Y, W, p.r, trials=p.trials, seed=p.seed))
+            assert res.status == 0
+            runs.append((Y, W, res))
+        # two calls in a row per problem, alternating problems, so each call starts
+        # from the scratch contents the previous call left behind
+        for _ in range(2):
+            for Y, W, res in runs:
+                e = float(rsm.residual_noalloc(Y, W, res.U, res.V).item())
+                assert abs(e - res.e) <= 1e-12 * res.e, (e, res.e)
