@@ -1,32 +1,62 @@
 // One-warp cyclic Jacobi eigensolver for a small symmetric matrix in shared
-// memory (FP64).  Textbook two-sided Jacobi (symmetric Schur decomposition,
-// Golub & Van Loan, "Matrix Computations", Sec. 8.5): a rotation in plane
-// (p, q) with tau = (a_qq - a_pp) / (2 a_pq), t = sign(tau) / (|tau| +
-// sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c annihilates a_pq.  The parallel
-// round-robin ordering applies the k/2 disjoint rotations of a round together.
-// A rotation is skipped when |a_pq| <= eps sqrt(|a_pp a_qq|); the sweeps stop
-// when a whole sweep skips every rotation.
+// memory.  Textbook two-sided Jacobi (symmetric Schur decomposition, Golub &
+// Van Loan, "Matrix Computations", Sec. 8.5): a rotation in plane (p, q) with
+// tau = (a_qq - a_pp) / (2 a_pq), t = sign(tau) / (|tau| + sqrt(1 + tau^2)),
+// c = 1/sqrt(1 + t^2), s = t c annihilates a_pq.  The parallel round-robin
+// ordering applies the k/2 disjoint rotations of a round together.
+//
+// A rotation is skipped when |a_pq| <= tol_abs or |a_pq| <= eps sqrt(|a_pp a_qq|);
+// the sweeps stop when a whole sweep skips every rotation.  tol_abs is a few
+// units of rounding of ||A||_F: below it the off-diagonal entries are rounding
+// noise, and rotating on them only creates new noise of the same size.
 #pragma once
 
 #include <cfloat>
 
 namespace rsm {
 
-struct JacobiScratch {
+template <typename T>
+struct JacobiScratchT {
   int p[16], q[16];
-  double c[16], s[16];
+  T c[16], s[16];
 };
+using JacobiScratch = JacobiScratchT<double>;
+
+template <typename T>
+__device__ __forceinline__ T jacobi_eps();
+template <>
+__device__ __forceinline__ double jacobi_eps<double>() { return DBL_EPSILON; }
+template <>
+__device__ __forceinline__ float jacobi_eps<float>() { return FLT_EPSILON; }
+
+// ||A||_F of a k x k matrix in shared memory (row stride ls), all lanes get it.
+template <typename T>
+__device__ inline T warp_frobenius(const T* A, int k, int ls) {
+  const int lane = threadIdx.x & 31;
+  T s = 0;
+  for (int i = lane; i < k * k; i += 32) {
+    const T v = A[(i / k) * ls + (i % k)];
+    s += v * v;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return sqrt(s);
+}
 
 // S: k x k symmetric (row stride ls), overwritten by its eigenvalues on the
-// diagonal; Vm: k x k (row stride ls) receives the eigenvectors as columns.
-// k <= 32.  All 32 lanes of the warp must call it.
-__device__ inline void warp_jacobi(double* S, double* Vm, int k, int ls, JacobiScratch& js, int max_sweeps = 40) {
+// diagonal; Vm: k x k (row stride ls) receives the eigenvectors as columns
+// (Vm is set to I first unless keep_v).  k <= 32.  All 32 lanes must call it.
+template <typename T>
+__device__ inline void warp_jacobi(T* S, T* Vm, int k, int ls, JacobiScratchT<T>& js, T tol_abs, int max_sweeps = 40,
+                                   bool keep_v = false) {
   const int lane = threadIdx.x & 31;
-  for (int i = lane; i < k * k; i += 32) {
-    const int a = i / k, b = i % k;
-    Vm[a * ls + b] = (a == b) ? 1.0 : 0.0;
-  }
+  if (!keep_v)
+    for (int i = lane; i < k * k; i += 32) {
+      const int a = i / k, b = i % k;
+      Vm[a * ls + b] = (a == b) ? (T)1 : (T)0;
+    }
   __syncwarp();
+  const T eps = jacobi_eps<T>();
   const int ne = (k + 1) & ~1;
   const int np = ne / 2;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
@@ -41,14 +71,14 @@ __device__ inline void warp_jacobi(double* S, double* Vm, int k, int ls, JacobiS
           a = b;
           b = tmp;
         }
-        double c = 1.0, s = 0.0;
+        T c = 1, s = 0;
         if (b < k) {
-          const double apq = S[a * ls + b];
-          const double app = S[a * ls + a], aqq = S[b * ls + b];
-          if (fabs(apq) > DBL_EPSILON * sqrt(fabs(app) * fabs(aqq)) && fabs(apq) > 1e-300) {
-            const double tau = (aqq - app) / (2.0 * apq);
-            const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + tt * tt);
+          const T apq = S[a * ls + b];
+          const T app = S[a * ls + a], aqq = S[b * ls + b];
+          if (fabs(apq) > tol_abs && fabs(apq) > eps * sqrt(fabs(app) * fabs(aqq))) {
+            const T tau = (aqq - app) / (2 * apq);
+            const T tt = (tau >= 0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt(1 + tau * tau));
+            c = 1 / sqrt(1 + tt * tt);
             s = tt * c;
           }
         } else {
@@ -60,42 +90,120 @@ __device__ inline void warp_jacobi(double* S, double* Vm, int k, int ls, JacobiS
         js.s[lane] = s;
       }
       __syncwarp();
-      const bool rot = lane < np && js.s[lane] != 0.0;
+      const bool rot = lane < np && js.s[lane] != (T)0;
       any |= __any_sync(0xffffffffu, rot);
       for (int it = lane; it < np * k; it += 32) {  // columns p, q of S and Vm
         const int r = it / k, i = it % k;
-        const double s = js.s[r];
-        if (s == 0.0) continue;
-        const double c = js.c[r];
+        const T s = js.s[r];
+        if (s == (T)0) continue;
+        const T c = js.c[r];
         const int a = js.p[r], b = js.q[r];
-        const double xp = S[i * ls + a], xq = S[i * ls + b];
+        const T xp = S[i * ls + a], xq = S[i * ls + b];
         S[i * ls + a] = c * xp - s * xq;
         S[i * ls + b] = s * xp + c * xq;
-        const double vp = Vm[i * ls + a], vq = Vm[i * ls + b];
+        const T vp = Vm[i * ls + a], vq = Vm[i * ls + b];
         Vm[i * ls + a] = c * vp - s * vq;
         Vm[i * ls + b] = s * vp + c * vq;
       }
       __syncwarp();
       for (int it = lane; it < np * k; it += 32) {  // rows p, q of S
         const int r = it / k, j = it % k;
-        const double s = js.s[r];
-        if (s == 0.0) continue;
-        const double c = js.c[r];
+        const T s = js.s[r];
+        if (s == (T)0) continue;
+        const T c = js.c[r];
         const int a = js.p[r], b = js.q[r];
-        const double xp = S[a * ls + j], xq = S[b * ls + j];
+        const T xp = S[a * ls + j], xq = S[b * ls + j];
         S[a * ls + j] = c * xp - s * xq;
         S[b * ls + j] = s * xp + c * xq;
       }
       __syncwarp();
       if (rot) {
         const int a = js.p[lane], b = js.q[lane];
-        S[a * ls + b] = 0.0;
-        S[b * ls + a] = 0.0;
+        S[a * ls + b] = 0;
+        S[b * ls + a] = 0;
       }
       __syncwarp();
     }
     if (!any) break;
   }
+}
+
+// Eigendecomposition of a k x k symmetric FP64 matrix (k <= 32) in two
+// precisions: Jacobi in FP32 on a rounded copy gives Q32 that nearly
+// diagonalises A; Q32 is made orthogonal in FP64 (Lowdin steps), B = Q^T A Q is
+// formed in FP64 and polished by FP64 Jacobi sweeps (quadratic convergence from
+// ~1e-7 off-diagonals), and the eigenvectors are Q * Q64.  The FP64 work is a
+// few sweeps instead of a full solve.
+// A (k x k, stride ls, FP64) is overwritten: eigenvalues on its diagonal.
+// Vd (k x k, stride ls, FP64) receives the eigenvectors.  Work areas: Sf, Vf
+// (FP32, stride ls), Td (FP64, stride ls).
+__device__ inline void warp_eig_mixed(double* A, double* Vd, float* Sf, float* Vf, double* Td, int k, int ls,
+                                      JacobiScratchT<float>& jsf, JacobiScratchT<double>& jsd) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < k * k; i += 32) Sf[(i / k) * ls + (i % k)] = (float)A[(i / k) * ls + (i % k)];
+  __syncwarp();
+  const double fro = warp_frobenius(A, k, ls);
+  warp_jacobi<float>(Sf, Vf, k, ls, jsf, (float)(4.0 * FLT_EPSILON * fro));
+  // Q = Q32 made orthogonal to FP64 accuracy by two Lowdin steps, Q <- Q (3I - Q^T Q) / 2
+  // (Q32 is orthogonal only to FP32 accuracy).  Q lives in Vd.
+  for (int i = lane; i < k * k; i += 32) Vd[(i / k) * ls + (i % k)] = (double)Vf[(i / k) * ls + (i % k)];
+  __syncwarp();
+  for (int step = 0; step < 2; ++step) {
+    for (int i = lane; i < k * k; i += 32) {  // Td = Q^T Q
+      const int a = i / k, b = i % k;
+      double s = 0.0;
+      for (int t = 0; t < k; ++t) s = fma(Vd[t * ls + a], Vd[t * ls + b], s);
+      Td[a * ls + b] = s;
+    }
+    __syncwarp();
+    double out[32];
+    int cnt = 0;
+    for (int i = lane; i < k * k; i += 32) {  // Q (3I - Td) / 2
+      const int a = i / k, b = i % k;
+      double s = 0.0;
+      for (int t = 0; t < k; ++t) s = fma(Vd[a * ls + t], ((t == b) ? 3.0 : 0.0) - Td[t * ls + b], s);
+      out[cnt++] = 0.5 * s;
+    }
+    __syncwarp();
+    cnt = 0;
+    for (int i = lane; i < k * k; i += 32) Vd[(i / k) * ls + (i % k)] = out[cnt++];
+    __syncwarp();
+  }
+  // Td = A * Q
+  for (int i = lane; i < k * k; i += 32) {
+    const int a = i / k, b = i % k;
+    double s = 0.0;
+    for (int t = 0; t < k; ++t) s = fma(A[a * ls + t], Vd[t * ls + b], s);
+    Td[a * ls + b] = s;
+  }
+  __syncwarp();
+  // B = Q^T Td (symmetrised; upper triangle mirrored), the nearly diagonal matrix to polish
+  double bv[32];
+  int nb = 0;
+  for (int i = lane; i < k * k; i += 32) {
+    const int a = i / k, b = i % k;
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    double s = 0.0;
+    for (int t = 0; t < k; ++t) s = fma(Vd[t * ls + lo], Td[t * ls + hi], s);
+    bv[nb++] = s;
+  }
+  __syncwarp();
+  nb = 0;
+  for (int i = lane; i < k * k; i += 32) A[(i / k) * ls + (i % k)] = bv[nb++];
+  __syncwarp();
+  warp_jacobi<double>(A, Td, k, ls, jsd, 4.0 * DBL_EPSILON * fro, 4);
+  // eigenvectors Q * Q64 (computed into registers, then stored in Vd)
+  nb = 0;
+  for (int i = lane; i < k * k; i += 32) {
+    const int a = i / k, b = i % k;
+    double s = 0.0;
+    for (int t = 0; t < k; ++t) s = fma(Vd[a * ls + t], Td[t * ls + b], s);
+    bv[nb++] = s;
+  }
+  __syncwarp();
+  nb = 0;
+  for (int i = lane; i < k * k; i += 32) Vd[(i / k) * ls + (i % k)] = bv[nb++];
+  __syncwarp();
 }
 
 }  // namespace rsm

@@ -58,18 +58,22 @@ __global__ void __launch_bounds__(256) k_eig_prep(const ProbDesc* __restrict__ d
 }
 
 // ------------------------------------------------------------------ Cholesky, step k
-// Factor the diagonal block in shared memory and invert the factor.
+// Factor the diagonal block and invert the factor; one thread per entry (32 x 32).
+// Step j: one thread takes the square root and reciprocal of the pivot, the
+// column-j threads scale, and the trailing threads update.  The inverse is
+// formed one column per warp by forward substitution with warp reductions.
 template <typename T>
-__global__ void __launch_bounds__(256) k_potrf(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
-                                              int nprob, int k) {
+__global__ void __launch_bounds__(1024) k_potrf(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
+                                               int nprob, int k) {
   __shared__ T a[BS][BS + 1];
-  __shared__ T inv[BS][BS + 1];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
   const int64_t np = npad_of(d);
+  const int i = threadIdx.x / BS, c = threadIdx.x % BS;  // row, column
   T* A = F1of<T>(d) + (int64_t)k * BS * np + (int64_t)k * BS;
-  for (int e = threadIdx.x; e < BS * BS; e += 256) a[e / BS][e % BS] = A[(e / BS) * np + (e % BS)];
+  a[i][c] = A[(int64_t)i * np + c];
   __syncthreads();
+  __shared__ T piv;
   for (int j = 0; j < BS; ++j) {
     if (threadIdx.x == 0) {
       T dj = a[j][j];
@@ -77,34 +81,28 @@ __global__ void __launch_bounds__(256) k_potrf(const ProbDesc* __restrict__ desc
         atomicAdd(&d.counters[3], 1ull);
         dj = (T)1e-30;
       }
-      a[j][j] = sqrt(dj);
+      const T s = sqrt(dj);
+      a[j][j] = s;
+      piv = (T)1 / s;
     }
     __syncthreads();
-    const T djj = a[j][j];
-    for (int i = j + 1 + threadIdx.x; i < BS; i += 256) a[i][j] /= djj;
+    if (c == j && i > j) a[i][j] *= piv;
     __syncthreads();
-    for (int e = threadIdx.x; e < BS * BS; e += 256) {
-      const int i = e / BS, c = e % BS;
-      if (c > j && c <= i) a[i][c] -= a[i][j] * a[c][j];
-    }
+    if (c > j && c <= i) a[i][c] -= a[i][j] * a[c][j];
     __syncthreads();
   }
-  // inverse of the lower-triangular factor: one column per thread, forward substitution
-  if (threadIdx.x < BS) {
-    const int c = threadIdx.x;
-    for (int i = 0; i < BS; ++i) {
-      T s = (i == c) ? (T)1 : (T)0;
-      for (int t = c; t < i; ++t) s -= a[i][t] * inv[t][c];
-      inv[i][c] = (i < c) ? (T)0 : s / a[i][i];
-    }
+  // inverse of the lower-triangular factor: warp w computes column w (lane t holds entry t)
+  const int col = threadIdx.x / 32, lane = threadIdx.x % 32;
+  T mine = (T)0;
+  for (int r = 0; r < BS; ++r) {
+    T term = (lane >= col && lane < r) ? a[r][lane] * mine : (T)0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) term += __shfl_xor_sync(0xffffffffu, term, o);
+    if (lane == r) mine = (r < col) ? (T)0 : (((r == col) ? (T)1 : (T)0) - term) / a[r][r];
   }
-  __syncthreads();
   T* D = Dinvof<T>(d) + (int64_t)k * BS * BS;
-  for (int e = threadIdx.x; e < BS * BS; e += 256) {
-    const int i = e / BS, c = e % BS;
-    A[i * np + c] = (c <= i) ? a[i][c] : (T)0;
-    D[e] = inv[i][c];
-  }
+  D[lane * BS + col] = mine;  // entry (lane, col) of inv(L_kk)
+  A[(int64_t)i * np + c] = (c <= i) ? a[i][c] : (T)0;
 }
 
 // 32 x 32 x 32 product helper: each of 256 threads owns 4 outputs (row ty + 8s, column tx).
@@ -177,56 +175,77 @@ __global__ void __launch_bounds__(256) k_trail(const ProbDesc* __restrict__ desc
 }
 
 // ------------------------------------------------------------------ L^-1 (into F2)
+// Right-looking block forward substitution of L X = I: X starts as I on the
+// diagonal blocks and 0 below; at step k block row k is final after
+// X_kj <- inv(L_kk) X_kj (j <= k), and every block X_ij (i > k, j <= k) then
+// subtracts L_ik X_kj.  Each CTA does one 32 x 32 x 32 product per launch.
 template <typename T>
-__global__ void __launch_bounds__(256) k_linv_diag(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
+__global__ void __launch_bounds__(256) k_linv_init(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                   int nprob) {
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
   const int64_t np = npad_of(d);
-  const int i = (int)(blockIdx.x - off[p]);
-  const T* D = Dinvof<T>(d) + (int64_t)i * BS * BS;
-  T* out = F2of<T>(d) + (int64_t)i * BS * np + (int64_t)i * BS;
-  for (int e = threadIdx.x; e < BS * BS; e += 256) out[(e / BS) * np + (e % BS)] = D[e];
+  int i, j;
+  tri_index(blockIdx.x - off[p], i, j);
+  T* out = F2of<T>(d) + (int64_t)i * BS * np + (int64_t)j * BS;
+  for (int e = threadIdx.x; e < BS * BS; e += 256) {
+    const int r = e / BS, c = e % BS;
+    out[(int64_t)r * np + c] = (i == j && r == c) ? (T)1 : (T)0;
+  }
 }
 
-// Block row i of L^-1: Linv_ij = -inv(L_ii) * sum_{t=j}^{i-1} L_it Linv_tj, for j < i.
 template <typename T>
-__global__ void __launch_bounds__(256) k_linv_step(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
-                                                  int nprob, int i) {
+__global__ void __launch_bounds__(256) k_linv_scale(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
+                                                   int nprob, int k) {
   __shared__ T x[BS][BS + 1], y[BS][BS + 1];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
   const int64_t np = npad_of(d);
-  const int j = (int)(blockIdx.x - off[p]);
+  const int j = (int)(blockIdx.x - off[p]);  // j <= k
+  T* Xkj = F2of<T>(d) + (int64_t)k * BS * np + (int64_t)j * BS;
+  const T* D = Dinvof<T>(d) + (int64_t)k * BS * BS;
+  for (int e = threadIdx.x; e < BS * BS; e += 256) {
+    x[e / BS][e % BS] = D[e];
+    y[e / BS][e % BS] = Xkj[(int64_t)(e / BS) * np + (e % BS)];
+  }
+  __syncthreads();
   const int tx = threadIdx.x % BS, ty = threadIdx.x / BS;
   T acc[4] = {(T)0, (T)0, (T)0, (T)0};
-  for (int t = j; t < i; ++t) {
-    const T* Lit = F1of<T>(d) + (int64_t)i * BS * np + (int64_t)t * BS;
-    const T* Ltj = F2of<T>(d) + (int64_t)t * BS * np + (int64_t)j * BS;
-    __syncthreads();
-    for (int e = threadIdx.x; e < BS * BS; e += 256) {
-      x[e / BS][e % BS] = Lit[(e / BS) * np + (e % BS)];
-      y[e / BS][e % BS] = Ltj[(e / BS) * np + (e % BS)];
-    }
-    __syncthreads();
-    for (int u = 0; u < BS; ++u) {
-      const T yv = y[u][tx];
+  for (int u = 0; u < BS; ++u) {
+    const T yv = y[u][tx];
 #pragma unroll
-      for (int s = 0; s < 4; ++s) acc[s] = fma(x[ty + 8 * s][u], yv, acc[s]);
-    }
+    for (int s = 0; s < 4; ++s) acc[s] = fma(x[ty + 8 * s][u], yv, acc[s]);
+  }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) Xkj[(int64_t)(ty + 8 * s) * np + tx] = acc[s];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_linv_update(const ProbDesc* __restrict__ descs,
+                                                    const int64_t* __restrict__ off, int nprob, int k) {
+  __shared__ T x[BS][BS + 1], y[BS][BS + 1];
+  const int p = find_problem(off, nprob, blockIdx.x);
+  const ProbDesc& d = descs[p];
+  const int64_t np = npad_of(d);
+  const int64_t local = blockIdx.x - off[p];
+  const int i = k + 1 + (int)(local / (k + 1)), j = (int)(local % (k + 1));
+  const T* Lik = F1of<T>(d) + (int64_t)i * BS * np + (int64_t)k * BS;
+  const T* Xkj = F2of<T>(d) + (int64_t)k * BS * np + (int64_t)j * BS;
+  T* Xij = F2of<T>(d) + (int64_t)i * BS * np + (int64_t)j * BS;
+  for (int e = threadIdx.x; e < BS * BS; e += 256) {
+    x[e / BS][e % BS] = Lik[(int64_t)(e / BS) * np + (e % BS)];
+    y[e / BS][e % BS] = Xkj[(int64_t)(e / BS) * np + (e % BS)];
   }
   __syncthreads();
-  const T* D = Dinvof<T>(d) + (int64_t)i * BS * BS;
-  for (int s = 0; s < 4; ++s) x[ty + 8 * s][tx] = acc[s];
-  for (int e = threadIdx.x; e < BS * BS; e += 256) y[e / BS][e % BS] = D[e];
-  __syncthreads();
-  T* out = F2of<T>(d) + (int64_t)i * BS * np + (int64_t)j * BS;
-  for (int s = 0; s < 4; ++s) {
-    const int r = ty + 8 * s;
-    T v = (T)0;
-    for (int u = 0; u <= r; ++u) v = fma(y[r][u], x[u][tx], v);
-    out[(int64_t)r * np + tx] = -v;
+  const int tx = threadIdx.x % BS, ty = threadIdx.x / BS;
+  T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+  for (int u = 0; u < BS; ++u) {
+    const T yv = y[u][tx];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) acc[s] = fma(x[ty + 8 * s][u], yv, acc[s]);
   }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) Xij[(int64_t)(ty + 8 * s) * np + tx] -= acc[s];
 }
 
 // T = A^-1 = L^-T L^-1:  T_ij = sum_{t >= max(i, j)} Linv_ti^T Linv_tj  (into F1, both triangles)
@@ -283,7 +302,8 @@ __global__ void __launch_bounds__(256) k_init_X(const ProbDesc* __restrict__ des
   d.X[e] = ((double)w.x + 0.5) * (2.0 / 4294967296.0) - 1.0;
 }
 
-constexpr int kSplit = 4;    // split of the inner dimension of the FP64 product
+constexpr int kSplit = 8;    // split of the inner dimension of the FP64 product M X
+constexpr int kPSplit = 4;   // split of the inner dimension of the preconditioner product
 constexpr int kRowTile = 32;  // rows per CTA of the n x kx products
 
 // out = M X (FP64), split over the inner dimension: part s covers j in [s n / kSplit, (s+1) n / kSplit).
@@ -376,14 +396,64 @@ __global__ void __launch_bounds__(256) k_xtx(const ProbDesc* __restrict__ descs,
   }
 }
 
-// One warp per problem: reduce the partials (fixed order), S = C C^T, H' = C^-1 H C^-T,
-// eig(H') by Jacobi, Q = C^-T Q' (columns sorted by ascending Ritz value).
-// small layout: [0, kx^2) = Q, [kx^2, kx^2 + kx) = theta.
+// Lane-parallel shifted Cholesky S + s I = C C^T in place (lower triangle),
+// s = 1e-15 trace(S): keeps the factor defined when the block is numerically
+// rank deficient (shifted CholeskyQR).  kx <= 32, lane i owns row i.
+__device__ inline void warp_chol_shifted(double (*S)[kMaxL + 1], int kx) {
+  const int lane = threadIdx.x & 31;
+  double trS = 0.0;
+  for (int j = 0; j < kx; ++j) trS += S[j][j];
+  __syncwarp();
+  if (lane < kx) S[lane][lane] += 1e-15 * trS;
+  __syncwarp();
+  for (int j = 0; j < kx; ++j) {
+    double v = S[j][j];
+    v = v > 0.0 ? sqrt(v) : 1e-300;
+    const double rv = 1.0 / v;
+    __syncwarp();
+    if (lane == j) S[j][j] = v;
+    if (lane > j && lane < kx) S[lane][j] *= rv;
+    __syncwarp();
+    if (lane > j && lane < kx) {
+      const double lij = S[lane][j];
+      for (int c = j + 1; c <= lane; ++c) S[lane][c] -= lij * S[c][j];
+    }
+    __syncwarp();
+  }
+  for (int e = lane; e < kx * kx; e += 32)
+    if (e / kx < e % kx) S[e / kx][e % kx] = 0.0;
+  __syncwarp();
+}
+
+// One warp per problem.  Reduce the partials (fixed order) into S = X^T X and
+// H = X^T M X, factor S + s I = C C^T (shifted CholeskyQR), and write
+// small = [Q | H' | theta] with X Q orthonormal and H' = Q^T H Q.
+// Intermediate steps (FINAL = false) stop there (Q = C^-T): the block
+// iteration X <- X - T (M X - X H') only needs the subspace to converge, and
+// any basis of it gives the same fixed point.  With the FP32 factor they run
+// in FP32, enough for an orthonormalisation that the next step repeats.
+// The final step (FINAL = true) also diagonalises H' (FP32 Jacobi + FP64
+// polish): Q = C^-T Q', H' = diag(theta), columns by ascending Ritz value.
+constexpr int kLs = kMaxL + 1;
+constexpr size_t kRRSmem = sizeof(double) * 4 * kMaxL * kLs + sizeof(float) * 4 * kMaxL * kLs;
+
+template <bool FINAL, typename CT>
 __global__ void __launch_bounds__(32) k_rayleigh_ritz(const ProbDesc* __restrict__ descs, int nprob,
                                                      const double* __restrict__ part_base,
                                                      const int64_t* __restrict__ part_off) {
-  __shared__ double S[kMaxL][kMaxL + 1], H[kMaxL][kMaxL + 1], Vq[kMaxL][kMaxL + 1], T[kMaxL][kMaxL + 1];
-  __shared__ JacobiScratch js;
+  extern __shared__ __align__(16) unsigned char rr_smem[];
+  typedef double DRow[kLs];
+  typedef float FRow[kLs];
+  DRow* S = reinterpret_cast<DRow*>(rr_smem);
+  DRow* H = S + kMaxL;
+  DRow* Vq = H + kMaxL;
+  DRow* T = Vq + kMaxL;
+  FRow* Sf = reinterpret_cast<FRow*>(T + kMaxL);
+  FRow* Vf = Sf + kMaxL;
+  FRow* Sj = Vf + kMaxL;
+  FRow* Vj = Sj + kMaxL;
+  __shared__ JacobiScratchT<float> jsf;
+  __shared__ JacobiScratchT<double> jsd;
   __shared__ int order[kMaxL];
   const int p = blockIdx.x;
   if (p >= nprob) return;
@@ -401,64 +471,112 @@ __global__ void __launch_bounds__(32) k_rayleigh_ritz(const ProbDesc* __restrict
     H[e / kx][e % kx] = h;
   }
   __syncwarp();
-  // symmetrise H (X^T M X is symmetric up to rounding)
-  for (int e = lane; e < kx * kx; e += 32) {
-    const int a = e / kx, b = e % kx;
-    if (a < b) {
-      const double v = 0.5 * (H[a][b] + H[b][a]);
-      H[a][b] = v;
-      H[b][a] = v;
+  double* out = d.small;
+  if (!FINAL) {
+    // (1) shifted Cholesky of S in precision CT (lane i owns row i); CT is the
+    // precision of the preconditioner's factor: FP64 when a step may amplify
+    // the wanted directions by ~1/tau ~ 1e11, FP32 otherwise
+    CT (*Sc)[kLs];
+    CT (*Vc)[kLs];
+    if constexpr (sizeof(CT) == 8) {
+      Sc = S;
+      Vc = Vq;
+    } else {
+      Sc = Sf;
+      Vc = Vf;
     }
-  }
-  __syncwarp();
-  // Cholesky of S + s I (lane 0; kx <= 32).  The tiny shift s = 1e-15 trace(S)
-  // keeps the factorisation defined when the block is numerically rank
-  // deficient (shifted CholeskyQR); a second pass restores orthonormality.
-  if (lane == 0) {
-    double trS = 0.0;
-    for (int j = 0; j < kx; ++j) trS += S[j][j];
-    const double shift = 1e-15 * trS;
-    for (int j = 0; j < kx; ++j) S[j][j] += shift;
+    CT trS = 0;
+    for (int j = 0; j < kx; ++j) trS += (CT)S[j][j];
+    if constexpr (sizeof(CT) != 8)
+      for (int e = lane; e < kx * kx; e += 32) Sc[e / kx][e % kx] = (CT)S[e / kx][e % kx];
+    __syncwarp();
+    if (lane < kx) Sc[lane][lane] += (CT)(sizeof(CT) == 8 ? 1e-15 : 1e-6) * trS;
+    __syncwarp();
     for (int j = 0; j < kx; ++j) {
-      double v = S[j][j];
-      for (int t = 0; t < j; ++t) v -= S[j][t] * S[j][t];
-      v = v > 0.0 ? sqrt(v) : 1e-300;
-      S[j][j] = v;
-      for (int i = j + 1; i < kx; ++i) {
-        double w = S[i][j];
-        for (int t = 0; t < j; ++t) w -= S[i][t] * S[j][t];
-        S[i][j] = w / v;
+      CT v = Sc[j][j];
+      v = v > (CT)0 ? sqrt(v) : (CT)1e-30;
+      const CT rv = (CT)1 / v;
+      __syncwarp();
+      if (lane == j) Sc[j][j] = v;
+      if (lane > j && lane < kx) Sc[lane][j] *= rv;
+      __syncwarp();
+      if (lane > j && lane < kx) {
+        const CT lij = Sc[lane][j];
+        for (int c = j + 1; c <= lane; ++c) Sc[lane][c] -= lij * Sc[c][j];
       }
-      for (int i = 0; i < j; ++i) S[i][j] = 0.0;
+      __syncwarp();
     }
+    // (2) Q1 = C^-T (upper triangular): column c solves C^T q = e_c
+    for (int c = lane; c < kx; c += 32)
+      for (int i = kx - 1; i >= 0; --i) {
+        CT v = (i == c) ? (CT)1 : (CT)0;
+        for (int t = i + 1; t < kx; ++t) v -= Sc[t][i] * Vc[t][c];
+        Vc[i][c] = (i > c) ? (CT)0 : v / Sc[i][i];
+      }
+    __syncwarp();
+    // (3) H1 = Q1^T H Q1 in FP64 (into S, free now)
+    for (int e = lane; e < kx * kx; e += 32) {
+      const int a = e / kx, b = e % kx;
+      double s = 0.0;
+      for (int t = 0; t < kx; ++t) s = fma(H[a][t], (double)Vc[t][b], s);
+      T[a][b] = s;
+    }
+    __syncwarp();
+    for (int e = lane; e < kx * kx; e += 32) {
+      const int a = e / kx, b = e % kx;
+      double s = 0.0;
+      for (int t = 0; t < kx; ++t) s = fma((double)Vc[t][a], T[t][b], s);
+      Sj[a][b] = (float)s;
+      S[a][b] = s;
+    }
+    __syncwarp();
+    // (4) Ritz rotation from FP32 Jacobi of H1; Q = Q1 Q2 and H_out = Q2^T H1 Q2 in FP64,
+    // so that R = M X Q - X Q H_out is exact for the basis actually used
+    const double fro = warp_frobenius(&S[0][0], kx, kLs);
+    warp_jacobi<float>(&Sj[0][0], &Vj[0][0], kx, kLs, jsf, (float)(4.0 * FLT_EPSILON * fro));
+    for (int e = lane; e < kx * kx; e += 32) {
+      const int a = e / kx, b = e % kx;
+      double q = 0.0, h = 0.0;
+      for (int t = 0; t < kx; ++t) {
+        q = fma((double)Vc[a][t], (double)Vj[t][b], q);
+        h = fma(S[a][t], (double)Vj[t][b], h);
+      }
+      T[a][b] = q;
+      H[a][b] = h;
+    }
+    __syncwarp();
+    for (int e = lane; e < kx * kx; e += 32) {
+      const int a = e / kx, b = e % kx;
+      double s = 0.0;
+      for (int t = 0; t < kx; ++t) s = fma((double)Vj[t][a], H[t][b], s);
+      out[e] = T[a][b];
+      out[kx * kx + e] = s;
+    }
+    return;
   }
-  __syncwarp();
+  warp_chol_shifted(S, kx);
   // T = C^-1 H  (forward substitution, one column per lane)
   for (int c = lane; c < kx; c += 32)
     for (int i = 0; i < kx; ++i) {
-      double v = H[i][c];
+      double v = 0.5 * (H[i][c] + H[c][i]);
       for (int t = 0; t < i; ++t) v -= S[i][t] * T[t][c];
       T[i][c] = v / S[i][i];
     }
   __syncwarp();
-  // H' = T C^-T = (C^-1 T^T)^T : solve C Z = T^T column by column, H'[a][b] = Z[b][a]
+  // H' = T C^-T: row c of H' solves C z = (row c of T)
   for (int c = lane; c < kx; c += 32)
     for (int i = 0; i < kx; ++i) {
       double v = T[c][i];
-      for (int t = 0; t < i; ++t) v -= S[i][t] * H[c][t];
-      H[c][i] = v / S[i][i];
+      for (int t = 0; t < i; ++t) v -= S[i][t] * Vq[c][t];
+      Vq[c][i] = v / S[i][i];
     }
   __syncwarp();
   for (int e = lane; e < kx * kx; e += 32) {
     const int a = e / kx, b = e % kx;
-    if (a < b) {
-      const double v = 0.5 * (H[a][b] + H[b][a]);
-      H[a][b] = v;
-      H[b][a] = v;
-    }
+    H[a][b] = 0.5 * (Vq[a][b] + Vq[b][a]);
   }
   __syncwarp();
-  warp_jacobi(&H[0][0], &Vq[0][0], kx, kMaxL + 1, js);
+  warp_eig_mixed(&H[0][0], &Vq[0][0], &Sf[0][0], &Vf[0][0], &T[0][0], kx, kLs, jsf, jsd);
   if (lane == 0) {  // ascending order of the Ritz values
     for (int i = 0; i < kx; ++i) order[i] = i;
     for (int a = 1; a < kx; ++a) {
@@ -473,7 +591,6 @@ __global__ void __launch_bounds__(32) k_rayleigh_ritz(const ProbDesc* __restrict
   }
   __syncwarp();
   // Q = C^-T Q'  (back substitution, one column per lane)
-  double* Q = d.small;
   for (int c = lane; c < kx; c += 32) {
     const int oc = order[c];
     for (int i = kx - 1; i >= 0; --i) {
@@ -483,77 +600,108 @@ __global__ void __launch_bounds__(32) k_rayleigh_ritz(const ProbDesc* __restrict
     }
   }
   __syncwarp();
-  for (int e = lane; e < kx * kx; e += 32) Q[e] = T[e / kx][e % kx];
-  for (int c = lane; c < kx; c += 32) Q[kx * kx + c] = H[order[c]][order[c]];
+  for (int e = lane; e < kx * kx; e += 32) {
+    const int a = e / kx, b = e % kx;
+    out[e] = T[a][b];
+    out[kx * kx + e] = (a == b) ? H[order[a]][order[a]] : 0.0;
+  }
+  for (int c = lane; c < kx; c += 32) out[2 * kx * kx + c] = H[order[c]][order[c]];
 }
 
-// X <- X Q, MX <- MX Q, R = MX - X diag(theta); one thread per row.
+// X <- X Q, MX <- MX Q, R = MX - X H'; one thread per row.
 __global__ void __launch_bounds__(128) k_rotate(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                int nprob) {
-  __shared__ double q[kMaxL * kMaxL + kMaxL];
+  __shared__ double q[2 * kMaxL * kMaxL];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
   const int kx = d.kx;
-  for (int e = threadIdx.x; e < kx * kx + kx; e += 128) q[e] = d.small[e];
+  for (int e = threadIdx.x; e < 2 * kx * kx; e += 128) q[e] = d.small[e];
   __syncthreads();
   const int64_t i = (blockIdx.x - off[p]) * 128 + threadIdx.x;
   if (i >= d.n) return;
-  double x[kMaxL], mx[kMaxL];
+  double x[kMaxL], mx[kMaxL], nx[kMaxL], nmx[kMaxL];
   for (int c = 0; c < kx; ++c) {
     x[c] = d.X[i * kx + c];
     mx[c] = d.MX[i * kx + c];
   }
+  const double* H = q + kx * kx;
   for (int c = 0; c < kx; ++c) {
     double a = 0.0, b = 0.0;
     for (int t = 0; t < kx; ++t) {
       a = fma(x[t], q[t * kx + c], a);
       b = fma(mx[t], q[t * kx + c], b);
     }
+    nx[c] = a;
+    nmx[c] = b;
     d.X[i * kx + c] = a;
     d.MX[i * kx + c] = b;
-    d.R[i * kx + c] = b - q[kx * kx + c] * a;
+  }
+  for (int c = 0; c < kx; ++c) {
+    double s = nmx[c];
+    for (int t = 0; t < kx; ++t) s = fma(-nx[t], H[t * kx + c], s);
+    d.R[i * kx + c] = s;
   }
 }
 
-// X <- X - A^-1 R with A^-1 at precision T (the preconditioner).
+// X <- X - A^-1 R with A^-1 at precision T (the preconditioner).  Split over the
+// inner dimension: CTA (row tile of 16, part s) writes its partial product to
+// R slot 1 + s; k_precond_apply sums the parts in a fixed order.
+constexpr int kPRows = 16;
 template <typename T>
 __global__ void __launch_bounds__(256) k_precond(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                 int nprob) {
-  __shared__ T ts[kRowTile][33];
-  __shared__ T rs[32][kMaxL + 1];
+  __shared__ T ts[kPRows][65];
+  __shared__ T rs[64][kMaxL + 1];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
   const int64_t n = d.n, np = npad_of(d);
   const int kx = d.kx;
-  const int64_t i0 = (blockIdx.x - off[p]) * kRowTile;
-  const int tr = threadIdx.x % kRowTile, tc = threadIdx.x / kRowTile;
-  T acc[4] = {(T)0, (T)0, (T)0, (T)0};
-  for (int64_t j0 = 0; j0 < n; j0 += 32) {
+  const int64_t local = blockIdx.x - off[p];
+  const int64_t ntile = (n + kPRows - 1) / kPRows;
+  const int split = (int)(local / ntile);
+  const int64_t i0 = (local % ntile) * kPRows;
+  const int64_t j_begin = split * n / kPSplit, j_end = (split + 1) * n / kPSplit;
+  const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
+  T acc[2] = {(T)0, (T)0};
+  for (int64_t j0 = j_begin; j0 < j_end; j0 += 64) {
     __syncthreads();
-    for (int e = threadIdx.x; e < kRowTile * 32; e += 256) {
-      const int r = e / 32, c = e % 32;
+    for (int e = threadIdx.x; e < kPRows * 64; e += 256) {
+      const int r = e / 64, c = e % 64;
       const int64_t i = i0 + r, j = j0 + c;
-      ts[r][c] = (i < n && j < n) ? F1of<T>(d)[i * np + j] : (T)0;
+      ts[r][c] = (i < n && j < j_end) ? F1of<T>(d)[i * np + j] : (T)0;
     }
-    for (int e = threadIdx.x; e < 32 * kx; e += 256) {
+    for (int e = threadIdx.x; e < 64 * kx; e += 256) {
       const int r = e / kx, c = e % kx;
       const int64_t j = j0 + r;
-      rs[r][c] = (j < n) ? (T)d.R[j * kx + c] : (T)0;
+      rs[r][c] = (j < j_end) ? (T)d.R[j * kx + c] : (T)0;
     }
     __syncthreads();
-    for (int u = 0; u < 32; ++u) {
+#pragma unroll 8
+    for (int u = 0; u < 64; ++u) {
       const T tv = ts[tr][u];
-#pragma unroll
-      for (int s = 0; s < 4; ++s) acc[s] = fma(tv, rs[u][tc + 8 * s < kx ? tc + 8 * s : 0], acc[s]);
+      acc[0] = fma(tv, rs[u][tc], acc[0]);
+      acc[1] = fma(tv, rs[u][tc + 16 < kx ? tc + 16 : tc], acc[1]);
     }
   }
   const int64_t i = i0 + tr;
-  if (i < n)
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const int c = tc + 8 * s;
-      if (c < kx) d.X[i * kx + c] -= (double)acc[s];
-    }
+  double* part = d.R + (int64_t)(1 + split) * n * kx;
+  if (i < n) {
+    if (tc < kx) part[i * kx + tc] = (double)acc[0];
+    if (tc + 16 < kx) part[i * kx + tc + 16] = (double)acc[1];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_precond_apply(const ProbDesc* __restrict__ descs,
+                                                      const int64_t* __restrict__ off, int nprob) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= off[nprob]) return;
+  const int p = find_problem(off, nprob, g);
+  const ProbDesc& d = descs[p];
+  const int64_t e = g - off[p];
+  const int64_t nk = d.n * d.kx;
+  double s = 0.0;
+  for (int q = 0; q < kPSplit; ++q) s += d.R[(int64_t)(1 + q) * nk + e];
+  d.X[e] -= s;
 }
 
 // V = first r columns of X (n x r column-major, ldv); eigenvalue estimates; residual norm.
@@ -585,7 +733,7 @@ __global__ void __launch_bounds__(256) k_eig_finish(const ProbDesc* __restrict__
     if (threadIdx.x == 0) mx = fmax(mx, sqrt(red[0]));
     __syncthreads();
   }
-  if (threadIdx.x < kx && threadIdx.x < 32) d.stats[threadIdx.x] = d.small[kx * kx + threadIdx.x];
+  if (threadIdx.x < kx && threadIdx.x < 32) d.stats[threadIdx.x] = d.small[2 * kx * kx + threadIdx.x];
   if (threadIdx.x == 0) d.stats[34] = mx;
 }
 
@@ -602,6 +750,10 @@ __global__ void __launch_bounds__(256) k_eig_finish(const ProbDesc* __restrict__
 
 template <typename T>
 static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, cudaStream_t s) {
+  cudaError_t ea = cudaFuncSetAttribute(k_rayleigh_ritz<true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRRSmem);
+  if (ea == cudaSuccess)
+    ea = cudaFuncSetAttribute(k_rayleigh_ritz<false, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRRSmem);
+  if (ea != cudaSuccess) return ea;
   const ProbDesc* D = P.descs;
   const int np = P.nprob;
   auto dev = [&](size_t pos) { return P.dT + pos; };
@@ -609,30 +761,42 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
   RSM_LAUNCH(k_eig_prep<T>, (total(P.pad2) + 255) / 256, 256, D, dev(P.pad2), np, shift_rel);
   for (int k = 0; k < P.max_nblk; ++k) {
     const size_t o1 = P.step + (size_t)k * 3 * (np + 1), o2 = o1 + (np + 1), o3 = o2 + (np + 1);
-    RSM_LAUNCH(k_potrf<T>, total(o1), 256, D, dev(o1), np, k);
+    RSM_LAUNCH(k_potrf<T>, total(o1), 1024, D, dev(o1), np, k);
     RSM_LAUNCH(k_panel<T>, total(o2), 256, D, dev(o2), np, k);
     RSM_LAUNCH(k_trail<T>, total(o3), 256, D, dev(o3), np, k);
   }
-  RSM_LAUNCH(k_linv_diag<T>, total(P.blk), 256, D, dev(P.blk), np);
-  for (int i = 1; i < P.max_nblk; ++i) {
-    const size_t o = P.linv + (size_t)i * (np + 1);
-    RSM_LAUNCH(k_linv_step<T>, total(o), 256, D, dev(o), np, i);
+  RSM_LAUNCH(k_linv_init<T>, total(P.tri), 256, D, dev(P.tri), np);
+  for (int k = 0; k < P.max_nblk; ++k) {
+    const size_t o1 = P.linv + (size_t)k * 2 * (np + 1), o2 = o1 + (np + 1);
+    RSM_LAUNCH(k_linv_scale<T>, total(o1), 256, D, dev(o1), np, k);
+    RSM_LAUNCH(k_linv_update<T>, total(o2), 256, D, dev(o2), np, k);
   }
   RSM_LAUNCH(k_ainv<T>, total(P.tri), 256, D, dev(P.tri), np);
   RSM_LAUNCH(k_init_X, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
   // The FP64 factor is an almost exact shift-invert: a step can amplify the
   // wanted directions by ~1/tau, so each step runs the Rayleigh-Ritz pass twice
-  // (the first re-orthonormalises a nearly rank-deficient block).
+  // (the first re-orthonormalises a nearly rank-deficient block).  The last two
+  // steps and the closing pass diagonalise in FP64 (polished); the others in FP32.
   const int passes = sizeof(T) == 8 ? 2 : 1;
   for (int it = 0; it <= iters; ++it) {
+    const bool final_rr = it >= iters - 1;
     RSM_LAUNCH(k_gemm_MX, total(P.mx), 256, D, dev(P.mx), np);
     RSM_LAUNCH(k_split_sum, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
     for (int pass = 0; pass < passes; ++pass) {
       RSM_LAUNCH(k_xtx, total(P.chunk), 256, D, dev(P.chunk), np, P.part, dev(P.part_off));
-      RSM_LAUNCH(k_rayleigh_ritz, np, 32, D, np, P.part, dev(P.part_off));
+      if (final_rr && pass == passes - 1) {
+        k_rayleigh_ritz<true, T><<<np, 32, kRRSmem, s>>>(D, np, P.part, dev(P.part_off));
+      } else {
+        k_rayleigh_ritz<false, T><<<np, 32, kRRSmem, s>>>(D, np, P.part, dev(P.part_off));
+      }
+      ++g_kernel_launches;
+      if (cudaGetLastError() != cudaSuccess) return cudaErrorLaunchFailure;
       RSM_LAUNCH(k_rotate, total(P.rot), 128, D, dev(P.rot), np);
     }
-    if (it < iters) RSM_LAUNCH(k_precond<T>, total(P.row_tile), 256, D, dev(P.row_tile), np);
+    if (it < iters) {
+      RSM_LAUNCH(k_precond<T>, total(P.row_tile), 256, D, dev(P.row_tile), np);
+      RSM_LAUNCH(k_precond_apply, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
+    }
   }
   RSM_LAUNCH(k_eig_finish, np, 256, D, np);
   return cudaSuccess;

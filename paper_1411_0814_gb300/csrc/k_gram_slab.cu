@@ -1,0 +1,210 @@
+// Stages a3 + a4 with an L2-resident row-slab schedule.
+//
+// Same result as k_select_gram (per trial: the rows known in all chosen
+// columns, and the Gram A_t^T A_t of the submatrix), organised for the memory
+// system: Y is swept in row slabs small enough to stay in L2 (32 MiB of Y per
+// slab), and one launch serves a slab to every trial.  The first trial that
+// touches a sector of the slab brings it from HBM; the ~l/n share of all other
+// trials that draw the same column then read it from L2.  HBM traffic drops
+// from ~32 B per selected element (one sector each) to about one read of Y.
+//
+// One warp per (trial, slab): lanes AND the l packed mask words of 32
+// consecutive 32-row groups, selected rows go to a per-warp ring buffer, and
+// every full batch of 32 rows is gathered (lane = row) and multiplied into
+// register accumulators of the l(l+1)/2 products.  At the end of the slab the
+// warp reduces its accumulators through shared memory (fixed order) and adds
+// them to the trial's FP64 Gram; slab 0 writes, later slabs add, one launch per
+// slab, so the sum over slabs is in a fixed order too.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rsm {
+
+constexpr int kSlabWarps = 4;
+constexpr int kRing = 1088;  // pending rows per warp: < 32 + 32 * 32
+
+template <int MODE>
+struct SlabT;
+template <>
+struct SlabT<0> {  // FP64
+  using acc_t = double;
+  using val_t = double;
+  __device__ static val_t load(const ProbDesc& d, int64_t idx) {
+    return d.y_dtype == 0 ? __ldg(static_cast<const double*>(d.Y) + idx)
+                          : (double)__ldg(static_cast<const float*>(d.Y) + idx);
+  }
+};
+template <>
+struct SlabT<2> {  // FP32
+  using acc_t = float;
+  using val_t = float;
+  __device__ static val_t load(const ProbDesc& d, int64_t idx) {
+    return d.y_dtype == 1 ? __ldg(static_cast<const float*>(d.Y) + idx)
+                          : __double2float_rn(__ldg(static_cast<const double*>(d.Y) + idx));
+  }
+};
+
+template <int MODE, int L>
+__global__ void __launch_bounds__(32 * kSlabWarps) k_gram_slab(const ProbDesc* __restrict__ descs,
+                                                               const int64_t* __restrict__ task_off, int nprob,
+                                                               int slab, int64_t slab_rows) {
+  using Tr = SlabT<MODE>;
+  using A = typename Tr::acc_t;
+  using V = typename Tr::val_t;
+  constexpr int P = L * (L + 1) / 2;
+  constexpr int kRedWords = (P * 33 * sizeof(A) + 3) / 4;
+  constexpr int kWarpWords = kRedWords > kRing ? kRedWords : kRing;
+  extern __shared__ __align__(16) int slab_smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int* ring = slab_smem + wid * kWarpWords;
+  A* red = reinterpret_cast<A*>(ring);
+
+  const int64_t g = (int64_t)blockIdx.x * kSlabWarps + wid;
+  if (g >= task_off[nprob]) return;
+  const int p = find_problem(task_off, nprob, g);
+  const ProbDesc& d = descs[p];
+  const int64_t t = g - task_off[p];
+  int64_t cidx[L];
+#pragma unroll
+  for (int k = 0; k < L; ++k) cidx[k] = (int64_t)__ldg(d.cols + t * L + k);
+  const int64_t r0 = (int64_t)slab * slab_rows;
+  const int64_t r1 = r0 + slab_rows < d.m ? r0 + slab_rows : d.m;
+  const int64_t w_begin = r0 >> 5, w_end = (r1 + 31) >> 5;
+
+  A acc[P];
+#pragma unroll
+  for (int q = 0; q < P; ++q) acc[q] = (A)0;
+  int pending = 0, count = 0;
+
+  auto consume = [&](int k) {  // gather row ring[k] and add its outer product
+    const int64_t row = ring[k];
+    V v[L];
+#pragma unroll
+    for (int a = 0; a < L; ++a) v[a] = Tr::load(d, row + cidx[a] * d.ldy);
+#pragma unroll
+    for (int a = 0; a < L; ++a)
+#pragma unroll
+      for (int b = a; b < L; ++b) {
+        const int q = a * L - a * (a - 1) / 2 + (b - a);
+        acc[q] = fma(v[a], v[b], acc[q]);
+      }
+  };
+
+  for (int64_t w0 = w_begin; w0 < w_end; w0 += 32) {
+    const int64_t w = w0 + lane;
+    uint32_t mask = 0;
+    if (w < w_end) {
+      mask = 0xffffffffu;
+#pragma unroll
+      for (int k = 0; k < L; ++k) mask &= __ldg(d.bits + cidx[k] * d.ldb + w);
+    }
+    const int cnt = __popc(mask);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int pos = pending + incl - cnt;
+    while (mask) {
+      const int b = __ffs(mask) - 1;
+      mask &= mask - 1;
+      ring[pos++] = (int)(w * 32 + b);
+    }
+    __syncwarp();
+    pending += total;
+    count += total;
+    int done = 0;
+    while (pending - done >= 32) {
+      consume(done + lane);
+      done += 32;
+    }
+    __syncwarp();
+    if (done) {  // move the remainder (< 32 rows) to the front
+      const int rest = pending - done;
+      const int keep = lane < rest ? ring[done + lane] : 0;
+      __syncwarp();
+      if (lane < rest) ring[lane] = keep;
+      __syncwarp();
+      pending = rest;
+    }
+  }
+  if (lane < pending) consume(lane);
+  __syncwarp();
+
+  // reduce the 32 lanes' accumulators through shared memory, lane q sums entry q
+#pragma unroll
+  for (int q = 0; q < P; ++q) red[q * 33 + lane] = acc[q];
+  __syncwarp();
+  double* G = d.gram + t * P;
+  for (int q = lane; q < P; q += 32) {
+    A s = (A)0;
+    for (int k = 0; k < 32; ++k) s += red[q * 33 + k];
+    G[q] = (slab == 0 ? 0.0 : G[q]) + (double)s;
+  }
+  if (lane == 0) {
+    const int32_t c0 = slab == 0 ? 0 : d.row_counts[t];
+    const int32_t c = c0 + count;
+    d.row_counts[t] = c;
+    if (d.debug_row_counts) d.debug_row_counts[t] = c;
+    if (count) atomicAdd(&d.counters[5], (unsigned long long)count);
+  }
+}
+
+template <int MODE, int L>
+static size_t slab_smem_bytes() {
+  using A = typename SlabT<MODE>::acc_t;
+  constexpr int P = L * (L + 1) / 2;
+  constexpr int kRedWords = (P * 33 * sizeof(A) + 3) / 4;
+  constexpr int kWarpWords = kRedWords > kRing ? kRedWords : kRing;
+  return (size_t)kSlabWarps * kWarpWords * 4;
+}
+
+template <int MODE, int L>
+static cudaError_t launch_slab_l(const SlabPlan& S, cudaStream_t s) {
+  const size_t smem = slab_smem_bytes<MODE, L>();
+  cudaError_t e = cudaFuncSetAttribute(k_gram_slab<MODE, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  for (int sl = 0; sl < S.nslab; ++sl) {
+    const int64_t tasks = S.hT[S.task_pos + (size_t)sl * (S.nprob + 1) + S.nprob];
+    if (tasks <= 0) continue;
+    k_gram_slab<MODE, L><<<(unsigned)((tasks + kSlabWarps - 1) / kSlabWarps), 32 * kSlabWarps, smem, s>>>(
+        S.descs, S.dT + S.task_pos + (size_t)sl * (S.nprob + 1), S.nprob, sl, S.slab_rows);
+    ++g_kernel_launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+bool slab_supported(int mode, int l) {
+  if (mode == 2) return l >= 2 && l <= 17;
+  if (mode == 0) return l >= 2 && l <= 12;
+  return false;
+}
+
+cudaError_t launch_gram_slab(int mode, int l, const SlabPlan& S, cudaStream_t s) {
+#define RSM_SLAB_CASE(M, LL) \
+  case LL:                   \
+    return launch_slab_l<M, LL>(S, s);
+  if (mode == 2) {
+    switch (l) {
+      RSM_SLAB_CASE(2, 2) RSM_SLAB_CASE(2, 3) RSM_SLAB_CASE(2, 4) RSM_SLAB_CASE(2, 5) RSM_SLAB_CASE(2, 6)
+      RSM_SLAB_CASE(2, 7) RSM_SLAB_CASE(2, 8) RSM_SLAB_CASE(2, 9) RSM_SLAB_CASE(2, 10) RSM_SLAB_CASE(2, 11)
+      RSM_SLAB_CASE(2, 12) RSM_SLAB_CASE(2, 13) RSM_SLAB_CASE(2, 14) RSM_SLAB_CASE(2, 15) RSM_SLAB_CASE(2, 16)
+      RSM_SLAB_CASE(2, 17)
+      default: break;
+    }
+  } else if (mode == 0) {
+    switch (l) {
+      RSM_SLAB_CASE(0, 2) RSM_SLAB_CASE(0, 3) RSM_SLAB_CASE(0, 4) RSM_SLAB_CASE(0, 5) RSM_SLAB_CASE(0, 6)
+      RSM_SLAB_CASE(0, 7) RSM_SLAB_CASE(0, 8) RSM_SLAB_CASE(0, 9) RSM_SLAB_CASE(0, 10) RSM_SLAB_CASE(0, 11)
+      RSM_SLAB_CASE(0, 12)
+      default: break;
+    }
+  }
+#undef RSM_SLAB_CASE
+  return cudaErrorNotSupported;
+}
+
+}  // namespace rsm

@@ -3,8 +3,8 @@
 //
 // a5: the right singular vectors of A_t for its l - r smallest singular values
 // (Section III) are the eigenvectors of G_t = A_t^T A_t for its smallest
-// eigenvalues.  One warp per trial runs the cyclic two-sided Jacobi method in
-// FP64 (jacobi.cuh).
+// eigenvalues.  One warp per trial: FP32 Jacobi (jacobi.cuh) for the eigenbasis,
+// then FP64 Newton refinement of the minor subspace (see k_minor_scatter).
 //
 // a6: M = Xi Xi^T = sum_t sum_j xi xi^T with xi = e(zeta) (eq. get_xi, eq. XI).
 // Trial t adds the projector Z_t Z_t^T (l x l) to M[C_t, C_t].  Contributions
@@ -20,11 +20,90 @@
 namespace rsm {
 
 constexpr int kMinorWarps = 4;
+constexpr int kNewtonSteps = 4;
 
+// Shared memory per warp (row stride ls = lmax + 1): G (FP64), the FP32 copy
+// and FP32 eigenvectors, Z and a second FP64 work matrix, three FP64 vectors.
+__host__ __device__ inline size_t minor_smem_per_warp(int lmax) {
+  const int ls = lmax + 1;
+  return sizeof(double) * (size_t)lmax * ls + 2 * sizeof(float) * (size_t)lmax * ls +
+         sizeof(double) * (2 * (size_t)lmax * ls + 3 * (size_t)ls);
+}
+
+// Newton refinement of the n_minor columns of Z (l x n_minor, FP64) against the
+// complement eigenvectors of the FP32 basis Qf (eigenvalues on Sf's diagonal).
+__device__ inline void newton_refine(const double* Gs, const float* Sf, const float* Qf, double* Z, double* rv,
+                                     double* cv, int l, int nm, int ls, const int* is_minor, double fro) {
+  const int lane = threadIdx.x & 31;
+  for (int step = 0; step < kNewtonSteps; ++step) {
+    for (int j = 0; j < nm; ++j) {
+      double gz = 0.0, za = 0.0;
+      if (lane < l) {
+        za = Z[lane * nm + j];
+        for (int b = 0; b < l; ++b) gz = fma(Gs[lane * ls + b], Z[b * nm + j], gz);
+      }
+      double th = za * gz;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) th += __shfl_xor_sync(0xffffffffu, th, o);
+      if (lane < l) rv[lane] = gz - th * za;
+      __syncwarp();
+      // block form: drop the part of r inside span(Z); only the part that leaves
+      // the current minor subspace is corrected against the complement
+      for (int k = 0; k < nm; ++k) {
+        double zr = lane < l ? Z[lane * nm + k] * rv[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) zr += __shfl_xor_sync(0xffffffffu, zr, o);
+        if (lane < l) rv[lane] -= zr * Z[lane * nm + k];
+        __syncwarp();
+      }
+      if (lane < l) {
+        double c = 0.0;
+        if (!is_minor[lane]) {
+          double qr = 0.0;
+          for (int a = 0; a < l; ++a) qr = fma((double)Qf[a * ls + lane], rv[a], qr);
+          c = qr / ((double)Sf[lane * ls + lane] - th);
+        }
+        cv[lane] = c;
+      }
+      __syncwarp();
+      if (lane < l) {
+        double zn = Z[lane * nm + j];
+        for (int i = 0; i < l; ++i) zn = fma(-cv[i], (double)Qf[lane * ls + i], zn);
+        Z[lane * nm + j] = zn;
+      }
+      __syncwarp();
+    }
+    for (int j = 0; j < nm; ++j) {  // Gram-Schmidt (twice) in FP64
+      for (int pass = 0; pass < 2; ++pass)
+        for (int k = 0; k < j; ++k) {
+          double pr = lane < l ? Z[lane * nm + k] * Z[lane * nm + j] : 0.0;
+#pragma unroll
+          for (int o = 16; o; o >>= 1) pr += __shfl_xor_sync(0xffffffffu, pr, o);
+          if (lane < l) Z[lane * nm + j] -= pr * Z[lane * nm + k];
+          __syncwarp();
+        }
+      double nn = lane < l ? Z[lane * nm + j] * Z[lane * nm + j] : 0.0;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+      const double inv = 1.0 / sqrt(nn);
+      if (lane < l) Z[lane * nm + j] *= inv;
+      __syncwarp();
+    }
+  }
+}
+
+// a5: the FP32 Jacobi eigenbasis Q of G (accurate to FP32 rounding) separates
+// the n_minor smallest eigenvalues from the rest; the minor subspace is then
+// refined in FP64 by Newton corrections against the complement of Q:
+//   z <- z - sum_{i not minor} q_i (q_i^T r') / (lambda_i - theta),
+//   theta = z^T G z,  r = G z - theta z,  r' = r - Z Z^T r,
+// followed by Gram-Schmidt.  Removing the part of r inside span(Z) (block
+// Newton) keeps the fixed point exact when several minor vectors are kept.  The fixed point is an exact eigenvector of the
+// FP64 Gram whatever the FP32 rounding of Q, and the error squares per step.
 __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDesc* __restrict__ descs,
                                                                    const int64_t* __restrict__ trial_off, int nprob,
                                                                    int lmax) {
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t g = (int64_t)blockIdx.x * kMinorWarps + wid;
   if (g >= trial_off[nprob]) return;
@@ -32,11 +111,20 @@ __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDe
   const ProbDesc& d = descs[p];
   const int64_t t = g - trial_off[p];
   const int l = d.l;
-  const int ls = lmax + 1;  // row stride of the shared matrices
-  double* S = sm + (size_t)wid * 2 * lmax * ls;
-  double* Vm = S + (size_t)lmax * ls;
-  __shared__ JacobiScratch js[kMinorWarps];
+  const int ls = lmax + 1;
+  unsigned char* base = smraw + (size_t)wid * minor_smem_per_warp(lmax);
+  double* Gs = reinterpret_cast<double*>(base);
+  float* Sf = reinterpret_cast<float*>(Gs + (size_t)lmax * ls);
+  float* Qf = Sf + (size_t)lmax * ls;
+  double* Z = reinterpret_cast<double*>(Qf + (size_t)lmax * ls);
+  double* Wd = Z + (size_t)lmax * ls;  // FP64 work matrix of the fallback path
+  double* gv = Wd + (size_t)lmax * ls;
+  double* rv = gv + ls;
+  double* cv = rv + ls;
+  __shared__ JacobiScratchT<float> js[kMinorWarps];
+  __shared__ JacobiScratchT<double> jsd[kMinorWarps];
   __shared__ int pick[kMinorWarps][kMaxL];
+  __shared__ int is_minor[kMinorWarps][kMaxL];
 
   const int count = d.row_counts[t];
   if (count < l) {  // rejected trial (fewer than l rows, i.e. not more than r)
@@ -46,7 +134,7 @@ __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDe
   }
   if (lane == 0) atomicAdd(&d.counters[0], 1ull);
 
-  // load the packed Gram into a full symmetric matrix, V = I
+  // packed Gram -> full symmetric FP64 matrix and its FP32 copy
   const int P = l * (l + 1) / 2;
   const double* G = d.gram + t * P;
   for (int q = lane; q < P; q += 32) {
@@ -57,32 +145,71 @@ __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDe
     }
     const int b = a + rem;
     const double v = G[q];
-    S[a * ls + b] = v;
-    S[b * ls + a] = v;
+    Gs[a * ls + b] = v;
+    Gs[b * ls + a] = v;
+    Sf[a * ls + b] = (float)v;
+    Sf[b * ls + a] = (float)v;
   }
   __syncwarp();
-
-  warp_jacobi(S, Vm, l, ls, js[wid]);
+  const double fro = warp_frobenius(Gs, l, ls);
+  warp_jacobi<float>(Sf, Qf, l, ls, js[wid], (float)(4.0 * FLT_EPSILON * fro));
 
   // the n_minor smallest eigenvalues (ties broken by index)
+  const int nm = d.n_minor;
   if (lane == 0) {
-    int used[kMaxL];
-    for (int i = 0; i < l; ++i) used[i] = 0;
-    for (int j = 0; j < d.n_minor; ++j) {
+    for (int i = 0; i < l; ++i) is_minor[wid][i] = 0;
+    for (int j = 0; j < nm; ++j) {
       int best = -1;
       for (int i = 0; i < l; ++i)
-        if (!used[i] && (best < 0 || S[i * ls + i] < S[best * ls + best])) best = i;
-      used[best] = 1;
+        if (!is_minor[wid][i] && (best < 0 || Sf[i * ls + i] < Sf[best * ls + best])) best = i;
+      is_minor[wid][best] = 1;
       pick[wid][j] = best;
     }
   }
   __syncwarp();
-  const int nm = d.n_minor;
-  if (d.debug_Z)
+  // Newton converges from the FP32 basis when every complement eigenvalue is at
+  // least 1e-4 ||G|| away from the minor ones ((u32 ||G|| / gap)^5 < 1e-16 after
+  // 4 steps).  Otherwise (a nearly degenerate pair across the split) the trial
+  // takes the FP32 Jacobi + FP64 polish path instead.
+  float gap_min = 3.0e38f;
+  if (lane < l && !is_minor[wid][lane])
+    for (int j = 0; j < nm; ++j) gap_min = fminf(gap_min, fabsf(Sf[lane * ls + lane] - Sf[pick[wid][j] * ls + pick[wid][j]]));
+#pragma unroll
+  for (int o = 16; o; o >>= 1) gap_min = fminf(gap_min, __shfl_xor_sync(0xffffffffu, gap_min, o));
+  const bool polish = gap_min < (float)(1e-4 * fro);
+  if (polish) {
+    // eigen-decomposition of the FP64 Gram: eigenvalues on Gs's diagonal, vectors in Z (stride ls)
+    warp_eig_mixed(Gs, Z, Sf, Qf, Wd, l, ls, js[wid], jsd[wid]);
+    if (lane == 0) {
+      for (int i = 0; i < l; ++i) is_minor[wid][i] = 0;
+      for (int j = 0; j < nm; ++j) {
+        int best = -1;
+        for (int i = 0; i < l; ++i)
+          if (!is_minor[wid][i] && (best < 0 || Gs[i * ls + i] < Gs[best * ls + best])) best = i;
+        is_minor[wid][best] = 1;
+        pick[wid][j] = best;
+      }
+    }
+    __syncwarp();
+    // compact the picked columns into Wd as the l x n_minor minor basis
     for (int it = lane; it < l * nm; it += 32) {
       const int a = it / nm, j = it % nm;
-      d.debug_Z[t * l * nm + it] = Vm[a * ls + pick[wid][j]];
+      Wd[a * nm + j] = Z[a * ls + pick[wid][j]];
     }
+    __syncwarp();
+    for (int it = lane; it < l * nm; it += 32) Z[it] = Wd[it];
+    __syncwarp();
+  } else {
+    for (int it = lane; it < l * nm; it += 32) {
+      const int a = it / nm, j = it % nm;
+      Z[a * nm + j] = (double)Qf[a * ls + pick[wid][j]];
+    }
+    __syncwarp();
+    newton_refine(Gs, Sf, Qf, Z, rv, cv, l, nm, ls, is_minor[wid], fro);
+  }
+
+  if (d.debug_Z)
+    for (int it = lane; it < l * nm; it += 32) d.debug_Z[t * l * nm + it] = Z[it];
 
   // scatter Z Z^T into M[C_t, C_t] in fixed point
   const int f = macc_frac_bits(d.counters[2]);
@@ -91,7 +218,7 @@ __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDe
   for (int it = lane; it < l * l; it += 32) {
     const int a = it / l, b = it % l;
     double pr = 0.0;
-    for (int j = 0; j < nm; ++j) pr = fma(Vm[a * ls + pick[wid][j]], Vm[b * ls + pick[wid][j]], pr);
+    for (int j = 0; j < nm; ++j) pr = fma(Z[a * nm + j], Z[b * nm + j], pr);
     const long long v = llrint(pr * scale);
     if (v) atomicAdd(&d.macc[(int64_t)C[a] * d.n + C[b]], (unsigned long long)v);
   }
@@ -115,7 +242,7 @@ __global__ void __launch_bounds__(256) k_finalize_M(const ProbDesc* __restrict__
 cudaError_t launch_minor_scatter(const ProbDesc* descs, const int64_t* trial_off, int nprob, int64_t total, int lmax,
                                  cudaStream_t s) {
   if (total <= 0) return cudaSuccess;
-  const size_t dyn = sizeof(double) * (size_t)kMinorWarps * 2 * lmax * (lmax + 1);
+  const size_t dyn = kMinorWarps * minor_smem_per_warp(lmax) + 16;
   cudaError_t e = cudaFuncSetAttribute(k_minor_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   if (e != cudaSuccess) return e;
   k_minor_scatter<<<(unsigned)((total + kMinorWarps - 1) / kMinorWarps), 32 * kMinorWarps, dyn, s>>>(descs, trial_off,

@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(32 * kPinvWarps) k_row_pinv(const ProbDesc* __
                                                              const unsigned long long* __restrict__ fail_count) {
   __shared__ double S[kPinvWarps][kMaxR][kMaxR + 1], Q[kPinvWarps][kMaxR][kMaxR + 1];
   __shared__ JacobiScratch js[kPinvWarps];
+  const double tol_scale = 4.0 * DBL_EPSILON;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned long long total = *fail_count;
   for (unsigned long long f = (unsigned long long)blockIdx.x * kPinvWarps + wid; f < total;
@@ -241,7 +242,8 @@ __global__ void __launch_bounds__(32 * kPinvWarps) k_row_pinv(const ProbDesc* __
       S[wid][b][a] = row[qq];
     }
     __syncwarp();
-    warp_jacobi(&S[wid][0][0], &Q[wid][0][0], r, kMaxR + 1, js[wid]);
+    const double fro = warp_frobenius(&S[wid][0][0], r, kMaxR + 1);
+    warp_jacobi<double>(&S[wid][0][0], &Q[wid][0][0], r, kMaxR + 1, js[wid], tol_scale * fro);
     double lmax = 0.0;
     for (int k = 0; k < r; ++k) lmax = fmax(lmax, S[wid][k][k]);
     // u_a = sum_k [lambda_k > tol] q_ak (q_k . b) / lambda_k, one output per lane

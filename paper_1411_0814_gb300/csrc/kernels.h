@@ -23,7 +23,7 @@ struct EigPlan {
   int max_nblk;
   const int64_t* dT;
   const int64_t* hT;
-  size_t pad2, step, blk, linv, tri, nk, mx, chunk, part_off, rot, row_tile;  // table positions
+  size_t pad2, step, blk, linv, tri, nk, mx, chunk, part_off, rot, row_tile;  // table positions (linv: 2 per step)
   double* part;  // partial Gram sums of the block iteration
 };
 
@@ -42,6 +42,21 @@ struct SolvePlan {
   unsigned long long* fail_list;   // row_total entries: (problem << 32) | row
   unsigned long long* fail_count;  // zero before the launch
 };
+
+// Row-slab schedule of the fused selection + Gram (k_gram_slab.cu).  Table
+// `task_pos` holds nslab prefix tables (nprob + 1 entries each): the trials of
+// every problem that has slab s.
+struct SlabPlan {
+  const ProbDesc* descs;
+  int nprob;
+  int nslab;
+  int64_t slab_rows;
+  const int64_t* dT;
+  const int64_t* hT;
+  size_t task_pos;
+};
+bool slab_supported(int mode, int l);
+cudaError_t launch_gram_slab(int mode, int l, const SlabPlan& S, cudaStream_t s);
 
 cudaError_t launch_pack_mask(const ProbDesc* descs, const int64_t* blk_off, int nprob, int64_t nblocks, cudaStream_t s);
 cudaError_t launch_sample(const ProbDesc* descs, const int64_t* trial_off, int nprob, int64_t total, cudaStream_t s);

@@ -6,7 +6,8 @@
 namespace rsm {
 
 namespace {
-constexpr int kEigSplit = 4;  // must equal kSplit in k_eig.cu
+constexpr int kEigSplit = 8;   // must equal kSplit in k_eig.cu
+constexpr int kPrecSplit = 4;  // must equal kPSplit in k_eig.cu
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -34,7 +35,7 @@ Sizes sizes_of(const rsm_problem& p, const Derived& dv) {
   s.X = align_up(n * dv.kx * 8);
   s.MX = s.X;
   s.R = align_up((size_t)kEigSplit * n * dv.kx * 8);
-  s.small = align_up((32 * 32 + 32) * 8);
+  s.small = align_up((2 * 32 * 32 + 32) * 8);
   s.Kmat = dv.solve_u ? align_up(n * dv.q_pad * 8) : 0;
   s.NB = dv.solve_u ? align_up(m * dv.q_pad * 8) : 0;
   return s;
@@ -140,7 +141,10 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
   }
   b.o_blk = prefix([&](int i) { return (int64_t)b.dv[i].nblk; });
   b.o_linv = T.size();
-  for (int k = 0; k < b.max_nblk; ++k) prefix([&](int i) { return (int64_t)(k < b.dv[i].nblk ? k : 0); });
+  for (int k = 0; k < b.max_nblk; ++k) {
+    prefix([&](int i) { return (int64_t)(k < b.dv[i].nblk ? k + 1 : 0); });
+    prefix([&](int i) { return (int64_t)(k < b.dv[i].nblk ? (b.dv[i].nblk - k - 1) * (k + 1) : 0); });
+  }
   b.o_tri = prefix([&](int i) { return (int64_t)b.dv[i].nblk * (b.dv[i].nblk + 1) / 2; });
   b.o_nk = prefix([&](int i) { return ps[i].n * b.dv[i].kx; });
   b.nk_total = total(b.o_nk);
@@ -149,7 +153,7 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
   b.o_part = prefix([&](int i) { return (int64_t)part_doubles(ps[i], b.dv[i]); });
   b.part_total = total(b.o_part);
   b.o_rot = prefix([&](int i) { return (ps[i].n + 127) / 128; });
-  b.o_rowtile = prefix([&](int i) { return (ps[i].n + 31) / 32; });
+  b.o_rowtile = prefix([&](int i) { return (int64_t)kPrecSplit * ((ps[i].n + 15) / 16); });
   b.o_k = prefix([&](int i) { return b.dv[i].solve_u ? ps[i].n * b.dv[i].q_pad : 0; });
   b.k_total = total(b.o_k);
   b.o_tile = prefix([&](int i) { return b.dv[i].solve_u ? ((ps[i].m + 63) / 64) * (b.dv[i].q_pad / 64) : 0; });
@@ -158,6 +162,23 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
   b.row_total = total(b.o_row);
   b.o_res = prefix([&](int i) { return (int64_t)res_blocks_of(ps[i], b.dv[i]); });
   b.res_blocks = total(b.o_res);
+
+  // Row slabs: 32 MiB of Y (summed over the batch's problems) per slab, at least 1024 rows.
+  b.lmin = b.lmax;
+  int64_t sum_n_bytes = 0;
+  for (int i = 0; i < count; ++i) {
+    b.lmin = std::min(b.lmin, b.dv[i].l);
+    sum_n_bytes += ps[i].n * (ps[i].y_dtype == RSM_F64 ? 8 : 4);
+  }
+  const int mode = ps[0].gram_prec == RSM_PREC_F64 ? 0 : ps[0].gram_prec == RSM_PREC_F32X2 ? 1 : 2;
+  b.slab = b.lmin == b.lmax && slab_supported(mode, b.lmax);
+  b.slab_rows = std::max<int64_t>(1024, ((int64_t)32 << 20) / std::max<int64_t>(1, sum_n_bytes) / 32 * 32);
+  b.nslab = 0;
+  for (int i = 0; i < count; ++i) b.nslab = std::max<int>(b.nslab, (int)((ps[i].m + b.slab_rows - 1) / b.slab_rows));
+  b.o_slab = T.size();
+  if (b.slab)
+    for (int sl = 0; sl < b.nslab; ++sl)
+      prefix([&](int i) { return (int64_t)sl * b.slab_rows < ps[i].m ? ps[i].trials : (int64_t)0; });
 
   // workspace: all zero regions first, then all data regions, then shared partial buffers
   b.zero_off.resize(count);

@@ -51,6 +51,11 @@ struct Batch {
   std::vector<size_t> zero_size, data_size;
   size_t part_bytes_off = 0, res_bytes_off = 0, fail_list_off = 0, fail_count_off = 0;
   int rmax = 0;
+  // row-slab schedule of the Gram (used when every problem has the same l)
+  bool slab = false;
+  int lmin = 0, nslab = 0;
+  int64_t slab_rows = 0;
+  size_t o_slab = 0;
   BatchLayout layout;
 };
 

@@ -178,8 +178,13 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
     RSM_CUDA(cudaEventRecord(slot.ev[2], s));
     if ((e = launch_sample(D, T + b.o_trial, np, b.trials_total, s)) != cudaSuccess) return cuda_fail(e, "sample");
     RSM_CUDA(cudaEventRecord(slot.ev[3], s));
-    if ((e = launch_select_gram(b.gram_mode, D, T + b.o_trial, np, b.trials_total, b.lmax, s)) != cudaSuccess)
+    if (b.slab) {
+      SlabPlan sp{D, np, b.nslab, b.slab_rows, T, b.tables.data(), b.o_slab};
+      if ((e = launch_gram_slab(b.gram_mode, b.lmax, sp, s)) != cudaSuccess) return cuda_fail(e, "gram_slab");
+    } else if ((e = launch_select_gram(b.gram_mode, D, T + b.o_trial, np, b.trials_total, b.lmax, s)) !=
+               cudaSuccess) {
       return cuda_fail(e, "select_gram");
+    }
     RSM_CUDA(cudaEventRecord(slot.ev[4], s));
     if ((e = launch_minor_scatter(D, T + b.o_trial, np, b.trials_total, b.lmax, s)) != cudaSuccess)
       return cuda_fail(e, "minor_scatter");
