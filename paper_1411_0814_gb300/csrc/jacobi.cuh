@@ -29,6 +29,14 @@ __device__ __forceinline__ double jacobi_eps<double>() { return DBL_EPSILON; }
 template <>
 __device__ __forceinline__ float jacobi_eps<float>() { return FLT_EPSILON; }
 
+// Below this |u| = |a_pq / (a_qq - a_pp)| the series rotation is exact to rounding.
+template <typename T>
+__device__ __forceinline__ T small_rot();
+template <>
+__device__ __forceinline__ double small_rot<double>() { return 1e-4; }
+template <>
+__device__ __forceinline__ float small_rot<float>() { return 1e-2f; }
+
 // ||A||_F of a k x k matrix in shared memory (row stride ls), all lanes get it.
 template <typename T>
 __device__ inline T warp_frobenius(const T* A, int k, int ls) {
@@ -75,11 +83,22 @@ __device__ inline void warp_jacobi(T* S, T* Vm, int k, int ls, JacobiScratchT<T>
         if (b < k) {
           const T apq = S[a * ls + b];
           const T app = S[a * ls + a], aqq = S[b * ls + b];
-          if (fabs(apq) > tol_abs && fabs(apq) > eps * sqrt(fabs(app) * fabs(aqq))) {
-            const T tau = (aqq - app) / (2 * apq);
-            const T tt = (tau >= 0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt(1 + tau * tau));
-            c = 1 / sqrt(1 + tt * tt);
-            s = tt * c;
+          if (fabs(apq) > tol_abs && apq * apq > eps * eps * fabs(app * aqq)) {
+            // u = a_pq / (a_qq - a_pp) = 1 / (2 tau).  When |u| is small, t = u (1 - u^2)
+            // and c = 1 - t^2 / 2 are exact to O(u^4) (series of the textbook formulas),
+            // which saves the square roots; otherwise use the textbook formulas.
+            const T den = aqq - app;
+            const T u = (fabs(den) > (T)0) ? apq / den : (T)1;
+            if (fabs(u) < small_rot<T>()) {
+              const T tt = u * (1 - u * u);
+              c = 1 - (T)0.5 * tt * tt;
+              s = tt * c;
+            } else {
+              const T tau = den / (2 * apq);
+              const T tt = (tau >= 0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt(1 + tau * tau));
+              c = 1 / sqrt(1 + tt * tt);
+              s = tt * c;
+            }
           }
         } else {
           b = a;

@@ -26,6 +26,8 @@
 namespace rsm {
 
 constexpr int BS = 32;  // block size of the FP32 factorisation
+constexpr int kConvFlag = 40;   // stats[40] != 0: the block iteration of this problem has converged
+constexpr double kConvTol = 1e-12;  // converged when max ||R_j|| <= kConvTol * (theta_{r+1} - theta_r)
 
 __device__ __forceinline__ int64_t npad_of(const ProbDesc& d) { return (int64_t)d.nblk * BS; }
 
@@ -45,6 +47,7 @@ __global__ void __launch_bounds__(256) k_eig_prep(const ProbDesc* __restrict__ d
   const int p = find_problem(off, nprob, g);
   const ProbDesc& d = descs[p];
   const int64_t e = g - off[p];
+  if (e == 0) d.stats[kConvFlag] = 0.0;
   const int64_t np = npad_of(d);
   const int64_t i = e / np, j = e % np;
   const double mean = (double)d.counters[0] * d.n_minor / (double)d.n;
@@ -314,6 +317,7 @@ __global__ void __launch_bounds__(256) k_gemm_MX(const ProbDesc* __restrict__ de
   __shared__ double xs[32][kMaxL + 1];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
+  if (d.stats[kConvFlag] != 0.0) return;  // converged: the rest of the iteration is skipped
   const int64_t local = blockIdx.x - off[p];
   const int64_t n = d.n;
   const int kx = d.kx;
@@ -360,6 +364,7 @@ __global__ void __launch_bounds__(256) k_split_sum(const ProbDesc* __restrict__ 
   if (g >= off[nprob]) return;
   const int p = find_problem(off, nprob, g);
   const ProbDesc& d = descs[p];
+  if (d.stats[kConvFlag] != 0.0) return;
   const int64_t e = g - off[p];
   const int64_t nk = d.n * d.kx;
   double s = d.R[e];
@@ -367,32 +372,35 @@ __global__ void __launch_bounds__(256) k_split_sum(const ProbDesc* __restrict__ 
   d.MX[e] = s;
 }
 
-// Partial Gram sums over chunks of 64 rows: part[chunk] = [X^T X | X^T MX] (2 kx^2 values).
+// Partial Gram sums over chunks of kChunk rows: part[chunk] = [X^T X | X^T MX] (2 kx^2 values).
 constexpr int kChunk = 64;
 __global__ void __launch_bounds__(256) k_xtx(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                             int nprob, double* __restrict__ part_base, const int64_t* __restrict__ part_off) {
-  __shared__ double xs[kChunk][kMaxL + 1], ys[kChunk][kMaxL + 1];
+  extern __shared__ double xtx_smem[];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
+  if (d.stats[kConvFlag] != 0.0) return;  // converged: the rest of the iteration is skipped
   const int64_t chunk = blockIdx.x - off[p];
   const int kx = d.kx;
+  double* xs = xtx_smem;                  // kChunk x kx
+  double* ys = xtx_smem + kChunk * kx;    // kChunk x kx
   const int64_t i0 = chunk * kChunk;
   for (int e = threadIdx.x; e < kChunk * kx; e += 256) {
-    const int r = e / kx, c = e % kx;
-    const int64_t i = i0 + r;
-    xs[r][c] = i < d.n ? d.X[i * kx + c] : 0.0;
-    ys[r][c] = i < d.n ? d.MX[i * kx + c] : 0.0;
+    const int64_t i = i0 + e / kx;
+    xs[e] = i < d.n ? d.X[i0 * kx + e] : 0.0;
+    ys[e] = i < d.n ? d.MX[i0 * kx + e] : 0.0;
   }
   __syncthreads();
   double* part = part_base + part_off[p] + chunk * 2 * kx * kx;
   for (int e = threadIdx.x; e < 2 * kx * kx; e += 256) {
     const int which = e / (kx * kx), ab = e % (kx * kx), a = ab / kx, b = ab % kx;
-    double s = 0.0;
-    if (which == 0)
-      for (int r = 0; r < kChunk; ++r) s = fma(xs[r][a], xs[r][b], s);
-    else
-      for (int r = 0; r < kChunk; ++r) s = fma(xs[r][a], ys[r][b], s);
-    part[e] = s;
+    const double* y = which == 0 ? xs : ys;
+    double s0 = 0.0, s1 = 0.0;
+    for (int r = 0; r < kChunk; r += 2) {
+      s0 = fma(xs[r * kx + a], y[r * kx + b], s0);
+      s1 = fma(xs[(r + 1) * kx + a], y[(r + 1) * kx + b], s1);
+    }
+    part[e] = s0 + s1;
   }
 }
 
@@ -458,11 +466,13 @@ __global__ void __launch_bounds__(32) k_rayleigh_ritz(const ProbDesc* __restrict
   const int p = blockIdx.x;
   if (p >= nprob) return;
   const ProbDesc& d = descs[p];
+  if (d.stats[kConvFlag] != 0.0) return;
   const int kx = d.kx, lane = threadIdx.x;
   const int64_t nchunk = (d.n + kChunk - 1) / kChunk;
   const double* part = part_base + part_off[p];
   for (int e = lane; e < kx * kx; e += 32) {
     double s = 0.0, h = 0.0;
+#pragma unroll 8
     for (int64_t c = 0; c < nchunk; ++c) {
       s += part[c * 2 * kx * kx + e];
       h += part[c * 2 * kx * kx + kx * kx + e];
@@ -514,45 +524,79 @@ __global__ void __launch_bounds__(32) k_rayleigh_ritz(const ProbDesc* __restrict
         Vc[i][c] = (i > c) ? (CT)0 : v / Sc[i][i];
       }
     __syncwarp();
-    // (3) H1 = Q1^T H Q1 in FP64 (into S, free now)
-    for (int e = lane; e < kx * kx; e += 32) {
-      const int a = e / kx, b = e % kx;
-      double s = 0.0;
-      for (int t = 0; t < kx; ++t) s = fma(H[a][t], (double)Vc[t][b], s);
-      T[a][b] = s;
-    }
-    __syncwarp();
-    for (int e = lane; e < kx * kx; e += 32) {
-      const int a = e / kx, b = e % kx;
-      double s = 0.0;
-      for (int t = 0; t < kx; ++t) s = fma((double)Vc[t][a], T[t][b], s);
-      Sj[a][b] = (float)s;
-      S[a][b] = s;
-    }
-    __syncwarp();
-    // (4) Ritz rotation from FP32 Jacobi of H1; Q = Q1 Q2 and H_out = Q2^T H1 Q2 in FP64,
-    // so that R = M X Q - X Q H_out is exact for the basis actually used
-    const double fro = warp_frobenius(&S[0][0], kx, kLs);
-    warp_jacobi<float>(&Sj[0][0], &Vj[0][0], kx, kLs, jsf, (float)(4.0 * FLT_EPSILON * fro));
-    for (int e = lane; e < kx * kx; e += 32) {
-      const int a = e / kx, b = e % kx;
-      double q = 0.0, h = 0.0;
-      for (int t = 0; t < kx; ++t) {
-        q = fma((double)Vc[a][t], (double)Vj[t][b], q);
-        h = fma(S[a][t], (double)Vj[t][b], h);
+    if constexpr (sizeof(CT) != 8) {
+      // FP32 factor: the Ritz rotation of an intermediate step is all FP32.
+      // (3) H1 = Q1^T H Q1 (into Sj)
+      for (int e = lane; e < kx * kx; e += 32) {
+        const int a = e / kx, b = e % kx;
+        float s = 0.f;
+        for (int t = 0; t < kx; ++t) s = fmaf((float)H[a][t], Vc[t][b], s);
+        T[a][b] = s;
       }
-      T[a][b] = q;
-      H[a][b] = h;
+      __syncwarp();
+      float fro2 = 0.f;
+      for (int e = lane; e < kx * kx; e += 32) {
+        const int a = e / kx, b = e % kx;
+        float s = 0.f;
+        for (int t = 0; t < kx; ++t) s = fmaf(Vc[t][a], (float)T[t][b], s);
+        Sj[a][b] = s;
+        fro2 += s * s;
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) fro2 += __shfl_xor_sync(0xffffffffu, fro2, o);
+      __syncwarp();
+      // (4) Ritz rotation Q2 from Jacobi; Q = Q1 Q2, H_out = Q2^T H1 Q2 (the rotated Sj)
+      warp_jacobi<float>(&Sj[0][0], &Vj[0][0], kx, kLs, jsf, 4.f * FLT_EPSILON * sqrtf(fro2));
+      for (int e = lane; e < kx * kx; e += 32) {
+        const int a = e / kx, b = e % kx;
+        float q = 0.f;
+        for (int t = 0; t < kx; ++t) q = fmaf(Vc[a][t], Vj[t][b], q);
+        out[e] = (double)q;
+        out[kx * kx + e] = (double)Sj[a][b];
+      }
+      return;
+    } else {
+      // FP64 factor: steps may amplify the wanted directions by ~1e11, keep the
+      // rotation in FP64 products of the FP64 basis.
+      // (3) H1 = Q1^T H Q1 in FP64 (into S, free now)
+      for (int e = lane; e < kx * kx; e += 32) {
+        const int a = e / kx, b = e % kx;
+        double s = 0.0;
+        for (int t = 0; t < kx; ++t) s = fma(H[a][t], (double)Vc[t][b], s);
+        T[a][b] = s;
+      }
+      __syncwarp();
+      for (int e = lane; e < kx * kx; e += 32) {
+        const int a = e / kx, b = e % kx;
+        double s = 0.0;
+        for (int t = 0; t < kx; ++t) s = fma((double)Vc[t][a], T[t][b], s);
+        Sj[a][b] = (float)s;
+        S[a][b] = s;
+      }
+      __syncwarp();
+      // (4) Ritz rotation from FP32 Jacobi of H1; Q = Q1 Q2 and H_out = Q2^T H1 Q2 in FP64
+      const double fro = warp_frobenius(&S[0][0], kx, kLs);
+      warp_jacobi<float>(&Sj[0][0], &Vj[0][0], kx, kLs, jsf, (float)(4.0 * FLT_EPSILON * fro));
+      for (int e = lane; e < kx * kx; e += 32) {
+        const int a = e / kx, b = e % kx;
+        double q = 0.0, h = 0.0;
+        for (int t = 0; t < kx; ++t) {
+          q = fma((double)Vc[a][t], (double)Vj[t][b], q);
+          h = fma(S[a][t], (double)Vj[t][b], h);
+        }
+        T[a][b] = q;
+        H[a][b] = h;
+      }
+      __syncwarp();
+      for (int e = lane; e < kx * kx; e += 32) {
+        const int a = e / kx, b = e % kx;
+        double s = 0.0;
+        for (int t = 0; t < kx; ++t) s = fma((double)Vj[t][a], H[t][b], s);
+        out[e] = T[a][b];
+        out[kx * kx + e] = s;
+      }
+      return;
     }
-    __syncwarp();
-    for (int e = lane; e < kx * kx; e += 32) {
-      const int a = e / kx, b = e % kx;
-      double s = 0.0;
-      for (int t = 0; t < kx; ++t) s = fma((double)Vj[t][a], H[t][b], s);
-      out[e] = T[a][b];
-      out[kx * kx + e] = s;
-    }
-    return;
   }
   warp_chol_shifted(S, kx);
   // T = C^-1 H  (forward substitution, one column per lane)
@@ -608,38 +652,52 @@ __global__ void __launch_bounds__(32) k_rayleigh_ritz(const ProbDesc* __restrict
   for (int c = lane; c < kx; c += 32) out[2 * kx * kx + c] = H[order[c]][order[c]];
 }
 
-// X <- X Q, MX <- MX Q, R = MX - X H'; one thread per row.
-__global__ void __launch_bounds__(128) k_rotate(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
+// X <- X Q, MX <- MX Q, R = MX - X H'.  A CTA takes 8 rows; thread (row, column)
+// computes one entry of each product from rows staged in shared memory.
+constexpr int kRotRows = 8;
+__global__ void __launch_bounds__(256) k_rotate(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                int nprob) {
   __shared__ double q[2 * kMaxL * kMaxL];
+  __shared__ double xs[kRotRows][kMaxL], ms[kRotRows][kMaxL], nxs[kRotRows][kMaxL];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
+  if (d.stats[kConvFlag] != 0.0) return;  // converged: the rest of the iteration is skipped
   const int kx = d.kx;
-  for (int e = threadIdx.x; e < 2 * kx * kx; e += 128) q[e] = d.small[e];
-  __syncthreads();
-  const int64_t i = (blockIdx.x - off[p]) * 128 + threadIdx.x;
-  if (i >= d.n) return;
-  double x[kMaxL], mx[kMaxL], nx[kMaxL], nmx[kMaxL];
-  for (int c = 0; c < kx; ++c) {
-    x[c] = d.X[i * kx + c];
-    mx[c] = d.MX[i * kx + c];
+  const int64_t i0 = (blockIdx.x - off[p]) * kRotRows;
+  for (int e = threadIdx.x; e < 2 * kx * kx; e += blockDim.x) q[e] = d.small[e];
+  for (int e = threadIdx.x; e < kRotRows * kx; e += blockDim.x) {
+    const int r = e / kx, c = e % kx;
+    const int64_t i = i0 + r;
+    xs[r][c] = i < d.n ? d.X[i * kx + c] : 0.0;
+    ms[r][c] = i < d.n ? d.MX[i * kx + c] : 0.0;
   }
+  __syncthreads();
   const double* H = q + kx * kx;
-  for (int c = 0; c < kx; ++c) {
+  double nmx[kMaxL * kRotRows / 256 + 1];
+  int cnt = 0;
+  for (int e = threadIdx.x; e < kRotRows * kx; e += blockDim.x) {
+    const int r = e / kx, c = e % kx;
     double a = 0.0, b = 0.0;
     for (int t = 0; t < kx; ++t) {
-      a = fma(x[t], q[t * kx + c], a);
-      b = fma(mx[t], q[t * kx + c], b);
+      a = fma(xs[r][t], q[t * kx + c], a);
+      b = fma(ms[r][t], q[t * kx + c], b);
     }
-    nx[c] = a;
-    nmx[c] = b;
-    d.X[i * kx + c] = a;
-    d.MX[i * kx + c] = b;
+    nxs[r][c] = a;
+    nmx[cnt++] = b;
   }
-  for (int c = 0; c < kx; ++c) {
-    double s = nmx[c];
-    for (int t = 0; t < kx; ++t) s = fma(-nx[t], H[t * kx + c], s);
-    d.R[i * kx + c] = s;
+  __syncthreads();
+  cnt = 0;
+  for (int e = threadIdx.x; e < kRotRows * kx; e += blockDim.x) {
+    const int r = e / kx, c = e % kx;
+    const int64_t i = i0 + r;
+    const double b = nmx[cnt++];
+    double s = b;
+    for (int t = 0; t < kx; ++t) s = fma(-nxs[r][t], H[t * kx + c], s);
+    if (i < d.n) {
+      d.X[i * kx + c] = nxs[r][c];
+      d.MX[i * kx + c] = b;
+      d.R[i * kx + c] = s;
+    }
   }
 }
 
@@ -654,6 +712,7 @@ __global__ void __launch_bounds__(256) k_precond(const ProbDesc* __restrict__ de
   __shared__ T rs[64][kMaxL + 1];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
+  if (d.stats[kConvFlag] != 0.0) return;  // converged: the rest of the iteration is skipped
   const int64_t n = d.n, np = npad_of(d);
   const int kx = d.kx;
   const int64_t local = blockIdx.x - off[p];
@@ -697,11 +756,45 @@ __global__ void __launch_bounds__(256) k_precond_apply(const ProbDesc* __restric
   if (g >= off[nprob]) return;
   const int p = find_problem(off, nprob, g);
   const ProbDesc& d = descs[p];
+  if (d.stats[kConvFlag] != 0.0) return;
   const int64_t e = g - off[p];
   const int64_t nk = d.n * d.kx;
   double s = 0.0;
   for (int q = 0; q < kPSplit; ++q) s += d.R[(int64_t)(1 + q) * nk + e];
   d.X[e] -= s;
+}
+
+// After a polished Rayleigh-Ritz step: largest residual column norm over the r
+// wanted Ritz pairs against the gap theta_{r+1} - theta_r; sets the flag that
+// skips the remaining iterations of the problem.
+__global__ void __launch_bounds__(256) k_conv_check(const ProbDesc* __restrict__ descs, int nprob) {
+  __shared__ double red[256];
+  const int p = blockIdx.x;
+  if (p >= nprob) return;
+  const ProbDesc& d = descs[p];
+  if (d.stats[kConvFlag] != 0.0) return;
+  const int kx = d.kx, r = d.r;
+  double mx = 0.0;
+  for (int c = 0; c < r; ++c) {
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < d.n; i += 256) {
+      const double v = d.R[i * kx + c];
+      s += v * v;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    mx = fmax(mx, sqrt(red[0]));
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double* th = d.small + 2 * kx * kx;
+    const double gap = r < kx ? th[r] - th[r - 1] : 0.0;
+    if (gap > 0.0 && mx <= kConvTol * gap) d.stats[kConvFlag] = 1.0;
+  }
 }
 
 // V = first r columns of X (n x r column-major, ldv); eigenvalue estimates; residual norm.
@@ -750,7 +843,10 @@ __global__ void __launch_bounds__(256) k_eig_finish(const ProbDesc* __restrict__
 
 template <typename T>
 static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, cudaStream_t s) {
-  cudaError_t ea = cudaFuncSetAttribute(k_rayleigh_ritz<true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRRSmem);
+  cudaError_t ea = cudaFuncSetAttribute(k_xtx, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(2 * kChunk * kMaxL * sizeof(double)));
+  if (ea == cudaSuccess)
+    ea = cudaFuncSetAttribute(k_rayleigh_ritz<true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRRSmem);
   if (ea == cudaSuccess)
     ea = cudaFuncSetAttribute(k_rayleigh_ritz<false, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRRSmem);
   if (ea != cudaSuccess) return ea;
@@ -775,15 +871,24 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
   RSM_LAUNCH(k_init_X, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
   // The FP64 factor is an almost exact shift-invert: a step can amplify the
   // wanted directions by ~1/tau, so each step runs the Rayleigh-Ritz pass twice
-  // (the first re-orthonormalises a nearly rank-deficient block).  The last two
-  // steps and the closing pass diagonalise in FP64 (polished); the others in FP32.
+  // (the first re-orthonormalises a nearly rank-deficient block).  The closing
+  // pass diagonalises in FP64 (polished); the steps before it in FP32.
   const int passes = sizeof(T) == 8 ? 2 : 1;
+  // Adaptive: steps before min_iters diagonalise in FP32; from min_iters on every
+  // step ends with the polished FP64 Rayleigh-Ritz and a convergence check, and a
+  // converged problem skips everything after it.  The last step never preconditions.
+  const int min_iters = sizeof(T) == 8 ? 2 : 5;
   for (int it = 0; it <= iters; ++it) {
-    const bool final_rr = it >= iters - 1;
+    const bool final_rr = it >= min_iters || it == iters;
     RSM_LAUNCH(k_gemm_MX, total(P.mx), 256, D, dev(P.mx), np);
     RSM_LAUNCH(k_split_sum, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
     for (int pass = 0; pass < passes; ++pass) {
-      RSM_LAUNCH(k_xtx, total(P.chunk), 256, D, dev(P.chunk), np, P.part, dev(P.part_off));
+      if (total(P.chunk) > 0) {
+        k_xtx<<<(unsigned)total(P.chunk), 256, 2 * kChunk * kMaxL * sizeof(double), s>>>(D, dev(P.chunk), np, P.part,
+                                                                                        dev(P.part_off));
+        ++g_kernel_launches;
+        if (cudaGetLastError() != cudaSuccess) return cudaErrorLaunchFailure;
+      }
       if (final_rr && pass == passes - 1) {
         k_rayleigh_ritz<true, T><<<np, 32, kRRSmem, s>>>(D, np, P.part, dev(P.part_off));
       } else {
@@ -791,8 +896,9 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
       }
       ++g_kernel_launches;
       if (cudaGetLastError() != cudaSuccess) return cudaErrorLaunchFailure;
-      RSM_LAUNCH(k_rotate, total(P.rot), 128, D, dev(P.rot), np);
+      RSM_LAUNCH(k_rotate, total(P.rot), 256, D, dev(P.rot), np);
     }
+    if (final_rr) RSM_LAUNCH(k_conv_check, np, 256, D, np);
     if (it < iters) {
       RSM_LAUNCH(k_precond<T>, total(P.row_tile), 256, D, dev(P.row_tile), np);
       RSM_LAUNCH(k_precond_apply, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);

@@ -262,64 +262,86 @@ __global__ void __launch_bounds__(32 * kPinvWarps) k_row_pinv(const ProbDesc* __
   }
 }
 
-// e numerator: sum over known entries of (y_ij - u_i . v_j)^2.  One thread per row,
-// columns of V staged in shared memory; one partial per CTA.
+// e numerator: sum over known entries of (y_ij - u_i . v_j)^2.  A CTA takes 32
+// consecutive rows (lane = row, so each column read is one coalesced 32-row
+// segment and one mask word) and its 8 warps split the columns; V is staged in
+// shared memory 64 columns at a time.  One partial per CTA, fixed-order tree.
+constexpr int kResRows = 32;
+constexpr int kResCols = 64;
 template <typename T>
 __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                  int nprob, double* __restrict__ partial) {
-  __shared__ T vs[32][kMaxR + 1];
-  __shared__ double red[256];
+  __shared__ T vs[kResCols][kMaxR + 1];
+  __shared__ double red[8];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
-  const int64_t i = (blockIdx.x - off[p]) * 256 + threadIdx.x;
+  const int lane = threadIdx.x & 31, wg = threadIdx.x >> 5;
+  const int64_t i0 = (blockIdx.x - off[p]) * kResRows;
+  const int64_t i = i0 + lane;
   const int r = d.r;
   T u[kMaxR];
-  for (int a = 0; a < kMaxR; ++a) u[a] = (T)0;
-  if (i < d.m)
-    for (int a = 0; a < r; ++a) u[a] = (T)d.U[(int64_t)a * d.ldu + i];
+#pragma unroll
+  for (int a = 0; a < kMaxR; ++a) u[a] = (a < r && i < d.m) ? (T)d.U[(int64_t)a * d.ldu + i] : (T)0;
   double acc = 0.0;
-  for (int64_t j0 = 0; j0 < d.n; j0 += 32) {
+  const int64_t wcol = i0 >> 5;
+  for (int64_t j0 = 0; j0 < d.n; j0 += kResCols) {
     __syncthreads();
-    for (int e = threadIdx.x; e < 32 * r; e += 256) {
+    for (int e = threadIdx.x; e < kResCols * r; e += 256) {
       const int jj = e / r, a = e % r;
       const int64_t j = j0 + jj;
       vs[jj][a] = j < d.n ? (T)d.V[(int64_t)a * d.ldv + j] : (T)0;
     }
     __syncthreads();
-    if (i < d.m) {
-      const int64_t jn = d.n - j0 < 32 ? d.n - j0 : 32;
-      for (int jj = 0; jj < jn; ++jj) {
-        const int64_t j = j0 + jj;
-        const uint32_t word = __ldg(d.bits + j * d.ldb + (i >> 5));
-        if (!((word >> (i & 31)) & 1u)) continue;
+    const int jn = d.n - j0 < kResCols ? (int)(d.n - j0) : kResCols;
+    // at most kResCols / 8 terms per chunk in the working precision, then one FP64 add
+    // (FP64 instructions are far slower than FP32 ones; one per chunk keeps them off the loop)
+    T part = (T)0;
+#pragma unroll 4
+    for (int jj = wg; jj < jn; jj += 8) {
+      const int64_t j = j0 + jj;
+      const uint32_t word = __ldg(d.bits + j * d.ldb + wcol);
+      if ((word >> lane) & 1u) {
         T pred = (T)0;
-#pragma unroll 8
+#pragma unroll
         for (int a = 0; a < kMaxR; ++a)
           if (a < r) pred = fma(u[a], vs[jj][a], pred);
         const T diff = load_y<T>(d, j * d.ldy + i) - pred;
-        acc += (double)(diff * diff);
+        part = fma(diff, diff, part);
       }
     }
+    acc += (double)part;
   }
-  red[threadIdx.x] = acc;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) red[wg] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += red[k];
+    partial[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_residual_final(const ProbDesc* __restrict__ descs,
+                                                       const int64_t* __restrict__ off, int nprob,
+                                                       const double* __restrict__ partial) {
+  __shared__ double red[256];
+  const int p = blockIdx.x;
+  if (p >= nprob) return;
+  const ProbDesc& d = descs[p];
+  double s = 0.0;  // strided partial sums, then a fixed tree: deterministic
+  for (int64_t b = off[p] + threadIdx.x; b < off[p + 1]; b += 256) s += partial[b];
+  red[threadIdx.x] = s;
   __syncthreads();
   for (int o = 128; o; o >>= 1) {
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
-}
-
-__global__ void __launch_bounds__(32) k_residual_final(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
-                                                      int nprob, const double* __restrict__ partial) {
-  const int p = blockIdx.x;
-  if (p >= nprob || threadIdx.x) return;
-  const ProbDesc& d = descs[p];
-  double s = 0.0;
-  for (int64_t b = off[p]; b < off[p + 1]; ++b) s += partial[b];
-  const double known = (double)d.counters[1];
-  d.stats[32] = s;
-  d.stats[33] = known > 0.0 ? sqrt(s / known) : 0.0;
+  if (threadIdx.x == 0) {
+    const double known = (double)d.counters[1];
+    d.stats[32] = red[0];
+    d.stats[33] = known > 0.0 ? sqrt(red[0] / known) : 0.0;
+  }
 }
 
 cudaError_t launch_solve_u(const SolvePlan& S, int mode, cudaStream_t s) {
@@ -372,7 +394,7 @@ cudaError_t launch_residual(const SolvePlan& S, int mode, double* partial, cudaS
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_residual_final<<<np, 32, 0, s>>>(D, S.res_off, np, partial);
+  k_residual_final<<<np, 256, 0, s>>>(D, S.res_off, np, partial);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

@@ -46,9 +46,9 @@ size_t data_sum(const Sizes& s) {
   return s.bits + s.cols + s.rowc + s.gram + s.M + s.F1 + s.F2 + s.Dinv + s.X + s.MX + s.R + s.small + s.Kmat + s.NB;
 }
 size_t part_doubles(const rsm_problem& p, const Derived& dv) {
-  return (size_t)((p.n + 63) / 64) * 2 * dv.kx * dv.kx;
+  return (size_t)((p.n + 63) / 64) * 2 * dv.kx * dv.kx;  // chunks of kChunk = 64 rows (k_eig.cu)
 }
-size_t res_blocks_of(const rsm_problem& p, const Derived& dv) { return dv.solve_u ? (size_t)((p.m + 255) / 256) : 0; }
+size_t res_blocks_of(const rsm_problem& p, const Derived& dv) { return dv.solve_u ? (size_t)((p.m + 31) / 32) : 0; }  // kResRows
 }  // namespace
 
 int validate_problem(const rsm_problem& p, Derived& dv, std::string* why) {
@@ -152,7 +152,7 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
   b.o_chunk = prefix([&](int i) { return (ps[i].n + 63) / 64; });
   b.o_part = prefix([&](int i) { return (int64_t)part_doubles(ps[i], b.dv[i]); });
   b.part_total = total(b.o_part);
-  b.o_rot = prefix([&](int i) { return (ps[i].n + 127) / 128; });
+  b.o_rot = prefix([&](int i) { return (ps[i].n + 7) / 8; });
   b.o_rowtile = prefix([&](int i) { return (int64_t)kPrecSplit * ((ps[i].n + 15) / 16); });
   b.o_k = prefix([&](int i) { return b.dv[i].solve_u ? ps[i].n * b.dv[i].q_pad : 0; });
   b.k_total = total(b.o_k);

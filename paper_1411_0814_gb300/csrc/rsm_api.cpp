@@ -54,8 +54,14 @@ int cuda_fail(cudaError_t e, const char* where) {
 
 constexpr double kShiftRel32 = 1e-3;   // tau / (trace(M) / n) with the FP32 factor
 constexpr double kShiftRel64 = 1e-11;  // tau / (trace(M) / n) with the FP64 factor
-constexpr int kEigIters32 = 10;        // preconditioned iterations with the FP32 factor
-constexpr int kEigIters64 = 5;         // iterations with the FP64 factor (near-exact shift-invert)
+#ifndef RSM_EIG_ITERS32
+#define RSM_EIG_ITERS32 14
+#endif
+#ifndef RSM_EIG_ITERS64
+#define RSM_EIG_ITERS64 8
+#endif
+constexpr int kEigIters32 = RSM_EIG_ITERS32;  // most preconditioned steps with the FP32 factor (stops when converged)
+constexpr int kEigIters64 = RSM_EIG_ITERS64;  // most steps with the FP64 factor (near-exact shift-invert)
 constexpr int64_t kSmallN = 256;       // at or below this n the FP64 factor is cheap: use it directly
 constexpr double kEigErrTol = 1e-11;   // a-posteriori bound that accepts the FP32-factor result
 constexpr double kRankTol = 1e-12;  // lambda_{r+1} <= kRankTol * trace(M): underdetermined
