@@ -60,6 +60,7 @@ struct ProbDesc {
   int32_t q_pad;
   int32_t status;  // device-written status of this problem
   int32_t pad_;
+  int64_t slab_rows;  // rows per slab of the row-slab Gram schedule (a function of n and the Y type only)
 };
 
 // ------------------------------------------------------------------ Philox4x32-10

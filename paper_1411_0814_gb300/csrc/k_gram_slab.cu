@@ -47,7 +47,7 @@ struct SlabT<2> {  // FP32
 template <int MODE, int L>
 __global__ void __launch_bounds__(32 * kSlabWarps) k_gram_slab(const ProbDesc* __restrict__ descs,
                                                                const int64_t* __restrict__ task_off, int nprob,
-                                                               int slab, int64_t slab_rows) {
+                                                               int slab) {
   using Tr = SlabT<MODE>;
   using A = typename Tr::acc_t;
   using V = typename Tr::val_t;
@@ -67,8 +67,8 @@ __global__ void __launch_bounds__(32 * kSlabWarps) k_gram_slab(const ProbDesc* _
   int64_t cidx[L];
 #pragma unroll
   for (int k = 0; k < L; ++k) cidx[k] = (int64_t)__ldg(d.cols + t * L + k);
-  const int64_t r0 = (int64_t)slab * slab_rows;
-  const int64_t r1 = r0 + slab_rows < d.m ? r0 + slab_rows : d.m;
+  const int64_t r0 = (int64_t)slab * d.slab_rows;
+  const int64_t r1 = r0 + d.slab_rows < d.m ? r0 + d.slab_rows : d.m;
   const int64_t w_begin = r0 >> 5, w_end = (r1 + 31) >> 5;
 
   A acc[P];
@@ -170,7 +170,7 @@ static cudaError_t launch_slab_l(const SlabPlan& S, cudaStream_t s) {
     const int64_t tasks = S.hT[S.task_pos + (size_t)sl * (S.nprob + 1) + S.nprob];
     if (tasks <= 0) continue;
     k_gram_slab<MODE, L><<<(unsigned)((tasks + kSlabWarps - 1) / kSlabWarps), 32 * kSlabWarps, smem, s>>>(
-        S.descs, S.dT + S.task_pos + (size_t)sl * (S.nprob + 1), S.nprob, sl, S.slab_rows);
+        S.descs, S.dT + S.task_pos + (size_t)sl * (S.nprob + 1), S.nprob, sl);
     ++g_kernel_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

@@ -50,7 +50,6 @@ struct SlabPlan {
   const ProbDesc* descs;
   int nprob;
   int nslab;
-  int64_t slab_rows;
   const int64_t* dT;
   const int64_t* hT;
   size_t task_pos;

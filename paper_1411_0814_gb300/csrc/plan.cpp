@@ -94,6 +94,14 @@ size_t problem_footprint(const rsm_problem& p, const Derived& dv) {
          align_up(dv.solve_u ? (size_t)p.m * 8 : 0) + kAlign;
 }
 
+// Rows per slab of the row-slab Gram: 32 MiB of the problem's Y (so that a
+// slab stays resident in L2 while every trial reads it), at least 1024 rows,
+// a multiple of 32 (whole mask words).
+int64_t slab_rows_of(const rsm_problem& p) {
+  const int64_t row_bytes = p.n * (p.y_dtype == RSM_F64 ? 8 : 4);
+  return std::max<int64_t>(1024, ((int64_t)32 << 20) / std::max<int64_t>(1, row_bytes) / 32 * 32);
+}
+
 void build_batch(const rsm_problem* ps, int count, Batch& b) {
   b.nprob = count;
   b.dv.resize(count);
@@ -163,22 +171,34 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
   b.o_res = prefix([&](int i) { return (int64_t)res_blocks_of(ps[i], b.dv[i]); });
   b.res_blocks = total(b.o_res);
 
-  // Row slabs: 32 MiB of Y (summed over the batch's problems) per slab, at least 1024 rows.
-  b.lmin = b.lmax;
-  int64_t sum_n_bytes = 0;
-  for (int i = 0; i < count; ++i) {
-    b.lmin = std::min(b.lmin, b.dv[i].l);
-    sum_n_bytes += ps[i].n * (ps[i].y_dtype == RSM_F64 ? 8 : 4);
-  }
+  // Row slabs: the slab size of a problem depends on its own n and Y type only,
+  // and problems are grouped by l, so a problem's Gram is summed in the same
+  // order alone and in any batch (results do not depend on the batch).
   const int mode = ps[0].gram_prec == RSM_PREC_F64 ? 0 : ps[0].gram_prec == RSM_PREC_F32X2 ? 1 : 2;
-  b.slab = b.lmin == b.lmax && slab_supported(mode, b.lmax);
-  b.slab_rows = std::max<int64_t>(1024, ((int64_t)32 << 20) / std::max<int64_t>(1, sum_n_bytes) / 32 * 32);
   b.nslab = 0;
-  for (int i = 0; i < count; ++i) b.nslab = std::max<int>(b.nslab, (int)((ps[i].m + b.slab_rows - 1) / b.slab_rows));
-  b.o_slab = T.size();
-  if (b.slab)
+  for (int i = 0; i < count; ++i) {
+    b.dv[i].slab_rows = slab_rows_of(ps[i]);
+    b.nslab = std::max<int>(b.nslab, (int)((ps[i].m + b.dv[i].slab_rows - 1) / b.dv[i].slab_rows));
+  }
+  std::vector<int> ls;
+  for (int i = 0; i < count; ++i)
+    if (slab_supported(mode, b.dv[i].l)) ls.push_back(b.dv[i].l);
+  std::sort(ls.begin(), ls.end());
+  ls.erase(std::unique(ls.begin(), ls.end()), ls.end());
+  b.slab_groups.clear();
+  for (int L : ls) {
+    Batch::SlabGroup g{L, T.size()};
     for (int sl = 0; sl < b.nslab; ++sl)
-      prefix([&](int i) { return (int64_t)sl * b.slab_rows < ps[i].m ? ps[i].trials : (int64_t)0; });
+      prefix([&](int i) {
+        return b.dv[i].l == L && (int64_t)sl * b.dv[i].slab_rows < ps[i].m ? ps[i].trials : (int64_t)0;
+      });
+    b.slab_groups.push_back(g);
+  }
+  b.o_trial_generic = prefix([&](int i) { return slab_supported(mode, b.dv[i].l) ? (int64_t)0 : ps[i].trials; });
+  b.generic_total = total(b.o_trial_generic);
+  b.generic_lmax = 0;
+  for (int i = 0; i < count; ++i)
+    if (!slab_supported(mode, b.dv[i].l)) b.generic_lmax = std::max(b.generic_lmax, b.dv[i].l);
 
   // workspace: all zero regions first, then all data regions, then shared partial buffers
   b.zero_off.resize(count);
@@ -243,6 +263,7 @@ void bind_batch(Batch& b, const rsm_problem* ps, unsigned char* ws) {
     d.debug_cols = p.debug_cols;
     d.debug_row_counts = p.debug_row_counts;
     d.kx = dv.kx;
+    d.slab_rows = dv.slab_rows;
     d.nblk = dv.nblk;
     d.q = dv.q;
     d.q_pad = dv.q_pad;

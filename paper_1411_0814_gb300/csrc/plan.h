@@ -15,7 +15,7 @@ namespace rsm {
 
 struct Derived {
   int l = 0, nm = 0, P_l = 0, nblk = 0, kx = 0, q = 0, q_pad = 0;
-  int64_t ldb = 0, npad = 0;
+  int64_t ldb = 0, npad = 0, slab_rows = 0;
   bool solve_u = false;
 };
 
@@ -51,11 +51,18 @@ struct Batch {
   std::vector<size_t> zero_size, data_size;
   size_t part_bytes_off = 0, res_bytes_off = 0, fail_list_off = 0, fail_count_off = 0;
   int rmax = 0;
-  // row-slab schedule of the Gram (used when every problem has the same l)
-  bool slab = false;
-  int lmin = 0, nslab = 0;
-  int64_t slab_rows = 0;
-  size_t o_slab = 0;
+  // Row-slab schedule of the Gram: one group per distinct l that the slab
+  // kernel supports (a launch per slab per group); problems of other l go
+  // through the per-trial kernel (table o_trial_generic).
+  struct SlabGroup {
+    int l;
+    size_t o_slab;  // nslab prefix tables over the problems of this l
+  };
+  std::vector<SlabGroup> slab_groups;
+  int nslab = 0;
+  size_t o_trial_generic = 0;
+  int64_t generic_total = 0;
+  int generic_lmax = 0;
   BatchLayout layout;
 };
 

@@ -184,13 +184,14 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
     RSM_CUDA(cudaEventRecord(slot.ev[2], s));
     if ((e = launch_sample(D, T + b.o_trial, np, b.trials_total, s)) != cudaSuccess) return cuda_fail(e, "sample");
     RSM_CUDA(cudaEventRecord(slot.ev[3], s));
-    if (b.slab) {
-      SlabPlan sp{D, np, b.nslab, b.slab_rows, T, b.tables.data(), b.o_slab};
-      if ((e = launch_gram_slab(b.gram_mode, b.lmax, sp, s)) != cudaSuccess) return cuda_fail(e, "gram_slab");
-    } else if ((e = launch_select_gram(b.gram_mode, D, T + b.o_trial, np, b.trials_total, b.lmax, s)) !=
-               cudaSuccess) {
-      return cuda_fail(e, "select_gram");
+    for (const auto& g : b.slab_groups) {
+      SlabPlan sp{D, np, b.nslab, T, b.tables.data(), g.o_slab};
+      if ((e = launch_gram_slab(b.gram_mode, g.l, sp, s)) != cudaSuccess) return cuda_fail(e, "gram_slab");
     }
+    if (b.generic_total > 0 &&
+        (e = launch_select_gram(b.gram_mode, D, T + b.o_trial_generic, np, b.generic_total, b.generic_lmax, s)) !=
+            cudaSuccess)
+      return cuda_fail(e, "select_gram");
     RSM_CUDA(cudaEventRecord(slot.ev[4], s));
     if ((e = launch_minor_scatter(D, T + b.o_trial, np, b.trials_total, b.lmax, s)) != cudaSuccess)
       return cuda_fail(e, "minor_scatter");
@@ -453,45 +454,60 @@ int32_t rsm_decompose(rsm_handle* h, const rsm_problem* p, rsm_result* res) {
 
 namespace {
 
+// Continuous batching: a free slot admits the oldest queued request whose
+// footprint fits the free budget, then every further queued request of the same
+// precisions that still fits (oldest first, up to kServeBatch), and runs them as one batch on its own
+// stream.  Other slots keep admitting while this batch is on the GPU, so the
+// work of requests that arrive while others run overlaps on the device.
+constexpr int kServeBatch = 16;
+
 void worker_loop(rsm_handle* h, int slot_id) {
   cudaSetDevice(h->device);
   Slot& slot = h->slots[slot_id];
   for (;;) {
-    std::shared_ptr<Request> req;
+    std::vector<std::shared_ptr<Request>> reqs;
     {
       std::unique_lock<std::mutex> lk(h->mu);
       for (;;) {
         if (h->stopping) return;
         if (!(h->fault & RSM_FAULT_STALL) && !h->queue.empty()) {
-          // admit the oldest request whose footprint fits the free budget
-          auto it = h->queue.begin();
-          for (; it != h->queue.end(); ++it) {
+          for (auto it = h->queue.begin(); it != h->queue.end() && (int)reqs.size() < kServeBatch;) {
             auto& r = h->reqs[*it];
-            if (r->footprint + h->in_use <= h->budget) break;
+            const bool same_prec = reqs.empty() || (r->prob.gram_prec == reqs[0]->prob.gram_prec &&
+                                                    r->prob.solve_prec == reqs[0]->prob.solve_prec);
+            if (same_prec && r->footprint + h->in_use <= h->budget) {
+              h->in_use += r->footprint;
+              r->state = 1;
+              r->t_start = std::chrono::steady_clock::now();
+              reqs.push_back(r);
+              it = h->queue.erase(it);
+            } else {
+              ++it;
+            }
           }
-          if (it != h->queue.end()) {
-            req = h->reqs[*it];
-            h->queue.erase(it);
-            h->in_use += req->footprint;
-            req->state = 1;
-            req->t_start = std::chrono::steady_clock::now();
-            break;
-          }
+          if (!reqs.empty()) break;
         }
         h->cv.wait(lk);
       }
     }
-    rsm_result res{};
-    int st = run_batch(h, slot, &req->prob, 1, &res);
-    if (st != RSM_OK && st != RSM_ERR_UNDERDETERMINED && st != RSM_ERR_ROWS_UNDERDETERMINED) res.status = st;
+    const int count = (int)reqs.size();
+    std::vector<rsm_problem> probs(count);
+    std::vector<rsm_result> res(count);
+    for (int i = 0; i < count; ++i) probs[i] = reqs[i]->prob;
+    const int st = run_batch(h, slot, probs.data(), count, res.data());
     {
       std::lock_guard<std::mutex> lk(h->mu);
-      req->t_end = std::chrono::steady_clock::now();
-      res.queue_ms = std::chrono::duration<double, std::milli>(req->t_start - req->t_submit).count();
-      res.run_ms = std::chrono::duration<double, std::milli>(req->t_end - req->t_start).count();
-      req->res = res;
-      req->state = 2;
-      h->in_use -= req->footprint;
+      const auto t_end = std::chrono::steady_clock::now();
+      for (int i = 0; i < count; ++i) {
+        auto& req = reqs[i];
+        if (st != RSM_OK && st != RSM_ERR_UNDERDETERMINED && st != RSM_ERR_ROWS_UNDERDETERMINED) res[i].status = st;
+        req->t_end = t_end;
+        res[i].queue_ms = std::chrono::duration<double, std::milli>(req->t_start - req->t_submit).count();
+        res[i].run_ms = std::chrono::duration<double, std::milli>(req->t_end - req->t_start).count();
+        req->res = res[i];
+        req->state = 2;
+        h->in_use -= req->footprint;
+      }
     }
     h->cv.notify_all();
     h->done_cv.notify_all();
