@@ -372,6 +372,7 @@ def bench_mine(args):
         "latency_ms": {"p50": pct(per, 50), "p99": pct(per, 99)},
         "angle_vs_fp64_form": angle,
         "eig_factor_bits": last.eig_factor_bits,
+        "eig_iterations": last.eig_iterations,
         "fp64_form": {"value": replica_throughput(ws, k64, max_over_ranks(total64, ws)), "unit": "decomps/s", "ms_per_step": total64 / k64,
                       "latency_ms": {"p50": pct(per64, 50), "p99": pct(per64, 99)}, "stage_ms": stage64},
         "stage_ms": stage,

@@ -118,7 +118,7 @@ typedef struct rsm_result {
   int64_t rows_selected;         /* sum over all trials of the rows kept (p_t) */
   int64_t kernel_launches;       /* CUDA kernels this call launched (whole batch) */
   int32_t eig_factor_bits;       /* 32 or 64: precision of the Cholesky preconditioner used for M */
-  int32_t reserved;
+  int32_t eig_iterations;        /* preconditioned block iterations of the eigensolve of M (last attempt) */
   double eig_M[32];              /* smallest eigenvalues of M, ascending */
   double eig_residual;           /* largest ||M v - lambda v|| over the r returned vectors */
   double e_known_rms;            /* eq. (ep): RMS residual over the known entries (NaN if U is NULL) */

@@ -79,7 +79,7 @@ class rsm_result(C.Structure):
         ("rows_selected", C.c_int64),
         ("kernel_launches", C.c_int64),
         ("eig_factor_bits", C.c_int32),
-        ("reserved", C.c_int32),
+        ("eig_iterations", C.c_int32),
         ("eig_M", C.c_double * 32),
         ("eig_residual", C.c_double),
         ("e_known_rms", C.c_double),

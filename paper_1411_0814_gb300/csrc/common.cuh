@@ -63,6 +63,50 @@ struct ProbDesc {
   int64_t slab_rows;  // rows per slab of the row-slab Gram schedule (a function of n and the Y type only)
 };
 
+// ------------------------------------------------------------------ FP64 reciprocal and square root
+// FP64 instructions issue at a small fraction of the FP32 rate on this part,
+// and the correctly rounded FP64 divide and square root expand into long FP64
+// sequences.  Where a last-ulp difference is harmless (pivots, rotations,
+// substitutions), seed from the FP32 hardware approximation and refine with
+// Newton-Raphson steps in FP64: each step squares the relative error
+// (2^-22 -> 2^-44 -> below 2^-53), so two steps give about one ulp.
+// Reciprocal: y <- y + y (1 - x y).  Inverse square root: y <- y + y (1/2 - x y^2 / 2).
+// Arguments whose FP32 conversion would overflow or underflow take the IEEE path.
+__device__ __forceinline__ double rcp64(double x) {
+  const double ax = fabs(x);
+  if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+  double y = (double)__frcp_rn((float)x);
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
+__device__ __forceinline__ double rsqrt64(double x) {  // x > 0
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+  double y = (double)rsqrtf((float)x);
+  const double h = 0.5 * x;
+  double e = fma(-h * y, y, 0.5);
+  y = fma(y, e, y);
+  e = fma(-h * y, y, 0.5);
+  return fma(y, e, y);
+}
+
+__device__ __forceinline__ double sqrt64(double x) {  // x >= 0
+  if (!(x > 1e-30 && x < 1e30)) return sqrt(x);
+  const double y = rsqrt64(x);
+  const double s = x * y;
+  return fma(0.5 * y, fma(-s, s, x), s);  // one correction of s = sqrt(x) with the residual x - s^2
+}
+
+// Type-generic forms for code templated on float / double.
+__device__ __forceinline__ float fast_rcp(float x) { return 1.0f / x; }
+__device__ __forceinline__ double fast_rcp(double x) { return rcp64(x); }
+__device__ __forceinline__ float fast_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double fast_sqrt(double x) { return sqrt64(x); }
+__device__ __forceinline__ float fast_rsqrt(float x) { return 1.0f / sqrtf(x); }
+__device__ __forceinline__ double fast_rsqrt(double x) { return rsqrt64(x); }
+
 // ------------------------------------------------------------------ Philox4x32-10
 // J. K. Salmon et al., "Parallel random numbers: as easy as 1, 2, 3" (SC'11):
 // ten rounds of the Philox S-box with multipliers 0xD2511F53 / 0xCD9E8D57 and

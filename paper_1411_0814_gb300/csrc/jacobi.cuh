@@ -13,6 +13,8 @@
 
 #include <cfloat>
 
+#include "common.cuh"
+
 namespace rsm {
 
 template <typename T>
@@ -48,15 +50,17 @@ __device__ inline T warp_frobenius(const T* A, int k, int ls) {
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return sqrt(s);
+  return fast_sqrt(s);
 }
 
 // S: k x k symmetric (row stride ls), overwritten by its eigenvalues on the
 // diagonal; Vm: k x k (row stride ls) receives the eigenvectors as columns
 // (Vm is set to I first unless keep_v).  k <= 32.  All 32 lanes must call it.
+// Returns the number of sweeps that applied at least one rotation (0: S was
+// already diagonal to the tolerance and Vm is the identity / unchanged).
 template <typename T>
-__device__ inline void warp_jacobi(T* S, T* Vm, int k, int ls, JacobiScratchT<T>& js, T tol_abs, int max_sweeps = 40,
-                                   bool keep_v = false) {
+__device__ inline int warp_jacobi(T* S, T* Vm, int k, int ls, JacobiScratchT<T>& js, T tol_abs, int max_sweeps = 40,
+                                  bool keep_v = false) {
   const int lane = threadIdx.x & 31;
   if (!keep_v)
     for (int i = lane; i < k * k; i += 32) {
@@ -67,6 +71,7 @@ __device__ inline void warp_jacobi(T* S, T* Vm, int k, int ls, JacobiScratchT<T>
   const T eps = jacobi_eps<T>();
   const int ne = (k + 1) & ~1;
   const int np = ne / 2;
+  int rotated = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     bool any = false;
     for (int round = 0; round < ne - 1; ++round) {
@@ -88,15 +93,15 @@ __device__ inline void warp_jacobi(T* S, T* Vm, int k, int ls, JacobiScratchT<T>
             // and c = 1 - t^2 / 2 are exact to O(u^4) (series of the textbook formulas),
             // which saves the square roots; otherwise use the textbook formulas.
             const T den = aqq - app;
-            const T u = (fabs(den) > (T)0) ? apq / den : (T)1;
+            const T u = (fabs(den) > (T)0) ? apq * fast_rcp(den) : (T)1;
             if (fabs(u) < small_rot<T>()) {
               const T tt = u * (1 - u * u);
               c = 1 - (T)0.5 * tt * tt;
               s = tt * c;
             } else {
-              const T tau = den / (2 * apq);
-              const T tt = (tau >= 0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt(1 + tau * tau));
-              c = 1 / sqrt(1 + tt * tt);
+              const T tau = den * fast_rcp(2 * apq);
+              const T tt = (tau >= 0 ? (T)1 : (T)-1) * fast_rcp(fabs(tau) + fast_sqrt(1 + tau * tau));
+              c = fast_rsqrt(1 + tt * tt);
               s = tt * c;
             }
           }
@@ -144,7 +149,9 @@ __device__ inline void warp_jacobi(T* S, T* Vm, int k, int ls, JacobiScratchT<T>
       __syncwarp();
     }
     if (!any) break;
+    ++rotated;
   }
+  return rotated;
 }
 
 // Eigendecomposition of a k x k symmetric FP64 matrix (k <= 32) in two

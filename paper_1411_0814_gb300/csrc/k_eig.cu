@@ -28,6 +28,9 @@ namespace rsm {
 constexpr int BS = 32;  // block size of the FP32 factorisation
 constexpr int kConvFlag = 40;   // stats[40] != 0: the block iteration of this problem has converged
 constexpr double kConvTol = 1e-12;  // converged when max ||R_j|| <= kConvTol * (theta_{r+1} - theta_r)
+constexpr double kStallTol = 1e-10;  // ... or when it stops falling (rounding floor) below kStallTol * gap
+constexpr int kPrevRes = 41;         // stats[41]: max ||R_j|| at the previous check
+constexpr int kIterCount = 43;       // stats[43]: block iterations run so far
 
 __device__ __forceinline__ int64_t npad_of(const ProbDesc& d) { return (int64_t)d.nblk * BS; }
 
@@ -41,13 +44,17 @@ __device__ __forceinline__ T* Dinvof(const ProbDesc& d) { return static_cast<T*>
 // ------------------------------------------------------------------ A = M + tau I (padded with I)
 template <typename T>
 __global__ void __launch_bounds__(256) k_eig_prep(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
-                                                 int nprob, double shift_rel) {
+                                                 int nprob, double shift_rel, int iter0) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= off[nprob]) return;
   const int p = find_problem(off, nprob, g);
   const ProbDesc& d = descs[p];
   const int64_t e = g - off[p];
-  if (e == 0) d.stats[kConvFlag] = 0.0;
+  if (e == 0) {
+    d.stats[kConvFlag] = 0.0;
+    d.stats[kPrevRes] = 0.0;
+    d.stats[kIterCount] = (double)iter0;  // the unchecked leading steps
+  }
   const int64_t np = npad_of(d);
   const int64_t i = e / np, j = e % np;
   const double mean = (double)d.counters[0] * d.n_minor / (double)d.n;
@@ -61,51 +68,59 @@ __global__ void __launch_bounds__(256) k_eig_prep(const ProbDesc* __restrict__ d
 }
 
 // ------------------------------------------------------------------ Cholesky, step k
-// Factor the diagonal block and invert the factor; one thread per entry (32 x 32).
-// Step j: one thread takes the square root and reciprocal of the pivot, the
-// column-j threads scale, and the trailing threads update.  The inverse is
-// formed one column per warp by forward substitution with warp reductions.
+// Factor the 32 x 32 diagonal block and invert the factor with one warp, all in
+// registers: lane i holds row i.  Step j takes the pivot from lane j, scales
+// column j, and updates the trailing columns with L[c][j] fetched by shuffle
+// from lane c (fully unrolled, so every register index is a constant).  The
+// inverse X = L^-1 is formed row by row: once row t is final on lane t it is
+// broadcast and every later row adds L[i][t] X[t][.] (forward substitution).
 template <typename T>
-__global__ void __launch_bounds__(1024) k_potrf(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
-                                               int nprob, int k) {
-  __shared__ T a[BS][BS + 1];
+__global__ void __launch_bounds__(32) k_potrf(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
+                                             int nprob, int k) {
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
   const int64_t np = npad_of(d);
-  const int i = threadIdx.x / BS, c = threadIdx.x % BS;  // row, column
+  const int lane = threadIdx.x;
   T* A = F1of<T>(d) + (int64_t)k * BS * np + (int64_t)k * BS;
-  a[i][c] = A[(int64_t)i * np + c];
-  __syncthreads();
-  __shared__ T piv;
-  for (int j = 0; j < BS; ++j) {
-    if (threadIdx.x == 0) {
-      T dj = a[j][j];
-      if (!(dj > (T)0)) {  // not positive definite at this precision: flag and continue with a tiny pivot
-        atomicAdd(&d.counters[3], 1ull);
-        dj = (T)1e-30;
-      }
-      const T s = sqrt(dj);
-      a[j][j] = s;
-      piv = (T)1 / s;
-    }
-    __syncthreads();
-    if (c == j && i > j) a[i][j] *= piv;
-    __syncthreads();
-    if (c > j && c <= i) a[i][c] -= a[i][j] * a[c][j];
-    __syncthreads();
-  }
-  // inverse of the lower-triangular factor: warp w computes column w (lane t holds entry t)
-  const int col = threadIdx.x / 32, lane = threadIdx.x % 32;
-  T mine = (T)0;
-  for (int r = 0; r < BS; ++r) {
-    T term = (lane >= col && lane < r) ? a[r][lane] * mine : (T)0;
+  T a[BS];
 #pragma unroll
-    for (int o = 16; o; o >>= 1) term += __shfl_xor_sync(0xffffffffu, term, o);
-    if (lane == r) mine = (r < col) ? (T)0 : (((r == col) ? (T)1 : (T)0) - term) / a[r][r];
+  for (int c = 0; c < BS; ++c) a[c] = A[(int64_t)lane * np + c];
+  bool bad = false;
+  T rinv = (T)1;  // 1 / L[lane][lane]
+#pragma unroll
+  for (int j = 0; j < BS; ++j) {
+    T piv = __shfl_sync(0xffffffffu, a[j], j);
+    if (!(piv > (T)0)) {  // not positive definite at this precision: flag, continue with a tiny pivot
+      bad = true;
+      piv = (T)1e-30;
+    }
+    const T dj = sqrt(piv);
+    const T ij = (T)1 / dj;
+    if (lane == j) rinv = ij;
+    a[j] = lane > j ? a[j] * ij : (lane == j ? dj : (T)0);
+#pragma unroll
+    for (int c = j + 1; c < BS; ++c) a[c] = fma(-a[j], __shfl_sync(0xffffffffu, a[j], c), a[c]);
+  }
+  if (bad && lane == 0) atomicAdd(&d.counters[3], 1ull);
+  T x[BS];
+#pragma unroll
+  for (int c = 0; c < BS; ++c) x[c] = (T)0;
+#pragma unroll
+  for (int t = 0; t < BS; ++t) {
+    const bool me = lane == t;
+#pragma unroll
+    for (int c = 0; c < t; ++c) x[c] = me ? -x[c] * rinv : x[c];
+    x[t] = me ? rinv : x[t];
+    const T lit = lane > t ? a[t] : (T)0;  // L[lane][t] for the rows still open
+#pragma unroll
+    for (int c = 0; c <= t; ++c) x[c] = fma(lit, __shfl_sync(0xffffffffu, x[c], t), x[c]);
   }
   T* D = Dinvof<T>(d) + (int64_t)k * BS * BS;
-  D[lane * BS + col] = mine;  // entry (lane, col) of inv(L_kk)
-  A[(int64_t)i * np + c] = (c <= i) ? a[i][c] : (T)0;
+#pragma unroll
+  for (int c = 0; c < BS; ++c) {
+    A[(int64_t)lane * np + c] = c <= lane ? a[c] : (T)0;
+    D[lane * BS + c] = c <= lane ? x[c] : (T)0;  // entry (lane, c) of inv(L_kk)
+  }
 }
 
 // 32 x 32 x 32 product helper: each of 256 threads owns 4 outputs (row ty + 8s, column tx).
@@ -372,8 +387,10 @@ __global__ void __launch_bounds__(256) k_split_sum(const ProbDesc* __restrict__ 
   d.MX[e] = s;
 }
 
-// Partial Gram sums over chunks of kChunk rows: part[chunk] = [X^T X | X^T MX] (2 kx^2 values).
+// Partial Gram sums over chunks of kChunk rows: part[chunk] = [X^T X | X^T MX]
+// (2 kx^2 values; the second half only when WITH_H).
 constexpr int kChunk = 64;
+template <bool WITH_H>
 __global__ void __launch_bounds__(256) k_xtx(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                             int nprob, double* __restrict__ part_base, const int64_t* __restrict__ part_off) {
   extern __shared__ double xtx_smem[];
@@ -388,11 +405,12 @@ __global__ void __launch_bounds__(256) k_xtx(const ProbDesc* __restrict__ descs,
   for (int e = threadIdx.x; e < kChunk * kx; e += 256) {
     const int64_t i = i0 + e / kx;
     xs[e] = i < d.n ? d.X[i0 * kx + e] : 0.0;
-    ys[e] = i < d.n ? d.MX[i0 * kx + e] : 0.0;
+    if (WITH_H) ys[e] = i < d.n ? d.MX[i0 * kx + e] : 0.0;
   }
   __syncthreads();
   double* part = part_base + part_off[p] + chunk * 2 * kx * kx;
-  for (int e = threadIdx.x; e < 2 * kx * kx; e += 256) {
+  const int outs = (WITH_H ? 2 : 1) * kx * kx;
+  for (int e = threadIdx.x; e < outs; e += 256) {
     const int which = e / (kx * kx), ab = e % (kx * kx), a = ab / kx, b = ab % kx;
     const double* y = which == 0 ? xs : ys;
     double s0 = 0.0, s1 = 0.0;
@@ -404,272 +422,272 @@ __global__ void __launch_bounds__(256) k_xtx(const ProbDesc* __restrict__ descs,
   }
 }
 
-// Lane-parallel shifted Cholesky S + s I = C C^T in place (lower triangle),
-// s = 1e-15 trace(S): keeps the factor defined when the block is numerically
-// rank deficient (shifted CholeskyQR).  kx <= 32, lane i owns row i.
-__device__ inline void warp_chol_shifted(double (*S)[kMaxL + 1], int kx) {
+// ------------------------------------------------------------------ small dense algebra (one CTA per problem)
+constexpr int kLs = kMaxL + 1;
+constexpr int kSmallThreads = 128;  // four warps: the FP64 products use all four schedulers
+typedef double DRow[kLs];
+typedef float FRow[kLs];
+
+// Sum the per-chunk partials in a fixed order: S = X^T X (and H = X^T M X).
+__device__ inline void reduce_partials(const ProbDesc& d, const double* part, DRow* S, DRow* H, int kx) {
+  const int64_t nchunk = (d.n + kChunk - 1) / kChunk;
+  for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) {
+    double s = 0.0, h = 0.0;
+#pragma unroll 4
+    for (int64_t c = 0; c < nchunk; ++c) {
+      s += part[c * 2 * kx * kx + e];
+      if (H) h += part[c * 2 * kx * kx + kx * kx + e];
+    }
+    S[e / kx][e % kx] = s;
+    if (H) H[e / kx][e % kx] = h;
+  }
+}
+
+// C = op(A) B for kx x kx blocks in shared memory, all threads of the CTA.
+__device__ inline void small_prod(DRow* C, const DRow* A, bool transA, const DRow* B, int kx) {
+  for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) {
+    const int a = e / kx, b = e % kx;
+    double s = 0.0;
+    for (int t = 0; t < kx; ++t) s = fma(transA ? A[t][a] : A[a][t], B[t][b], s);
+    C[a][b] = s;
+  }
+}
+
+// Shifted Cholesky S + s I = C C^T in place (lower triangle), s = shift_rel
+// trace(S): keeps the factor defined when the block is numerically rank
+// deficient (shifted CholeskyQR).  One warp, lane i owns row i; rdiag[j] = 1 / C_jj.
+template <typename CT>
+__device__ inline void warp_chol_shifted(CT (*S)[kLs], CT* rdiag, int kx, CT shift_rel) {
   const int lane = threadIdx.x & 31;
-  double trS = 0.0;
+  CT trS = 0;
   for (int j = 0; j < kx; ++j) trS += S[j][j];
   __syncwarp();
-  if (lane < kx) S[lane][lane] += 1e-15 * trS;
+  if (lane < kx) S[lane][lane] += shift_rel * trS;
   __syncwarp();
   for (int j = 0; j < kx; ++j) {
-    double v = S[j][j];
-    v = v > 0.0 ? sqrt(v) : 1e-300;
-    const double rv = 1.0 / v;
+    CT v = S[j][j];
+    v = v > (CT)0 ? fast_sqrt(v) : (CT)1e-30;
+    const CT rv = fast_rcp(v);
     __syncwarp();
-    if (lane == j) S[j][j] = v;
+    if (lane == j) {
+      S[j][j] = v;
+      rdiag[j] = rv;
+    }
     if (lane > j && lane < kx) S[lane][j] *= rv;
     __syncwarp();
     if (lane > j && lane < kx) {
-      const double lij = S[lane][j];
+      const CT lij = S[lane][j];
       for (int c = j + 1; c <= lane; ++c) S[lane][c] -= lij * S[c][j];
     }
     __syncwarp();
   }
-  for (int e = lane; e < kx * kx; e += 32)
-    if (e / kx < e % kx) S[e / kx][e % kx] = 0.0;
-  __syncwarp();
 }
 
-// One warp per problem.  Reduce the partials (fixed order) into S = X^T X and
-// H = X^T M X, factor S + s I = C C^T (shifted CholeskyQR), and write
-// small = [Q | H' | theta] with X Q orthonormal and H' = Q^T H Q.
-// Intermediate steps (FINAL = false) stop there (Q = C^-T): the block
-// iteration X <- X - T (M X - X H') only needs the subspace to converge, and
-// any basis of it gives the same fixed point.  With the FP32 factor they run
-// in FP32, enough for an orthonormalisation that the next step repeats.
-// The final step (FINAL = true) also diagonalises H' (FP32 Jacobi + FP64
-// polish): Q = C^-T Q', H' = diag(theta), columns by ascending Ritz value.
-constexpr int kLs = kMaxL + 1;
-constexpr size_t kRRSmem = sizeof(double) * 4 * kMaxL * kLs + sizeof(float) * 4 * kMaxL * kLs;
+// Q = C^-T (upper triangular) by back substitution, column c per thread.
+template <typename CT>
+__device__ inline void inv_transpose_factor(const CT (*C)[kLs], const CT* rdiag, CT (*Q)[kLs], int kx) {
+  for (int c = threadIdx.x; c < kx; c += kSmallThreads)
+    for (int i = kx - 1; i >= 0; --i) {
+      CT v = (i == c) ? (CT)1 : (CT)0;
+      for (int t = i + 1; t < kx; ++t) v -= C[t][i] * Q[t][c];
+      Q[i][c] = (i > c) ? (CT)0 : v * rdiag[i];
+    }
+}
 
-template <bool FINAL, typename CT>
-__global__ void __launch_bounds__(32) k_rayleigh_ritz(const ProbDesc* __restrict__ descs, int nprob,
-                                                     const double* __restrict__ part_base,
-                                                     const int64_t* __restrict__ part_off) {
+// Orthonormalisation step of the subspace iteration: S = X^T X (FP64 partial
+// sums), S + s I = C C^T in precision CT, small[0 .. kx^2) = Q = C^-T so that
+// X Q has orthonormal columns.
+template <typename CT>
+__global__ void __launch_bounds__(kSmallThreads) k_orth(const ProbDesc* __restrict__ descs, int nprob,
+                                                      const double* __restrict__ part_base,
+                                                      const int64_t* __restrict__ part_off) {
+  __shared__ CT S[kMaxL][kLs], Q[kMaxL][kLs];
+  __shared__ DRow Sd[kMaxL];
+  __shared__ CT rdiag[kMaxL];
+  const int p = blockIdx.x;
+  if (p >= nprob) return;
+  const ProbDesc& d = descs[p];
+  const int kx = d.kx;
+  reduce_partials(d, part_base + part_off[p], Sd, nullptr, kx);
+  __syncthreads();
+  for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) S[e / kx][e % kx] = (CT)Sd[e / kx][e % kx];
+  __syncthreads();
+  if (threadIdx.x < 32) warp_chol_shifted<CT>(S, rdiag, kx, (CT)(sizeof(CT) == 8 ? 1e-15 : 1e-6));
+  __syncthreads();
+  inv_transpose_factor<CT>(S, rdiag, Q, kx);
+  __syncthreads();
+  for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) d.small[e] = (double)Q[e / kx][e % kx];
+}
+
+// Rayleigh-Ritz step of the FP64 block iteration, one CTA per problem.
+// Reduce S = X^T X and H = X^T M X, factor S + s I = C C^T (FP64), Q1 = C^-T,
+// H1 = Q1^T H Q1.  Then, with FP64 work kept to a few kx^3 products (FP64
+// issues far slower than FP32 here, and an FP64 Jacobi sweep costs tens of
+// microseconds on one warp):
+//  - FP32 Jacobi on H1 gives eigenvectors to FP32 accuracy, sorted by Ritz value;
+//  - two Lowdin steps Q2 <- Q2 (3I - Q2^T Q2) / 2 make them orthogonal in FP64;
+//  - B = Q2^T H1 Q2 is diagonal up to the FP32 error; what matters is the
+//    coupling B12 between the r wanted and the kx - r other columns, which a
+//    first-order rotation removes: G = I + A with A_pq = B_pq / (B_qq - B_pp)
+//    (p < r <= q, A_qp = -A_pq; the gap theta_{r+1} - theta_r keeps it
+//    defined), made orthogonal by one Lowdin step.  The coupling left is
+//    second order, ||B12||^2 / gap.  Mixing inside the wanted (or the other)
+//    block is harmless: only the two subspaces matter.
+// Writes small = [Q | H' | theta] with Q = Q1 Q2 G, H' = Q^T H Q (FP64) and
+// theta = diag(H') in ascending order of the FP32 Ritz values.
+constexpr size_t kRRSmem = sizeof(DRow) * kMaxL * 7 + sizeof(FRow) * kMaxL * 2;
+
+__device__ inline void lowdin_step(DRow* Q, DRow* W1, DRow* W2, int kx) {  // Q <- Q (3I - Q^T Q) / 2
+  small_prod(W1, Q, true, Q, kx);
+  __syncthreads();
+  for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) {
+    const int a = e / kx, b = e % kx;
+    double s = 0.0;
+    for (int t = 0; t < kx; ++t) s = fma(Q[a][t], ((t == b) ? 3.0 : 0.0) - W1[t][b], s);
+    W2[a][b] = 0.5 * s;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) Q[e / kx][e % kx] = W2[e / kx][e % kx];
+  __syncthreads();
+}
+
+__device__ inline void sym_congruence(DRow* out, const DRow* Q, const DRow* A, DRow* W, int kx) {  // out = Q^T A Q
+  small_prod(W, A, false, Q, kx);
+  __syncthreads();
+  for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) {
+    const int a = e / kx, b = e % kx;
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    double s = 0.0;
+    for (int t = 0; t < kx; ++t) s = fma(Q[t][lo], W[t][hi], s);
+    out[a][b] = s;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSmallThreads) k_rr64(const ProbDesc* __restrict__ descs, int nprob,
+                                                      const double* __restrict__ part_base,
+                                                      const int64_t* __restrict__ part_off) {
   extern __shared__ __align__(16) unsigned char rr_smem[];
-  typedef double DRow[kLs];
-  typedef float FRow[kLs];
   DRow* S = reinterpret_cast<DRow*>(rr_smem);
   DRow* H = S + kMaxL;
-  DRow* Vq = H + kMaxL;
-  DRow* T = Vq + kMaxL;
-  FRow* Sf = reinterpret_cast<FRow*>(T + kMaxL);
+  DRow* Q1 = H + kMaxL;
+  DRow* W1 = Q1 + kMaxL;
+  DRow* H1 = W1 + kMaxL;
+  DRow* Q2 = H1 + kMaxL;
+  DRow* W2 = Q2 + kMaxL;
+  FRow* Sf = reinterpret_cast<FRow*>(W2 + kMaxL);
   FRow* Vf = Sf + kMaxL;
-  FRow* Sj = Vf + kMaxL;
-  FRow* Vj = Sj + kMaxL;
   __shared__ JacobiScratchT<float> jsf;
-  __shared__ JacobiScratchT<double> jsd;
   __shared__ int order[kMaxL];
+  __shared__ double rdiag[kMaxL];
+  __shared__ int rotated, coupled;
   const int p = blockIdx.x;
   if (p >= nprob) return;
   const ProbDesc& d = descs[p];
   if (d.stats[kConvFlag] != 0.0) return;
-  const int kx = d.kx, lane = threadIdx.x;
-  const int64_t nchunk = (d.n + kChunk - 1) / kChunk;
-  const double* part = part_base + part_off[p];
-  for (int e = lane; e < kx * kx; e += 32) {
-    double s = 0.0, h = 0.0;
-#pragma unroll 8
-    for (int64_t c = 0; c < nchunk; ++c) {
-      s += part[c * 2 * kx * kx + e];
-      h += part[c * 2 * kx * kx + kx * kx + e];
-    }
-    S[e / kx][e % kx] = s;
-    H[e / kx][e % kx] = h;
-  }
-  __syncwarp();
-  double* out = d.small;
-  if (!FINAL) {
-    // (1) shifted Cholesky of S in precision CT (lane i owns row i); CT is the
-    // precision of the preconditioner's factor: FP64 when a step may amplify
-    // the wanted directions by ~1/tau ~ 1e11, FP32 otherwise
-    CT (*Sc)[kLs];
-    CT (*Vc)[kLs];
-    if constexpr (sizeof(CT) == 8) {
-      Sc = S;
-      Vc = Vq;
-    } else {
-      Sc = Sf;
-      Vc = Vf;
-    }
-    CT trS = 0;
-    for (int j = 0; j < kx; ++j) trS += (CT)S[j][j];
-    if constexpr (sizeof(CT) != 8)
-      for (int e = lane; e < kx * kx; e += 32) Sc[e / kx][e % kx] = (CT)S[e / kx][e % kx];
-    __syncwarp();
-    if (lane < kx) Sc[lane][lane] += (CT)(sizeof(CT) == 8 ? 1e-15 : 1e-6) * trS;
-    __syncwarp();
-    for (int j = 0; j < kx; ++j) {
-      CT v = Sc[j][j];
-      v = v > (CT)0 ? sqrt(v) : (CT)1e-30;
-      const CT rv = (CT)1 / v;
-      __syncwarp();
-      if (lane == j) Sc[j][j] = v;
-      if (lane > j && lane < kx) Sc[lane][j] *= rv;
-      __syncwarp();
-      if (lane > j && lane < kx) {
-        const CT lij = Sc[lane][j];
-        for (int c = j + 1; c <= lane; ++c) Sc[lane][c] -= lij * Sc[c][j];
-      }
-      __syncwarp();
-    }
-    // (2) Q1 = C^-T (upper triangular): column c solves C^T q = e_c
-    for (int c = lane; c < kx; c += 32)
-      for (int i = kx - 1; i >= 0; --i) {
-        CT v = (i == c) ? (CT)1 : (CT)0;
-        for (int t = i + 1; t < kx; ++t) v -= Sc[t][i] * Vc[t][c];
-        Vc[i][c] = (i > c) ? (CT)0 : v / Sc[i][i];
-      }
-    __syncwarp();
-    if constexpr (sizeof(CT) != 8) {
-      // FP32 factor: the Ritz rotation of an intermediate step is all FP32.
-      // (3) H1 = Q1^T H Q1 (into Sj)
-      for (int e = lane; e < kx * kx; e += 32) {
-        const int a = e / kx, b = e % kx;
-        float s = 0.f;
-        for (int t = 0; t < kx; ++t) s = fmaf((float)H[a][t], Vc[t][b], s);
-        T[a][b] = s;
-      }
-      __syncwarp();
-      float fro2 = 0.f;
-      for (int e = lane; e < kx * kx; e += 32) {
-        const int a = e / kx, b = e % kx;
-        float s = 0.f;
-        for (int t = 0; t < kx; ++t) s = fmaf(Vc[t][a], (float)T[t][b], s);
-        Sj[a][b] = s;
-        fro2 += s * s;
-      }
-#pragma unroll
-      for (int o = 16; o; o >>= 1) fro2 += __shfl_xor_sync(0xffffffffu, fro2, o);
-      __syncwarp();
-      // (4) Ritz rotation Q2 from Jacobi; Q = Q1 Q2, H_out = Q2^T H1 Q2 (the rotated Sj)
-      warp_jacobi<float>(&Sj[0][0], &Vj[0][0], kx, kLs, jsf, 4.f * FLT_EPSILON * sqrtf(fro2));
-      for (int e = lane; e < kx * kx; e += 32) {
-        const int a = e / kx, b = e % kx;
-        float q = 0.f;
-        for (int t = 0; t < kx; ++t) q = fmaf(Vc[a][t], Vj[t][b], q);
-        out[e] = (double)q;
-        out[kx * kx + e] = (double)Sj[a][b];
-      }
-      return;
-    } else {
-      // FP64 factor: steps may amplify the wanted directions by ~1e11, keep the
-      // rotation in FP64 products of the FP64 basis.
-      // (3) H1 = Q1^T H Q1 in FP64 (into S, free now)
-      for (int e = lane; e < kx * kx; e += 32) {
-        const int a = e / kx, b = e % kx;
-        double s = 0.0;
-        for (int t = 0; t < kx; ++t) s = fma(H[a][t], (double)Vc[t][b], s);
-        T[a][b] = s;
-      }
-      __syncwarp();
-      for (int e = lane; e < kx * kx; e += 32) {
-        const int a = e / kx, b = e % kx;
-        double s = 0.0;
-        for (int t = 0; t < kx; ++t) s = fma((double)Vc[t][a], T[t][b], s);
-        Sj[a][b] = (float)s;
-        S[a][b] = s;
-      }
-      __syncwarp();
-      // (4) Ritz rotation from FP32 Jacobi of H1; Q = Q1 Q2 and H_out = Q2^T H1 Q2 in FP64
-      const double fro = warp_frobenius(&S[0][0], kx, kLs);
-      warp_jacobi<float>(&Sj[0][0], &Vj[0][0], kx, kLs, jsf, (float)(4.0 * FLT_EPSILON * fro));
-      for (int e = lane; e < kx * kx; e += 32) {
-        const int a = e / kx, b = e % kx;
-        double q = 0.0, h = 0.0;
-        for (int t = 0; t < kx; ++t) {
-          q = fma((double)Vc[a][t], (double)Vj[t][b], q);
-          h = fma(S[a][t], (double)Vj[t][b], h);
+  const int kx = d.kx, r = d.r, tid = threadIdx.x;
+  reduce_partials(d, part_base + part_off[p], S, H, kx);
+  __syncthreads();
+  if (tid < 32) warp_chol_shifted<double>(S, rdiag, kx, 1e-15);
+  __syncthreads();
+  inv_transpose_factor<double>(S, rdiag, Q1, kx);
+  __syncthreads();
+  sym_congruence(H1, Q1, H, W1, kx);  // H1 = Q1^T H Q1
+  // FP32 Jacobi of H1, then the eigenvector columns in ascending order of the Ritz values
+  for (int e = tid; e < kx * kx; e += kSmallThreads) Sf[e / kx][e % kx] = (float)H1[e / kx][e % kx];
+  __syncthreads();
+  if (tid < 32) {
+    const float fro = warp_frobenius(&Sf[0][0], kx, kLs);
+    const int sweeps = warp_jacobi<float>(&Sf[0][0], &Vf[0][0], kx, kLs, jsf, 4.f * FLT_EPSILON * fro);
+    if (tid == 0) {
+      rotated = sweeps;
+      coupled = 0;
+      for (int i = 0; i < kx; ++i) order[i] = i;
+      for (int a = 1; a < kx; ++a) {
+        const int v = order[a];
+        int b = a - 1;
+        while (b >= 0 && Sf[order[b]][order[b]] > Sf[v][v]) {
+          order[b + 1] = order[b];
+          --b;
         }
-        T[a][b] = q;
-        H[a][b] = h;
+        order[b + 1] = v;
       }
-      __syncwarp();
-      for (int e = lane; e < kx * kx; e += 32) {
-        const int a = e / kx, b = e % kx;
-        double s = 0.0;
-        for (int t = 0; t < kx; ++t) s = fma((double)Vj[t][a], H[t][b], s);
-        out[e] = T[a][b];
-        out[kx * kx + e] = s;
-      }
-      return;
     }
   }
-  warp_chol_shifted(S, kx);
-  // T = C^-1 H  (forward substitution, one column per lane)
-  for (int c = lane; c < kx; c += 32)
-    for (int i = 0; i < kx; ++i) {
-      double v = 0.5 * (H[i][c] + H[c][i]);
-      for (int t = 0; t < i; ++t) v -= S[i][t] * T[t][c];
-      T[i][c] = v / S[i][i];
-    }
-  __syncwarp();
-  // H' = T C^-T: row c of H' solves C z = (row c of T)
-  for (int c = lane; c < kx; c += 32)
-    for (int i = 0; i < kx; ++i) {
-      double v = T[c][i];
-      for (int t = 0; t < i; ++t) v -= S[i][t] * Vq[c][t];
-      Vq[c][i] = v / S[i][i];
-    }
-  __syncwarp();
-  for (int e = lane; e < kx * kx; e += 32) {
+  __syncthreads();
+  for (int e = tid; e < kx * kx; e += kSmallThreads) Q2[e / kx][e % kx] = (double)Vf[e / kx][order[e % kx]];
+  __syncthreads();
+  if (rotated) {  // FP32 rotations: make them orthogonal in FP64, then B = Q2^T H1 Q2
+    lowdin_step(Q2, W1, W2, kx);
+    lowdin_step(Q2, W1, W2, kx);
+    sym_congruence(S, Q2, H1, W1, kx);  // into S: the factor is no longer needed
+  } else {  // H1 was already diagonal to FP32 accuracy: Q2 is a permutation, B a reordering of H1
+    for (int e = tid; e < kx * kx; e += kSmallThreads) S[e / kx][e % kx] = H1[order[e / kx]][order[e % kx]];
+    __syncthreads();
+  }
+  // first-order decoupling of the wanted block: G = I + A (into W2), then one Lowdin step
+  for (int e = tid; e < kx * kx; e += kSmallThreads) {
     const int a = e / kx, b = e % kx;
-    H[a][b] = 0.5 * (Vq[a][b] + Vq[b][a]);
-  }
-  __syncwarp();
-  warp_eig_mixed(&H[0][0], &Vq[0][0], &Sf[0][0], &Vf[0][0], &T[0][0], kx, kLs, jsf, jsd);
-  if (lane == 0) {  // ascending order of the Ritz values
-    for (int i = 0; i < kx; ++i) order[i] = i;
-    for (int a = 1; a < kx; ++a) {
-      const int v = order[a];
-      int b = a - 1;
-      while (b >= 0 && H[order[b]][order[b]] > H[v][v]) {
-        order[b + 1] = order[b];
-        --b;
-      }
-      order[b + 1] = v;
+    double g = (a == b) ? 1.0 : 0.0;
+    if (a < r && b >= r) {
+      g = S[a][b] * rcp64(S[b][b] - S[a][a]);
+    } else if (a >= r && b < r) {
+      g = -S[b][a] * rcp64(S[a][a] - S[b][b]);
     }
+    if (a != b && fabs(g) > 1e-9) atomicOr(&coupled, 1);
+    W2[a][b] = g;
   }
-  __syncwarp();
-  // Q = C^-T Q'  (back substitution, one column per lane)
-  for (int c = lane; c < kx; c += 32) {
-    const int oc = order[c];
-    for (int i = kx - 1; i >= 0; --i) {
-      double v = Vq[i][oc];
-      for (int t = i + 1; t < kx; ++t) v -= S[t][i] * T[t][c];
-      T[i][c] = v / S[i][i];
+  __syncthreads();
+  for (int e = tid; e < kx * kx; e += kSmallThreads) H1[e / kx][e % kx] = W2[e / kx][e % kx];  // G in H1
+  __syncthreads();
+  // I + A is orthogonal up to ||A||^2: below 1e-18 it needs no Lowdin step
+  if (coupled) lowdin_step(H1, W1, W2, kx);
+  if (rotated) {
+    small_prod(W1, Q2, false, H1, kx);  // W1 = Q2 G
+  } else {
+    for (int e = tid; e < kx * kx; e += kSmallThreads) W1[e / kx][e % kx] = H1[e / kx][e % kx];
+    __syncthreads();
+    for (int e = tid; e < kx * kx; e += kSmallThreads) {  // W1 = P G (P the permutation Q2): rows by order
+      const int a = e / kx, b = e % kx;
+      W2[order[a]][b] = W1[a][b];
     }
+    __syncthreads();
+    for (int e = tid; e < kx * kx; e += kSmallThreads) W1[e / kx][e % kx] = W2[e / kx][e % kx];
   }
-  __syncwarp();
-  for (int e = lane; e < kx * kx; e += 32) {
-    const int a = e / kx, b = e % kx;
-    out[e] = T[a][b];
-    out[kx * kx + e] = (a == b) ? H[order[a]][order[a]] : 0.0;
+  __syncthreads();
+  small_prod(Q2, Q1, false, W1, kx);  // Q = Q1 Q2 G (into Q2)
+  __syncthreads();
+  sym_congruence(W2, Q2, H, W1, kx);  // H' = Q^T H Q
+  double* out = d.small;
+  for (int e = tid; e < kx * kx; e += kSmallThreads) {
+    out[e] = Q2[e / kx][e % kx];
+    out[kx * kx + e] = W2[e / kx][e % kx];
   }
-  for (int c = lane; c < kx; c += 32) out[2 * kx * kx + c] = H[order[c]][order[c]];
+  for (int c = tid; c < kx; c += kSmallThreads) out[2 * kx * kx + c] = W2[c][c];
 }
 
-// X <- X Q, MX <- MX Q, R = MX - X H'.  A CTA takes 8 rows; thread (row, column)
-// computes one entry of each product from rows staged in shared memory.
+// X <- X Q (FULL: also MX <- MX Q and R = MX - X H').  A CTA takes 8 rows;
+// thread (row, column) computes one entry of each product from rows staged in
+// shared memory.
 constexpr int kRotRows = 8;
+constexpr int kResSlot = 7;  // R slot of the per-tile residual sums of squares (slots 1..kPSplit: preconditioner parts)
+template <bool FULL>
 __global__ void __launch_bounds__(256) k_rotate(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                int nprob) {
   __shared__ double q[2 * kMaxL * kMaxL];
   __shared__ double xs[kRotRows][kMaxL], ms[kRotRows][kMaxL], nxs[kRotRows][kMaxL];
+  __shared__ double rsq[FULL ? kRotRows : 1][kMaxL];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
   if (d.stats[kConvFlag] != 0.0) return;  // converged: the rest of the iteration is skipped
   const int kx = d.kx;
   const int64_t i0 = (blockIdx.x - off[p]) * kRotRows;
-  for (int e = threadIdx.x; e < 2 * kx * kx; e += blockDim.x) q[e] = d.small[e];
+  for (int e = threadIdx.x; e < (FULL ? 2 : 1) * kx * kx; e += blockDim.x) q[e] = d.small[e];
   for (int e = threadIdx.x; e < kRotRows * kx; e += blockDim.x) {
     const int r = e / kx, c = e % kx;
     const int64_t i = i0 + r;
     xs[r][c] = i < d.n ? d.X[i * kx + c] : 0.0;
-    ms[r][c] = i < d.n ? d.MX[i * kx + c] : 0.0;
+    if (FULL) ms[r][c] = i < d.n ? d.MX[i * kx + c] : 0.0;
   }
   __syncthreads();
   const double* H = q + kx * kx;
@@ -680,7 +698,7 @@ __global__ void __launch_bounds__(256) k_rotate(const ProbDesc* __restrict__ des
     double a = 0.0, b = 0.0;
     for (int t = 0; t < kx; ++t) {
       a = fma(xs[r][t], q[t * kx + c], a);
-      b = fma(ms[r][t], q[t * kx + c], b);
+      if (FULL) b = fma(ms[r][t], q[t * kx + c], b);
     }
     nxs[r][c] = a;
     nmx[cnt++] = b;
@@ -691,21 +709,34 @@ __global__ void __launch_bounds__(256) k_rotate(const ProbDesc* __restrict__ des
     const int r = e / kx, c = e % kx;
     const int64_t i = i0 + r;
     const double b = nmx[cnt++];
-    double s = b;
-    for (int t = 0; t < kx; ++t) s = fma(-nxs[r][t], H[t * kx + c], s);
+    double s = 0.0;
     if (i < d.n) {
       d.X[i * kx + c] = nxs[r][c];
-      d.MX[i * kx + c] = b;
-      d.R[i * kx + c] = s;
+      if (FULL) {
+        s = b;
+        for (int t = 0; t < kx; ++t) s = fma(-nxs[r][t], H[t * kx + c], s);
+        d.MX[i * kx + c] = b;
+        d.R[i * kx + c] = s;
+      }
+    }
+    if (FULL) rsq[r][c] = s * s;
+  }
+  if (FULL) {  // this tile's sum of squares per column, for the residual norms (fixed order later)
+    __syncthreads();
+    if (threadIdx.x < kx) {
+      double t = 0.0;
+      for (int r = 0; r < kRotRows; ++r) t += rsq[r][threadIdx.x];
+      d.R[(int64_t)kResSlot * d.n * kx + (blockIdx.x - off[p]) * kx + threadIdx.x] = t;
     }
   }
 }
 
-// X <- X - A^-1 R with A^-1 at precision T (the preconditioner).  Split over the
-// inner dimension: CTA (row tile of 16, part s) writes its partial product to
-// R slot 1 + s; k_precond_apply sums the parts in a fixed order.
+// Product with the preconditioner A^-1 = (M + tau I)^-1 at precision T.  SRC 0:
+// of the residual R (block iteration); SRC 1: of X itself (subspace iteration).
+// Split over the inner dimension: CTA (row tile of 16, part s) writes its
+// partial product to R slot 1 + s; k_precond_apply sums the parts in a fixed order.
 constexpr int kPRows = 16;
-template <typename T>
+template <typename T, int SRC>
 __global__ void __launch_bounds__(256) k_precond(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                 int nprob) {
   __shared__ T ts[kPRows][65];
@@ -715,6 +746,7 @@ __global__ void __launch_bounds__(256) k_precond(const ProbDesc* __restrict__ de
   if (d.stats[kConvFlag] != 0.0) return;  // converged: the rest of the iteration is skipped
   const int64_t n = d.n, np = npad_of(d);
   const int kx = d.kx;
+  const double* src = SRC == 0 ? d.R : d.X;
   const int64_t local = blockIdx.x - off[p];
   const int64_t ntile = (n + kPRows - 1) / kPRows;
   const int split = (int)(local / ntile);
@@ -732,7 +764,7 @@ __global__ void __launch_bounds__(256) k_precond(const ProbDesc* __restrict__ de
     for (int e = threadIdx.x; e < 64 * kx; e += 256) {
       const int r = e / kx, c = e % kx;
       const int64_t j = j0 + r;
-      rs[r][c] = (j < j_end) ? (T)d.R[j * kx + c] : (T)0;
+      rs[r][c] = (j < j_end) ? (T)src[j * kx + c] : (T)0;
     }
     __syncthreads();
 #pragma unroll 8
@@ -750,6 +782,8 @@ __global__ void __launch_bounds__(256) k_precond(const ProbDesc* __restrict__ de
   }
 }
 
+// MODE 0: X <- X - sum of the parts (block iteration); MODE 1: X <- sum of the parts.
+template <int MODE>
 __global__ void __launch_bounds__(256) k_precond_apply(const ProbDesc* __restrict__ descs,
                                                       const int64_t* __restrict__ off, int nprob) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -761,103 +795,105 @@ __global__ void __launch_bounds__(256) k_precond_apply(const ProbDesc* __restric
   const int64_t nk = d.n * d.kx;
   double s = 0.0;
   for (int q = 0; q < kPSplit; ++q) s += d.R[(int64_t)(1 + q) * nk + e];
-  d.X[e] -= s;
+  d.X[e] = MODE == 0 ? d.X[e] - s : s;
 }
 
-// After a polished Rayleigh-Ritz step: largest residual column norm over the r
-// wanted Ritz pairs against the gap theta_{r+1} - theta_r; sets the flag that
-// skips the remaining iterations of the problem.
+// Largest residual column norm ||R_j|| over the r wanted columns, from the
+// per-tile sums of squares of k_rotate (summed in a fixed order).  256 threads:
+// 8 groups split the tiles, lane = column.
+__device__ inline double wanted_residual_norm(const ProbDesc& d) {
+  __shared__ double red[8][32];
+  const int kx = d.kx, r = d.r;
+  const int64_t ntile = (d.n + kRotRows - 1) / kRotRows;
+  const double* pr = d.R + (int64_t)kResSlot * d.n * kx;
+  const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
+  double s = 0.0;
+  if (c < r)
+    for (int64_t t = g; t < ntile; t += 8) s += pr[t * kx + c];
+  red[g][c] = s;
+  __syncthreads();
+  double mx = 0.0;
+  if (threadIdx.x < 32) {
+    double tot = 0.0;
+    for (int k = 0; k < 8; ++k) tot += red[k][c];
+    mx = c < r ? sqrt64(tot) : 0.0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  return mx;  // valid in thread 0
+}
+
+// After a Rayleigh-Ritz step: the largest wanted residual norm against the gap
+// theta_{r+1} - theta_r; sets the flag that skips the remaining iterations.
 __global__ void __launch_bounds__(256) k_conv_check(const ProbDesc* __restrict__ descs, int nprob) {
-  __shared__ double red[256];
   const int p = blockIdx.x;
   if (p >= nprob) return;
   const ProbDesc& d = descs[p];
   if (d.stats[kConvFlag] != 0.0) return;
   const int kx = d.kx, r = d.r;
-  double mx = 0.0;
-  for (int c = 0; c < r; ++c) {
-    double s = 0.0;
-    for (int64_t i = threadIdx.x; i < d.n; i += 256) {
-      const double v = d.R[i * kx + c];
-      s += v * v;
-    }
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 128; o; o >>= 1) {
-      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-      __syncthreads();
-    }
-    mx = fmax(mx, sqrt(red[0]));
-    __syncthreads();
-  }
+  const double mx = wanted_residual_norm(d);
   if (threadIdx.x == 0) {
     const double* th = d.small + 2 * kx * kx;
     const double gap = r < kx ? th[r] - th[r - 1] : 0.0;
-    if (gap > 0.0 && mx <= kConvTol * gap) d.stats[kConvFlag] = 1.0;
+    const double prev = d.stats[kPrevRes];
+    // converged: below the target, or no longer falling (at the FP64 rounding
+    // floor of M X - X Theta) while already below kStallTol * gap
+    const bool stalled = prev > 0.0 && mx > 0.5 * prev && mx <= kStallTol * gap;
+    if (gap > 0.0 && (mx <= kConvTol * gap || stalled)) d.stats[kConvFlag] = 1.0;
+    d.stats[kPrevRes] = mx;
+    d.stats[kIterCount] += 1.0;
   }
 }
 
-// V = first r columns of X (n x r column-major, ldv); eigenvalue estimates; residual norm.
+// V = first r columns of X (n x r column-major, ldv); Ritz values; residual norm.
 __global__ void __launch_bounds__(256) k_eig_finish(const ProbDesc* __restrict__ descs, int nprob) {
-  __shared__ double red[256];
   const int p = blockIdx.x;
   if (p >= nprob) return;
   const ProbDesc& d = descs[p];
   const int kx = d.kx, r = d.r;
-  double mx = 0.0;
-  for (int64_t e = threadIdx.x; e < d.n * r; e += 256) {
-    const int64_t i = e / r;
-    const int c = (int)(e % r);
-    d.V[(int64_t)c * d.ldv + i] = d.X[i * kx + c];
-  }
-  // largest residual column norm among the r wanted Ritz pairs
-  for (int c = 0; c < r; ++c) {
-    double s = 0.0;
-    for (int64_t i = threadIdx.x; i < d.n; i += 256) {
-      const double v = d.R[i * kx + c];
-      s += v * v;
-    }
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 128; o; o >>= 1) {
-      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) mx = fmax(mx, sqrt(red[0]));
-    __syncthreads();
-  }
+  for (int c = 0; c < r; ++c)
+    for (int64_t i = threadIdx.x; i < d.n; i += 256) d.V[(int64_t)c * d.ldv + i] = d.X[i * kx + c];
+  const double mx = wanted_residual_norm(d);
   if (threadIdx.x < kx && threadIdx.x < 32) d.stats[threadIdx.x] = d.small[2 * kx * kx + threadIdx.x];
   if (threadIdx.x == 0) d.stats[34] = mx;
 }
 
 // ------------------------------------------------------------------ launchers
-#define RSM_LAUNCH(kernel, blocks, threads, ...)                   \
-  do {                                                             \
-    if ((blocks) > 0) {                                            \
-      kernel<<<(unsigned)(blocks), threads, 0, s>>>(__VA_ARGS__);  \
-      ++g_kernel_launches;                                         \
-      cudaError_t e_ = cudaGetLastError();                         \
-      if (e_ != cudaSuccess) return e_;                            \
-    }                                                              \
+#define RSM_LAUNCH_SMEM(kernel, blocks, threads, smem, ...)            \
+  do {                                                                \
+    if ((blocks) > 0) {                                               \
+      kernel<<<(unsigned)(blocks), threads, smem, s>>>(__VA_ARGS__);  \
+      ++g_kernel_launches;                                            \
+      cudaError_t e_ = cudaGetLastError();                            \
+      if (e_ != cudaSuccess) return e_;                               \
+    }                                                                 \
   } while (0)
+#define RSM_LAUNCH(kernel, blocks, threads, ...) RSM_LAUNCH_SMEM(kernel, blocks, threads, 0, __VA_ARGS__)
 
 template <typename T>
 static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, cudaStream_t s) {
-  cudaError_t ea = cudaFuncSetAttribute(k_xtx, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(2 * kChunk * kMaxL * sizeof(double)));
-  if (ea == cudaSuccess)
-    ea = cudaFuncSetAttribute(k_rayleigh_ritz<true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRRSmem);
-  if (ea == cudaSuccess)
-    ea = cudaFuncSetAttribute(k_rayleigh_ritz<false, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRRSmem);
+  const int xtx_smem = (int)(2 * kChunk * kMaxL * sizeof(double));
+  cudaError_t ea = cudaFuncSetAttribute(k_xtx<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, xtx_smem);
+  if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_xtx<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, xtx_smem);
+  if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_rr64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRRSmem);
   if (ea != cudaSuccess) return ea;
   const ProbDesc* D = P.descs;
   const int np = P.nprob;
   auto dev = [&](size_t pos) { return P.dT + pos; };
   auto total = [&](size_t pos) { return P.hT[pos + np]; };
-  RSM_LAUNCH(k_eig_prep<T>, (total(P.pad2) + 255) / 256, 256, D, dev(P.pad2), np, shift_rel);
+  // Phase A: subspace iteration X <- orth(A^-1 X) with the factor alone (no
+  // product with M), until span(X) holds the wanted eigenvectors to about the
+  // factor's precision.  The FP64 factor is an almost exact shift-invert whose
+  // steps amplify the wanted directions by up to ~1/tau: two steps, each
+  // orthonormalised twice (shifted CholeskyQR2); three single-pass steps with
+  // the FP32 factor.
+  const int a_iters = sizeof(T) == 8 ? 2 : 3, a_passes = sizeof(T) == 8 ? 2 : 1;
+  auto* precond_x = k_precond<T, 1>;  // A^-1 X
+  auto* precond_r = k_precond<T, 0>;  // A^-1 R
+  RSM_LAUNCH(k_eig_prep<T>, (total(P.pad2) + 255) / 256, 256, D, dev(P.pad2), np, shift_rel, a_iters);
   for (int k = 0; k < P.max_nblk; ++k) {
     const size_t o1 = P.step + (size_t)k * 3 * (np + 1), o2 = o1 + (np + 1), o3 = o2 + (np + 1);
-    RSM_LAUNCH(k_potrf<T>, total(o1), 1024, D, dev(o1), np, k);
+    RSM_LAUNCH(k_potrf<T>, total(o1), 32, D, dev(o1), np, k);
     RSM_LAUNCH(k_panel<T>, total(o2), 256, D, dev(o2), np, k);
     RSM_LAUNCH(k_trail<T>, total(o3), 256, D, dev(o3), np, k);
   }
@@ -869,39 +905,36 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
   }
   RSM_LAUNCH(k_ainv<T>, total(P.tri), 256, D, dev(P.tri), np);
   RSM_LAUNCH(k_init_X, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
-  // The FP64 factor is an almost exact shift-invert: a step can amplify the
-  // wanted directions by ~1/tau, so each step runs the Rayleigh-Ritz pass twice
-  // (the first re-orthonormalises a nearly rank-deficient block).  The closing
-  // pass diagonalises in FP64 (polished); the steps before it in FP32.
-  const int passes = sizeof(T) == 8 ? 2 : 1;
-  // Adaptive: steps before min_iters diagonalise in FP32; from min_iters on every
-  // step ends with the polished FP64 Rayleigh-Ritz and a convergence check, and a
-  // converged problem skips everything after it.  The last step never preconditions.
-  const int min_iters = sizeof(T) == 8 ? 2 : 5;
+  auto orthonormalise = [&]() -> cudaError_t {
+    RSM_LAUNCH_SMEM(k_xtx<false>, total(P.chunk), 256, xtx_smem, D, dev(P.chunk), np, P.part, dev(P.part_off));
+    RSM_LAUNCH(k_orth<T>, np, kSmallThreads, D, np, P.part, dev(P.part_off));
+    RSM_LAUNCH(k_rotate<false>, total(P.rot), 256, D, dev(P.rot), np);
+    return cudaSuccess;
+  };
+  cudaError_t e;
+  for (int it = 0; it < a_iters; ++it) {
+    RSM_LAUNCH(precond_x, total(P.row_tile), 256, D, dev(P.row_tile), np);
+    RSM_LAUNCH(k_precond_apply<1>, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
+    for (int pass = 0; pass < a_passes; ++pass)
+      if ((e = orthonormalise()) != cudaSuccess) return e;
+  }
+  // Phase B: preconditioned block iteration X <- X - A^-1 (M X - X Theta) with
+  // FP64 products with M and an FP64 Rayleigh-Ritz step each time; every step
+  // ends with a convergence check, and a converged problem skips everything
+  // after it.  With the FP64 factor a step can again collapse the block, so X is
+  // re-orthonormalised before each product.  The last step never preconditions.
   for (int it = 0; it <= iters; ++it) {
-    const bool final_rr = it >= min_iters || it == iters;
+    if (sizeof(T) == 8 && it > 0)
+      if ((e = orthonormalise()) != cudaSuccess) return e;
     RSM_LAUNCH(k_gemm_MX, total(P.mx), 256, D, dev(P.mx), np);
     RSM_LAUNCH(k_split_sum, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
-    for (int pass = 0; pass < passes; ++pass) {
-      if (total(P.chunk) > 0) {
-        k_xtx<<<(unsigned)total(P.chunk), 256, 2 * kChunk * kMaxL * sizeof(double), s>>>(D, dev(P.chunk), np, P.part,
-                                                                                        dev(P.part_off));
-        ++g_kernel_launches;
-        if (cudaGetLastError() != cudaSuccess) return cudaErrorLaunchFailure;
-      }
-      if (final_rr && pass == passes - 1) {
-        k_rayleigh_ritz<true, T><<<np, 32, kRRSmem, s>>>(D, np, P.part, dev(P.part_off));
-      } else {
-        k_rayleigh_ritz<false, T><<<np, 32, kRRSmem, s>>>(D, np, P.part, dev(P.part_off));
-      }
-      ++g_kernel_launches;
-      if (cudaGetLastError() != cudaSuccess) return cudaErrorLaunchFailure;
-      RSM_LAUNCH(k_rotate, total(P.rot), 256, D, dev(P.rot), np);
-    }
-    if (final_rr) RSM_LAUNCH(k_conv_check, np, 256, D, np);
+    RSM_LAUNCH_SMEM(k_xtx<true>, total(P.chunk), 256, xtx_smem, D, dev(P.chunk), np, P.part, dev(P.part_off));
+    RSM_LAUNCH_SMEM(k_rr64, np, kSmallThreads, kRRSmem, D, np, P.part, dev(P.part_off));
+    RSM_LAUNCH(k_rotate<true>, total(P.rot), 256, D, dev(P.rot), np);
+    RSM_LAUNCH(k_conv_check, np, 256, D, np);
     if (it < iters) {
-      RSM_LAUNCH(k_precond<T>, total(P.row_tile), 256, D, dev(P.row_tile), np);
-      RSM_LAUNCH(k_precond_apply, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
+      RSM_LAUNCH(precond_r, total(P.row_tile), 256, D, dev(P.row_tile), np);
+      RSM_LAUNCH(k_precond_apply<0>, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
     }
   }
   RSM_LAUNCH(k_eig_finish, np, 256, D, np);

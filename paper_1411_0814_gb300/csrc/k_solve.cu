@@ -29,6 +29,7 @@ __device__ __forceinline__ void pair_of(int q, int r, int& a, int& b) {
   b = a + rem;
 }
 
+template <typename TK>
 __global__ void __launch_bounds__(256) k_build_K(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                 int nprob) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -49,7 +50,7 @@ __global__ void __launch_bounds__(256) k_build_K(const ProbDesc* __restrict__ de
   } else if (qq == P + r) {
     v = 1.0;
   }
-  d.Kmat[e] = v;
+  static_cast<TK*>(static_cast<void*>(d.Kmat))[e] = (TK)v;  // FP32 forms keep Kmat in FP32
 }
 
 template <typename T>
@@ -63,6 +64,11 @@ constexpr int kQT = 64;  // outputs per tile
 constexpr int kJT = 16;  // inner chunk
 
 // MODE 0: FP64 multiply-add; MODE 2: FP32 multiply-add (output stored as FP64).
+// Per 16-column chunk every thread loads 4 (row, column) entries of Y and
+// their mask words (32 consecutive rows of one column per warp: coalesced) and
+// 4 entries of Kmat; the loads of chunk k + 1 are issued before the products of
+// chunk k, so their latency overlaps the arithmetic.  Y is read whether or not
+// the entry is known and masked afterwards (unknown entries never reach the sum).
 template <int MODE>
 __global__ void __launch_bounds__(256) k_normal(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                int nprob) {
@@ -70,6 +76,7 @@ __global__ void __launch_bounds__(256) k_normal(const ProbDesc* __restrict__ des
   __shared__ T ys[kJT][kNT], ws[kJT][kNT], ks[kJT][kQT];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
+  const T* __restrict__ Kmat = static_cast<const T*>(static_cast<const void*>(d.Kmat));
   const int64_t local = blockIdx.x - off[p];
   const int nqt = d.q_pad / kQT;
   const int64_t i0 = (local / nqt) * kNT;
@@ -88,28 +95,33 @@ __global__ void __launch_bounds__(256) k_normal(const ProbDesc* __restrict__ des
 #pragma unroll
     for (int o = 0; o < 4; ++o) acc[s][o] = (T)0;
   const int64_t m = d.m, n = d.n;
+  // loader mapping: entry e = threadIdx.x + 256 k -> (column e / 64, row or output e % 64)
+  const int lr = threadIdx.x & 63, lj = threadIdx.x >> 6;
+  const int64_t li = i0 + lr;
+  T ypre[4], kpre[4];
+  uint32_t wpre[4];
+  auto load_chunk = [&](int64_t j0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t j = j0 + lj + 4 * k;
+      const bool in = li < m && j < n;
+      wpre[k] = in ? __ldg(d.bits + j * d.ldb + (li >> 5)) : 0u;
+      ypre[k] = in ? load_y<T>(d, j * d.ldy + li) : (T)0;
+      kpre[k] = j < n ? __ldg(Kmat + j * d.q_pad + q0 + lr) : (T)0;
+    }
+  };
+  load_chunk(0);
   for (int64_t j0 = 0; j0 < n; j0 += kJT) {
     __syncthreads();
-    for (int e = threadIdx.x; e < kJT * kNT; e += 256) {
-      const int jj = e / kNT, rr = e % kNT;
-      const int64_t i = i0 + rr, j = j0 + jj;
-      T yv = (T)0, wv = (T)0;
-      if (i < m && j < n) {
-        const uint32_t word = __ldg(d.bits + j * d.ldb + (i >> 5));
-        if ((word >> (i & 31)) & 1u) {
-          wv = (T)1;
-          yv = load_y<T>(d, j * d.ldy + i);
-        }
-      }
-      ys[jj][rr] = yv;
-      ws[jj][rr] = wv;
-    }
-    for (int e = threadIdx.x; e < kJT * kQT; e += 256) {
-      const int jj = e / kQT, qq = e % kQT;
-      const int64_t j = j0 + jj;
-      ks[jj][qq] = (j < n) ? (T)d.Kmat[j * d.q_pad + q0 + qq] : (T)0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const bool known = (wpre[k] >> (li & 31)) & 1u;
+      ws[lj + 4 * k][lr] = known ? (T)1 : (T)0;
+      ys[lj + 4 * k][lr] = known ? ypre[k] : (T)0;
+      ks[lj + 4 * k][lr] = kpre[k];
     }
     __syncthreads();
+    if (j0 + kJT < n) load_chunk(j0 + kJT);
 #pragma unroll 4
     for (int jj = 0; jj < kJT; ++jj) {
       T kv[4], wv[4], yv[4];
@@ -268,7 +280,7 @@ __global__ void __launch_bounds__(32 * kPinvWarps) k_row_pinv(const ProbDesc* __
 // shared memory 64 columns at a time.  One partial per CTA, fixed-order tree.
 constexpr int kResRows = 32;
 constexpr int kResCols = 64;
-template <typename T>
+template <typename T, int RM>
 __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                  int nprob, double* __restrict__ partial) {
   __shared__ T vs[kResCols][kMaxR + 1];
@@ -278,42 +290,46 @@ __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ d
   const int lane = threadIdx.x & 31, wg = threadIdx.x >> 5;
   const int64_t i0 = (blockIdx.x - off[p]) * kResRows;
   const int64_t i = i0 + lane;
-  const int r = d.r;
-  T u[kMaxR];
+  const bool row_in = i < d.m;
+  const int r = d.r, P = r * (r + 1) / 2;
+  // V: in the FP32 forms the Kmat columns P .. P + r - 1 hold V in FP32 already
+  const T* __restrict__ Kv = static_cast<const T*>(static_cast<const void*>(d.Kmat));
+  T u[RM];
 #pragma unroll
-  for (int a = 0; a < kMaxR; ++a) u[a] = (a < r && i < d.m) ? (T)d.U[(int64_t)a * d.ldu + i] : (T)0;
-  double acc = 0.0;
+  for (int a = 0; a < RM; ++a) u[a] = (a < r && row_in) ? (T)d.U[(int64_t)a * d.ldu + i] : (T)0;
+  // at most n / 8 terms per thread in the working precision (FP64 arithmetic is
+  // far slower than FP32 on this part; one conversion per thread at the end)
+  T acc = (T)0;
   const int64_t wcol = i0 >> 5;
+  const int64_t irow = row_in ? i : i0;  // in-bounds row for the unconditional load
   for (int64_t j0 = 0; j0 < d.n; j0 += kResCols) {
     __syncthreads();
     for (int e = threadIdx.x; e < kResCols * r; e += 256) {
       const int jj = e / r, a = e % r;
       const int64_t j = j0 + jj;
-      vs[jj][a] = j < d.n ? (T)d.V[(int64_t)a * d.ldv + j] : (T)0;
+      T v = (T)0;
+      if (j < d.n) v = sizeof(T) == 8 ? (T)d.V[(int64_t)a * d.ldv + j] : Kv[j * d.q_pad + P + a];
+      vs[jj][a] = v;
     }
     __syncthreads();
     const int jn = d.n - j0 < kResCols ? (int)(d.n - j0) : kResCols;
-    // at most kResCols / 8 terms per chunk in the working precision, then one FP64 add
-    // (FP64 instructions are far slower than FP32 ones; one per chunk keeps them off the loop)
-    T part = (T)0;
 #pragma unroll 4
     for (int jj = wg; jj < jn; jj += 8) {
       const int64_t j = j0 + jj;
       const uint32_t word = __ldg(d.bits + j * d.ldb + wcol);
-      if ((word >> lane) & 1u) {
-        T pred = (T)0;
+      const T y = load_y<T>(d, j * d.ldy + irow);
+      T pred = (T)0;
 #pragma unroll
-        for (int a = 0; a < kMaxR; ++a)
-          if (a < r) pred = fma(u[a], vs[jj][a], pred);
-        const T diff = load_y<T>(d, j * d.ldy + i) - pred;
-        part = fma(diff, diff, part);
-      }
+      for (int a = 0; a < RM; ++a)
+        if (a < r) pred = fma(u[a], vs[jj][a], pred);
+      const T diff = (row_in && ((word >> lane) & 1u)) ? y - pred : (T)0;
+      acc = fma(diff, diff, acc);
     }
-    acc += (double)part;
   }
+  double dacc = (double)acc;
 #pragma unroll
-  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) red[wg] = acc;
+  for (int o = 16; o; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+  if (lane == 0) red[wg] = dacc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
@@ -349,7 +365,10 @@ cudaError_t launch_solve_u(const SolvePlan& S, int mode, cudaStream_t s) {
   const int np = S.nprob;
   cudaError_t e;
   if (S.k_total > 0) {
-    k_build_K<<<(unsigned)((S.k_total + 255) / 256), 256, 0, s>>>(D, S.k_off, np);
+    if (mode == 0)
+      k_build_K<double><<<(unsigned)((S.k_total + 255) / 256), 256, 0, s>>>(D, S.k_off, np);
+    else
+      k_build_K<float><<<(unsigned)((S.k_total + 255) / 256), 256, 0, s>>>(D, S.k_off, np);
     ++g_kernel_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -385,11 +404,13 @@ cudaError_t launch_residual(const SolvePlan& S, int mode, double* partial, cudaS
   const ProbDesc* D = S.descs;
   const int np = S.nprob;
   if (S.res_blocks > 0) {
+#define RSM_RES(T, RM) k_residual<T, RM><<<(unsigned)S.res_blocks, 256, 0, s>>>(D, S.res_off, np, partial)
     if (mode == 0) {
-      k_residual<double><<<(unsigned)S.res_blocks, 256, 0, s>>>(D, S.res_off, np, partial);
+      if (S.rmax <= 8) RSM_RES(double, 8); else if (S.rmax <= 16) RSM_RES(double, 16); else RSM_RES(double, 32);
     } else {
-      k_residual<float><<<(unsigned)S.res_blocks, 256, 0, s>>>(D, S.res_off, np, partial);
+      if (S.rmax <= 8) RSM_RES(float, 8); else if (S.rmax <= 16) RSM_RES(float, 16); else RSM_RES(float, 32);
     }
+#undef RSM_RES
     ++g_kernel_launches;
   }
   cudaError_t e = cudaGetLastError();

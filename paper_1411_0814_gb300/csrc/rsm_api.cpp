@@ -52,13 +52,13 @@ int cuda_fail(cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
   } while (0)
 
-constexpr double kShiftRel32 = 1e-3;   // tau / (trace(M) / n) with the FP32 factor
+constexpr double kShiftRel32 = 3e-4;   // tau / (trace(M) / n) with the FP32 factor
 constexpr double kShiftRel64 = 1e-11;  // tau / (trace(M) / n) with the FP64 factor
 #ifndef RSM_EIG_ITERS32
-#define RSM_EIG_ITERS32 14
+#define RSM_EIG_ITERS32 8
 #endif
 #ifndef RSM_EIG_ITERS64
-#define RSM_EIG_ITERS64 8
+#define RSM_EIG_ITERS64 6
 #endif
 constexpr int kEigIters32 = RSM_EIG_ITERS32;  // most preconditioned steps with the FP32 factor (stops when converged)
 constexpr int kEigIters64 = RSM_EIG_ITERS64;  // most steps with the FP64 factor (near-exact shift-invert)
@@ -326,6 +326,7 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
     r.rows_selected = (int64_t)c[5];
     r.kernel_launches = launches;
     r.eig_factor_bits = fp64 ? 64 : 32;
+    r.eig_iterations = (int32_t)stats[43];
     r.n_eig = b.dv[i].kx;
     for (int k = 0; k < 32; ++k) r.eig_M[k] = k < r.n_eig ? stats[k] : 0.0;
     r.eig_residual = stats[34];

@@ -65,6 +65,7 @@ class Result:
     rows_selected: int
     kernel_launches: int
     eig_factor_bits: int
+    eig_iterations: int
     eig_M: List[float]
     eig_residual: float
     e: float
@@ -86,7 +87,7 @@ class Result:
 def _result(res: rsm_result, outs: dict) -> Result:
     return Result(status=res.status, accepted_trials=res.accepted_trials, rows_underdetermined=res.rows_underdetermined,
                   rows_selected=res.rows_selected, kernel_launches=res.kernel_launches,
-                  eig_factor_bits=res.eig_factor_bits, eig_M=[res.eig_M[i] for i in range(res.n_eig)],
+                  eig_factor_bits=res.eig_factor_bits, eig_iterations=res.eig_iterations, eig_M=[res.eig_M[i] for i in range(res.n_eig)],
                   eig_residual=res.eig_residual, e=res.e_known_rms,
                   stage_ms={k: float(res.stage_ms[i]) for i, k in enumerate(_abi.STAGES)}, queue_ms=res.queue_ms,
                   run_ms=res.run_ms, **outs)
