@@ -100,11 +100,13 @@ __device__ __forceinline__ double sqrt64(double x) {  // x >= 0
 }
 
 // Type-generic forms for code templated on float / double.
-__device__ __forceinline__ float fast_rcp(float x) { return 1.0f / x; }
+// FP32: the hardware approximations (a few ulp), enough for rotations and pivots
+// whose result is refined or rounded to FP32 anyway.
+__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double fast_rcp(double x) { return rcp64(x); }
 __device__ __forceinline__ float fast_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double fast_sqrt(double x) { return sqrt64(x); }
-__device__ __forceinline__ float fast_rsqrt(float x) { return 1.0f / sqrtf(x); }
+__device__ __forceinline__ float fast_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double fast_rsqrt(double x) { return rsqrt64(x); }
 
 // ------------------------------------------------------------------ Philox4x32-10

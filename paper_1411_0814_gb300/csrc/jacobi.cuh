@@ -58,9 +58,11 @@ __device__ inline T warp_frobenius(const T* A, int k, int ls) {
 // (Vm is set to I first unless keep_v).  k <= 32.  All 32 lanes must call it.
 // Returns the number of sweeps that applied at least one rotation (0: S was
 // already diagonal to the tolerance and Vm is the identity / unchanged).
+// Lane r < ceil(k/2) computes the rotation of pair r of the round; the other
+// lanes fetch it by shuffle, so the updates read no indices from memory.
 template <typename T>
-__device__ inline int warp_jacobi(T* S, T* Vm, int k, int ls, JacobiScratchT<T>& js, T tol_abs, int max_sweeps = 40,
-                                  bool keep_v = false) {
+__device__ inline int warp_jacobi(T* S, T* Vm, int k, int ls, JacobiScratchT<T>& /*unused*/, T tol_abs,
+                                  int max_sweeps = 40, bool keep_v = false) {
   const int lane = threadIdx.x & 31;
   if (!keep_v)
     for (int i = lane; i < k * k; i += 32) {
@@ -71,20 +73,22 @@ __device__ inline int warp_jacobi(T* S, T* Vm, int k, int ls, JacobiScratchT<T>&
   const T eps = jacobi_eps<T>();
   const int ne = (k + 1) & ~1;
   const int np = ne / 2;
+  const int nitem = np * k;  // (pair, row) items of one round
   int rotated = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     bool any = false;
     for (int round = 0; round < ne - 1; ++round) {
+      int a = 0, b = 0;
+      T c = 1, s = 0;
       if (lane < np) {
         const int s0 = lane, s1 = ne - 1 - lane;
-        int a = (s0 == 0) ? 0 : ((s0 - 1 + round) % (ne - 1)) + 1;
-        int b = (s1 == 0) ? 0 : ((s1 - 1 + round) % (ne - 1)) + 1;
+        a = (s0 == 0) ? 0 : ((s0 - 1 + round) % (ne - 1)) + 1;
+        b = (s1 == 0) ? 0 : ((s1 - 1 + round) % (ne - 1)) + 1;
         if (a > b) {
           const int tmp = a;
           a = b;
           b = tmp;
         }
-        T c = 1, s = 0;
         if (b < k) {
           const T apq = S[a * ls + b];
           const T app = S[a * ls + a], aqq = S[b * ls + b];
@@ -108,41 +112,40 @@ __device__ inline int warp_jacobi(T* S, T* Vm, int k, int ls, JacobiScratchT<T>&
         } else {
           b = a;
         }
-        js.p[lane] = a;
-        js.q[lane] = b;
-        js.c[lane] = c;
-        js.s[lane] = s;
+      }
+      if (!__any_sync(0xffffffffu, s != (T)0)) continue;
+      any = true;
+      __syncwarp();
+      // columns p, q of S and Vm
+      for (int base = 0; base < nitem; base += 32) {
+        const int it = base + lane;
+        const int r = it < nitem ? it / k : 0, i = it < nitem ? it % k : 0;
+        const int pr = __shfl_sync(0xffffffffu, a, r), qr = __shfl_sync(0xffffffffu, b, r);
+        const T cr = __shfl_sync(0xffffffffu, c, r), sr = __shfl_sync(0xffffffffu, s, r);
+        if (it < nitem && sr != (T)0) {
+          const T xp = S[i * ls + pr], xq = S[i * ls + qr];
+          const T vp = Vm[i * ls + pr], vq = Vm[i * ls + qr];
+          S[i * ls + pr] = cr * xp - sr * xq;
+          S[i * ls + qr] = sr * xp + cr * xq;
+          Vm[i * ls + pr] = cr * vp - sr * vq;
+          Vm[i * ls + qr] = sr * vp + cr * vq;
+        }
       }
       __syncwarp();
-      const bool rot = lane < np && js.s[lane] != (T)0;
-      any |= __any_sync(0xffffffffu, rot);
-      for (int it = lane; it < np * k; it += 32) {  // columns p, q of S and Vm
-        const int r = it / k, i = it % k;
-        const T s = js.s[r];
-        if (s == (T)0) continue;
-        const T c = js.c[r];
-        const int a = js.p[r], b = js.q[r];
-        const T xp = S[i * ls + a], xq = S[i * ls + b];
-        S[i * ls + a] = c * xp - s * xq;
-        S[i * ls + b] = s * xp + c * xq;
-        const T vp = Vm[i * ls + a], vq = Vm[i * ls + b];
-        Vm[i * ls + a] = c * vp - s * vq;
-        Vm[i * ls + b] = s * vp + c * vq;
+      // rows p, q of S
+      for (int base = 0; base < nitem; base += 32) {
+        const int it = base + lane;
+        const int r = it < nitem ? it / k : 0, j = it < nitem ? it % k : 0;
+        const int pr = __shfl_sync(0xffffffffu, a, r), qr = __shfl_sync(0xffffffffu, b, r);
+        const T cr = __shfl_sync(0xffffffffu, c, r), sr = __shfl_sync(0xffffffffu, s, r);
+        if (it < nitem && sr != (T)0) {
+          const T xp = S[pr * ls + j], xq = S[qr * ls + j];
+          S[pr * ls + j] = cr * xp - sr * xq;
+          S[qr * ls + j] = sr * xp + cr * xq;
+        }
       }
       __syncwarp();
-      for (int it = lane; it < np * k; it += 32) {  // rows p, q of S
-        const int r = it / k, j = it % k;
-        const T s = js.s[r];
-        if (s == (T)0) continue;
-        const T c = js.c[r];
-        const int a = js.p[r], b = js.q[r];
-        const T xp = S[a * ls + j], xq = S[b * ls + j];
-        S[a * ls + j] = c * xp - s * xq;
-        S[b * ls + j] = s * xp + c * xq;
-      }
-      __syncwarp();
-      if (rot) {
-        const int a = js.p[lane], b = js.q[lane];
+      if (lane < np && s != (T)0) {
         S[a * ls + b] = 0;
         S[b * ls + a] = 0;
       }

@@ -588,17 +588,48 @@ __global__ void __launch_bounds__(kSmallThreads) k_rr64(const ProbDesc* __restri
   const int kx = d.kx, r = d.r, tid = threadIdx.x;
   reduce_partials(d, part_base + part_off[p], S, H, kx);
   __syncthreads();
-  if (tid < 32) warp_chol_shifted<double>(S, rdiag, kx, 1e-15);
+  // S = X^T X is close to I here (X was orthonormalised before its last small
+  // update), so: FP32 Cholesky S + s I = C C^T and Q0 = C^-T, then one
+  // Newton-Schulz step in FP64, Q1 = Q0 (3I - Q0^T S Q0) / 2, which squares the
+  // FP32 error: X Q1 is orthonormal to FP64 accuracy.
+  for (int e = tid; e < kx * kx; e += kSmallThreads) Sf[e / kx][e % kx] = (float)S[e / kx][e % kx];
   __syncthreads();
-  inv_transpose_factor<double>(S, rdiag, Q1, kx);
+  if (tid < 32) warp_chol_shifted<float>(Sf, reinterpret_cast<float*>(rdiag), kx, 1e-7f);
+  __syncthreads();
+  inv_transpose_factor<float>(Sf, reinterpret_cast<const float*>(rdiag), Vf, kx);
+  __syncthreads();
+  for (int e = tid; e < kx * kx; e += kSmallThreads) Q2[e / kx][e % kx] = (double)Vf[e / kx][e % kx];
+  __syncthreads();
+  sym_congruence(W2, Q2, S, W1, kx);  // Z = Q0^T S Q0
+  for (int e = tid; e < kx * kx; e += kSmallThreads) {
+    const int a = e / kx, b = e % kx;
+    double s = 0.0;
+    for (int t = 0; t < kx; ++t) s = fma(Q2[a][t], ((t == b) ? 3.0 : 0.0) - W2[t][b], s);
+    Q1[a][b] = 0.5 * s;
+  }
   __syncthreads();
   sym_congruence(H1, Q1, H, W1, kx);  // H1 = Q1^T H Q1
-  // FP32 Jacobi of H1, then the eigenvector columns in ascending order of the Ritz values
+  // FP32 Jacobi of H1 when it has off-diagonal entries FP32 can resolve; then
+  // the eigenvector columns in ascending order of the Ritz values
   for (int e = tid; e < kx * kx; e += kSmallThreads) Sf[e / kx][e % kx] = (float)H1[e / kx][e % kx];
   __syncthreads();
   if (tid < 32) {
-    const float fro = warp_frobenius(&Sf[0][0], kx, kLs);
-    const int sweeps = warp_jacobi<float>(&Sf[0][0], &Vf[0][0], kx, kLs, jsf, 4.f * FLT_EPSILON * fro);
+    float f = 0.f, o = 0.f;
+    for (int e = tid; e < kx * kx; e += 32) {
+      const float v = Sf[e / kx][e % kx];
+      f += v * v;
+      if (e / kx != e % kx) o = fmaxf(o, fabsf(v));
+    }
+#pragma unroll
+    for (int s = 16; s; s >>= 1) {
+      f += __shfl_xor_sync(0xffffffffu, f, s);
+      o = fmaxf(o, __shfl_xor_sync(0xffffffffu, o, s));
+    }
+    const float tol = 4.f * FLT_EPSILON * sqrtf(f);
+    int sweeps = 0;
+    if (o > tol) {
+      sweeps = warp_jacobi<float>(&Sf[0][0], &Vf[0][0], kx, kLs, jsf, tol);
+    }
     if (tid == 0) {
       rotated = sweeps;
       coupled = 0;
@@ -615,7 +646,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_rr64(const ProbDesc* __restri
     }
   }
   __syncthreads();
-  for (int e = tid; e < kx * kx; e += kSmallThreads) Q2[e / kx][e % kx] = (double)Vf[e / kx][order[e % kx]];
+  for (int e = tid; e < kx * kx; e += kSmallThreads)
+    Q2[e / kx][e % kx] = rotated ? (double)Vf[e / kx][order[e % kx]] : (e / kx == order[e % kx] ? 1.0 : 0.0);
   __syncthreads();
   if (rotated) {  // FP32 rotations: make them orthogonal in FP64, then B = Q2^T H1 Q2
     lowdin_step(Q2, W1, W2, kx);
