@@ -32,7 +32,9 @@ constexpr double kStallTol = 1e-10;  // ... or when it stops falling (rounding f
 constexpr int kPrevRes = 41;         // stats[41]: max ||R_j|| at the previous check
 constexpr int kIterCount = 43;       // stats[43]: block iterations run so far
 
-__device__ __forceinline__ int64_t npad_of(const ProbDesc& d) { return (int64_t)d.nblk * BS; }
+// Index arithmetic of the eigen stage is 32-bit (n <= 32768 is validated on the host): 64-bit
+// integer multiplies and adds are slow on this part.
+__device__ __forceinline__ int npad_of(const ProbDesc& d) { return d.nblk * BS; }
 
 template <typename T>
 __device__ __forceinline__ T* F1of(const ProbDesc& d) { return static_cast<T*>(d.F1); }
@@ -55,7 +57,7 @@ __global__ void __launch_bounds__(256) k_eig_prep(const ProbDesc* __restrict__ d
     d.stats[kPrevRes] = 0.0;
     d.stats[kIterCount] = (double)iter0;  // the unchecked leading steps
   }
-  const int64_t np = npad_of(d);
+  const int np = npad_of(d);
   const int64_t i = e / np, j = e % np;
   const double mean = (double)d.counters[0] * d.n_minor / (double)d.n;
   const double tau = mean > 0.0 ? shift_rel * mean : 1.0;
@@ -79,12 +81,12 @@ __global__ void __launch_bounds__(32) k_potrf(const ProbDesc* __restrict__ descs
                                              int nprob, int k) {
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
-  const int64_t np = npad_of(d);
+  const int np = npad_of(d);
   const int lane = threadIdx.x;
   T* A = F1of<T>(d) + (int64_t)k * BS * np + (int64_t)k * BS;
   T a[BS];
 #pragma unroll
-  for (int c = 0; c < BS; ++c) a[c] = A[(int64_t)lane * np + c];
+  for (int c = 0; c < BS; ++c) a[c] = A[lane * np + c];
   bool bad = false;
   T rinv = (T)1;  // 1 / L[lane][lane]
 #pragma unroll
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(32) k_potrf(const ProbDesc* __restrict__ descs
   T* D = Dinvof<T>(d) + (int64_t)k * BS * BS;
 #pragma unroll
   for (int c = 0; c < BS; ++c) {
-    A[(int64_t)lane * np + c] = c <= lane ? a[c] : (T)0;
+    A[lane * np + c] = c <= lane ? a[c] : (T)0;
     D[lane * BS + c] = c <= lane ? x[c] : (T)0;  // entry (lane, c) of inv(L_kk)
   }
 }
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(256) k_panel(const ProbDesc* __restrict__ desc
   __shared__ T x[BS][BS + 1], y[BS][BS + 1];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
-  const int64_t np = npad_of(d);
+  const int np = npad_of(d);
   const int i = k + 1 + (int)(blockIdx.x - off[p]);
   T* Aik = F1of<T>(d) + (int64_t)i * BS * np + (int64_t)k * BS;
   const T* D = Dinvof<T>(d) + (int64_t)k * BS * BS;
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__(256) k_panel(const ProbDesc* __restrict__ desc
     for (int s = 0; s < 4; ++s) acc[s] = fma(x[ty + 8 * s][t], yv, acc[s]);
   }
 #pragma unroll
-  for (int s = 0; s < 4; ++s) Aik[(int64_t)(ty + 8 * s) * np + tx] = acc[s];
+  for (int s = 0; s < 4; ++s) Aik[(ty + 8 * s) * np + tx] = acc[s];
 }
 
 __device__ __forceinline__ void tri_index(int64_t u, int& i, int& j) {
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(256) k_trail(const ProbDesc* __restrict__ desc
   __shared__ T x[BS][BS + 1], y[BS][BS + 1];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
-  const int64_t np = npad_of(d);
+  const int np = npad_of(d);
   int ii, jj;
   tri_index(blockIdx.x - off[p], ii, jj);
   const int i = k + 1 + ii, j = k + 1 + jj;
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(256) k_trail(const ProbDesc* __restrict__ desc
     for (int s = 0; s < 4; ++s) acc[s] = fma(x[ty + 8 * s][t], yv, acc[s]);
   }
 #pragma unroll
-  for (int s = 0; s < 4; ++s) Aij[(int64_t)(ty + 8 * s) * np + tx] -= acc[s];
+  for (int s = 0; s < 4; ++s) Aij[(ty + 8 * s) * np + tx] -= acc[s];
 }
 
 // ------------------------------------------------------------------ L^-1 (into F2)
@@ -202,13 +204,13 @@ __global__ void __launch_bounds__(256) k_linv_init(const ProbDesc* __restrict__ 
                                                   int nprob) {
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
-  const int64_t np = npad_of(d);
+  const int np = npad_of(d);
   int i, j;
   tri_index(blockIdx.x - off[p], i, j);
   T* out = F2of<T>(d) + (int64_t)i * BS * np + (int64_t)j * BS;
   for (int e = threadIdx.x; e < BS * BS; e += 256) {
     const int r = e / BS, c = e % BS;
-    out[(int64_t)r * np + c] = (i == j && r == c) ? (T)1 : (T)0;
+    out[r * np + c] = (i == j && r == c) ? (T)1 : (T)0;
   }
 }
 
@@ -218,13 +220,13 @@ __global__ void __launch_bounds__(256) k_linv_scale(const ProbDesc* __restrict__
   __shared__ T x[BS][BS + 1], y[BS][BS + 1];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
-  const int64_t np = npad_of(d);
+  const int np = npad_of(d);
   const int j = (int)(blockIdx.x - off[p]);  // j <= k
   T* Xkj = F2of<T>(d) + (int64_t)k * BS * np + (int64_t)j * BS;
   const T* D = Dinvof<T>(d) + (int64_t)k * BS * BS;
   for (int e = threadIdx.x; e < BS * BS; e += 256) {
     x[e / BS][e % BS] = D[e];
-    y[e / BS][e % BS] = Xkj[(int64_t)(e / BS) * np + (e % BS)];
+    y[e / BS][e % BS] = Xkj[(e / BS) * np + (e % BS)];
   }
   __syncthreads();
   const int tx = threadIdx.x % BS, ty = threadIdx.x / BS;
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(256) k_linv_scale(const ProbDesc* __restrict__
     for (int s = 0; s < 4; ++s) acc[s] = fma(x[ty + 8 * s][u], yv, acc[s]);
   }
 #pragma unroll
-  for (int s = 0; s < 4; ++s) Xkj[(int64_t)(ty + 8 * s) * np + tx] = acc[s];
+  for (int s = 0; s < 4; ++s) Xkj[(ty + 8 * s) * np + tx] = acc[s];
 }
 
 template <typename T>
@@ -244,15 +246,15 @@ __global__ void __launch_bounds__(256) k_linv_update(const ProbDesc* __restrict_
   __shared__ T x[BS][BS + 1], y[BS][BS + 1];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
-  const int64_t np = npad_of(d);
+  const int np = npad_of(d);
   const int64_t local = blockIdx.x - off[p];
   const int i = k + 1 + (int)(local / (k + 1)), j = (int)(local % (k + 1));
   const T* Lik = F1of<T>(d) + (int64_t)i * BS * np + (int64_t)k * BS;
   const T* Xkj = F2of<T>(d) + (int64_t)k * BS * np + (int64_t)j * BS;
   T* Xij = F2of<T>(d) + (int64_t)i * BS * np + (int64_t)j * BS;
   for (int e = threadIdx.x; e < BS * BS; e += 256) {
-    x[e / BS][e % BS] = Lik[(int64_t)(e / BS) * np + (e % BS)];
-    y[e / BS][e % BS] = Xkj[(int64_t)(e / BS) * np + (e % BS)];
+    x[e / BS][e % BS] = Lik[(e / BS) * np + (e % BS)];
+    y[e / BS][e % BS] = Xkj[(e / BS) * np + (e % BS)];
   }
   __syncthreads();
   const int tx = threadIdx.x % BS, ty = threadIdx.x / BS;
@@ -263,7 +265,7 @@ __global__ void __launch_bounds__(256) k_linv_update(const ProbDesc* __restrict_
     for (int s = 0; s < 4; ++s) acc[s] = fma(x[ty + 8 * s][u], yv, acc[s]);
   }
 #pragma unroll
-  for (int s = 0; s < 4; ++s) Xij[(int64_t)(ty + 8 * s) * np + tx] -= acc[s];
+  for (int s = 0; s < 4; ++s) Xij[(ty + 8 * s) * np + tx] -= acc[s];
 }
 
 // T = A^-1 = L^-T L^-1:  T_ij = sum_{t >= max(i, j)} Linv_ti^T Linv_tj  (into F1, both triangles)
@@ -273,7 +275,7 @@ __global__ void __launch_bounds__(256) k_ainv(const ProbDesc* __restrict__ descs
   __shared__ T x[BS][BS + 1], y[BS][BS + 1];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
-  const int64_t np = npad_of(d);
+  const int np = npad_of(d);
   int i, j;
   tri_index(blockIdx.x - off[p], i, j);  // j <= i
   const int tx = threadIdx.x % BS, ty = threadIdx.x / BS;
@@ -298,12 +300,12 @@ __global__ void __launch_bounds__(256) k_ainv(const ProbDesc* __restrict__ descs
   __syncthreads();
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
-    Tij[(int64_t)(ty + 8 * s) * np + tx] = acc[s];
+    Tij[(ty + 8 * s) * np + tx] = acc[s];
     x[ty + 8 * s][tx] = acc[s];
   }
   __syncthreads();
   if (i != j)
-    for (int e = threadIdx.x; e < BS * BS; e += 256) Tji[(int64_t)(e / BS) * np + (e % BS)] = x[e % BS][e / BS];
+    for (int e = threadIdx.x; e < BS * BS; e += 256) Tji[(e / BS) * np + (e % BS)] = x[e % BS][e / BS];
 }
 
 // ------------------------------------------------------------------ block iteration (FP64)
@@ -333,25 +335,25 @@ __global__ void __launch_bounds__(256) k_gemm_MX(const ProbDesc* __restrict__ de
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
   if (d.stats[kConvFlag] != 0.0) return;  // converged: the rest of the iteration is skipped
-  const int64_t local = blockIdx.x - off[p];
-  const int64_t n = d.n;
+  const int local = (int)(blockIdx.x - off[p]);
+  const int n = (int)d.n;
   const int kx = d.kx;
-  const int64_t ntile = (n + kRowTile - 1) / kRowTile;
-  const int split = (int)(local / ntile);
-  const int64_t i0 = (local % ntile) * kRowTile;
-  const int64_t j_begin = split * n / kSplit, j_end = (split + 1) * n / kSplit;
+  const int ntile = (n + kRowTile - 1) / kRowTile;
+  const int split = local / ntile;
+  const int i0 = (local % ntile) * kRowTile;
+  const int j_begin = split * n / kSplit, j_end = (split + 1) * n / kSplit;
   const int tr = threadIdx.x % kRowTile, tc = threadIdx.x / kRowTile;  // 8 column groups
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int64_t j0 = j_begin; j0 < j_end; j0 += 32) {
+  for (int j0 = j_begin; j0 < j_end; j0 += 32) {
     __syncthreads();
     for (int e = threadIdx.x; e < kRowTile * 32; e += 256) {
       const int r = e / 32, c = e % 32;
-      const int64_t i = i0 + r, j = j0 + c;
+      const int i = i0 + r, j = j0 + c;
       ms[r][c] = (i < n && j < j_end) ? d.M[i * n + j] : 0.0;
     }
     for (int e = threadIdx.x; e < 32 * kx; e += 256) {
       const int r = e / kx, c = e % kx;
-      const int64_t j = j0 + r;
+      const int j = j0 + r;
       xs[r][c] = (j < j_end) ? d.X[j * kx + c] : 0.0;
     }
     __syncthreads();
@@ -364,12 +366,12 @@ __global__ void __launch_bounds__(256) k_gemm_MX(const ProbDesc* __restrict__ de
       }
     }
   }
-  const int64_t i = i0 + tr;
+  const int i = i0 + tr;
   if (i < n)
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
       const int c = tc + 8 * s;
-      if (c < kx) d.R[((int64_t)split * n + i) * kx + c] = acc[s];
+      if (c < kx) d.R[(split * n + i) * kx + c] = acc[s];
     }
 }
 
@@ -380,8 +382,8 @@ __global__ void __launch_bounds__(256) k_split_sum(const ProbDesc* __restrict__ 
   const int p = find_problem(off, nprob, g);
   const ProbDesc& d = descs[p];
   if (d.stats[kConvFlag] != 0.0) return;
-  const int64_t e = g - off[p];
-  const int64_t nk = d.n * d.kx;
+  const int e = (int)(g - off[p]);
+  const int nk = (int)d.n * d.kx;
   double s = d.R[e];
   for (int q = 1; q < kSplit; ++q) s += d.R[q * nk + e];
   d.MX[e] = s;
@@ -397,13 +399,13 @@ __global__ void __launch_bounds__(256) k_xtx(const ProbDesc* __restrict__ descs,
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
   if (d.stats[kConvFlag] != 0.0) return;  // converged: the rest of the iteration is skipped
-  const int64_t chunk = blockIdx.x - off[p];
+  const int chunk = (int)(blockIdx.x - off[p]);
   const int kx = d.kx;
   double* xs = xtx_smem;                  // kChunk x kx
   double* ys = xtx_smem + kChunk * kx;    // kChunk x kx
-  const int64_t i0 = chunk * kChunk;
+  const int i0 = chunk * kChunk;
   for (int e = threadIdx.x; e < kChunk * kx; e += 256) {
-    const int64_t i = i0 + e / kx;
+    const int i = i0 + e / kx;
     xs[e] = i < d.n ? d.X[i0 * kx + e] : 0.0;
     if (WITH_H) ys[e] = i < d.n ? d.MX[i0 * kx + e] : 0.0;
   }
@@ -430,11 +432,11 @@ typedef float FRow[kLs];
 
 // Sum the per-chunk partials in a fixed order: S = X^T X (and H = X^T M X).
 __device__ inline void reduce_partials(const ProbDesc& d, const double* part, DRow* S, DRow* H, int kx) {
-  const int64_t nchunk = (d.n + kChunk - 1) / kChunk;
+  const int nchunk = (int)((d.n + kChunk - 1) / kChunk);
   for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) {
     double s = 0.0, h = 0.0;
 #pragma unroll 4
-    for (int64_t c = 0; c < nchunk; ++c) {
+    for (int c = 0; c < nchunk; ++c) {
       s += part[c * 2 * kx * kx + e];
       if (H) h += part[c * 2 * kx * kx + kx * kx + e];
     }
@@ -713,11 +715,11 @@ __global__ void __launch_bounds__(256) k_rotate(const ProbDesc* __restrict__ des
   const ProbDesc& d = descs[p];
   if (d.stats[kConvFlag] != 0.0) return;  // converged: the rest of the iteration is skipped
   const int kx = d.kx;
-  const int64_t i0 = (blockIdx.x - off[p]) * kRotRows;
+  const int i0 = (int)(blockIdx.x - off[p]) * kRotRows;
   for (int e = threadIdx.x; e < (FULL ? 2 : 1) * kx * kx; e += blockDim.x) q[e] = d.small[e];
   for (int e = threadIdx.x; e < kRotRows * kx; e += blockDim.x) {
     const int r = e / kx, c = e % kx;
-    const int64_t i = i0 + r;
+    const int i = i0 + r;
     xs[r][c] = i < d.n ? d.X[i * kx + c] : 0.0;
     if (FULL) ms[r][c] = i < d.n ? d.MX[i * kx + c] : 0.0;
   }
@@ -739,7 +741,7 @@ __global__ void __launch_bounds__(256) k_rotate(const ProbDesc* __restrict__ des
   cnt = 0;
   for (int e = threadIdx.x; e < kRotRows * kx; e += blockDim.x) {
     const int r = e / kx, c = e % kx;
-    const int64_t i = i0 + r;
+    const int i = i0 + r;
     const double b = nmx[cnt++];
     double s = 0.0;
     if (i < d.n) {
@@ -776,26 +778,26 @@ __global__ void __launch_bounds__(256) k_precond(const ProbDesc* __restrict__ de
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
   if (d.stats[kConvFlag] != 0.0) return;  // converged: the rest of the iteration is skipped
-  const int64_t n = d.n, np = npad_of(d);
+  const int n = (int)d.n, np = npad_of(d);
   const int kx = d.kx;
   const double* src = SRC == 0 ? d.R : d.X;
-  const int64_t local = blockIdx.x - off[p];
-  const int64_t ntile = (n + kPRows - 1) / kPRows;
-  const int split = (int)(local / ntile);
-  const int64_t i0 = (local % ntile) * kPRows;
-  const int64_t j_begin = split * n / kPSplit, j_end = (split + 1) * n / kPSplit;
+  const int local = (int)(blockIdx.x - off[p]);
+  const int ntile = (n + kPRows - 1) / kPRows;
+  const int split = local / ntile;
+  const int i0 = (local % ntile) * kPRows;
+  const int j_begin = split * n / kPSplit, j_end = (split + 1) * n / kPSplit;
   const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
   T acc[2] = {(T)0, (T)0};
-  for (int64_t j0 = j_begin; j0 < j_end; j0 += 64) {
+  for (int j0 = j_begin; j0 < j_end; j0 += 64) {
     __syncthreads();
     for (int e = threadIdx.x; e < kPRows * 64; e += 256) {
       const int r = e / 64, c = e % 64;
-      const int64_t i = i0 + r, j = j0 + c;
+      const int i = i0 + r, j = j0 + c;
       ts[r][c] = (i < n && j < j_end) ? F1of<T>(d)[i * np + j] : (T)0;
     }
     for (int e = threadIdx.x; e < 64 * kx; e += 256) {
       const int r = e / kx, c = e % kx;
-      const int64_t j = j0 + r;
+      const int j = j0 + r;
       rs[r][c] = (j < j_end) ? (T)src[j * kx + c] : (T)0;
     }
     __syncthreads();
@@ -806,8 +808,8 @@ __global__ void __launch_bounds__(256) k_precond(const ProbDesc* __restrict__ de
       acc[1] = fma(tv, rs[u][tc + 16 < kx ? tc + 16 : tc], acc[1]);
     }
   }
-  const int64_t i = i0 + tr;
-  double* part = d.R + (int64_t)(1 + split) * n * kx;
+  const int i = i0 + tr;
+  double* part = d.R + (1 + split) * n * kx;
   if (i < n) {
     if (tc < kx) part[i * kx + tc] = (double)acc[0];
     if (tc + 16 < kx) part[i * kx + tc + 16] = (double)acc[1];
@@ -823,10 +825,10 @@ __global__ void __launch_bounds__(256) k_precond_apply(const ProbDesc* __restric
   const int p = find_problem(off, nprob, g);
   const ProbDesc& d = descs[p];
   if (d.stats[kConvFlag] != 0.0) return;
-  const int64_t e = g - off[p];
-  const int64_t nk = d.n * d.kx;
+  const int e = (int)(g - off[p]);
+  const int nk = (int)d.n * d.kx;
   double s = 0.0;
-  for (int q = 0; q < kPSplit; ++q) s += d.R[(int64_t)(1 + q) * nk + e];
+  for (int q = 0; q < kPSplit; ++q) s += d.R[(1 + q) * nk + e];
   d.X[e] = MODE == 0 ? d.X[e] - s : s;
 }
 
@@ -836,12 +838,12 @@ __global__ void __launch_bounds__(256) k_precond_apply(const ProbDesc* __restric
 __device__ inline double wanted_residual_norm(const ProbDesc& d) {
   __shared__ double red[8][32];
   const int kx = d.kx, r = d.r;
-  const int64_t ntile = (d.n + kRotRows - 1) / kRotRows;
+  const int ntile = (int)((d.n + kRotRows - 1) / kRotRows);
   const double* pr = d.R + (int64_t)kResSlot * d.n * kx;
   const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
   double s = 0.0;
   if (c < r)
-    for (int64_t t = g; t < ntile; t += 8) s += pr[t * kx + c];
+    for (int t = g; t < ntile; t += 8) s += pr[t * kx + c];
   red[g][c] = s;
   __syncthreads();
   double mx = 0.0;

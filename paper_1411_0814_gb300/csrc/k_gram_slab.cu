@@ -26,22 +26,18 @@ constexpr int kRing = 1088;  // pending rows per warp: < 32 + 32 * 32
 template <int MODE>
 struct SlabT;
 template <>
-struct SlabT<0> {  // FP64
+struct SlabT<0> {  // FP64 Gram of FP64 Y
   using acc_t = double;
   using val_t = double;
-  __device__ static val_t load(const ProbDesc& d, int64_t idx) {
-    return d.y_dtype == 0 ? __ldg(static_cast<const double*>(d.Y) + idx)
-                          : (double)__ldg(static_cast<const float*>(d.Y) + idx);
-  }
+  using src_t = double;
+  __device__ static val_t cvt(src_t x) { return x; }
 };
 template <>
-struct SlabT<2> {  // FP32
+struct SlabT<2> {  // FP32 Gram of FP32 Y
   using acc_t = float;
   using val_t = float;
-  __device__ static val_t load(const ProbDesc& d, int64_t idx) {
-    return d.y_dtype == 1 ? __ldg(static_cast<const float*>(d.Y) + idx)
-                          : __double2float_rn(__ldg(static_cast<const double*>(d.Y) + idx));
-  }
+  using src_t = float;
+  __device__ static val_t cvt(src_t x) { return x; }
 };
 
 template <int MODE, int L>
@@ -64,9 +60,15 @@ __global__ void __launch_bounds__(32 * kSlabWarps) k_gram_slab(const ProbDesc* _
   const int p = find_problem(task_off, nprob, g);
   const ProbDesc& d = descs[p];
   const int64_t t = g - task_off[p];
-  int64_t cidx[L];
+  // per-column base pointers (64-bit once per warp); rows are 32-bit offsets from them
+  const typename Tr::src_t* ycol[L];
+  const uint32_t* bcol[L];
 #pragma unroll
-  for (int k = 0; k < L; ++k) cidx[k] = (int64_t)__ldg(d.cols + t * L + k);
+  for (int k = 0; k < L; ++k) {
+    const int64_t c = (int64_t)__ldg(d.cols + t * L + k);
+    ycol[k] = static_cast<const typename Tr::src_t*>(d.Y) + c * d.ldy;
+    bcol[k] = d.bits + c * d.ldb;
+  }
   const int64_t r0 = (int64_t)slab * d.slab_rows;
   const int64_t r1 = r0 + d.slab_rows < d.m ? r0 + d.slab_rows : d.m;
   const int64_t w_begin = r0 >> 5, w_end = (r1 + 31) >> 5;
@@ -77,10 +79,10 @@ __global__ void __launch_bounds__(32 * kSlabWarps) k_gram_slab(const ProbDesc* _
   int pending = 0, count = 0;
 
   auto consume = [&](int k) {  // gather row ring[k] and add its outer product
-    const int64_t row = ring[k];
+    const uint32_t row = (uint32_t)ring[k];
     V v[L];
 #pragma unroll
-    for (int a = 0; a < L; ++a) v[a] = Tr::load(d, row + cidx[a] * d.ldy);
+    for (int a = 0; a < L; ++a) v[a] = Tr::cvt(__ldg(ycol[a] + row));
 #pragma unroll
     for (int a = 0; a < L; ++a)
 #pragma unroll
@@ -91,12 +93,12 @@ __global__ void __launch_bounds__(32 * kSlabWarps) k_gram_slab(const ProbDesc* _
   };
 
   for (int64_t w0 = w_begin; w0 < w_end; w0 += 32) {
-    const int64_t w = w0 + lane;
+    const uint32_t w = (uint32_t)(w0 + lane);
     uint32_t mask = 0;
-    if (w < w_end) {
+    if (w < (uint32_t)w_end) {
       mask = 0xffffffffu;
 #pragma unroll
-      for (int k = 0; k < L; ++k) mask &= __ldg(d.bits + cidx[k] * d.ldb + w);
+      for (int k = 0; k < L; ++k) mask &= __ldg(bcol[k] + w);
     }
     const int cnt = __popc(mask);
     int incl = cnt;
@@ -110,7 +112,7 @@ __global__ void __launch_bounds__(32 * kSlabWarps) k_gram_slab(const ProbDesc* _
     while (mask) {
       const int b = __ffs(mask) - 1;
       mask &= mask - 1;
-      ring[pos++] = (int)(w * 32 + b);
+      ring[pos++] = (int)(w * 32u + (uint32_t)b);
     }
     __syncwarp();
     pending += total;
@@ -177,9 +179,11 @@ static cudaError_t launch_slab_l(const SlabPlan& S, cudaStream_t s) {
   return cudaSuccess;
 }
 
-bool slab_supported(int mode, int l) {
-  if (mode == 2) return l >= 2 && l <= 17;
-  if (mode == 0) return l >= 2 && l <= 12;
+// The slab kernel reads Y in the Gram's own precision (FP32 Gram of FP32 Y,
+// FP64 Gram of FP64 Y); other combinations take the per-trial kernel.
+bool slab_supported(int mode, int l, int y_dtype) {
+  if (mode == 2) return y_dtype == 1 && l >= 2 && l <= 17;
+  if (mode == 0) return y_dtype == 0 && l >= 2 && l <= 12;
   return false;
 }
 

@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDe
     double pr = 0.0;
     for (int j = 0; j < nm; ++j) pr = fma(Z[a * nm + j], Z[b * nm + j], pr);
     const long long v = llrint(pr * scale);
-    if (v) atomicAdd(&d.macc[(int64_t)C[a] * d.n + C[b]], (unsigned long long)v);
+    if (v) atomicAdd(&d.macc[(uint32_t)C[a] * (uint32_t)d.n + (uint32_t)C[b]], (unsigned long long)v);
   }
 }
 

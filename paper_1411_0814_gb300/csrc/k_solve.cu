@@ -53,8 +53,10 @@ __global__ void __launch_bounds__(256) k_build_K(const ProbDesc* __restrict__ de
   static_cast<TK*>(static_cast<void*>(d.Kmat))[e] = (TK)v;  // FP32 forms keep Kmat in FP32
 }
 
+// Element offsets inside Y, the mask and Kmat are 32-bit (the host checks that
+// they fit): 64-bit integer multiplies and adds are slow on this part.
 template <typename T>
-__device__ __forceinline__ T load_y(const ProbDesc& d, int64_t idx) {
+__device__ __forceinline__ T load_y(const ProbDesc& d, uint32_t idx) {
   if (d.y_dtype == 0) return (T)__ldg(static_cast<const double*>(d.Y) + idx);
   return (T)__ldg(static_cast<const float*>(d.Y) + idx);
 }
@@ -97,21 +99,22 @@ __global__ void __launch_bounds__(256) k_normal(const ProbDesc* __restrict__ des
   const int64_t m = d.m, n = d.n;
   // loader mapping: entry e = threadIdx.x + 256 k -> (column e / 64, row or output e % 64)
   const int lr = threadIdx.x & 63, lj = threadIdx.x >> 6;
-  const int64_t li = i0 + lr;
+  const uint32_t li = (uint32_t)(i0 + lr);
+  const uint32_t ldy = (uint32_t)d.ldy, ldb = (uint32_t)d.ldb, qp = (uint32_t)d.q_pad;
   T ypre[4], kpre[4];
   uint32_t wpre[4];
-  auto load_chunk = [&](int64_t j0) {
+  auto load_chunk = [&](uint32_t j0) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const int64_t j = j0 + lj + 4 * k;
-      const bool in = li < m && j < n;
-      wpre[k] = in ? __ldg(d.bits + j * d.ldb + (li >> 5)) : 0u;
-      ypre[k] = in ? load_y<T>(d, j * d.ldy + li) : (T)0;
-      kpre[k] = j < n ? __ldg(Kmat + j * d.q_pad + q0 + lr) : (T)0;
+      const uint32_t j = j0 + lj + 4 * k;
+      const bool in = li < (uint32_t)m && j < (uint32_t)n;
+      wpre[k] = in ? __ldg(d.bits + (j * ldb + (li >> 5))) : 0u;
+      ypre[k] = in ? load_y<T>(d, j * ldy + li) : (T)0;
+      kpre[k] = j < (uint32_t)n ? __ldg(Kmat + (j * qp + q0 + lr)) : (T)0;
     }
   };
   load_chunk(0);
-  for (int64_t j0 = 0; j0 < n; j0 += kJT) {
+  for (uint32_t j0 = 0; j0 < (uint32_t)n; j0 += kJT) {
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -121,7 +124,7 @@ __global__ void __launch_bounds__(256) k_normal(const ProbDesc* __restrict__ des
       ks[lj + 4 * k][lr] = kpre[k];
     }
     __syncthreads();
-    if (j0 + kJT < n) load_chunk(j0 + kJT);
+    if (j0 + kJT < (uint32_t)n) load_chunk(j0 + kJT);
 #pragma unroll 4
     for (int jj = 0; jj < kJT; ++jj) {
       T kv[4], wv[4], yv[4];
@@ -300,8 +303,9 @@ __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ d
   // at most n / 8 terms per thread in the working precision (FP64 arithmetic is
   // far slower than FP32 on this part; one conversion per thread at the end)
   T acc = (T)0;
-  const int64_t wcol = i0 >> 5;
-  const int64_t irow = row_in ? i : i0;  // in-bounds row for the unconditional load
+  const uint32_t wcol = (uint32_t)(i0 >> 5);
+  const uint32_t irow = (uint32_t)(row_in ? i : i0);  // in-bounds row for the unconditional load
+  const uint32_t ldy = (uint32_t)d.ldy, ldb = (uint32_t)d.ldb;
   for (int64_t j0 = 0; j0 < d.n; j0 += kResCols) {
     __syncthreads();
     for (int e = threadIdx.x; e < kResCols * r; e += 256) {
@@ -315,9 +319,9 @@ __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ d
     const int jn = d.n - j0 < kResCols ? (int)(d.n - j0) : kResCols;
 #pragma unroll 4
     for (int jj = wg; jj < jn; jj += 8) {
-      const int64_t j = j0 + jj;
-      const uint32_t word = __ldg(d.bits + j * d.ldb + wcol);
-      const T y = load_y<T>(d, j * d.ldy + irow);
+      const uint32_t j = (uint32_t)j0 + jj;
+      const uint32_t word = __ldg(d.bits + (j * ldb + wcol));
+      const T y = load_y<T>(d, j * ldy + irow);
       T pred = (T)0;
 #pragma unroll
       for (int a = 0; a < RM; ++a)

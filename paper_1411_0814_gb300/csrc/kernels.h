@@ -54,7 +54,7 @@ struct SlabPlan {
   const int64_t* hT;
   size_t task_pos;
 };
-bool slab_supported(int mode, int l);
+bool slab_supported(int mode, int l, int y_dtype);
 cudaError_t launch_gram_slab(int mode, int l, const SlabPlan& S, cudaStream_t s);
 
 cudaError_t launch_pack_mask(const ProbDesc* descs, const int64_t* blk_off, int nprob, int64_t nblocks, cudaStream_t s);

@@ -79,6 +79,18 @@ int validate_problem(const rsm_problem& p, Derived& dv, std::string* why) {
   }
   dv.P_l = dv.l * (dv.l + 1) / 2;
   dv.ldb = (((p.m + 31) / 32) + 3) / 4 * 4;
+  // The kernels index Y, W, the packed mask and the n x n work matrices with
+  // 32-bit offsets (64-bit integer arithmetic is slow on the device).
+  if (p.n > 32768) {
+    if (why) *why = "n > 32768 is not supported";
+    return (int)RSM_ERR_NOT_IMPLEMENTED;
+  }
+  const uint64_t lim = (uint64_t)1 << 32;
+  if ((uint64_t)p.ldy * (uint64_t)p.n >= lim || (uint64_t)p.ldw * (uint64_t)p.n >= lim ||
+      (uint64_t)p.m * 64u >= lim) {
+    if (why) *why = "ldy * n, ldw * n and 64 m must stay below 2^32";
+    return (int)RSM_ERR_NOT_IMPLEMENTED;
+  }
   dv.nblk = (int)((p.n + 31) / 32);
   dv.npad = (int64_t)dv.nblk * 32;
   dv.kx = (int)std::min<int64_t>(std::min<int64_t>(p.n, 32), p.r + 8);
@@ -182,7 +194,7 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
   }
   std::vector<int> ls;
   for (int i = 0; i < count; ++i)
-    if (slab_supported(mode, b.dv[i].l)) ls.push_back(b.dv[i].l);
+    if (slab_supported(mode, b.dv[i].l, ps[i].y_dtype)) ls.push_back(b.dv[i].l);
   std::sort(ls.begin(), ls.end());
   ls.erase(std::unique(ls.begin(), ls.end()), ls.end());
   b.slab_groups.clear();
@@ -190,15 +202,18 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
     Batch::SlabGroup g{L, T.size()};
     for (int sl = 0; sl < b.nslab; ++sl)
       prefix([&](int i) {
-        return b.dv[i].l == L && (int64_t)sl * b.dv[i].slab_rows < ps[i].m ? ps[i].trials : (int64_t)0;
+        return b.dv[i].l == L && slab_supported(mode, L, ps[i].y_dtype) && (int64_t)sl * b.dv[i].slab_rows < ps[i].m
+                   ? ps[i].trials
+                   : (int64_t)0;
       });
     b.slab_groups.push_back(g);
   }
-  b.o_trial_generic = prefix([&](int i) { return slab_supported(mode, b.dv[i].l) ? (int64_t)0 : ps[i].trials; });
+  b.o_trial_generic =
+      prefix([&](int i) { return slab_supported(mode, b.dv[i].l, ps[i].y_dtype) ? (int64_t)0 : ps[i].trials; });
   b.generic_total = total(b.o_trial_generic);
   b.generic_lmax = 0;
   for (int i = 0; i < count; ++i)
-    if (!slab_supported(mode, b.dv[i].l)) b.generic_lmax = std::max(b.generic_lmax, b.dv[i].l);
+    if (!slab_supported(mode, b.dv[i].l, ps[i].y_dtype)) b.generic_lmax = std::max(b.generic_lmax, b.dv[i].l);
 
   // workspace: all zero regions first, then all data regions, then shared partial buffers
   b.zero_off.resize(count);
