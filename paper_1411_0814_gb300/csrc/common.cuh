@@ -61,6 +61,13 @@ struct ProbDesc {
   int32_t status;  // device-written status of this problem
   int32_t pad_;
   int64_t slab_rows;  // rows per slab of the row-slab Gram schedule (a function of n and the Y type only)
+  // normal equations on the tensor cores (FP32 form): padded N of the W x Kw product, V columns per row of
+  // the FP32 V copy; V in FP32 for the FP32 residual (row j at vf32 + j * vf_ld)
+  int32_t tc;  // 1: this problem's normal equations run on the tensor cores
+  int32_t tc_npad;
+  int32_t tc_rb;
+  int32_t vf_ld;
+  const float* vf32;
 };
 
 // ------------------------------------------------------------------ FP64 reciprocal and square root

@@ -1,0 +1,361 @@
+// Stage a8 (the per-row normal equations of eq. solve.barU), FP32 form, on the
+// 5th-generation tensor cores.
+//
+// For every row i the solve needs N_i = sum_{j in K_i} v_j v_j^T (packed, P =
+// r(r+1)/2 entries), b_i = sum_{j in K_i} y_ij v_j and |K_i|.  N_i and |K_i|
+// are one dense product over all rows:
+//     [N_flat | |K|] (m x (P+1)) = W (m x n, 0/1) x Kw (n x (P+1)),
+// Kw[j] = (v_ja v_jb for a <= b, 1).  W is exact in TF32, so Kw is split into
+// a TF32 head and an FP32 tail (Kw = hi + lo, the tail's own truncation leaves
+// ~2^-22 relative) and the product runs as two tcgen05.mma kind::tf32 passes
+// accumulating in FP32 in tensor memory.  b_i (r values) runs on the CUDA cores
+// in the same pass over Y (r FMAs per known entry).
+//
+// A CTA owns 128 rows (the MMA M); it walks the columns in chunks of 32 with a
+// two-stage ring in shared memory: the threads build the chunk's W tile from
+// the mask words (one thread per row) and copy the chunk's pre-laid-out B tiles
+// (Kw hi / lo) while the tensor core works on the previous chunk; one thread
+// issues the MMAs and commits them to the stage's mbarrier, which the threads
+// wait on before refilling that stage.  Operands use the canonical K-major
+// layout without swizzle: 8-row x 16-byte core matrices, 128 bytes each,
+// 8-row groups 128 B apart (SBO), K-adjacent core matrices LBO apart.
+//
+// Every mbarrier wait is bounded; on expiry the CTA flags the problem
+// (counters[6]), waits (bounded) for its last commit, frees its tensor memory
+// and returns.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rsm {
+
+namespace {
+
+constexpr int kRows = 128;      // MMA M: rows per CTA
+constexpr int kChunkK = 32;     // columns per stage
+constexpr int kThreads = 128;
+constexpr uint32_t kWaitLimit = 1u << 26;  // polls of one mbarrier wait before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor: start address, leading (K-direction) and
+// stride (M/N-direction) byte offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::tf32: D FP32, A and B TF32, both K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+// Bounded wait for completion `parity` of the barrier; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's lane (warp w reads lanes 32 w .. 32 w + 31).
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+}  // namespace
+
+// Bytes of one stage: W tile, Kw hi and lo tiles, the chunk's V (RB per column), mask words.
+__host__ __device__ constexpr size_t tc_stage_bytes(int npad, int rb) {
+  return (size_t)kRows * kChunkK * 4 + (size_t)2 * npad * kChunkK * 4 + (size_t)kChunkK * rb * 4 + kChunkK * 4 * 4;
+}
+
+// Columns of tensor memory for an N of npad (a power of two, at least 32).
+__host__ __device__ inline int tc_tmem_cols(int npad) {
+  int c = 32;
+  while (c < npad) c <<= 1;
+  return c;
+}
+
+// B operand image of every chunk, in the shared-memory layout (K-major, no
+// swizzle): chunk c holds Kw hi then Kw lo for columns 32 c .. 32 c + 31,
+// entry (q, jj) at (jj / 4) (npad 16) + (q / 8) 128 + (q % 8) 16 + (jj % 4) 4
+// bytes; then V in FP32 (n_pad x RB).  Kw column q < P: v_a v_b (pair q), q = P: 1.
+__global__ void __launch_bounds__(256) k_build_B_tc(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
+                                                   int nprob) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= off[nprob]) return;
+  const int p = find_problem(off, nprob, g);
+  const ProbDesc& d = descs[p];
+  const int r = d.r, P = r * (r + 1) / 2, npad = d.tc_npad, rb = d.tc_rb;
+  const int n_pad = (int)((d.n + kChunkK - 1) / kChunkK) * kChunkK;
+  const int e = (int)(g - off[p]);  // over n_pad x (npad + rb)
+  const int j = e / (npad + rb), q = e % (npad + rb);
+  float* img = reinterpret_cast<float*>(d.Kmat);
+  if (q < npad) {
+    double v = 0.0;
+    if (j < d.n) {
+      if (q < P) {
+        int a = 0, rem = q;
+        while (rem >= r - a) {
+          rem -= r - a;
+          ++a;
+        }
+        const int b = a + rem;
+        v = d.V[(int64_t)a * d.ldv + j] * d.V[(int64_t)b * d.ldv + j];
+      } else if (q == P) {
+        v = 1.0;
+      }
+    }
+    const float x = (float)v;
+    const float hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);  // TF32 head (low 13 bits cleared)
+    const float lo = x - hi;
+    const int c = j / kChunkK, jj = j % kChunkK;
+    float* base = img + (size_t)c * 2 * npad * kChunkK;
+    const int o = (jj >> 2) * (npad * 4) + (q >> 3) * 32 + (q & 7) * 4 + (jj & 3);  // in floats
+    base[o] = hi;
+    base[npad * kChunkK + o] = lo;
+  } else {
+    const int a = q - npad;
+    float* vf = img + (size_t)n_pad * 2 * npad;
+    vf[(size_t)j * rb + a] = (j < d.n && a < r) ? (float)d.V[(int64_t)a * d.ldv + j] : 0.f;
+  }
+}
+
+template <int RB>
+__global__ void __launch_bounds__(kThreads) k_normal_tc(const ProbDesc* __restrict__ descs,
+                                                       const int64_t* __restrict__ off, int nprob) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ __align__(8) unsigned long long bars[2];
+  __shared__ uint32_t tmem_slot;
+  const int p = find_problem(off, nprob, blockIdx.x);
+  const ProbDesc& d = descs[p];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r = d.r, P = r * (r + 1) / 2, npad = d.tc_npad;
+  const int ncols = tc_tmem_cols(npad);
+  const uint32_t m = (uint32_t)d.m, n = (uint32_t)d.n;
+  const uint32_t i0 = (uint32_t)(blockIdx.x - off[p]) * kRows;
+  const uint32_t row = i0 + tid;
+  const bool row_in = row < m;
+  const int nchunk = (int)((n + kChunkK - 1) / kChunkK);
+  const size_t a_bytes = (size_t)kRows * kChunkK * 4, b_bytes = (size_t)npad * kChunkK * 4;
+  const size_t stage_bytes = tc_stage_bytes(npad, RB);
+  const float* img = reinterpret_cast<const float*>(d.Kmat);
+  const float* vf = img + (size_t)nchunk * kChunkK * 2 * npad;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(smem_u32(&bars[0]), 1);
+    mbar_init(smem_u32(&bars[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = idesc_tf32(npad);
+  const uint32_t ldy = (uint32_t)d.ldy, ldb = (uint32_t)d.ldb;
+  const float* Y = static_cast<const float*>(d.Y);
+
+  float bacc[RB];
+#pragma unroll
+  for (int a = 0; a < RB; ++a) bacc[a] = 0.f;
+  float ypre[kChunkK];
+  auto load_y = [&](int c) {
+#pragma unroll
+    for (int jj = 0; jj < kChunkK; ++jj) {
+      const uint32_t j = (uint32_t)c * kChunkK + jj;
+      ypre[jj] = (row_in && j < n) ? __ldg(Y + (j * ldy + row)) : 0.f;
+    }
+  };
+  load_y(0);
+  bool failed = false;
+  for (int c = 0; c < nchunk; ++c) {
+    const int s = c & 1;
+    unsigned char* st = tc_smem + (size_t)s * stage_bytes;
+    float* As = reinterpret_cast<float*>(st);
+    float* Bs = reinterpret_cast<float*>(st + a_bytes);
+    float* Vs = reinterpret_cast<float*>(st + a_bytes + 2 * b_bytes);
+    uint32_t* Ws = reinterpret_cast<uint32_t*>(st + a_bytes + 2 * b_bytes + (size_t)kChunkK * RB * 4);
+    if (c >= 2 && !failed) failed = !mbar_wait(smem_u32(&bars[s]), (uint32_t)((c - 2) >> 1) & 1u);
+    if (__syncthreads_or(failed)) {
+      failed = true;
+      break;
+    }
+    // mask words of the chunk for this CTA's 128 rows: thread (column tid / 4, word tid % 4)
+    {
+      const uint32_t j = (uint32_t)c * kChunkK + (tid >> 2);
+      Ws[tid] = j < n ? __ldg(d.bits + (j * ldb + (i0 >> 5) + (tid & 3))) : 0u;
+    }
+    // B tiles (already in the shared-memory layout) and the chunk's V
+    {
+      const float4* src = reinterpret_cast<const float4*>(img + (size_t)c * 2 * npad * kChunkK);
+      float4* dst = reinterpret_cast<float4*>(Bs);
+      for (int e = tid; e < 2 * npad * kChunkK / 4; e += kThreads) dst[e] = __ldg(src + e);
+      const float4* vsrc = reinterpret_cast<const float4*>(vf + (size_t)c * kChunkK * RB);
+      float4* vdst = reinterpret_cast<float4*>(Vs);
+      for (int e = tid; e < kChunkK * RB / 4; e += kThreads) vdst[e] = __ldg(vsrc + e);
+    }
+    __syncthreads();
+    // W tile (thread = row): 8 core-matrix columns of 4 values; and b_i on the CUDA cores
+    {
+      float w[kChunkK];
+#pragma unroll
+      for (int jj = 0; jj < kChunkK; ++jj) w[jj] = (float)((Ws[jj * 4 + (tid >> 5)] >> lane) & 1u);
+      float4* arow = reinterpret_cast<float4*>(As) + (tid >> 3) * 8 + (tid & 7);
+#pragma unroll
+      for (int kc = 0; kc < kChunkK / 4; ++kc)
+        arow[kc * (kRows * 4 / 4)] = make_float4(w[4 * kc], w[4 * kc + 1], w[4 * kc + 2], w[4 * kc + 3]);
+#pragma unroll
+      for (int jj = 0; jj < kChunkK; ++jj) {
+        const float yw = w[jj] != 0.f ? ypre[jj] : 0.f;
+        const float4* vrow = reinterpret_cast<const float4*>(Vs + jj * RB);
+#pragma unroll
+        for (int a4 = 0; a4 < RB / 4; ++a4) {
+          const float4 v = vrow[a4];
+          bacc[4 * a4] = fmaf(yw, v.x, bacc[4 * a4]);
+          bacc[4 * a4 + 1] = fmaf(yw, v.y, bacc[4 * a4 + 1]);
+          bacc[4 * a4 + 2] = fmaf(yw, v.z, bacc[4 * a4 + 2]);
+          bacc[4 * a4 + 3] = fmaf(yw, v.w, bacc[4 * a4 + 3]);
+        }
+      }
+    }
+    if (c + 1 < nchunk) load_y(c + 1);
+    proxy_fence();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+      const uint32_t a_lbo = kRows * 16, b_lbo = (uint32_t)npad * 16;
+#pragma unroll
+      for (int ks = 0; ks < kChunkK / 8; ++ks) {  // K = 8 per instruction: two core matrices along K
+        const uint64_t ad = smem_desc(a0 + ks * 2 * a_lbo, a_lbo, 128);
+        const uint64_t bh = smem_desc(b0 + ks * 2 * b_lbo, b_lbo, 128);
+        const uint64_t bl = smem_desc(b0 + (uint32_t)b_bytes + ks * 2 * b_lbo, b_lbo, 128);
+        tc_mma_tf32(tmem, ad, bh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+        tc_mma_tf32(tmem, ad, bl, idesc, 1u);
+      }
+      tc_commit(smem_u32(&bars[s]));
+    }
+  }
+  // the last commit covers every MMA issued before it
+  if (nchunk > 0) {
+    const int c = nchunk - 1;
+    if (!mbar_wait(smem_u32(&bars[c & 1]), (uint32_t)(c >> 1) & 1u)) failed = true;
+  }
+  failed = __syncthreads_or(failed) != 0;  // the same decision in every thread
+  tc_fence_after();
+  if (failed) {
+    if (tid == 0) atomicAdd(&d.counters[6], 1ull);
+  } else {
+    // tensor-memory loads are warp-wide: every lane loads, only rows < m store
+    double* out = d.NB + (size_t)(row_in ? row : 0) * d.q_pad;
+    for (int cb = 0; cb < npad; cb += 16) {
+      float v[16];
+      tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+      if (row_in) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int q = cb + k;
+          if (q < P)
+            out[q] = (double)v[k];
+          else if (q == P)
+            out[P + r] = (double)v[k];  // |K_i|
+        }
+      }
+    }
+    if (row_in) {
+#pragma unroll
+      for (int a = 0; a < RB; ++a)
+        if (a < r) out[P + a] = (double)bacc[a];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+bool normal_tc_supported(int r) { return r >= 1 && r <= 21; }
+
+int normal_tc_rb(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : 24; }
+int normal_tc_npad(int r) { return ((r * (r + 1) / 2 + 1) + 15) / 16 * 16; }
+
+cudaError_t launch_normal_tc(const SolvePlan& S, int rb_max, int npad_max, cudaStream_t s) {
+  const ProbDesc* D = S.descs;
+  const int np = S.nprob;
+  cudaError_t e;
+  if (S.b_total > 0) {
+    k_build_B_tc<<<(unsigned)((S.b_total + 255) / 256), 256, 0, s>>>(D, S.b_off, np);
+    ++g_kernel_launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (S.tc_tiles <= 0) return cudaSuccess;
+  const size_t smem = 2 * tc_stage_bytes(npad_max, rb_max);
+#define RSM_TC(RB)                                                                                             \
+  do {                                                                                                         \
+    if ((e = cudaFuncSetAttribute(k_normal_tc<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != \
+        cudaSuccess)                                                                                           \
+      return e;                                                                                                \
+    k_normal_tc<RB><<<(unsigned)S.tc_tiles, kThreads, smem, s>>>(D, S.tc_off, np);                            \
+  } while (0)
+  if (rb_max <= 8)
+    RSM_TC(8);
+  else if (rb_max <= 16)
+    RSM_TC(16);
+  else
+    RSM_TC(24);
+#undef RSM_TC
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+}  // namespace rsm

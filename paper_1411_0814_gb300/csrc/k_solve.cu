@@ -295,8 +295,7 @@ __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ d
   const int64_t i = i0 + lane;
   const bool row_in = i < d.m;
   const int r = d.r, P = r * (r + 1) / 2;
-  // V: in the FP32 forms the Kmat columns P .. P + r - 1 hold V in FP32 already
-  const T* __restrict__ Kv = static_cast<const T*>(static_cast<const void*>(d.Kmat));
+  // V: the FP32 forms keep a copy of V in FP32 (row j at vf32 + j * vf_ld)
   T u[RM];
 #pragma unroll
   for (int a = 0; a < RM; ++a) u[a] = (a < r && row_in) ? (T)d.U[(int64_t)a * d.ldu + i] : (T)0;
@@ -312,7 +311,7 @@ __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ d
       const int jj = e / r, a = e % r;
       const int64_t j = j0 + jj;
       T v = (T)0;
-      if (j < d.n) v = sizeof(T) == 8 ? (T)d.V[(int64_t)a * d.ldv + j] : Kv[j * d.q_pad + P + a];
+      if (j < d.n) v = sizeof(T) == 8 ? (T)d.V[(int64_t)a * d.ldv + j] : (T)d.vf32[j * d.vf_ld + a];
       vs[jj][a] = v;
     }
     __syncthreads();
@@ -375,6 +374,9 @@ cudaError_t launch_solve_u(const SolvePlan& S, int mode, cudaStream_t s) {
       k_build_K<float><<<(unsigned)((S.k_total + 255) / 256), 256, 0, s>>>(D, S.k_off, np);
     ++g_kernel_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (S.tc_tiles > 0 || S.b_total > 0) {
+    if ((e = launch_normal_tc(S, S.tc_rb, S.tc_npad_max, s)) != cudaSuccess) return e;
   }
   if (S.tile_off_host_total > 0) {
     if (mode == 0) {

@@ -41,7 +41,17 @@ struct SolvePlan {
   int rmax;                  // largest r of the batch
   unsigned long long* fail_list;   // row_total entries: (problem << 32) | row
   unsigned long long* fail_count;  // zero before the launch
+  // tensor-core normal equations (problems with tc set)
+  int64_t b_total;
+  const int64_t* b_off;      // n_pad * (tc_npad + tc_rb) per problem
+  int64_t tc_tiles;
+  const int64_t* tc_off;     // ceil(m / 128) per problem
+  int tc_rb, tc_npad_max;
 };
+bool normal_tc_supported(int r);
+int normal_tc_rb(int r);
+int normal_tc_npad(int r);
+cudaError_t launch_normal_tc(const SolvePlan& S, int rb_max, int npad_max, cudaStream_t s);
 
 // Row-slab schedule of the fused selection + Gram (k_gram_slab.cu).  Table
 // `task_pos` holds nslab prefix tables (nprob + 1 entries each): the trials of

@@ -36,7 +36,10 @@ Sizes sizes_of(const rsm_problem& p, const Derived& dv) {
   s.MX = s.X;
   s.R = align_up((size_t)kEigSplit * n * dv.kx * 8);
   s.small = align_up((2 * 32 * 32 + 32) * 8);
-  s.Kmat = dv.solve_u ? align_up(n * dv.q_pad * 8) : 0;
+  // Kmat: the SIMT form's n x q_pad table, or the tensor-core form's B images
+  // (n_pad x 2 npad FP32) plus V in FP32 (n_pad x 24 at most)
+  const size_t n_pad = (n + 31) / 32 * 32;
+  s.Kmat = dv.solve_u ? align_up(std::max(n * dv.q_pad * 8, n_pad * (2 * (size_t)normal_tc_npad(p.r) + 24) * 4)) : 0;
   s.NB = dv.solve_u ? align_up(m * dv.q_pad * 8) : 0;
   return s;
 }
@@ -129,6 +132,18 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
     b.any_solve |= b.dv[i].solve_u;
     b.rmax = std::max(b.rmax, ps[i].r);
   }
+  // normal equations on the tensor cores: FP32 solve of FP32 Y, r small enough for one N tile
+  b.tc_rb = 0;
+  b.tc_npad_max = 0;
+  for (int i = 0; i < count; ++i) {
+    Derived& dv = b.dv[i];
+    dv.tc = dv.solve_u && ps[i].solve_prec == RSM_PREC_F32 && ps[i].y_dtype == RSM_F32 && normal_tc_supported(ps[i].r);
+    dv.tc_npad = dv.tc ? normal_tc_npad(ps[i].r) : 0;
+    if (dv.tc) {
+      b.tc_rb = std::max(b.tc_rb, normal_tc_rb(ps[i].r));
+      b.tc_npad_max = std::max(b.tc_npad_max, dv.tc_npad);
+    }
+  }
   std::vector<int64_t>& T = b.tables;
   T.clear();
   auto prefix = [&](auto per) -> size_t {  // append an exclusive prefix table, return its position
@@ -174,10 +189,18 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
   b.part_total = total(b.o_part);
   b.o_rot = prefix([&](int i) { return (ps[i].n + 7) / 8; });
   b.o_rowtile = prefix([&](int i) { return (int64_t)kPrecSplit * ((ps[i].n + 15) / 16); });
-  b.o_k = prefix([&](int i) { return b.dv[i].solve_u ? ps[i].n * b.dv[i].q_pad : 0; });
+  b.o_k = prefix([&](int i) { return b.dv[i].solve_u && !b.dv[i].tc ? ps[i].n * b.dv[i].q_pad : 0; });
   b.k_total = total(b.o_k);
-  b.o_tile = prefix([&](int i) { return b.dv[i].solve_u ? ((ps[i].m + 63) / 64) * (b.dv[i].q_pad / 64) : 0; });
+  b.o_tile = prefix([&](int i) {
+    return b.dv[i].solve_u && !b.dv[i].tc ? ((ps[i].m + 63) / 64) * (b.dv[i].q_pad / 64) : 0;
+  });
   b.tile_total = total(b.o_tile);
+  b.o_b = prefix([&](int i) {
+    return b.dv[i].tc ? (ps[i].n + 31) / 32 * 32 * (int64_t)(b.dv[i].tc_npad + b.tc_rb) : 0;
+  });
+  b.b_total = total(b.o_b);
+  b.o_tc = prefix([&](int i) { return b.dv[i].tc ? (ps[i].m + 127) / 128 : 0; });
+  b.tc_total = total(b.o_tc);
   b.o_row = prefix([&](int i) { return b.dv[i].solve_u ? ps[i].m : 0; });
   b.row_total = total(b.o_row);
   b.o_res = prefix([&](int i) { return (int64_t)res_blocks_of(ps[i], b.dv[i]); });
@@ -310,6 +333,19 @@ void bind_batch(Batch& b, const rsm_problem* ps, unsigned char* ws) {
     d.small = reinterpret_cast<double*>(take(s.small));
     d.Kmat = s.Kmat ? reinterpret_cast<double*>(take(s.Kmat)) : nullptr;
     d.NB = s.NB ? reinterpret_cast<double*>(take(s.NB)) : nullptr;
+    d.tc = dv.tc ? 1 : 0;
+    d.tc_npad = dv.tc_npad;
+    d.tc_rb = b.tc_rb;
+    if (d.Kmat) {
+      const float* kf = reinterpret_cast<const float*>(d.Kmat);
+      if (dv.tc) {  // V follows the B images
+        d.vf32 = kf + (size_t)((p.n + 31) / 32 * 32) * 2 * dv.tc_npad;
+        d.vf_ld = b.tc_rb;
+      } else {  // the FP32 Kmat holds V in columns P .. P + r - 1
+        d.vf32 = kf + p.r * (p.r + 1) / 2;
+        d.vf_ld = dv.q_pad;
+      }
+    }
   }
 }
 

@@ -17,6 +17,8 @@ struct Derived {
   int l = 0, nm = 0, P_l = 0, nblk = 0, kx = 0, q = 0, q_pad = 0;
   int64_t ldb = 0, npad = 0, slab_rows = 0;
   bool solve_u = false;
+  bool tc = false;  // normal equations on the tensor cores
+  int tc_npad = 0;
 };
 
 // Validate a problem and fill its derived sizes.  Returns RSM_OK or
@@ -42,9 +44,11 @@ struct Batch {
   std::vector<int64_t> tables;  // all int64 offset tables, concatenated
   // positions (in int64 elements) of each table inside `tables`
   size_t o_pack = 0, o_trial = 0, o_ent = 0, o_pad2 = 0, o_step = 0, o_blk = 0, o_linv = 0, o_tri = 0, o_nk = 0,
-         o_mx = 0, o_chunk = 0, o_part = 0, o_rot = 0, o_rowtile = 0, o_k = 0, o_tile = 0, o_row = 0, o_res = 0;
+         o_mx = 0, o_chunk = 0, o_part = 0, o_rot = 0, o_rowtile = 0, o_k = 0, o_tile = 0, o_row = 0, o_res = 0,
+         o_b = 0, o_tc = 0;
   int64_t pack_blocks = 0, trials_total = 0, ent_total = 0, pad2_total = 0, nk_total = 0, part_total = 0,
-          k_total = 0, tile_total = 0, row_total = 0, res_blocks = 0;
+          k_total = 0, tile_total = 0, row_total = 0, res_blocks = 0, b_total = 0, tc_total = 0;
+  int tc_rb = 0, tc_npad_max = 0;  // batch-wide V stride and largest N of the tensor-core normal equations
   int max_nblk = 0;
   // per-problem byte offsets inside the workspace
   std::vector<size_t> zero_off, data_off;

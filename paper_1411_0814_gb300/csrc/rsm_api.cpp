@@ -232,6 +232,12 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
     sp.res_blocks = b.res_blocks;
     sp.res_off = T + b.o_res;
     sp.rmax = b.rmax;
+    sp.b_total = b.b_total;
+    sp.b_off = T + b.o_b;
+    sp.tc_tiles = b.tc_total;
+    sp.tc_off = T + b.o_tc;
+    sp.tc_rb = b.tc_rb;
+    sp.tc_npad_max = b.tc_npad_max;
     sp.fail_list = reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(slot.ws.ptr) + b.fail_list_off);
     sp.fail_count = reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(slot.ws.ptr) + b.fail_count_off);
     if ((e = launch_solve_u(sp, b.solve_mode, s)) != cudaSuccess) return cuda_fail(e, "solve_u");

@@ -149,3 +149,28 @@ def test_serving_admission_cancel_and_wait_limit():
         results = [h.wait(t, timeout_ns=60 * 10 ** 9) for t in tickets]
         assert all(r.status == abi.RSM_OK for r in results)
         assert max(r.queue_ms for r in results) > 0.0
+
+
+def test_fp32_normal_equations_match_oracle():
+    """FP32 form of the U solve (normal equations on the tensor cores for r <= 21)
+    across ranks that use every accumulator width, in one batch: U V^T on the
+    known entries within 1e-5 of the oracle run on the same FP32-rounded Y."""
+    specs = [(3000, 64, 2, 0.8), (4000, 96, 8, 0.85), (3500, 128, 13, 0.9), (5000, 160, 21, 0.95)]
+    probs = []
+    for k, (m, n, r, rho) in enumerate(specs):
+        p = lowrank_problem(m, n, r, rho, 1e-4, trials=20 * n, seed=70 + k)
+        p.Y = np.asfortranarray(p.Y.astype(np.float32).astype(np.float64))  # the values the device sees
+        probs.append(p)
+    oracles = [oracle.decompose(p.Y, p.W, p.r, p.l, p.trials, p.seed, problem_id=i) for i, p in enumerate(probs)]
+    with rsm.RSM(0) as h:
+        dev = [to_device(p, torch.float32) for p in probs]
+        batch = [rsm.Problem(Y, W, p.r, trials=p.trials, l=p.l, seed=p.seed, problem_id=i, gram="f64", solve="f32")
+                 for i, (p, (Y, W)) in enumerate(zip(probs, dev))]
+        results = h.decompose_batch(batch)
+    for res, o, p in zip(results, oracles, probs):
+        assert res.status == _status_of(o) == abi.RSM_OK
+        Vg = _np(res.V)
+        assert oracle.subspace_angle(Vg, o.V) <= 1e-9
+        rel = known_relative_diff(_np(res.U), Vg, o.U, o.V, p.W, p.Y)
+        print(f"r={p.r}: recon_rel={rel:.3e}")
+        assert rel <= 1e-5
