@@ -168,7 +168,9 @@ __global__ void __launch_bounds__(256) k_build_B_tc(const ProbDesc* __restrict__
 
 template <int RB>
 __global__ void __launch_bounds__(kThreads) k_normal_tc(const ProbDesc* __restrict__ descs,
-                                                       const int64_t* __restrict__ off, int nprob) {
+                                                       const int64_t* __restrict__ off, int nprob,
+                                                       unsigned long long* __restrict__ fail_list,
+                                                       unsigned long long* __restrict__ fail_count) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   __shared__ __align__(8) unsigned long long bars[2];
   __shared__ uint32_t tmem_slot;
@@ -296,6 +298,90 @@ __global__ void __launch_bounds__(kThreads) k_normal_tc(const ProbDesc* __restri
   tc_fence_after();
   if (failed) {
     if (tid == 0) atomicAdd(&d.counters[6], 1ull);
+  } else if (RB == 8) {
+    // r <= 8: solve the r x r system of this row right here, in FP32 (the FP32
+    // form's N_i and b_i carry FP32 rounding anyway).  N_i goes through shared
+    // memory (the stages are idle now) so the packed index can depend on r.
+    float* nsm = reinterpret_cast<float*>(tc_smem) + tid * 37;
+    float cnt = 0.f;
+    for (int cb = 0; cb < npad; cb += 16) {
+      float v[16];
+      tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int q = cb + k;
+        if (q < P) nsm[q] = v[k];
+        if (q == P) cnt = v[k];
+      }
+    }
+    float L[36], u[8];
+    float tr = 0.f;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      if (a >= r) break;
+#pragma unroll
+      for (int b = 0; b <= a; ++b) L[a * (a + 1) / 2 + b] = nsm[b * r - b * (b - 1) / 2 + (a - b)];
+      tr += L[a * (a + 1) / 2 + a];
+    }
+    bool ok = cnt >= (float)r;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (j >= r || !ok) break;
+      float v = L[j * (j + 1) / 2 + j];
+#pragma unroll
+      for (int t = 0; t < j; ++t) v -= L[j * (j + 1) / 2 + t] * L[j * (j + 1) / 2 + t];
+      if (!(v > 1e-6f * tr)) {
+        ok = false;
+        break;
+      }
+      v = sqrtf(v);
+      L[j * (j + 1) / 2 + j] = v;
+      const float iv = 1.0f / v;
+#pragma unroll
+      for (int k = j + 1; k < 8; ++k) {
+        if (k >= r) break;
+        float w = L[k * (k + 1) / 2 + j];
+#pragma unroll
+        for (int t = 0; t < j; ++t) w -= L[k * (k + 1) / 2 + t] * L[j * (j + 1) / 2 + t];
+        L[k * (k + 1) / 2 + j] = w * iv;
+      }
+    }
+    if (row_in) {
+      if (ok) {
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {  // C y = b
+          if (a >= r) break;
+          float v = bacc[a];
+#pragma unroll
+          for (int t = 0; t < a; ++t) v -= L[a * (a + 1) / 2 + t] * u[t];
+          u[a] = v / L[a * (a + 1) / 2 + a];
+        }
+#pragma unroll
+        for (int a = 7; a >= 0; --a) {  // C^T u = y
+          if (a >= r) continue;
+          float v = u[a];
+#pragma unroll
+          for (int t = a + 1; t < 8; ++t)
+            if (t < r) v -= L[t * (t + 1) / 2 + a] * u[t];
+          u[a] = v / L[a * (a + 1) / 2 + a];
+        }
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+          if (a < r) d.U[(int64_t)a * d.ldu + row] = (double)u[a];
+      } else {
+        // too few known entries or a (numerically) singular N_i: hand the row to the
+        // minimum-norm path with its data in the FP64 table
+        double* out = d.NB + (size_t)row * d.q_pad;
+        for (int q = 0; q < P; ++q) out[q] = (double)nsm[q];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+          if (a < r) out[P + a] = (double)bacc[a];
+        out[P + r] = (double)cnt;
+        if (cnt < (float)r) atomicAdd(&d.counters[4], 1ull);
+        const unsigned long long slot = atomicAdd(fail_count, 1ull);
+        fail_list[slot] = ((unsigned long long)p << 32) | (unsigned long long)row;
+      }
+    }
   } else {
     // tensor-memory loads are warp-wide: every lane loads, only rows < m store
     double* out = d.NB + (size_t)(row_in ? row : 0) * d.q_pad;
@@ -345,7 +431,7 @@ cudaError_t launch_normal_tc(const SolvePlan& S, int rb_max, int npad_max, cudaS
     if ((e = cudaFuncSetAttribute(k_normal_tc<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != \
         cudaSuccess)                                                                                           \
       return e;                                                                                                \
-    k_normal_tc<RB><<<(unsigned)S.tc_tiles, kThreads, smem, s>>>(D, S.tc_off, np);                            \
+    k_normal_tc<RB><<<(unsigned)S.tc_tiles, kThreads, smem, s>>>(D, S.tc_off, np, S.fail_list, S.fail_count);  \
   } while (0)
   if (rb_max <= 8)
     RSM_TC(8);

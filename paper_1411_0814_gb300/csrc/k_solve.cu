@@ -400,6 +400,8 @@ cudaError_t launch_solve_u(const SolvePlan& S, int mode, cudaStream_t s) {
     }
     ++g_kernel_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (S.any_solve) {  // rows that any of the solvers handed to the minimum-norm path
     k_row_pinv<<<152, 32 * kPinvWarps, 0, s>>>(D, S.fail_list, S.fail_count);
     ++g_kernel_launches;
   }

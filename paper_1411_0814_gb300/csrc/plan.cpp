@@ -201,8 +201,13 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
   b.b_total = total(b.o_b);
   b.o_tc = prefix([&](int i) { return b.dv[i].tc ? (ps[i].m + 127) / 128 : 0; });
   b.tc_total = total(b.o_tc);
-  b.o_row = prefix([&](int i) { return b.dv[i].solve_u ? ps[i].m : 0; });
+  // rows for k_row_solve: the tensor-core form with r <= 8 (batch-wide accumulator width 8)
+  // solves its rows in its own epilogue
+  b.o_row = prefix([&](int i) { return b.dv[i].solve_u && !(b.dv[i].tc && b.tc_rb == 8) ? ps[i].m : 0; });
   b.row_total = total(b.o_row);
+  b.solve_rows = 0;
+  for (int i = 0; i < count; ++i)
+    if (b.dv[i].solve_u) b.solve_rows += ps[i].m;
   b.o_res = prefix([&](int i) { return (int64_t)res_blocks_of(ps[i], b.dv[i]); });
   b.res_blocks = total(b.o_res);
 
@@ -263,7 +268,7 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
   b.res_bytes_off = off;
   off += align_up((size_t)b.res_blocks * 8);
   b.fail_list_off = off;
-  off += align_up((size_t)b.row_total * 8);
+  off += align_up((size_t)b.solve_rows * 8);  // any solved row may take the minimum-norm path
   b.layout.total_bytes = off;
   b.layout.plan_bytes = align_up(sizeof(ProbDesc) * count) + align_up(T.size() * 8);
   b.gram_mode = ps[0].gram_prec == RSM_PREC_F64 ? 0 : ps[0].gram_prec == RSM_PREC_F32X2 ? 1 : 2;

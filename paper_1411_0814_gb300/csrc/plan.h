@@ -48,6 +48,7 @@ struct Batch {
          o_b = 0, o_tc = 0;
   int64_t pack_blocks = 0, trials_total = 0, ent_total = 0, pad2_total = 0, nk_total = 0, part_total = 0,
           k_total = 0, tile_total = 0, row_total = 0, res_blocks = 0, b_total = 0, tc_total = 0;
+  int64_t solve_rows = 0;  // rows of all problems that solve for U
   int tc_rb = 0, tc_npad_max = 0;  // batch-wide V stride and largest N of the tensor-core normal equations
   int max_nblk = 0;
   // per-problem byte offsets inside the workspace
