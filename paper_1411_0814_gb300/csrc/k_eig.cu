@@ -925,18 +925,32 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
   auto* precond_x = k_precond<T, 1>;  // A^-1 X
   auto* precond_r = k_precond<T, 0>;  // A^-1 R
   RSM_LAUNCH(k_eig_prep<T>, (total(P.pad2) + 255) / 256, 256, D, dev(P.pad2), np, shift_rel, a_iters);
+  // Blocked Cholesky on the stream; the inverse factor X = L^-1 on the second
+  // stream, step k of it as soon as block column k of L is final (after the
+  // panel of step k), so the two sequential chains overlap.
+  cudaError_t ee;
+  if ((ee = cudaEventRecord(P.fork, s)) != cudaSuccess || (ee = cudaStreamWaitEvent(P.aux, P.fork, 0)) != cudaSuccess)
+    return ee;
+  {
+    cudaStream_t s = P.aux;
+    RSM_LAUNCH(k_linv_init<T>, total(P.tri), 256, D, dev(P.tri), np);
+  }
   for (int k = 0; k < P.max_nblk; ++k) {
     const size_t o1 = P.step + (size_t)k * 3 * (np + 1), o2 = o1 + (np + 1), o3 = o2 + (np + 1);
     RSM_LAUNCH(k_potrf<T>, total(o1), 32, D, dev(o1), np, k);
     RSM_LAUNCH(k_panel<T>, total(o2), 256, D, dev(o2), np, k);
+    if ((ee = cudaEventRecord(P.fork, s)) != cudaSuccess || (ee = cudaStreamWaitEvent(P.aux, P.fork, 0)) != cudaSuccess)
+      return ee;
+    {
+      cudaStream_t s = P.aux;
+      const size_t l1 = P.linv + (size_t)k * 2 * (np + 1), l2 = l1 + (np + 1);
+      RSM_LAUNCH(k_linv_scale<T>, total(l1), 256, D, dev(l1), np, k);
+      RSM_LAUNCH(k_linv_update<T>, total(l2), 256, D, dev(l2), np, k);
+    }
     RSM_LAUNCH(k_trail<T>, total(o3), 256, D, dev(o3), np, k);
   }
-  RSM_LAUNCH(k_linv_init<T>, total(P.tri), 256, D, dev(P.tri), np);
-  for (int k = 0; k < P.max_nblk; ++k) {
-    const size_t o1 = P.linv + (size_t)k * 2 * (np + 1), o2 = o1 + (np + 1);
-    RSM_LAUNCH(k_linv_scale<T>, total(o1), 256, D, dev(o1), np, k);
-    RSM_LAUNCH(k_linv_update<T>, total(o2), 256, D, dev(o2), np, k);
-  }
+  if ((ee = cudaEventRecord(P.join, P.aux)) != cudaSuccess || (ee = cudaStreamWaitEvent(s, P.join, 0)) != cudaSuccess)
+    return ee;
   RSM_LAUNCH(k_ainv<T>, total(P.tri), 256, D, dev(P.tri), np);
   RSM_LAUNCH(k_init_X, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
   auto orthonormalise = [&]() -> cudaError_t {

@@ -25,6 +25,8 @@ struct EigPlan {
   const int64_t* hT;
   size_t pad2, step, blk, linv, tri, nk, mx, chunk, part_off, rot, row_tile;  // table positions (linv: 2 per step)
   double* part;  // partial Gram sums of the block iteration
+  cudaStream_t aux;          // second stream for the inverse factor
+  cudaEvent_t fork, join;    // events between the two streams (no timing)
 };
 
 struct SolvePlan {

@@ -114,10 +114,12 @@ struct PinBuf {
 // workspace, a plan buffer, pinned readback space and stage events.
 struct Slot {
   cudaStream_t stream = nullptr;
+  cudaStream_t aux = nullptr;  // second stream: the inverse factor overlaps the factorisation
   bool own_stream = false;
   DevBuf ws, plan;
   PinBuf host;
   cudaEvent_t ev[10] = {};
+  cudaEvent_t fork = nullptr, join = nullptr;  // timing-free events between stream and aux
   int init(cudaStream_t external) {
     if (external) {
       stream = external;
@@ -125,10 +127,18 @@ struct Slot {
       RSM_CUDA(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
       own_stream = true;
     }
+    RSM_CUDA(cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking));
     for (auto& e : ev) RSM_CUDA(cudaEventCreate(&e));
+    RSM_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    RSM_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
     return RSM_OK;
   }
   void destroy() {
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    fork = join = nullptr;
+    if (aux) cudaStreamDestroy(aux);
+    aux = nullptr;
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
     ws.release();
@@ -216,6 +226,9 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
   ep.rot = b.o_rot;
   ep.row_tile = b.o_rowtile;
   ep.part = reinterpret_cast<double*>(static_cast<unsigned char*>(slot.ws.ptr) + b.part_bytes_off);
+  ep.aux = slot.aux;
+  ep.fork = slot.fork;
+  ep.join = slot.join;
   if ((e = launch_eig(ep, fp64_factor, shift_rel, fp64_factor ? kEigIters64 : kEigIters32, s)) != cudaSuccess)
     return cuda_fail(e, "eig");
   RSM_CUDA(cudaEventRecord(slot.ev[6], s));
