@@ -32,10 +32,14 @@ __host__ __device__ inline size_t minor_smem_per_warp(int lmax) {
 
 // Newton refinement of the n_minor columns of Z (l x n_minor, FP64) against the
 // complement eigenvectors of the FP32 basis Qf (eigenvalues on Sf's diagonal).
-__device__ inline void newton_refine(const double* Gs, const float* Sf, const float* Qf, double* Z, double* rv,
+// Qd (l x l, stride ls) and lam (l) are FP64 copies of the FP32 eigenvectors and
+// eigenvalues, made once per trial so the steps convert nothing.  The steps stop
+// early once every correction is below 1e-17 (z has unit norm).
+__device__ inline void newton_refine(const double* Gs, const double* Qd, const double* lam, double* Z, double* rv,
                                      double* cv, int l, int nm, int ls, const int* is_minor, double fro) {
   const int lane = threadIdx.x & 31;
   for (int step = 0; step < kNewtonSteps; ++step) {
+    double cmax = 0.0;
     for (int j = 0; j < nm; ++j) {
       double gz = 0.0, za = 0.0;
       if (lane < l) {
@@ -60,19 +64,22 @@ __device__ inline void newton_refine(const double* Gs, const float* Sf, const fl
         double c = 0.0;
         if (!is_minor[lane]) {
           double qr = 0.0;
-          for (int a = 0; a < l; ++a) qr = fma((double)Qf[a * ls + lane], rv[a], qr);
-          c = qr / ((double)Sf[lane * ls + lane] - th);
+          for (int a = 0; a < l; ++a) qr = fma(Qd[a * ls + lane], rv[a], qr);
+          c = qr * rcp64(lam[lane] - th);
         }
         cv[lane] = c;
+        cmax = fmax(cmax, fabs(c));
       }
       __syncwarp();
       if (lane < l) {
         double zn = Z[lane * nm + j];
-        for (int i = 0; i < l; ++i) zn = fma(-cv[i], (double)Qf[lane * ls + i], zn);
+        for (int i = 0; i < l; ++i) zn = fma(-cv[i], Qd[lane * ls + i], zn);
         Z[lane * nm + j] = zn;
       }
       __syncwarp();
     }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
     for (int j = 0; j < nm; ++j) {  // Gram-Schmidt (twice) in FP64
       for (int pass = 0; pass < 2; ++pass)
         for (int k = 0; k < j; ++k) {
@@ -85,10 +92,11 @@ __device__ inline void newton_refine(const double* Gs, const float* Sf, const fl
       double nn = lane < l ? Z[lane * nm + j] * Z[lane * nm + j] : 0.0;
 #pragma unroll
       for (int o = 16; o; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
-      const double inv = 1.0 / sqrt(nn);
+      const double inv = rsqrt64(nn);
       if (lane < l) Z[lane * nm + j] *= inv;
       __syncwarp();
     }
+    if (cmax < 1e-17) break;
   }
 }
 
@@ -204,8 +212,10 @@ __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDe
       const int a = it / nm, j = it % nm;
       Z[a * nm + j] = (double)Qf[a * ls + pick[wid][j]];
     }
+    for (int it = lane; it < l * l; it += 32) Wd[(it / l) * ls + (it % l)] = (double)Qf[(it / l) * ls + (it % l)];
+    if (lane < l) gv[lane] = (double)Sf[lane * ls + lane];
     __syncwarp();
-    newton_refine(Gs, Sf, Qf, Z, rv, cv, l, nm, ls, is_minor[wid], fro);
+    newton_refine(Gs, Wd, gv, Z, rv, cv, l, nm, ls, is_minor[wid], fro);
   }
 
   if (d.debug_Z)

@@ -286,7 +286,7 @@ constexpr int kResCols = 64;
 template <typename T, int RM>
 __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                  int nprob, double* __restrict__ partial) {
-  __shared__ T vs[kResCols][kMaxR + 1];
+  __shared__ __align__(16) T vs[kResCols][RM];  // zero past r, so the products need no guard
   __shared__ double red[8];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
@@ -307,11 +307,11 @@ __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ d
   const uint32_t ldy = (uint32_t)d.ldy, ldb = (uint32_t)d.ldb;
   for (int64_t j0 = 0; j0 < d.n; j0 += kResCols) {
     __syncthreads();
-    for (int e = threadIdx.x; e < kResCols * r; e += 256) {
-      const int jj = e / r, a = e % r;
+    for (int e = threadIdx.x; e < kResCols * RM; e += 256) {
+      const int jj = e / RM, a = e % RM;
       const int64_t j = j0 + jj;
       T v = (T)0;
-      if (j < d.n) v = sizeof(T) == 8 ? (T)d.V[(int64_t)a * d.ldv + j] : (T)d.vf32[j * d.vf_ld + a];
+      if (j < d.n && a < r) v = sizeof(T) == 8 ? (T)d.V[(int64_t)a * d.ldv + j] : (T)d.vf32[j * d.vf_ld + a];
       vs[jj][a] = v;
     }
     __syncthreads();
@@ -322,9 +322,20 @@ __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ d
       const uint32_t word = __ldg(d.bits + (j * ldb + wcol));
       const T y = load_y<T>(d, j * ldy + irow);
       T pred = (T)0;
+      if constexpr (sizeof(T) == 4) {  // V row by 16-byte shared-memory loads
+        const float4* vr = reinterpret_cast<const float4*>(&vs[jj][0]);
 #pragma unroll
-      for (int a = 0; a < RM; ++a)
-        if (a < r) pred = fma(u[a], vs[jj][a], pred);
+        for (int a4 = 0; a4 < RM / 4; ++a4) {
+          const float4 v = vr[a4];
+          pred = fmaf(u[4 * a4], v.x, pred);
+          pred = fmaf(u[4 * a4 + 1], v.y, pred);
+          pred = fmaf(u[4 * a4 + 2], v.z, pred);
+          pred = fmaf(u[4 * a4 + 3], v.w, pred);
+        }
+      } else {
+#pragma unroll
+        for (int a = 0; a < RM; ++a) pred = fma(u[a], vs[jj][a], pred);
+      }
       const T diff = (row_in && ((word >> lane) & 1u)) ? y - pred : (T)0;
       acc = fma(diff, diff, acc);
     }

@@ -1,0 +1,59 @@
+// Small copy kernels that keep the per-call plan upload, workspace zeroing and
+// result readback off the DMA engines.  Host buffers are pinned
+// (cudaMallocHost) and therefore directly addressable from the device under
+// unified addressing, so a kernel moves them: a caller's large asynchronous
+// host<->device copy on another stream (queued on a copy engine) then does not
+// hold back a decomposition's first launch.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rsm {
+
+// dst[0 .. n16) = src[0 .. n16) in 16-byte words (either side may be pinned host memory).
+__global__ void __launch_bounds__(256) k_copy16(const uint4* __restrict__ src, uint4* __restrict__ dst, int64_t n16) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+__global__ void __launch_bounds__(256) k_zero16(uint4* __restrict__ dst, int64_t n16) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Per problem: counters (8 x u64) then stats (64 x f64) into host memory at stride `stride` bytes.
+__global__ void __launch_bounds__(128) k_readback(const ProbDesc* __restrict__ descs, int nprob,
+                                                 unsigned char* __restrict__ host, int stride) {
+  const int p = blockIdx.x;
+  if (p >= nprob) return;
+  const ProbDesc& d = descs[p];
+  unsigned long long* c = reinterpret_cast<unsigned long long*>(host + (size_t)p * stride);
+  double* st = reinterpret_cast<double*>(host + (size_t)p * stride + 64);
+  if (threadIdx.x < 8) c[threadIdx.x] = d.counters[threadIdx.x];
+  if (threadIdx.x < 64) st[threadIdx.x] = d.stats[threadIdx.x];
+}
+
+cudaError_t launch_copy16(const void* src, void* dst, size_t bytes, cudaStream_t s) {
+  const int64_t n16 = (int64_t)(bytes / 16);
+  if (n16 <= 0) return cudaSuccess;
+  const int64_t blocks = (n16 + 255) / 256 < 1024 ? (n16 + 255) / 256 : 1024;
+  k_copy16<<<(unsigned)blocks, 256, 0, s>>>(static_cast<const uint4*>(src), static_cast<uint4*>(dst), n16);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero16(void* dst, size_t bytes, cudaStream_t s) {
+  const int64_t n16 = (int64_t)(bytes / 16);
+  if (n16 <= 0) return cudaSuccess;
+  const int64_t blocks = (n16 + 255) / 256 < 4096 ? (n16 + 255) / 256 : 4096;
+  k_zero16<<<(unsigned)blocks, 256, 0, s>>>(static_cast<uint4*>(dst), n16);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_readback(const ProbDesc* descs, int nprob, void* host, int stride, cudaStream_t s) {
+  k_readback<<<nprob, 128, 0, s>>>(descs, nprob, static_cast<unsigned char*>(host), stride);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+}  // namespace rsm

@@ -70,6 +70,9 @@ struct SlabPlan {
 bool slab_supported(int mode, int l, int y_dtype);
 cudaError_t launch_gram_slab(int mode, int l, const SlabPlan& S, cudaStream_t s);
 
+cudaError_t launch_copy16(const void* src, void* dst, size_t bytes, cudaStream_t s);  // bytes: multiple of 16
+cudaError_t launch_zero16(void* dst, size_t bytes, cudaStream_t s);
+cudaError_t launch_readback(const ProbDesc* descs, int nprob, void* host, int stride, cudaStream_t s);
 cudaError_t launch_pack_mask(const ProbDesc* descs, const int64_t* blk_off, int nprob, int64_t nblocks, cudaStream_t s);
 cudaError_t launch_sample(const ProbDesc* descs, const int64_t* trial_off, int nprob, int64_t total, cudaStream_t s);
 cudaError_t launch_sample_range(const ProbDesc& d, int64_t t0, int64_t count, int32_t* cols, cudaStream_t s);

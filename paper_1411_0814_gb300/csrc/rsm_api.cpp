@@ -269,11 +269,8 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
 constexpr size_t kReadback = 8 * 8 + 64 * 8;
 
 int enqueue_readback(Batch& b, Slot& slot) {
-  for (int i = 0; i < b.nprob; ++i) {
-    unsigned char* dst = static_cast<unsigned char*>(slot.host.ptr) + (size_t)i * kReadback;
-    RSM_CUDA(cudaMemcpyAsync(dst, b.descs[i].counters, 64, cudaMemcpyDeviceToHost, slot.stream));
-    RSM_CUDA(cudaMemcpyAsync(dst + 64, b.descs[i].stats, 64 * 8, cudaMemcpyDeviceToHost, slot.stream));
-  }
+  const ProbDesc* D = reinterpret_cast<const ProbDesc*>(slot.plan.ptr);
+  RSM_CUDA(launch_readback(D, b.nprob, slot.host.ptr, kReadback, slot.stream));
   return RSM_OK;
 }
 
@@ -294,8 +291,9 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
   std::memcpy(hp + dsz, b.tables.data(), b.tables.size() * 8);
   const int64_t launches0 = g_kernel_launches;
   RSM_CUDA(cudaEventRecord(slot.ev[0], slot.stream));
-  RSM_CUDA(cudaMemcpyAsync(slot.plan.ptr, hp, dsz + b.tables.size() * 8, cudaMemcpyHostToDevice, slot.stream));
-  RSM_CUDA(cudaMemsetAsync(slot.ws.ptr, 0, b.layout.zero_bytes, slot.stream));
+  // plan upload and zeroing by kernels, not by the copy engines (see k_util.cu)
+  RSM_CUDA(launch_copy16(hp, slot.plan.ptr, (dsz + b.tables.size() * 8 + 15) / 16 * 16, slot.stream));
+  RSM_CUDA(launch_zero16(slot.ws.ptr, (b.layout.zero_bytes + 15) / 16 * 16, slot.stream));
   RSM_CUDA(cudaEventRecord(slot.ev[1], slot.stream));
   int64_t max_n = 0;
   for (int i = 0; i < count; ++i) max_n = std::max<int64_t>(max_n, ps[i].n);
