@@ -21,6 +21,9 @@
 namespace rsm {
 
 constexpr int kSlabWarps = 4;
+#ifndef RSM_SLAB_MINB
+#define RSM_SLAB_MINB 4
+#endif
 constexpr int kRing = 1088;  // pending rows per warp: < 32 + 32 * 32
 
 template <int MODE>
@@ -41,7 +44,7 @@ struct SlabT<2> {  // FP32 Gram of FP32 Y
 };
 
 template <int MODE, int L>
-__global__ void __launch_bounds__(32 * kSlabWarps) k_gram_slab(const ProbDesc* __restrict__ descs,
+__global__ void __launch_bounds__(32 * kSlabWarps, RSM_SLAB_MINB) k_gram_slab(const ProbDesc* __restrict__ descs,
                                                                const int64_t* __restrict__ task_off, int nprob,
                                                                int slab) {
   using Tr = SlabT<MODE>;

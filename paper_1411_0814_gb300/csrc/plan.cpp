@@ -1,6 +1,10 @@
 // Host-side planning of a batch of problems (see plan.h).
 #include "plan.h"
 
+#ifndef RSM_EIG_EXTRA
+#define RSM_EIG_EXTRA 4  // extra vectors of the eigen block iteration beyond r (the gap at r is wide)
+#endif
+
 #include <algorithm>
 
 namespace rsm {
@@ -96,7 +100,7 @@ int validate_problem(const rsm_problem& p, Derived& dv, std::string* why) {
   }
   dv.nblk = (int)((p.n + 31) / 32);
   dv.npad = (int64_t)dv.nblk * 32;
-  dv.kx = (int)std::min<int64_t>(std::min<int64_t>(p.n, 32), p.r + 8);
+  dv.kx = (int)std::min<int64_t>(std::min<int64_t>(p.n, 32), p.r + RSM_EIG_EXTRA);
   dv.q = p.r * (p.r + 1) / 2 + p.r + 1;
   dv.q_pad = (dv.q + 63) / 64 * 64;
   dv.solve_u = p.U != nullptr;
