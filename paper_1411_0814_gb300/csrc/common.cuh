@@ -32,6 +32,7 @@ struct ProbDesc {
   double* gram;         // trials x l(l+1)/2, packed upper triangle (a <= b), row-major by a
   unsigned long long* macc;  // n x n fixed-point accumulator of M
   double* M;                 // n x n
+  float2* Mdf;               // n x n, M as FP32 pairs (hi, lo) for the products M X
   void* F1;                  // npad x npad work (Cholesky factor, then A^-1), FP32 or FP64
   void* F2;                  // npad x npad work (inverse factor)
   void* Dinv;                // nblk diagonal-block inverses, 32 x 32 each

@@ -62,10 +62,14 @@ __global__ void __launch_bounds__(256) k_eig_prep(const ProbDesc* __restrict__ d
   const double mean = (double)d.counters[0] * d.n_minor / (double)d.n;
   const double tau = mean > 0.0 ? shift_rel * mean : 1.0;
   T v;
-  if (i < d.n && j < d.n)
-    v = (T)(d.M[i * d.n + j] + (i == j ? tau : 0.0));
-  else
+  if (i < d.n && j < d.n) {
+    const double mij = d.M[i * d.n + j];
+    v = (T)(mij + (i == j ? tau : 0.0));
+    const float hi = __double2float_rn(mij);  // M as an FP32 pair for the products M X
+    d.Mdf[i * d.n + j] = make_float2(hi, __double2float_rn(mij - (double)hi));
+  } else {
     v = (i == j) ? (T)1 : (T)0;
+  }
   F1of<T>(d)[e] = v;
 }
 
@@ -322,57 +326,76 @@ __global__ void __launch_bounds__(256) k_init_X(const ProbDesc* __restrict__ des
   d.X[e] = ((double)w.x + 0.5) * (2.0 / 4294967296.0) - 1.0;
 }
 
-constexpr int kSplit = 8;    // split of the inner dimension of the FP64 product M X
+constexpr int kSplit = 32;   // split of the inner dimension of the product M X (R slots)
 constexpr int kPSplit = 4;   // split of the inner dimension of the preconditioner product
-constexpr int kRowTile = 32;  // rows per CTA of the n x kx products
+constexpr int kMxRows = 128;  // rows per CTA of M X (one per thread)
+constexpr int kMxSub = 64;    // columns of X staged per pass
 
-// out = M X (FP64), split over the inner dimension: part s covers j in [s n / kSplit, (s+1) n / kSplit).
-// Partial results go to d.R (kSplit x n x kx) and are summed in fixed order by k_split_sum.
-__global__ void __launch_bounds__(256) k_gemm_MX(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
-                                                int nprob) {
-  __shared__ double ms[kRowTile][33];
-  __shared__ double xs[32][kMaxL + 1];
+// out = M X to about FP64 accuracy on the FP32 pipes (FP64 instructions issue
+// far slower than FP32 ones here).  M is held as FP32 pairs (hi + lo, 48
+// significant bits, written by k_eig_prep); X is split the same way when it is
+// staged.  Per term: the head product hi*hi is split exactly (TwoProduct by
+// FMA), the cross terms hi*lo + lo*hi are single FP32 products, and the running
+// sum is a float pair updated by TwoSum (Knuth), so the accumulation carries
+// about 2^-44 relative accuracy; the lo*lo term (2^-48) is dropped.
+// Thread = row i (M is symmetric, so M[j][i] is read: consecutive threads read
+// consecutive addresses); split s covers columns j in [s n / kSplit, (s+1) n / kSplit);
+// the parts go to R slots and k_split_sum adds them in FP64 in a fixed order.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+template <int KXB>
+__global__ void __launch_bounds__(kMxRows) k_gemm_MX(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
+                                                    int nprob) {
+  __shared__ float2 xs[kMxSub][KXB];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
   if (d.stats[kConvFlag] != 0.0) return;  // converged: the rest of the iteration is skipped
   const int local = (int)(blockIdx.x - off[p]);
   const int n = (int)d.n;
   const int kx = d.kx;
-  const int ntile = (n + kRowTile - 1) / kRowTile;
+  const int ntile = (n + kMxRows - 1) / kMxRows;
   const int split = local / ntile;
-  const int i0 = (local % ntile) * kRowTile;
+  const int i = (local % ntile) * kMxRows + threadIdx.x;
   const int j_begin = split * n / kSplit, j_end = (split + 1) * n / kSplit;
-  const int tr = threadIdx.x % kRowTile, tc = threadIdx.x / kRowTile;  // 8 column groups
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int j0 = j_begin; j0 < j_end; j0 += 32) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < kRowTile * 32; e += 256) {
-      const int r = e / 32, c = e % 32;
-      const int i = i0 + r, j = j0 + c;
-      ms[r][c] = (i < n && j < j_end) ? d.M[i * n + j] : 0.0;
-    }
-    for (int e = threadIdx.x; e < 32 * kx; e += 256) {
-      const int r = e / kx, c = e % kx;
-      const int j = j0 + r;
-      xs[r][c] = (j < j_end) ? d.X[j * kx + c] : 0.0;
-    }
-    __syncthreads();
-    for (int u = 0; u < 32; ++u) {
-      const double mv = ms[tr][u];
+  float sh[KXB], sl[KXB];
 #pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const int c = tc + 8 * s;
-        if (c < kx) acc[s] = fma(mv, xs[u][c], acc[s]);
+  for (int c = 0; c < KXB; ++c) sh[c] = sl[c] = 0.f;
+  const float2* __restrict__ Mdf = d.Mdf;
+  for (int j0 = j_begin; j0 < j_end; j0 += kMxSub) {
+    const int jn = j_end - j0 < kMxSub ? j_end - j0 : kMxSub;
+    __syncthreads();
+    for (int e = threadIdx.x; e < jn * KXB; e += kMxRows) {
+      const int jj = e / KXB, c = e % KXB;
+      const double x = c < kx ? d.X[(j0 + jj) * kx + c] : 0.0;
+      const float xh = __double2float_rn(x);
+      xs[jj][c] = make_float2(xh, __double2float_rn(x - (double)xh));
+    }
+    __syncthreads();
+    if (i < n) {
+      for (int jj = 0; jj < jn; ++jj) {
+        const float2 m = __ldg(Mdf + (j0 + jj) * n + i);
+#pragma unroll
+        for (int c = 0; c < KXB; ++c) {
+          const float2 x = xs[jj][c];
+          const float ph = __fmul_rn(m.x, x.x);
+          const float pe = __fmaf_rn(m.x, x.x, -ph);
+          const float cross = __fmaf_rn(m.x, x.y, __fmul_rn(m.y, x.x));
+          float s, er;
+          two_sum(sh[c], ph, s, er);
+          sh[c] = s;
+          sl[c] = __fadd_rn(sl[c], __fadd_rn(er, __fadd_rn(pe, cross)));
+        }
       }
     }
   }
-  const int i = i0 + tr;
   if (i < n)
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const int c = tc + 8 * s;
-      if (c < kx) d.R[(split * n + i) * kx + c] = acc[s];
-    }
+    for (int c = 0; c < KXB; ++c)
+      if (c < kx) d.R[(split * n + i) * kx + c] = (double)sh[c] + (double)sl[c];
 }
 
 __global__ void __launch_bounds__(256) k_split_sum(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
@@ -974,7 +997,10 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
   for (int it = 0; it <= iters; ++it) {
     if (sizeof(T) == 8 && it > 0)
       if ((e = orthonormalise()) != cudaSuccess) return e;
-    RSM_LAUNCH(k_gemm_MX, total(P.mx), 256, D, dev(P.mx), np);
+    if (P.kx_max <= 16)
+      RSM_LAUNCH(k_gemm_MX<16>, total(P.mx), kMxRows, D, dev(P.mx), np);
+    else
+      RSM_LAUNCH(k_gemm_MX<32>, total(P.mx), kMxRows, D, dev(P.mx), np);
     RSM_LAUNCH(k_split_sum, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
     RSM_LAUNCH_SMEM(k_xtx<true>, total(P.chunk), 256, xtx_smem, D, dev(P.chunk), np, P.part, dev(P.part_off));
     RSM_LAUNCH_SMEM(k_rr64, np, kSmallThreads, kRRSmem, D, np, P.part, dev(P.part_off));

@@ -21,6 +21,7 @@ struct EigPlan {
   const ProbDesc* descs;
   int nprob;
   int max_nblk;
+  int kx_max;  // largest block width of the batch
   const int64_t* dT;
   const int64_t* hT;
   size_t pad2, step, blk, linv, tri, nk, mx, chunk, part_off, rot, row_tile;  // table positions (linv: 2 per step)

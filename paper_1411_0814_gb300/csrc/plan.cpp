@@ -10,7 +10,7 @@
 namespace rsm {
 
 namespace {
-constexpr int kEigSplit = 8;   // must equal kSplit in k_eig.cu
+constexpr int kEigSplit = 32;  // must equal kSplit in k_eig.cu
 constexpr int kPrecSplit = 4;  // must equal kPSplit in k_eig.cu
 constexpr size_t kAlign = 256;
 
@@ -18,7 +18,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Sizes {
   size_t macc, counters, colcount, stats;                    // zero region
-  size_t bits, cols, rowc, gram, M, F1, F2, Dinv, X, MX, R, small, Kmat, NB;  // data region
+  size_t bits, cols, rowc, gram, M, Mdf, F1, F2, Dinv, X, MX, R, small, Kmat, NB;  // data region
 };
 
 Sizes sizes_of(const rsm_problem& p, const Derived& dv) {
@@ -33,6 +33,7 @@ Sizes sizes_of(const rsm_problem& p, const Derived& dv) {
   s.rowc = align_up(I * 4);
   s.gram = align_up(I * dv.P_l * 8);
   s.M = align_up(n * n * 8);
+  s.Mdf = align_up(n * n * 8);
   s.F1 = align_up((size_t)dv.npad * dv.npad * 8);
   s.F2 = s.F1;
   s.Dinv = align_up((size_t)dv.nblk * 32 * 32 * 8);
@@ -50,7 +51,7 @@ Sizes sizes_of(const rsm_problem& p, const Derived& dv) {
 
 size_t zero_sum(const Sizes& s) { return s.macc + s.counters + s.colcount + s.stats; }
 size_t data_sum(const Sizes& s) {
-  return s.bits + s.cols + s.rowc + s.gram + s.M + s.F1 + s.F2 + s.Dinv + s.X + s.MX + s.R + s.small + s.Kmat + s.NB;
+  return s.bits + s.cols + s.rowc + s.gram + s.M + s.Mdf + s.F1 + s.F2 + s.Dinv + s.X + s.MX + s.R + s.small + s.Kmat + s.NB;
 }
 size_t part_doubles(const rsm_problem& p, const Derived& dv) {
   return (size_t)((p.n + 63) / 64) * 2 * dv.kx * dv.kx;  // chunks of kChunk = 64 rows (k_eig.cu)
@@ -187,7 +188,7 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
   b.o_tri = prefix([&](int i) { return (int64_t)b.dv[i].nblk * (b.dv[i].nblk + 1) / 2; });
   b.o_nk = prefix([&](int i) { return ps[i].n * b.dv[i].kx; });
   b.nk_total = total(b.o_nk);
-  b.o_mx = prefix([&](int i) { return (int64_t)kEigSplit * ((ps[i].n + 31) / 32); });
+  b.o_mx = prefix([&](int i) { return (int64_t)kEigSplit * ((ps[i].n + 127) / 128); });
   b.o_chunk = prefix([&](int i) { return (ps[i].n + 63) / 64; });
   b.o_part = prefix([&](int i) { return (int64_t)part_doubles(ps[i], b.dv[i]); });
   b.part_total = total(b.o_part);
@@ -333,6 +334,7 @@ void bind_batch(Batch& b, const rsm_problem* ps, unsigned char* ws) {
     d.row_counts = reinterpret_cast<int32_t*>(take(s.rowc));
     d.gram = reinterpret_cast<double*>(take(s.gram));
     d.M = reinterpret_cast<double*>(take(s.M));
+    d.Mdf = reinterpret_cast<float2*>(take(s.Mdf));
     d.F1 = take(s.F1);
     d.F2 = take(s.F2);
     d.Dinv = take(s.Dinv);

@@ -212,6 +212,8 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
   ep.descs = D;
   ep.nprob = np;
   ep.max_nblk = b.max_nblk;
+  ep.kx_max = 0;
+  for (int i = 0; i < b.nprob; ++i) ep.kx_max = std::max(ep.kx_max, b.dv[i].kx);
   ep.dT = T;
   ep.hT = b.tables.data();
   ep.pad2 = b.o_pad2;
