@@ -63,14 +63,15 @@ __global__ void __launch_bounds__(32 * kSlabWarps, RSM_SLAB_MINB) k_gram_slab(co
   const int p = find_problem(task_off, nprob, g);
   const ProbDesc& d = descs[p];
   const int64_t t = g - task_off[p];
-  // per-column base pointers (64-bit once per warp); rows are 32-bit offsets from them
-  const typename Tr::src_t* ycol[L];
-  const uint32_t* bcol[L];
+  // 32-bit column offsets into Y and the mask (the host checks ldy n, ldb n < 2^32)
+  const typename Tr::src_t* __restrict__ Yb = static_cast<const typename Tr::src_t*>(d.Y);
+  const uint32_t* __restrict__ Bb = d.bits;
+  uint32_t yofs[L], bofs[L];
 #pragma unroll
   for (int k = 0; k < L; ++k) {
-    const int64_t c = (int64_t)__ldg(d.cols + t * L + k);
-    ycol[k] = static_cast<const typename Tr::src_t*>(d.Y) + c * d.ldy;
-    bcol[k] = d.bits + c * d.ldb;
+    const uint32_t c = (uint32_t)__ldg(d.cols + t * L + k);
+    yofs[k] = c * (uint32_t)d.ldy;
+    bofs[k] = c * (uint32_t)d.ldb;
   }
   const int64_t r0 = (int64_t)slab * d.slab_rows;
   const int64_t r1 = r0 + d.slab_rows < d.m ? r0 + d.slab_rows : d.m;
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(32 * kSlabWarps, RSM_SLAB_MINB) k_gram_slab(co
     const uint32_t row = (uint32_t)ring[k];
     V v[L];
 #pragma unroll
-    for (int a = 0; a < L; ++a) v[a] = Tr::cvt(__ldg(ycol[a] + row));
+    for (int a = 0; a < L; ++a) v[a] = Tr::cvt(__ldg(Yb + (yofs[a] + row)));
 #pragma unroll
     for (int a = 0; a < L; ++a)
 #pragma unroll
@@ -95,14 +96,22 @@ __global__ void __launch_bounds__(32 * kSlabWarps, RSM_SLAB_MINB) k_gram_slab(co
       }
   };
 
+  // The mask words of the next 32-word step are loaded before this step's rows
+  // are gathered, so their latency overlaps the gathers and products.
+  uint32_t nextw[L];
+  auto load_words = [&](int64_t w0) {
+    const uint32_t w = (uint32_t)(w0 + lane);
+    const bool in = w < (uint32_t)w_end;
+#pragma unroll
+    for (int k = 0; k < L; ++k) nextw[k] = in ? __ldg(Bb + (bofs[k] + w)) : 0u;
+  };
+  if (w_begin < w_end) load_words(w_begin);
   for (int64_t w0 = w_begin; w0 < w_end; w0 += 32) {
     const uint32_t w = (uint32_t)(w0 + lane);
-    uint32_t mask = 0;
-    if (w < (uint32_t)w_end) {
-      mask = 0xffffffffu;
+    uint32_t mask = 0xffffffffu;
 #pragma unroll
-      for (int k = 0; k < L; ++k) mask &= __ldg(bcol[k] + w);
-    }
+    for (int k = 0; k < L; ++k) mask &= nextw[k];
+    if (w0 + 32 < w_end) load_words(w0 + 32);
     const int cnt = __popc(mask);
     int incl = cnt;
 #pragma unroll
