@@ -34,9 +34,11 @@ __host__ __device__ inline size_t minor_smem_per_warp(int lmax) {
 // complement eigenvectors of the FP32 basis Qf (eigenvalues on Sf's diagonal).
 // Qd (l x l, stride ls) and lam (l) are FP64 copies of the FP32 eigenvectors and
 // eigenvalues, made once per trial so the steps convert nothing.  The steps stop
-// early once every correction is below 1e-17 (z has unit norm).
+// early once every correction is below `stop` (z has unit norm): 1e-17 for an
+// FP64 or FP32-pair Gram; 1e-10 for an FP32 Gram, whose own rounding (~1e-7
+// relative) already bounds how well its minor vectors are defined.
 __device__ inline void newton_refine(const double* Gs, const double* Qd, const double* lam, double* Z, double* rv,
-                                     double* cv, int l, int nm, int ls, const int* is_minor, double fro) {
+                                     double* cv, int l, int nm, int ls, const int* is_minor, double fro, double stop) {
   const int lane = threadIdx.x & 31;
   for (int step = 0; step < kNewtonSteps; ++step) {
     double cmax = 0.0;
@@ -96,7 +98,7 @@ __device__ inline void newton_refine(const double* Gs, const double* Qd, const d
       if (lane < l) Z[lane * nm + j] *= inv;
       __syncwarp();
     }
-    if (cmax < 1e-17) break;
+    if (cmax < stop) break;
   }
 }
 
@@ -215,7 +217,7 @@ __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDe
     for (int it = lane; it < l * l; it += 32) Wd[(it / l) * ls + (it % l)] = (double)Qf[(it / l) * ls + (it % l)];
     if (lane < l) gv[lane] = (double)Sf[lane * ls + lane];
     __syncwarp();
-    newton_refine(Gs, Wd, gv, Z, rv, cv, l, nm, ls, is_minor[wid], fro);
+    newton_refine(Gs, Wd, gv, Z, rv, cv, l, nm, ls, is_minor[wid], fro, d.gram_fp32 ? 1e-10 : 1e-17);
   }
 
   if (d.debug_Z)

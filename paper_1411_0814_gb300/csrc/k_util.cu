@@ -1,9 +1,10 @@
-// Small copy kernels that keep the per-call plan upload, workspace zeroing and
-// result readback off the DMA engines.  Host buffers are pinned
-// (cudaMallocHost) and therefore directly addressable from the device under
-// unified addressing, so a kernel moves them: a caller's large asynchronous
-// host<->device copy on another stream (queued on a copy engine) then does not
-// hold back a decomposition's first launch.
+// Small copy kernels that keep the per-call plan upload and workspace zeroing
+// off the DMA engines, and gather the per-problem results for one small copy
+// back.  Host buffers are pinned (cudaMallocHost) and therefore directly
+// addressable from the device under unified addressing, so a kernel reads the
+// plan from them: a caller's large asynchronous host-to-device copy on another
+// stream (queued on a copy engine) then does not hold back a decomposition's
+// first launch.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -20,7 +21,7 @@ __global__ void __launch_bounds__(256) k_zero16(uint4* __restrict__ dst, int64_t
     dst[i] = make_uint4(0u, 0u, 0u, 0u);
 }
 
-// Per problem: counters (8 x u64) then stats (64 x f64) into host memory at stride `stride` bytes.
+// Per problem: counters (8 x u64) then stats (64 x f64) at stride `stride` bytes (device staging area).
 __global__ void __launch_bounds__(128) k_readback(const ProbDesc* __restrict__ descs, int nprob,
                                                  unsigned char* __restrict__ host, int stride) {
   const int p = blockIdx.x;

@@ -345,6 +345,7 @@ void bind_batch(Batch& b, const rsm_problem* ps, unsigned char* ws) {
     d.Kmat = s.Kmat ? reinterpret_cast<double*>(take(s.Kmat)) : nullptr;
     d.NB = s.NB ? reinterpret_cast<double*>(take(s.NB)) : nullptr;
     d.tc = dv.tc ? 1 : 0;
+    d.gram_fp32 = p.gram_prec == RSM_PREC_F32 ? 1 : 0;
     d.tc_npad = dv.tc_npad;
     d.tc_rb = b.tc_rb;
     if (d.Kmat) {

@@ -272,7 +272,10 @@ constexpr size_t kReadback = 8 * 8 + 64 * 8;
 
 int enqueue_readback(Batch& b, Slot& slot) {
   const ProbDesc* D = reinterpret_cast<const ProbDesc*>(slot.plan.ptr);
-  RSM_CUDA(launch_readback(D, b.nprob, slot.host.ptr, kReadback, slot.stream));
+  // gather into a device staging area behind the plan, then one small copy to the host
+  unsigned char* staging = static_cast<unsigned char*>(slot.plan.ptr) + b.layout.plan_bytes;
+  RSM_CUDA(launch_readback(D, b.nprob, staging, kReadback, slot.stream));
+  RSM_CUDA(cudaMemcpyAsync(slot.host.ptr, staging, (size_t)b.nprob * kReadback, cudaMemcpyDeviceToHost, slot.stream));
   return RSM_OK;
 }
 
@@ -283,7 +286,7 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
   build_batch(ps, count, b);
   int st = slot.ws.reserve(b.layout.total_bytes);
   if (st != RSM_OK) return st;
-  if ((st = slot.plan.reserve(b.layout.plan_bytes)) != RSM_OK) return st;
+  if ((st = slot.plan.reserve(b.layout.plan_bytes + (size_t)count * kReadback)) != RSM_OK) return st;
   if ((st = slot.host.reserve(std::max(b.layout.plan_bytes, (size_t)count * kReadback))) != RSM_OK) return st;
   bind_batch(b, ps, static_cast<unsigned char*>(slot.ws.ptr));
   // plan upload through the pinned buffer
