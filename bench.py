@@ -39,7 +39,7 @@ STAGES = ["setup", "pack_mask", "sample_cols", "select_gram", "minor_scatter", "
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
     ap.add_argument("--fp64-steps", type=int, default=0, help="timed steps of the FP64 form (default max(3, steps/4))")
@@ -111,7 +111,8 @@ class ClockSampler:
         try:
             self.f = open(self.out_path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                          "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.5)  # nvidia-smi takes a moment to emit its first sample
         except (OSError, FileNotFoundError):
             self.proc = None
 
