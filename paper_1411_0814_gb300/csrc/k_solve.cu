@@ -352,15 +352,101 @@ __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ d
   }
 }
 
+// FP32 form of FP32 Y with 16-byte aligned columns: each lane takes 4
+// consecutive rows (one 16-byte load per column), a CTA 128 rows, its 8 warps
+// split the columns; 4 columns are loaded before any is used, so each warp has
+// 2 KB of Y in flight.  Partials as in k_residual.
+constexpr int kRes4Rows = 128;
+template <int RM>
+__global__ void __launch_bounds__(256) k_residual4(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
+                                                  int nprob, double* __restrict__ partial) {
+  __shared__ __align__(16) float vs[kResCols][RM];
+  __shared__ double red[8];
+  const int p = find_problem(off, nprob, blockIdx.x);
+  const ProbDesc& d = descs[p];
+  const int lane = threadIdx.x & 31, wg = threadIdx.x >> 5;
+  const uint32_t i0 = (uint32_t)(blockIdx.x - off[p]) * kRes4Rows;
+  const uint32_t ib = i0 + 4u * lane;  // first of this lane's 4 rows
+  const uint32_t m = (uint32_t)d.m;
+  const bool quad_in = ib < m;
+  const int r = d.r;
+  float u[4][RM];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int a = 0; a < RM; ++a) u[k][a] = (a < r && ib + k < m) ? (float)d.U[(int64_t)a * d.ldu + ib + k] : 0.f;
+  const float* __restrict__ Y = static_cast<const float*>(d.Y);
+  const uint32_t ldy = (uint32_t)d.ldy, ldb = (uint32_t)d.ldb, n = (uint32_t)d.n;
+  const uint32_t wrow = ib >> 5, shift = ib & 31u;
+  float acc = 0.f;
+  for (uint32_t j0 = 0; j0 < n; j0 += kResCols) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < kResCols * RM; e += 256) {
+      const int jj = e / RM, a = e % RM;
+      const uint32_t j = j0 + jj;
+      vs[jj][a] = (j < n && a < r) ? d.vf32[j * d.vf_ld + a] : 0.f;
+    }
+    __syncthreads();
+    const int jn = n - j0 < (uint32_t)kResCols ? (int)(n - j0) : kResCols;
+    for (int jb = wg; jb < jn; jb += 32) {  // 4 columns per pass: jb, jb + 8, jb + 16, jb + 24
+      float4 y[4];
+      uint32_t bits[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int jj = jb + 8 * q;
+        const uint32_t j = j0 + jj;
+        const bool ok = jj < jn && quad_in;
+        y[q] = ok ? __ldg(reinterpret_cast<const float4*>(Y + (j * ldy + ib))) : make_float4(0.f, 0.f, 0.f, 0.f);
+        bits[q] = ok ? (__ldg(d.bits + (j * ldb + wrow)) >> shift) & 0xFu : 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int jj = jb + 8 * q;
+        if (jj >= jn) break;
+        float pr[4] = {0.f, 0.f, 0.f, 0.f};
+        const float4* vr = reinterpret_cast<const float4*>(&vs[jj][0]);
+#pragma unroll
+        for (int a4 = 0; a4 < RM / 4; ++a4) {
+          const float4 v = vr[a4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            pr[k] = fmaf(u[k][4 * a4], v.x, pr[k]);
+            pr[k] = fmaf(u[k][4 * a4 + 1], v.y, pr[k]);
+            pr[k] = fmaf(u[k][4 * a4 + 2], v.z, pr[k]);
+            pr[k] = fmaf(u[k][4 * a4 + 3], v.w, pr[k]);
+          }
+        }
+        const float yv[4] = {y[q].x, y[q].y, y[q].z, y[q].w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float diff = ((bits[q] >> k) & 1u) ? yv[k] - pr[k] : 0.f;
+          acc = fmaf(diff, diff, acc);
+        }
+      }
+    }
+  }
+  double dacc = (double)acc;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+  if (lane == 0) red[wg] = dacc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += red[k];
+    partial[blockIdx.x] = t;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_residual_final(const ProbDesc* __restrict__ descs,
-                                                       const int64_t* __restrict__ off, int nprob,
-                                                       const double* __restrict__ partial) {
+                                                       const int64_t* __restrict__ off, const int64_t* __restrict__ off4,
+                                                       int64_t base4, int nprob, const double* __restrict__ partial) {
   __shared__ double red[256];
   const int p = blockIdx.x;
   if (p >= nprob) return;
   const ProbDesc& d = descs[p];
-  double s = 0.0;  // strided partial sums, then a fixed tree: deterministic
+  double s = 0.0;  // strided partial sums over this problem's partials (one of the two ranges), then a fixed tree
   for (int64_t b = off[p] + threadIdx.x; b < off[p + 1]; b += 256) s += partial[b];
+  for (int64_t b = base4 + off4[p] + threadIdx.x; b < base4 + off4[p + 1]; b += 256) s += partial[b];
   red[threadIdx.x] = s;
   __syncthreads();
   for (int o = 128; o; o >>= 1) {
@@ -432,9 +518,19 @@ cudaError_t launch_residual(const SolvePlan& S, int mode, double* partial, cudaS
 #undef RSM_RES
     ++g_kernel_launches;
   }
+  if (S.res4_blocks > 0) {
+    double* p4 = partial + S.res_blocks;
+    if (S.rmax <= 8)
+      k_residual4<8><<<(unsigned)S.res4_blocks, 256, 0, s>>>(D, S.res4_off, np, p4);
+    else if (S.rmax <= 16)
+      k_residual4<16><<<(unsigned)S.res4_blocks, 256, 0, s>>>(D, S.res4_off, np, p4);
+    else
+      k_residual4<32><<<(unsigned)S.res4_blocks, 256, 0, s>>>(D, S.res4_off, np, p4);
+    ++g_kernel_launches;
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_residual_final<<<np, 256, 0, s>>>(D, S.res_off, np, partial);
+  k_residual_final<<<np, 256, 0, s>>>(D, S.res_off, S.res4_off, S.res_blocks, np, partial);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

@@ -40,7 +40,9 @@ struct SolvePlan {
   int64_t row_total;
   const int64_t* row_off;    // m per problem
   int64_t res_blocks;
-  const int64_t* res_off;    // ceil(m / 32) per problem
+  const int64_t* res_off;    // ceil(m / 32) per problem (scalar residual kernel)
+  int64_t res4_blocks;
+  const int64_t* res4_off;   // ceil(m / 128) per problem (4-row residual kernel); its partials follow the others
   int rmax;                  // largest r of the batch
   unsigned long long* fail_list;   // row_total entries: (problem << 32) | row
   unsigned long long* fail_count;  // zero before the launch

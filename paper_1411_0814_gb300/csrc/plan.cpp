@@ -56,7 +56,15 @@ size_t data_sum(const Sizes& s) {
 size_t part_doubles(const rsm_problem& p, const Derived& dv) {
   return (size_t)((p.n + 63) / 64) * 2 * dv.kx * dv.kx;  // chunks of kChunk = 64 rows (k_eig.cu)
 }
-size_t res_blocks_of(const rsm_problem& p, const Derived& dv) { return dv.solve_u ? (size_t)((p.m + 31) / 32) : 0; }  // kResRows
+// The 4-row residual kernel: FP32 form of FP32 Y whose columns start on 16-byte boundaries.
+bool res4_of(const rsm_problem& p, const Derived& dv) {
+  return dv.solve_u && p.solve_prec == RSM_PREC_F32 && p.y_dtype == RSM_F32 && p.ldy % 4 == 0 &&
+         (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0;
+}
+size_t res_blocks_of(const rsm_problem& p, const Derived& dv) {  // partial sums of the residual
+  if (!dv.solve_u) return 0;
+  return res4_of(p, dv) ? (size_t)((p.m + 127) / 128) : (size_t)((p.m + 31) / 32);
+}
 }  // namespace
 
 int validate_problem(const rsm_problem& p, Derived& dv, std::string* why) {
@@ -213,8 +221,10 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
   b.solve_rows = 0;
   for (int i = 0; i < count; ++i)
     if (b.dv[i].solve_u) b.solve_rows += ps[i].m;
-  b.o_res = prefix([&](int i) { return (int64_t)res_blocks_of(ps[i], b.dv[i]); });
+  b.o_res = prefix([&](int i) { return res4_of(ps[i], b.dv[i]) ? (int64_t)0 : (int64_t)res_blocks_of(ps[i], b.dv[i]); });
   b.res_blocks = total(b.o_res);
+  b.o_res4 = prefix([&](int i) { return res4_of(ps[i], b.dv[i]) ? (int64_t)res_blocks_of(ps[i], b.dv[i]) : (int64_t)0; });
+  b.res4_blocks = total(b.o_res4);
 
   // Row slabs: the slab size of a problem depends on its own n and Y type only,
   // and problems are grouped by l, so a problem's Gram is summed in the same
@@ -271,7 +281,7 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
   b.part_bytes_off = off;
   off += align_up((size_t)b.part_total * 8);
   b.res_bytes_off = off;
-  off += align_up((size_t)b.res_blocks * 8);
+  off += align_up((size_t)(b.res_blocks + b.res4_blocks) * 8);
   b.fail_list_off = off;
   off += align_up((size_t)b.solve_rows * 8);  // any solved row may take the minimum-norm path
   b.layout.total_bytes = off;

@@ -45,9 +45,9 @@ struct Batch {
   // positions (in int64 elements) of each table inside `tables`
   size_t o_pack = 0, o_trial = 0, o_ent = 0, o_pad2 = 0, o_step = 0, o_blk = 0, o_linv = 0, o_tri = 0, o_nk = 0,
          o_mx = 0, o_chunk = 0, o_part = 0, o_rot = 0, o_rowtile = 0, o_k = 0, o_tile = 0, o_row = 0, o_res = 0,
-         o_b = 0, o_tc = 0;
+         o_b = 0, o_tc = 0, o_res4 = 0;
   int64_t pack_blocks = 0, trials_total = 0, ent_total = 0, pad2_total = 0, nk_total = 0, part_total = 0,
-          k_total = 0, tile_total = 0, row_total = 0, res_blocks = 0, b_total = 0, tc_total = 0;
+          k_total = 0, tile_total = 0, row_total = 0, res_blocks = 0, b_total = 0, tc_total = 0, res4_blocks = 0;
   int64_t solve_rows = 0;  // rows of all problems that solve for U
   int tc_rb = 0, tc_npad_max = 0;  // batch-wide V stride and largest N of the tensor-core normal equations
   int max_nblk = 0;

@@ -253,6 +253,8 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
     sp.tc_off = T + b.o_tc;
     sp.tc_rb = b.tc_rb;
     sp.tc_npad_max = b.tc_npad_max;
+    sp.res4_blocks = b.res4_blocks;
+    sp.res4_off = T + b.o_res4;
     sp.any_solve = b.any_solve;
     sp.fail_list = reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(slot.ws.ptr) + b.fail_list_off);
     sp.fail_count = reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(slot.ws.ptr) + b.fail_count_off);

@@ -179,5 +179,7 @@ def test_fp32_normal_equations_match_oracle():
         Vg = _np(res.V)
         assert oracle.subspace_angle(Vg, o.V) <= 1e-9
         rel = known_relative_diff(_np(res.U), Vg, o.U, o.V, p.W, p.Y)
-        print(f"r={p.r}: recon_rel={rel:.3e}")
+        print(f"r={p.r}: recon_rel={rel:.3e} e={res.e:.6e} oracle e={o.e:.6e}")
         assert rel <= 1e-5
+        # eq. (ep) in FP32 sums: within 1e-4 relative of the oracle's error (e ~ sigma here)
+        assert abs(res.e - o.e) <= 1e-4 * o.e
