@@ -80,17 +80,13 @@ __global__ void __launch_bounds__(256) k_eig_prep(const ProbDesc* __restrict__ d
 // from lane c (fully unrolled, so every register index is a constant).  The
 // inverse X = L^-1 is formed row by row: once row t is final on lane t it is
 // broadcast and every later row adds L[i][t] X[t][.] (forward substitution).
+// Factor and invert one diagonal block held as a[c] = A_kk[lane][c] (row per
+// lane); writes L_kk (lower, zeros above) at A and its inverse at Dinv[k].
 template <typename T>
-__global__ void __launch_bounds__(32) k_potrf(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
-                                             int nprob, int k) {
-  const int p = find_problem(off, nprob, blockIdx.x);
-  const ProbDesc& d = descs[p];
-  const int np = npad_of(d);
-  const int lane = threadIdx.x;
+__device__ __forceinline__ void warp_potrf_block(T (&a)[BS], const ProbDesc& d, int k, int np, bool write_global,
+                                                 T (*dinv_smem)[BS + 1]) {
+  const int lane = threadIdx.x & 31;
   T* A = F1of<T>(d) + (int64_t)k * BS * np + (int64_t)k * BS;
-  T a[BS];
-#pragma unroll
-  for (int c = 0; c < BS; ++c) a[c] = A[lane * np + c];
   bool bad = false;
   T rinv = (T)1;  // 1 / L[lane][lane]
 #pragma unroll
@@ -100,8 +96,8 @@ __global__ void __launch_bounds__(32) k_potrf(const ProbDesc* __restrict__ descs
       bad = true;
       piv = (T)1e-30;
     }
-    const T dj = sqrt(piv);
-    const T ij = (T)1 / dj;
+    const T ij = fast_rsqrt(piv);  // the FP32 factor is a preconditioner: the hardware approximation suffices
+    const T dj = piv * ij;
     if (lane == j) rinv = ij;
     a[j] = lane > j ? a[j] * ij : (lane == j ? dj : (T)0);
 #pragma unroll
@@ -121,18 +117,29 @@ __global__ void __launch_bounds__(32) k_potrf(const ProbDesc* __restrict__ descs
 #pragma unroll
     for (int c = 0; c <= t; ++c) x[c] = fma(lit, __shfl_sync(0xffffffffu, x[c], t), x[c]);
   }
-  T* D = Dinvof<T>(d) + (int64_t)k * BS * BS;
+  if (write_global) {
+    T* D = Dinvof<T>(d) + (int64_t)k * BS * BS;
 #pragma unroll
-  for (int c = 0; c < BS; ++c) {
-    A[lane * np + c] = c <= lane ? a[c] : (T)0;
-    D[lane * BS + c] = c <= lane ? x[c] : (T)0;  // entry (lane, c) of inv(L_kk)
+    for (int c = 0; c < BS; ++c) {
+      A[lane * np + c] = c <= lane ? a[c] : (T)0;
+      D[lane * BS + c] = c <= lane ? x[c] : (T)0;  // entry (lane, c) of inv(L_kk)
+    }
   }
+  if (dinv_smem)
+#pragma unroll
+    for (int c = 0; c < BS; ++c) dinv_smem[lane][c] = c <= lane ? x[c] : (T)0;
 }
+
 
 // 32 x 32 x 32 product helper: each of 256 threads owns 4 outputs (row ty + 8s, column tx).
 // out[r][c] = sum_t X[r][t] * Y(t, c) with Y accessed through the functor.
 
 // Panel: L_ik = A_ik * inv(L_kk)^T for i > k.
+// Step k of the factorisation: block column k.  CTA 0 of a problem factors
+// and inverts the diagonal block A_kk and writes L_kk and inv(L_kk); CTA
+// q >= 1 factors A_kk as well (the same arithmetic, so the same result, in
+// parallel with CTA 0) and forms L_{k+q,k} = A_{k+q,k} inv(L_kk)^T.  One
+// launch per step replaces a factorisation launch followed by a panel launch.
 template <typename T>
 __global__ void __launch_bounds__(256) k_panel(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                               int nprob, int k) {
@@ -140,18 +147,24 @@ __global__ void __launch_bounds__(256) k_panel(const ProbDesc* __restrict__ desc
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
   const int np = npad_of(d);
-  const int i = k + 1 + (int)(blockIdx.x - off[p]);
-  T* Aik = F1of<T>(d) + (int64_t)i * BS * np + (int64_t)k * BS;
-  const T* D = Dinvof<T>(d) + (int64_t)k * BS * BS;
-  for (int e = threadIdx.x; e < BS * BS; e += 256) {
-    x[e / BS][e % BS] = Aik[(e / BS) * np + (e % BS)];
-    y[e / BS][e % BS] = D[e];
+  const int q = (int)(blockIdx.x - off[p]);
+  if (threadIdx.x < 32) {
+    const T* Akk = F1of<T>(d) + (int64_t)k * BS * np + (int64_t)k * BS;
+    T a[BS];
+#pragma unroll
+    for (int c = 0; c < BS; ++c) a[c] = Akk[threadIdx.x * np + c];
+    __syncwarp();
+    warp_potrf_block<T>(a, d, k, np, q == 0, q == 0 ? nullptr : y);
   }
+  if (q == 0) return;
+  const int i = k + q;
+  T* Aik = F1of<T>(d) + (int64_t)i * BS * np + (int64_t)k * BS;
+  for (int e = threadIdx.x; e < BS * BS; e += 256) x[e / BS][e % BS] = Aik[(e / BS) * np + (e % BS)];
   __syncthreads();
   const int tx = threadIdx.x % BS, ty = threadIdx.x / BS;
   T acc[4] = {(T)0, (T)0, (T)0, (T)0};
   for (int t = 0; t < BS; ++t) {
-    const T yv = y[tx][t];  // (inv L_kk)^T [t][tx]
+    const T yv = y[tx][t];  // inv(L_kk)[tx][t]
 #pragma unroll
     for (int s = 0; s < 4; ++s) acc[s] = fma(x[ty + 8 * s][t], yv, acc[s]);
   }
@@ -959,9 +972,8 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
     RSM_LAUNCH(k_linv_init<T>, total(P.tri), 256, D, dev(P.tri), np);
   }
   for (int k = 0; k < P.max_nblk; ++k) {
-    const size_t o1 = P.step + (size_t)k * 3 * (np + 1), o2 = o1 + (np + 1), o3 = o2 + (np + 1);
-    RSM_LAUNCH(k_potrf<T>, total(o1), 32, D, dev(o1), np, k);
-    RSM_LAUNCH(k_panel<T>, total(o2), 256, D, dev(o2), np, k);
+    const size_t o1 = P.step + (size_t)k * 3 * (np + 1), o3 = o1 + 2 * (np + 1);
+    RSM_LAUNCH(k_panel<T>, total(o1), 256, D, dev(o1), np, k);  // diagonal block + block column k
     if ((ee = cudaEventRecord(P.fork, s)) != cudaSuccess || (ee = cudaStreamWaitEvent(P.aux, P.fork, 0)) != cudaSuccess)
       return ee;
     {

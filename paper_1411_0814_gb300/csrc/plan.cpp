@@ -179,9 +179,9 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
   b.o_pad2 = prefix([&](int i) { return b.dv[i].npad * b.dv[i].npad; });
   b.pad2_total = total(b.o_pad2);
   b.o_step = T.size();
-  for (int k = 0; k < b.max_nblk; ++k) {
-    prefix([&](int i) { return (int64_t)(k < b.dv[i].nblk ? 1 : 0); });
-    prefix([&](int i) { return (int64_t)std::max(0, b.dv[i].nblk - k - 1); });
+  for (int k = 0; k < b.max_nblk; ++k) {  // per step: block column k (diagonal + below), unused, trailing update
+    prefix([&](int i) { return (int64_t)std::max(0, b.dv[i].nblk - k); });
+    prefix([&](int i) { return (int64_t)0; });
     prefix([&](int i) {
       const int64_t t = std::max(0, b.dv[i].nblk - k - 1);
       return t * (t + 1) / 2;
