@@ -58,7 +58,7 @@ __device__ __forceinline__ void draw_columns(const ProbDesc& d, int64_t t, int32
   int32_t c[kMaxL];
   if (d.variant == 1) {
     uint4 w = philox4x32_10(make_uint4((uint32_t)t, d.pid, 0u, (uint32_t)(t >> 32)), k0, k1);
-    const int64_t s = (int64_t)(((uint64_t)w.x * (uint64_t)(n - l + 1)) >> 32);
+    const int64_t s = (int64_t)__umulhi(w.x, (uint32_t)(n - l + 1));  // (x range) >> 32
     for (int k = 0; k < l; ++k) out[k] = (int32_t)(s + k);
     return;
   }
@@ -67,8 +67,8 @@ __device__ __forceinline__ void draw_columns(const ProbDesc& d, int64_t t, int32
     if ((dd & 3) == 0)
       blk = philox4x32_10(make_uint4((uint32_t)t, d.pid, (uint32_t)(dd >> 2), (uint32_t)(t >> 32)), k0, k1);
     const uint32_t word = (dd & 3) == 0 ? blk.x : (dd & 3) == 1 ? blk.y : (dd & 3) == 2 ? blk.z : blk.w;
-    const int64_t j = n - l + dd;
-    int32_t x = (int32_t)(((uint64_t)word * (uint64_t)(j + 1)) >> 32);
+    const int32_t j = (int32_t)(n - l + dd);
+    int32_t x = (int32_t)__umulhi(word, (uint32_t)(j + 1));  // multiply-shift draw in [0, j]
     bool taken = false;
     for (int e = 0; e < dd; ++e) taken |= (c[e] == x);
     c[dd] = taken ? (int32_t)j : x;
@@ -97,10 +97,13 @@ __global__ void __launch_bounds__(256) k_sample(const ProbDesc* __restrict__ des
   const int64_t t = g - trial_off[p];
   int32_t* out = d.cols + t * d.l;
   draw_columns(d, t, out);
-  for (int k = 0; k < d.l; ++k) {
-    int v = atomicAdd(&d.colcount[out[k]], 1) + 1;
-    atomicMax(&d.counters[2], (unsigned long long)v);
-  }
+  int vmax = 0;
+  for (int k = 0; k < d.l; ++k) vmax = max(vmax, atomicAdd(&d.colcount[out[k]], 1) + 1);
+  // one atomic per warp and problem for the largest column count (lanes of a warp may
+  // belong to two problems of a batch: reduce among the lanes of the same problem)
+  const unsigned same = __match_any_sync(__activemask(), p);
+  const int wmax = __reduce_max_sync(same, vmax);
+  if ((threadIdx.x & 31) == __ffs(same) - 1) atomicMax(&d.counters[2], (unsigned long long)wmax);
   if (d.debug_cols)
     for (int k = 0; k < d.l; ++k) d.debug_cols[t * d.l + k] = out[k];
 }

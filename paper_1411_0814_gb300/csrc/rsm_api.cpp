@@ -55,7 +55,7 @@ int cuda_fail(cudaError_t e, const char* where) {
 constexpr double kShiftRel32 = 3e-4;   // tau / (trace(M) / n) with the FP32 factor
 constexpr double kShiftRel64 = 1e-11;  // tau / (trace(M) / n) with the FP64 factor
 #ifndef RSM_EIG_ITERS32
-#define RSM_EIG_ITERS32 8
+#define RSM_EIG_ITERS32 5
 #endif
 #ifndef RSM_EIG_ITERS64
 #define RSM_EIG_ITERS64 6
