@@ -118,6 +118,23 @@ __device__ __forceinline__ double fast_sqrt(double x) { return sqrt64(x); }
 __device__ __forceinline__ float fast_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double fast_rsqrt(double x) { return rsqrt64(x); }
 
+// ------------------------------------------------------------------ division by a small runtime divisor
+// q = floor(e / d) as a high multiply with m = ceil(2^32 / d) (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994),
+// exact for e d < 2^32 (here e < 2^16, d <= 32768).  The plain integer division
+// by a runtime divisor is a long instruction sequence.
+struct SmallDiv {
+  uint32_t d, m;
+  __device__ __forceinline__ explicit SmallDiv(uint32_t dd) : d(dd), m(dd > 1 ? 0xFFFFFFFFu / dd + 1u : 0u) {}
+  __device__ __forceinline__ uint32_t div(uint32_t e) const { return d > 1 ? __umulhi(e, m) : e; }
+  __device__ __forceinline__ void divmod(uint32_t e, uint32_t& q, uint32_t& r) const {
+    q = div(e);
+    r = e - q * d;
+  }
+  __device__ __forceinline__ int q(int e) const { return (int)div((uint32_t)e); }
+  __device__ __forceinline__ int r(int e) const { return e - (int)div((uint32_t)e) * (int)d; }
+};
+
 // ------------------------------------------------------------------ Philox4x32-10
 // J. K. Salmon et al., "Parallel random numbers: as easy as 1, 2, 3" (SC'11):
 // ten rounds of the Philox S-box with multipliers 0xD2511F53 / 0xCD9E8D57 and

@@ -74,6 +74,19 @@ __device__ inline int warp_jacobi(T* S, T* Vm, int k, int ls, JacobiScratchT<T>&
   const int ne = (k + 1) & ~1;
   const int np = ne / 2;
   const int nitem = np * k;  // (pair, row) items of one round
+  // this lane's items it = lane + 32 m as (pair, row), computed once (no division in the rounds)
+  constexpr int kMaxItems = (16 * 32 + 31) / 32;
+  int it_r[kMaxItems], it_i[kMaxItems];
+  {
+    const SmallDiv dk((uint32_t)k);
+#pragma unroll
+    for (int m = 0; m < kMaxItems; ++m) {
+      uint32_t q, rr;
+      dk.divmod((uint32_t)(lane + 32 * m), q, rr);
+      it_r[m] = (int)q;
+      it_i[m] = (int)rr;
+    }
+  }
   int rotated = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     bool any = false;
@@ -82,8 +95,11 @@ __device__ inline int warp_jacobi(T* S, T* Vm, int k, int ls, JacobiScratchT<T>&
       T c = 1, s = 0;
       if (lane < np) {
         const int s0 = lane, s1 = ne - 1 - lane;
-        a = (s0 == 0) ? 0 : ((s0 - 1 + round) % (ne - 1)) + 1;
-        b = (s1 == 0) ? 0 : ((s1 - 1 + round) % (ne - 1)) + 1;
+        int pa = s0 - 1 + round, pb = s1 - 1 + round;  // positions on the ring of ne - 1
+        if (pa >= ne - 1) pa -= ne - 1;
+        if (pb >= ne - 1) pb -= ne - 1;
+        a = (s0 == 0) ? 0 : pa + 1;
+        b = (s1 == 0) ? 0 : pb + 1;
         if (a > b) {
           const int tmp = a;
           a = b;
@@ -117,9 +133,11 @@ __device__ inline int warp_jacobi(T* S, T* Vm, int k, int ls, JacobiScratchT<T>&
       any = true;
       __syncwarp();
       // columns p, q of S and Vm
-      for (int base = 0; base < nitem; base += 32) {
-        const int it = base + lane;
-        const int r = it < nitem ? it / k : 0, i = it < nitem ? it % k : 0;
+#pragma unroll
+      for (int m = 0; m < kMaxItems; ++m) {
+        if (32 * m >= nitem) break;
+        const int it = 32 * m + lane;
+        const int r = it < nitem ? it_r[m] : 0, i = it < nitem ? it_i[m] : 0;
         const int pr = __shfl_sync(0xffffffffu, a, r), qr = __shfl_sync(0xffffffffu, b, r);
         const T cr = __shfl_sync(0xffffffffu, c, r), sr = __shfl_sync(0xffffffffu, s, r);
         if (it < nitem && sr != (T)0) {
@@ -133,9 +151,11 @@ __device__ inline int warp_jacobi(T* S, T* Vm, int k, int ls, JacobiScratchT<T>&
       }
       __syncwarp();
       // rows p, q of S
-      for (int base = 0; base < nitem; base += 32) {
-        const int it = base + lane;
-        const int r = it < nitem ? it / k : 0, j = it < nitem ? it % k : 0;
+#pragma unroll
+      for (int m = 0; m < kMaxItems; ++m) {
+        if (32 * m >= nitem) break;
+        const int it = 32 * m + lane;
+        const int r = it < nitem ? it_r[m] : 0, j = it < nitem ? it_i[m] : 0;
         const int pr = __shfl_sync(0xffffffffu, a, r), qr = __shfl_sync(0xffffffffu, b, r);
         const T cr = __shfl_sync(0xffffffffu, c, r), sr = __shfl_sync(0xffffffffu, s, r);
         if (it < nitem && sr != (T)0) {

@@ -437,11 +437,12 @@ __global__ void __launch_bounds__(256) k_xtx(const ProbDesc* __restrict__ descs,
   if (d.stats[kConvFlag] != 0.0) return;  // converged: the rest of the iteration is skipped
   const int chunk = (int)(blockIdx.x - off[p]);
   const int kx = d.kx;
+  const SmallDiv dkx((uint32_t)kx);  // quotient and remainder by kx without an integer division
   double* xs = xtx_smem;                  // kChunk x kx
   double* ys = xtx_smem + kChunk * kx;    // kChunk x kx
   const int i0 = chunk * kChunk;
   for (int e = threadIdx.x; e < kChunk * kx; e += 256) {
-    const int i = i0 + e / kx;
+    const int i = i0 + dkx.q(e);
     xs[e] = i < d.n ? d.X[i0 * kx + e] : 0.0;
     if (WITH_H) ys[e] = i < d.n ? d.MX[i0 * kx + e] : 0.0;
   }
@@ -449,7 +450,7 @@ __global__ void __launch_bounds__(256) k_xtx(const ProbDesc* __restrict__ descs,
   double* part = part_base + part_off[p] + chunk * 2 * kx * kx;
   const int outs = (WITH_H ? 2 : 1) * kx * kx;
   for (int e = threadIdx.x; e < outs; e += 256) {
-    const int which = e / (kx * kx), ab = e % (kx * kx), a = ab / kx, b = ab % kx;
+    const int which = e / (kx * kx), ab = e % (kx * kx), a = dkx.q(ab), b = dkx.r(ab);
     const double* y = which == 0 ? xs : ys;
     double s0 = 0.0, s1 = 0.0;
     for (int r = 0; r < kChunk; r += 2) {
@@ -468,6 +469,7 @@ typedef float FRow[kLs];
 
 // Sum the per-chunk partials in a fixed order: S = X^T X (and H = X^T M X).
 __device__ inline void reduce_partials(const ProbDesc& d, const double* part, DRow* S, DRow* H, int kx) {
+  const SmallDiv dkx((uint32_t)kx);  // quotient and remainder by kx without an integer division
   const int nchunk = (int)((d.n + kChunk - 1) / kChunk);
   for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) {
     double s = 0.0, h = 0.0;
@@ -476,15 +478,16 @@ __device__ inline void reduce_partials(const ProbDesc& d, const double* part, DR
       s += part[c * 2 * kx * kx + e];
       if (H) h += part[c * 2 * kx * kx + kx * kx + e];
     }
-    S[e / kx][e % kx] = s;
-    if (H) H[e / kx][e % kx] = h;
+    S[dkx.q(e)][dkx.r(e)] = s;
+    if (H) H[dkx.q(e)][dkx.r(e)] = h;
   }
 }
 
 // C = op(A) B for kx x kx blocks in shared memory, all threads of the CTA.
 __device__ inline void small_prod(DRow* C, const DRow* A, bool transA, const DRow* B, int kx) {
+  const SmallDiv dkx((uint32_t)kx);  // quotient and remainder by kx without an integer division
   for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) {
-    const int a = e / kx, b = e % kx;
+    const int a = dkx.q(e), b = dkx.r(e);
     double s = 0.0;
     for (int t = 0; t < kx; ++t) s = fma(transA ? A[t][a] : A[a][t], B[t][b], s);
     C[a][b] = s;
@@ -546,15 +549,16 @@ __global__ void __launch_bounds__(kSmallThreads) k_orth(const ProbDesc* __restri
   if (p >= nprob) return;
   const ProbDesc& d = descs[p];
   const int kx = d.kx;
+  const SmallDiv dkx((uint32_t)kx);  // quotient and remainder by kx without an integer division
   reduce_partials(d, part_base + part_off[p], Sd, nullptr, kx);
   __syncthreads();
-  for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) S[e / kx][e % kx] = (CT)Sd[e / kx][e % kx];
+  for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) S[dkx.q(e)][dkx.r(e)] = (CT)Sd[dkx.q(e)][dkx.r(e)];
   __syncthreads();
   if (threadIdx.x < 32) warp_chol_shifted<CT>(S, rdiag, kx, (CT)(sizeof(CT) == 8 ? 1e-15 : 1e-6));
   __syncthreads();
   inv_transpose_factor<CT>(S, rdiag, Q, kx);
   __syncthreads();
-  for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) d.small[e] = (double)Q[e / kx][e % kx];
+  for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) d.small[e] = (double)Q[dkx.q(e)][dkx.r(e)];
 }
 
 // Rayleigh-Ritz step of the FP64 block iteration, one CTA per problem.
@@ -576,24 +580,26 @@ __global__ void __launch_bounds__(kSmallThreads) k_orth(const ProbDesc* __restri
 constexpr size_t kRRSmem = sizeof(DRow) * kMaxL * 7 + sizeof(FRow) * kMaxL * 2;
 
 __device__ inline void lowdin_step(DRow* Q, DRow* W1, DRow* W2, int kx) {  // Q <- Q (3I - Q^T Q) / 2
+  const SmallDiv dkx((uint32_t)kx);  // quotient and remainder by kx without an integer division
   small_prod(W1, Q, true, Q, kx);
   __syncthreads();
   for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) {
-    const int a = e / kx, b = e % kx;
+    const int a = dkx.q(e), b = dkx.r(e);
     double s = 0.0;
     for (int t = 0; t < kx; ++t) s = fma(Q[a][t], ((t == b) ? 3.0 : 0.0) - W1[t][b], s);
     W2[a][b] = 0.5 * s;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) Q[e / kx][e % kx] = W2[e / kx][e % kx];
+  for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) Q[dkx.q(e)][dkx.r(e)] = W2[dkx.q(e)][dkx.r(e)];
   __syncthreads();
 }
 
 __device__ inline void sym_congruence(DRow* out, const DRow* Q, const DRow* A, DRow* W, int kx) {  // out = Q^T A Q
+  const SmallDiv dkx((uint32_t)kx);  // quotient and remainder by kx without an integer division
   small_prod(W, A, false, Q, kx);
   __syncthreads();
   for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) {
-    const int a = e / kx, b = e % kx;
+    const int a = dkx.q(e), b = dkx.r(e);
     const int lo = a < b ? a : b, hi = a < b ? b : a;
     double s = 0.0;
     for (int t = 0; t < kx; ++t) s = fma(Q[t][lo], W[t][hi], s);
@@ -624,23 +630,24 @@ __global__ void __launch_bounds__(kSmallThreads) k_rr64(const ProbDesc* __restri
   const ProbDesc& d = descs[p];
   if (d.stats[kConvFlag] != 0.0) return;
   const int kx = d.kx, r = d.r, tid = threadIdx.x;
+  const SmallDiv dkx((uint32_t)kx);  // quotient and remainder by kx without an integer division
   reduce_partials(d, part_base + part_off[p], S, H, kx);
   __syncthreads();
   // S = X^T X is close to I here (X was orthonormalised before its last small
   // update), so: FP32 Cholesky S + s I = C C^T and Q0 = C^-T, then one
   // Newton-Schulz step in FP64, Q1 = Q0 (3I - Q0^T S Q0) / 2, which squares the
   // FP32 error: X Q1 is orthonormal to FP64 accuracy.
-  for (int e = tid; e < kx * kx; e += kSmallThreads) Sf[e / kx][e % kx] = (float)S[e / kx][e % kx];
+  for (int e = tid; e < kx * kx; e += kSmallThreads) Sf[dkx.q(e)][dkx.r(e)] = (float)S[dkx.q(e)][dkx.r(e)];
   __syncthreads();
   if (tid < 32) warp_chol_shifted<float>(Sf, reinterpret_cast<float*>(rdiag), kx, 1e-7f);
   __syncthreads();
   inv_transpose_factor<float>(Sf, reinterpret_cast<const float*>(rdiag), Vf, kx);
   __syncthreads();
-  for (int e = tid; e < kx * kx; e += kSmallThreads) Q2[e / kx][e % kx] = (double)Vf[e / kx][e % kx];
+  for (int e = tid; e < kx * kx; e += kSmallThreads) Q2[dkx.q(e)][dkx.r(e)] = (double)Vf[dkx.q(e)][dkx.r(e)];
   __syncthreads();
   sym_congruence(W2, Q2, S, W1, kx);  // Z = Q0^T S Q0
   for (int e = tid; e < kx * kx; e += kSmallThreads) {
-    const int a = e / kx, b = e % kx;
+    const int a = dkx.q(e), b = dkx.r(e);
     double s = 0.0;
     for (int t = 0; t < kx; ++t) s = fma(Q2[a][t], ((t == b) ? 3.0 : 0.0) - W2[t][b], s);
     Q1[a][b] = 0.5 * s;
@@ -649,14 +656,14 @@ __global__ void __launch_bounds__(kSmallThreads) k_rr64(const ProbDesc* __restri
   sym_congruence(H1, Q1, H, W1, kx);  // H1 = Q1^T H Q1
   // FP32 Jacobi of H1 when it has off-diagonal entries FP32 can resolve; then
   // the eigenvector columns in ascending order of the Ritz values
-  for (int e = tid; e < kx * kx; e += kSmallThreads) Sf[e / kx][e % kx] = (float)H1[e / kx][e % kx];
+  for (int e = tid; e < kx * kx; e += kSmallThreads) Sf[dkx.q(e)][dkx.r(e)] = (float)H1[dkx.q(e)][dkx.r(e)];
   __syncthreads();
   if (tid < 32) {
     float f = 0.f, o = 0.f;
     for (int e = tid; e < kx * kx; e += 32) {
-      const float v = Sf[e / kx][e % kx];
+      const float v = Sf[dkx.q(e)][dkx.r(e)];
       f += v * v;
-      if (e / kx != e % kx) o = fmaxf(o, fabsf(v));
+      if (dkx.q(e) != dkx.r(e)) o = fmaxf(o, fabsf(v));
     }
 #pragma unroll
     for (int s = 16; s; s >>= 1) {
@@ -685,19 +692,19 @@ __global__ void __launch_bounds__(kSmallThreads) k_rr64(const ProbDesc* __restri
   }
   __syncthreads();
   for (int e = tid; e < kx * kx; e += kSmallThreads)
-    Q2[e / kx][e % kx] = rotated ? (double)Vf[e / kx][order[e % kx]] : (e / kx == order[e % kx] ? 1.0 : 0.0);
+    Q2[dkx.q(e)][dkx.r(e)] = rotated ? (double)Vf[dkx.q(e)][order[dkx.r(e)]] : (dkx.q(e) == order[dkx.r(e)] ? 1.0 : 0.0);
   __syncthreads();
   if (rotated) {  // FP32 rotations: make them orthogonal in FP64, then B = Q2^T H1 Q2
     lowdin_step(Q2, W1, W2, kx);
     lowdin_step(Q2, W1, W2, kx);
     sym_congruence(S, Q2, H1, W1, kx);  // into S: the factor is no longer needed
   } else {  // H1 was already diagonal to FP32 accuracy: Q2 is a permutation, B a reordering of H1
-    for (int e = tid; e < kx * kx; e += kSmallThreads) S[e / kx][e % kx] = H1[order[e / kx]][order[e % kx]];
+    for (int e = tid; e < kx * kx; e += kSmallThreads) S[dkx.q(e)][dkx.r(e)] = H1[order[dkx.q(e)]][order[dkx.r(e)]];
     __syncthreads();
   }
   // first-order decoupling of the wanted block: G = I + A (into W2), then one Lowdin step
   for (int e = tid; e < kx * kx; e += kSmallThreads) {
-    const int a = e / kx, b = e % kx;
+    const int a = dkx.q(e), b = dkx.r(e);
     double g = (a == b) ? 1.0 : 0.0;
     if (a < r && b >= r) {
       g = S[a][b] * rcp64(S[b][b] - S[a][a]);
@@ -708,21 +715,21 @@ __global__ void __launch_bounds__(kSmallThreads) k_rr64(const ProbDesc* __restri
     W2[a][b] = g;
   }
   __syncthreads();
-  for (int e = tid; e < kx * kx; e += kSmallThreads) H1[e / kx][e % kx] = W2[e / kx][e % kx];  // G in H1
+  for (int e = tid; e < kx * kx; e += kSmallThreads) H1[dkx.q(e)][dkx.r(e)] = W2[dkx.q(e)][dkx.r(e)];  // G in H1
   __syncthreads();
   // I + A is orthogonal up to ||A||^2: below 1e-18 it needs no Lowdin step
   if (coupled) lowdin_step(H1, W1, W2, kx);
   if (rotated) {
     small_prod(W1, Q2, false, H1, kx);  // W1 = Q2 G
   } else {
-    for (int e = tid; e < kx * kx; e += kSmallThreads) W1[e / kx][e % kx] = H1[e / kx][e % kx];
+    for (int e = tid; e < kx * kx; e += kSmallThreads) W1[dkx.q(e)][dkx.r(e)] = H1[dkx.q(e)][dkx.r(e)];
     __syncthreads();
     for (int e = tid; e < kx * kx; e += kSmallThreads) {  // W1 = P G (P the permutation Q2): rows by order
-      const int a = e / kx, b = e % kx;
+      const int a = dkx.q(e), b = dkx.r(e);
       W2[order[a]][b] = W1[a][b];
     }
     __syncthreads();
-    for (int e = tid; e < kx * kx; e += kSmallThreads) W1[e / kx][e % kx] = W2[e / kx][e % kx];
+    for (int e = tid; e < kx * kx; e += kSmallThreads) W1[dkx.q(e)][dkx.r(e)] = W2[dkx.q(e)][dkx.r(e)];
   }
   __syncthreads();
   small_prod(Q2, Q1, false, W1, kx);  // Q = Q1 Q2 G (into Q2)
@@ -730,8 +737,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_rr64(const ProbDesc* __restri
   sym_congruence(W2, Q2, H, W1, kx);  // H' = Q^T H Q
   double* out = d.small;
   for (int e = tid; e < kx * kx; e += kSmallThreads) {
-    out[e] = Q2[e / kx][e % kx];
-    out[kx * kx + e] = W2[e / kx][e % kx];
+    out[e] = Q2[dkx.q(e)][dkx.r(e)];
+    out[kx * kx + e] = W2[dkx.q(e)][dkx.r(e)];
   }
   for (int c = tid; c < kx; c += kSmallThreads) out[2 * kx * kx + c] = W2[c][c];
 }
@@ -751,10 +758,11 @@ __global__ void __launch_bounds__(256) k_rotate(const ProbDesc* __restrict__ des
   const ProbDesc& d = descs[p];
   if (d.stats[kConvFlag] != 0.0) return;  // converged: the rest of the iteration is skipped
   const int kx = d.kx;
+  const SmallDiv dkx((uint32_t)kx);  // quotient and remainder by kx without an integer division
   const int i0 = (int)(blockIdx.x - off[p]) * kRotRows;
   for (int e = threadIdx.x; e < (FULL ? 2 : 1) * kx * kx; e += blockDim.x) q[e] = d.small[e];
   for (int e = threadIdx.x; e < kRotRows * kx; e += blockDim.x) {
-    const int r = e / kx, c = e % kx;
+    const int r = dkx.q(e), c = dkx.r(e);
     const int i = i0 + r;
     xs[r][c] = i < d.n ? d.X[i * kx + c] : 0.0;
     if (FULL) ms[r][c] = i < d.n ? d.MX[i * kx + c] : 0.0;
@@ -764,7 +772,7 @@ __global__ void __launch_bounds__(256) k_rotate(const ProbDesc* __restrict__ des
   double nmx[kMaxL * kRotRows / 256 + 1];
   int cnt = 0;
   for (int e = threadIdx.x; e < kRotRows * kx; e += blockDim.x) {
-    const int r = e / kx, c = e % kx;
+    const int r = dkx.q(e), c = dkx.r(e);
     double a = 0.0, b = 0.0;
     for (int t = 0; t < kx; ++t) {
       a = fma(xs[r][t], q[t * kx + c], a);
@@ -776,7 +784,7 @@ __global__ void __launch_bounds__(256) k_rotate(const ProbDesc* __restrict__ des
   __syncthreads();
   cnt = 0;
   for (int e = threadIdx.x; e < kRotRows * kx; e += blockDim.x) {
-    const int r = e / kx, c = e % kx;
+    const int r = dkx.q(e), c = dkx.r(e);
     const int i = i0 + r;
     const double b = nmx[cnt++];
     double s = 0.0;
@@ -816,6 +824,7 @@ __global__ void __launch_bounds__(256) k_precond(const ProbDesc* __restrict__ de
   if (d.stats[kConvFlag] != 0.0) return;  // converged: the rest of the iteration is skipped
   const int n = (int)d.n, np = npad_of(d);
   const int kx = d.kx;
+  const SmallDiv dkx((uint32_t)kx);  // quotient and remainder by kx without an integer division
   const double* src = SRC == 0 ? d.R : d.X;
   const int local = (int)(blockIdx.x - off[p]);
   const int ntile = (n + kPRows - 1) / kPRows;
@@ -832,7 +841,7 @@ __global__ void __launch_bounds__(256) k_precond(const ProbDesc* __restrict__ de
       ts[r][c] = (i < n && j < j_end) ? F1of<T>(d)[i * np + j] : (T)0;
     }
     for (int e = threadIdx.x; e < 64 * kx; e += 256) {
-      const int r = e / kx, c = e % kx;
+      const int r = dkx.q(e), c = dkx.r(e);
       const int j = j0 + r;
       rs[r][c] = (j < j_end) ? (T)src[j * kx + c] : (T)0;
     }

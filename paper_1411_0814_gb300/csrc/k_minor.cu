@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDe
 
   // the n_minor smallest eigenvalues (ties broken by index)
   const int nm = d.n_minor;
+  const SmallDiv dnm((uint32_t)nm), dl((uint32_t)l);  // quotients by nm and l without integer division
   if (lane == 0) {
     for (int i = 0; i < l; ++i) is_minor[wid][i] = 0;
     for (int j = 0; j < nm; ++j) {
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDe
     __syncwarp();
     // compact the picked columns into Wd as the l x n_minor minor basis
     for (int it = lane; it < l * nm; it += 32) {
-      const int a = it / nm, j = it % nm;
+      const int a = dnm.q(it), j = dnm.r(it);
       Wd[a * nm + j] = Z[a * ls + pick[wid][j]];
     }
     __syncwarp();
@@ -211,10 +212,10 @@ __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDe
     __syncwarp();
   } else {
     for (int it = lane; it < l * nm; it += 32) {
-      const int a = it / nm, j = it % nm;
+      const int a = dnm.q(it), j = dnm.r(it);
       Z[a * nm + j] = (double)Qf[a * ls + pick[wid][j]];
     }
-    for (int it = lane; it < l * l; it += 32) Wd[(it / l) * ls + (it % l)] = (double)Qf[(it / l) * ls + (it % l)];
+    for (int it = lane; it < l * l; it += 32) Wd[dl.q(it) * ls + dl.r(it)] = (double)Qf[dl.q(it) * ls + dl.r(it)];
     if (lane < l) gv[lane] = (double)Sf[lane * ls + lane];
     __syncwarp();
     newton_refine(Gs, Wd, gv, Z, rv, cv, l, nm, ls, is_minor[wid], fro, d.gram_fp32 ? 1e-10 : 1e-17);
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDe
   const double scale = ldexp(1.0, f);
   const int32_t* C = d.cols + t * l;
   for (int it = lane; it < l * l; it += 32) {
-    const int a = it / l, b = it % l;
+    const int a = dl.q(it), b = dl.r(it);
     double pr = 0.0;
     for (int j = 0; j < nm; ++j) pr = fma(Z[a * nm + j], Z[b * nm + j], pr);
     const long long v = llrint(pr * scale);
