@@ -35,6 +35,7 @@ namespace {
 constexpr int kRows = 128;      // MMA M: rows per CTA
 constexpr int kChunkK = 32;     // columns per stage
 constexpr int kThreads = 128;
+constexpr int kMaxStages = 3;  // shared-memory ring: chunk c + 1 is copied in while chunk c is built
 constexpr uint32_t kWaitLimit = 1u << 26;  // polls of one mbarrier wait before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -87,6 +88,17 @@ __device__ __forceinline__ void tc_mma_tf32(uint32_t dtmem, uint64_t adesc, uint
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+
+// Asynchronous global -> shared copies (no register staging), grouped and waited on per stage.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_t src_bytes) {  // 0: zero fill
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -170,9 +182,9 @@ template <int RB>
 __global__ void __launch_bounds__(kThreads) k_normal_tc(const ProbDesc* __restrict__ descs,
                                                        const int64_t* __restrict__ off, int nprob,
                                                        unsigned long long* __restrict__ fail_list,
-                                                       unsigned long long* __restrict__ fail_count) {
+                                                       unsigned long long* __restrict__ fail_count, int nstage) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
-  __shared__ __align__(8) unsigned long long bars[2];
+  __shared__ __align__(8) unsigned long long bars[kMaxStages];
   __shared__ uint32_t tmem_slot;
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
@@ -196,8 +208,7 @@ __global__ void __launch_bounds__(kThreads) k_normal_tc(const ProbDesc* __restri
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(smem_u32(&bars[0]), 1);
-    mbar_init(smem_u32(&bars[1]), 1);
+    for (int k = 0; k < nstage; ++k) mbar_init(smem_u32(&bars[k]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc_fence_before();
@@ -219,35 +230,43 @@ __global__ void __launch_bounds__(kThreads) k_normal_tc(const ProbDesc* __restri
       ypre[jj] = (row_in && j < n) ? __ldg(Y + (j * ldy + row)) : 0.f;
     }
   };
+  // the mask words, Kw tiles and V of a chunk go straight to their stage by cp.async
+  auto issue_copies = [&](int c) {
+    unsigned char* st = tc_smem + (size_t)(c % nstage) * stage_bytes;
+    const uint32_t bs = smem_u32(st + a_bytes), vs = smem_u32(st + a_bytes + 2 * b_bytes);
+    const uint32_t ws = smem_u32(st + a_bytes + 2 * b_bytes + (size_t)kChunkK * RB * 4);
+    const uint32_t j = (uint32_t)c * kChunkK + (tid >> 2);  // word tid % 4 of column tid / 4
+    const uint32_t* wsrc = j < n ? d.bits + (j * ldb + (i0 >> 5) + (tid & 3)) : d.bits;
+    cp_async4(ws + 4u * tid, wsrc, j < n ? 4u : 0u);
+    const float4* src = reinterpret_cast<const float4*>(img + (size_t)c * 2 * npad * kChunkK);
+    for (int e = tid; e < 2 * npad * kChunkK / 4; e += kThreads) cp_async16(bs + 16u * e, src + e);
+    const float4* vsrc = reinterpret_cast<const float4*>(vf + (size_t)c * kChunkK * RB);
+    for (int e = tid; e < kChunkK * RB / 4; e += kThreads) cp_async16(vs + 16u * e, vsrc + e);
+    cp_async_commit();
+  };
   load_y(0);
+  if (nchunk > 0) issue_copies(0);
   bool failed = false;
   for (int c = 0; c < nchunk; ++c) {
-    const int s = c & 1;
+    const int s = c % nstage;
     unsigned char* st = tc_smem + (size_t)s * stage_bytes;
     float* As = reinterpret_cast<float*>(st);
     float* Bs = reinterpret_cast<float*>(st + a_bytes);
     float* Vs = reinterpret_cast<float*>(st + a_bytes + 2 * b_bytes);
     uint32_t* Ws = reinterpret_cast<uint32_t*>(st + a_bytes + 2 * b_bytes + (size_t)kChunkK * RB * 4);
-    if (c >= 2 && !failed) failed = !mbar_wait(smem_u32(&bars[s]), (uint32_t)((c - 2) >> 1) & 1u);
+    if (c + 1 < nchunk) {
+      // stage of chunk c + 1 was last read by the MMAs of chunk c + 1 - nstage
+      if (c + 1 >= nstage && !failed)
+        failed = !mbar_wait(smem_u32(&bars[(c + 1) % nstage]), (uint32_t)((c + 1 - nstage) / nstage) & 1u);
+      issue_copies(c + 1);
+      cp_async_wait<1>();  // this thread's copies of chunk c have landed
+    } else {
+      cp_async_wait<0>();
+    }
     if (__syncthreads_or(failed)) {
       failed = true;
       break;
     }
-    // mask words of the chunk for this CTA's 128 rows: thread (column tid / 4, word tid % 4)
-    {
-      const uint32_t j = (uint32_t)c * kChunkK + (tid >> 2);
-      Ws[tid] = j < n ? __ldg(d.bits + (j * ldb + (i0 >> 5) + (tid & 3))) : 0u;
-    }
-    // B tiles (already in the shared-memory layout) and the chunk's V
-    {
-      const float4* src = reinterpret_cast<const float4*>(img + (size_t)c * 2 * npad * kChunkK);
-      float4* dst = reinterpret_cast<float4*>(Bs);
-      for (int e = tid; e < 2 * npad * kChunkK / 4; e += kThreads) dst[e] = __ldg(src + e);
-      const float4* vsrc = reinterpret_cast<const float4*>(vf + (size_t)c * kChunkK * RB);
-      float4* vdst = reinterpret_cast<float4*>(Vs);
-      for (int e = tid; e < kChunkK * RB / 4; e += kThreads) vdst[e] = __ldg(vsrc + e);
-    }
-    __syncthreads();
     // W tile (thread = row): 8 core-matrix columns of 4 values; and b_i on the CUDA cores
     {
       float w[kChunkK];
@@ -290,10 +309,11 @@ __global__ void __launch_bounds__(kThreads) k_normal_tc(const ProbDesc* __restri
     }
   }
   // the last commit covers every MMA issued before it
-  if (nchunk > 0) {
+  if (nchunk > 0 && !failed) {
     const int c = nchunk - 1;
-    if (!mbar_wait(smem_u32(&bars[c & 1]), (uint32_t)(c >> 1) & 1u)) failed = true;
+    if (!mbar_wait(smem_u32(&bars[c % nstage]), (uint32_t)(c / nstage) & 1u)) failed = true;
   }
+  cp_async_wait<0>();  // nothing of this thread's may still be landing when the CTA ends
   failed = __syncthreads_or(failed) != 0;  // the same decision in every thread
   tc_fence_after();
   if (failed) {
@@ -425,13 +445,18 @@ cudaError_t launch_normal_tc(const SolvePlan& S, int rb_max, int npad_max, cudaS
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (S.tc_tiles <= 0) return cudaSuccess;
-  const size_t smem = 2 * tc_stage_bytes(npad_max, rb_max);
+  // three stages when they fit in shared memory (227 KB per CTA), else two
+  const int stages = 3 * tc_stage_bytes(npad_max, rb_max) <= 232448 ? 3 : 2;
+  const size_t smem = stages * tc_stage_bytes(npad_max, rb_max);
 #define RSM_TC(RB)                                                                                             \
   do {                                                                                                         \
     if ((e = cudaFuncSetAttribute(k_normal_tc<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != \
-        cudaSuccess)                                                                                           \
+        cudaSuccess) {                                                                                         \
+      cudaGetLastError();                                                                                      \
       return e;                                                                                                \
-    k_normal_tc<RB><<<(unsigned)S.tc_tiles, kThreads, smem, s>>>(D, S.tc_off, np, S.fail_list, S.fail_count);  \
+    }                                                                                                          \
+    k_normal_tc<RB><<<(unsigned)S.tc_tiles, kThreads, smem, s>>>(D, S.tc_off, np, S.fail_list, S.fail_count,   \
+                                                                 stages);                                      \
   } while (0)
   if (rb_max <= 8)
     RSM_TC(8);
