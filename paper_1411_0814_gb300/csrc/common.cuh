@@ -42,7 +42,9 @@ struct ProbDesc {
   double* small;             // per-problem small matrices (k x k blocks)
   double* Kmat;              // n x q_pad products of V for the normal equations
   double* NB;                // m x q_pad normal-equation data (N_i packed, b_i)
-  unsigned long long* counters;  // [0] accepted trials, [1] known entries, [2] max column count, [3] chol fail
+  unsigned long long* counters;  // [0] accepted trials, [1] known entries, [2] max column count, [3] chol fail,
+                                 // [4] underdetermined rows, [5] selected rows, [6] device waits that ran out
+  unsigned* tflag;               // 3 nblk^2 tile states of the factor launch (zeroed before it)
   int32_t* colcount;             // n: how many trials drew each column
   double* stats;                 // [0..31] eigenvalues, [32] residual num, [33] e, [34] eig residual
   // outputs

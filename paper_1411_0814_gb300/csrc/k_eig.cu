@@ -42,6 +42,11 @@ template <typename T>
 __device__ __forceinline__ T* F2of(const ProbDesc& d) { return static_cast<T*>(d.F2); }
 template <typename T>
 __device__ __forceinline__ T* Dinvof(const ProbDesc& d) { return static_cast<T*>(d.Dinv); }
+// T = A^-1 (npad x npad) follows the factor in the F1 region.
+template <typename T>
+__device__ __forceinline__ T* Tof(const ProbDesc& d) {
+  return static_cast<T*>(d.F1) + d.nblk * BS * d.nblk * BS;
+}
 
 // ------------------------------------------------------------------ A = M + tau I (padded with I)
 template <typename T>
@@ -71,258 +76,656 @@ __global__ void __launch_bounds__(256) k_eig_prep(const ProbDesc* __restrict__ d
     v = (i == j) ? (T)1 : (T)0;
   }
   F1of<T>(d)[e] = v;
+  if (j / BS <= i / BS) F2of<T>(d)[e] = (i == j) ? (T)1 : (T)0;  // L^-1 starts as I (lower blocks)
 }
 
-// ------------------------------------------------------------------ Cholesky, step k
-// Factor the 32 x 32 diagonal block and invert the factor with one warp, all in
-// registers: lane i holds row i.  Step j takes the pivot from lane j, scales
-// column j, and updates the trailing columns with L[c][j] fetched by shuffle
-// from lane c (fully unrolled, so every register index is a constant).  The
-// inverse X = L^-1 is formed row by row: once row t is final on lane t it is
-// broadcast and every later row adds L[i][t] X[t][.] (forward substitution).
-// Factor and invert one diagonal block held as a[c] = A_kk[lane][c] (row per
-// lane); writes L_kk (lower, zeros above) at A and its inverse at Dinv[k].
+// ------------------------------------------------------------------ the 32 x 32 diagonal block
+// Factor one diagonal block A_kk = L_u D L_u^T (L_u unit lower triangular)
+// with one warp; lane i holds row i as a[c].  Step j takes the pivot d_j and
+// the next row's entry a_{j+1,j} by shuffle (the chain from one pivot to the
+// next runs through shuffles and registers only), publishes the rest of
+// column j through the shared array col (16-byte broadcast reads), and updates
+// the trailing entries a[c] -= (a[j] / d_j) a_cj (fully unrolled, so every
+// register index is a constant).  On return a[c] = L_u[lane][c] (1 on the
+// diagonal, 0 above) and the result is d_lane.  A non-positive pivot is
+// flagged (counters[3]) and replaced by a tiny one.
 template <typename T>
-__device__ __forceinline__ void warp_potrf_block(T (&a)[BS], const ProbDesc& d, int k, int np, bool write_global,
-                                                 T (*dinv_smem)[BS + 1]) {
+__device__ __forceinline__ T warp_ldl_block(T (&a)[BS], T* col, const ProbDesc& d) {
   const int lane = threadIdx.x & 31;
-  T* A = F1of<T>(d) + (int64_t)k * BS * np + (int64_t)k * BS;
+  constexpr int V = 16 / (int)sizeof(T);  // column entries per 16-byte shared load (col is 16-byte aligned)
   bool bad = false;
-  T rinv = (T)1;  // 1 / L[lane][lane]
+  T dl = (T)1;
 #pragma unroll
   for (int j = 0; j < BS; ++j) {
     T piv = __shfl_sync(0xffffffffu, a[j], j);
+    const T cnext = j + 1 < BS ? __shfl_sync(0xffffffffu, a[j], j + 1) : (T)0;  // a_{j+1,j}
+    col[lane] = a[j];
+    __syncwarp();
     if (!(piv > (T)0)) {  // not positive definite at this precision: flag, continue with a tiny pivot
       bad = true;
       piv = (T)1e-30;
     }
-    const T ij = fast_rsqrt(piv);  // the FP32 factor is a preconditioner: the hardware approximation suffices
-    const T dj = piv * ij;
-    if (lane == j) rinv = ij;
-    a[j] = lane > j ? a[j] * ij : (lane == j ? dj : (T)0);
+    const T t = a[j] * fast_rcp(piv);  // L_u[lane][j] for lane > j
+    if (j + 1 < BS) a[j + 1] = fma(-t, cnext, a[j + 1]);
+    T cv[BS];  // col[c] for c >= j + 2, read 16 bytes at a time
 #pragma unroll
-    for (int c = j + 1; c < BS; ++c) a[c] = fma(-a[j], __shfl_sync(0xffffffffu, a[j], c), a[c]);
+    for (int g = 0; g < BS / V; ++g) {
+      if ((g + 1) * V - 1 < j + 2) continue;
+      if constexpr (V == 4) {
+        const float4 q = reinterpret_cast<const float4*>(col)[g];
+        cv[4 * g] = q.x, cv[4 * g + 1] = q.y, cv[4 * g + 2] = q.z, cv[4 * g + 3] = q.w;
+      } else {
+        const double2 q = reinterpret_cast<const double2*>(col)[g];
+        cv[2 * g] = q.x, cv[2 * g + 1] = q.y;
+      }
+    }
+#pragma unroll
+    for (int c = j + 2; c < BS; ++c) a[c] = fma(-t, cv[c], a[c]);
+    if (lane == j) dl = piv;
+    a[j] = lane > j ? t : (lane == j ? (T)1 : (T)0);
+    __syncwarp();
   }
   if (bad && lane == 0) atomicAdd(&d.counters[3], 1ull);
-  T x[BS];
-#pragma unroll
-  for (int c = 0; c < BS; ++c) x[c] = (T)0;
-#pragma unroll
-  for (int t = 0; t < BS; ++t) {
-    const bool me = lane == t;
-#pragma unroll
-    for (int c = 0; c < t; ++c) x[c] = me ? -x[c] * rinv : x[c];
-    x[t] = me ? rinv : x[t];
-    const T lit = lane > t ? a[t] : (T)0;  // L[lane][t] for the rows still open
-#pragma unroll
-    for (int c = 0; c <= t; ++c) x[c] = fma(lit, __shfl_sync(0xffffffffu, x[c], t), x[c]);
-  }
-  if (write_global) {
-    T* D = Dinvof<T>(d) + (int64_t)k * BS * BS;
-#pragma unroll
-    for (int c = 0; c < BS; ++c) {
-      A[lane * np + c] = c <= lane ? a[c] : (T)0;
-      D[lane * BS + c] = c <= lane ? x[c] : (T)0;  // entry (lane, c) of inv(L_kk)
-    }
-  }
-  if (dinv_smem)
-#pragma unroll
-    for (int c = 0; c < BS; ++c) dinv_smem[lane][c] = c <= lane ? x[c] : (T)0;
+  return dl;
 }
 
-
-// 32 x 32 x 32 product helper: each of 256 threads owns 4 outputs (row ty + 8s, column tx).
-// out[r][c] = sum_t X[r][t] * Y(t, c) with Y accessed through the functor.
-
-// Panel: L_ik = A_ik * inv(L_kk)^T for i > k.
-// Step k of the factorisation: block column k.  CTA 0 of a problem factors
-// and inverts the diagonal block A_kk and writes L_kk and inv(L_kk); CTA
-// q >= 1 factors A_kk as well (the same arithmetic, so the same result, in
-// parallel with CTA 0) and forms L_{k+q,k} = A_{k+q,k} inv(L_kk)^T.  One
-// launch per step replaces a factorisation launch followed by a panel launch.
+// X = L^-1 of a unit lower-triangular 32 x 32 block by doubling, with all 256
+// threads: with X holding the inverses of the diagonal blocks of size s,
+//   [L11 0; L21 L22]^-1 = [X11 0; -X22 (L21 X11) X22]
+// fills the blocks of size 2 s (s = 1, 2, ..., 16; at each size 16 s entries,
+// one per thread).  L in l, X in x (its diagonal already 1, zero elsewhere),
+// z scratch.
 template <typename T>
-__global__ void __launch_bounds__(256) k_panel(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
-                                              int nprob, int k) {
-  __shared__ T x[BS][BS + 1], y[BS][BS + 1];
-  const int p = find_problem(off, nprob, blockIdx.x);
-  const ProbDesc& d = descs[p];
-  const int np = npad_of(d);
-  const int q = (int)(blockIdx.x - off[p]);
-  if (threadIdx.x < 32) {
-    const T* Akk = F1of<T>(d) + (int64_t)k * BS * np + (int64_t)k * BS;
+__device__ __forceinline__ void tri_inverse_block(const T (*l)[BS + 1], T (*x)[BS + 1], T (*z)[BS + 1]) {
+#pragma unroll
+  for (int s = 1; s < BS; s *= 2) {
+    const int e = threadIdx.x;
+    const bool act = e < 16 * s;
+    // entry e of this size: block b = e / (s s), row r0 + e % (s s) / s, column c0 + e % s
+    const int b = e / (s * s), r = 2 * s * b + s + (e % (s * s)) / s, c = 2 * s * b + e % s;
+    const int base = 2 * s * b;
+    if (act) {
+      T acc = (T)0;
+#pragma unroll
+      for (int t = 0; t < s; ++t) acc = fma(l[r][base + t], x[base + t][c], acc);  // (L21 X11)[r][c]
+      z[r][c] = acc;
+    }
+    __syncthreads();
+    if (act) {
+      T acc = (T)0;
+#pragma unroll
+      for (int t = 0; t < s; ++t) acc = fma(x[r][base + s + t], z[base + s + t][c], acc);  // (X22 Y)[r][c]; X22 is 0 above its diagonal
+      x[r][c] = -acc;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ factor tasks
+// Each task is one 32 x 32 tile operation done by a CTA of 256 threads (4
+// outputs per thread: row ty + 8 s, column tx) with its operands staged in
+// the shared tiles x and y.  Offsets are 32-bit (npad^2 < 2^31).
+template <typename T>
+using Tile = T (*)[BS + 1];
+
+// u -> (i, j) with 0 <= j <= i and u = i (i + 1) / 2 + j (u < 2^24, exact in FP32).
+__device__ __forceinline__ void tri_index(int u, int& i, int& j) {
+  int r = (int)((sqrtf(8.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
+  while ((r + 1) * (r + 2) / 2 <= u) ++r;
+  while (r * (r + 1) / 2 > u) --r;
+  i = r;
+  j = u - r * (r + 1) / 2;
+}
+
+// out (-)= X Y^T or X Y, 32 x 32 x 32, operands in the shared tiles.
+template <typename T, bool YT>
+__device__ __forceinline__ void tile_product(Tile<T> x, Tile<T> y, T (&acc)[4]) {
+  const int tx = threadIdx.x % BS, ty = threadIdx.x / BS;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) acc[s] = (T)0;
+#pragma unroll 8
+  for (int t = 0; t < BS; ++t) {
+    const T yv = YT ? y[tx][t] : y[t][tx];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) acc[s] = fma(x[ty + 8 * s][t], yv, acc[s]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_two(Tile<T> x, const T* X, Tile<T> y, const T* Y, int ldx, int ldy) {
+  // every global load is issued before the first shared store (the compiler
+  // cannot reorder them across stores it cannot prove disjoint)
+  const int tx = threadIdx.x % BS, ty = threadIdx.x / BS;
+  T rx[4], ry[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    rx[s] = X[(ty + 8 * s) * ldx + tx];
+    ry[s] = Y[(ty + 8 * s) * ldy + tx];
+  }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    x[ty + 8 * s][tx] = rx[s];
+    y[ty + 8 * s][tx] = ry[s];
+  }
+  __syncthreads();
+}
+
+// A contiguous 32 x 32 tile (a diagonal-block inverse) into shared memory.
+template <typename T>
+__device__ __forceinline__ void load_dense(Tile<T> x, const T* X) {
+  const int tx = threadIdx.x % BS, ty = threadIdx.x / BS;
+  T rx[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) rx[s] = X[(ty + 8 * s) * BS + tx];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) x[ty + 8 * s][tx] = rx[s];
+}
+
+// Pair u of the trailing update of step k (t = nblk - k - 1 blocks remain):
+// column by column, the diagonal tile first, so the next block column is
+// complete early.
+__device__ __forceinline__ void trail_pair(int k, int t, int u, int& i, int& j) {
+  int a, b;
+  tri_index(t * (t + 1) / 2 - 1 - u, a, b);
+  j = k + 1 + (t - 1 - a);
+  i = k + 1 + (t - 1 - b);
+}
+
+// ------------------------------------------------------------------ the factor as one dataflow launch
+// The blocked Cholesky A = L L^T, the inverse factor X = L^-1 and T = A^-1 =
+// X^T X are one launch of 32 x 32 tile tasks (nb blocks, step k = block
+// column k):
+//   C        the chain of one or more problems, step by step: A_kk -= L_{k,k-1}
+//            L_{k,k-1}^T, factor, write inv(L_kk); the two blocks below the
+//            diagonal of the previous column and of this one, L_{k+1,k-1} (its
+//            last trailing update, from step k - 2, applied here) and L_{k+1,k}.
+//            This is the critical path; one CTA runs it without handing over
+//            between steps, and the only block it takes from another task
+//            (L_{k+1,k-2}) was released two steps earlier.
+//   P(k) i   i >= k + 3: A_ik -= L_{i,k-1} L_{k,k-1}^T, then L_ik = A_ik inv(L_kk)^T
+//   T(k) i,j trailing update of the columns j >= k + 2: A_ij -= L_ik L_jk^T
+//   S(k) j   row k of X: X_kj = inv(L_kk) (X_kj - L_{k,k-1} X_{k-1,j}) (j < k), X_kk = inv(L_kk)
+//   U(k) i,j i >= k + 2, j <= k: X_ij -= L_ik X_kj
+//   R(t) i,j j <= i <= t: row t's share of T_ij = sum_{t >= i} X_ti^T X_tj, added
+//            in the order of t (the last one also writes T_ji = T_ij^T)
+// Tasks are claimed from one counter: first the G chains (problem p belongs
+// to chain p mod G), then for k = 0, 1, ...: P(k), T(k), S(k - lag),
+// U(k - lag), R(k - lag); then the last lag steps of S, U and R.  Each task
+// waits only for the tiles it reads and writes, through per-tile states
+// (tflag, zeroed before the launch):
+//   SA(i, j), j <= i:  trailing updates applied to tile (i, j) of A by T tasks
+//                      (k after T(k - 1)); j + 1 once L_ij (i > j) or inv(L_jj)
+//                      (i = j) is written.
+//   SX(i, j), j <= i:  U updates applied to tile (i, j) of X (i - j - 1 after
+//                      U(i - 2)); i - j + 1 once S(i) has made it final.
+//   ST(i, j), j <= i:  rows of X added into T_ij (t - i + 1 after R(t)).
+//   C step k:  SA(k, k), SA(k + 1, k) >= k - 1, SA(k + 1, k - 1) >= k - 2, SA(k + 1, k - 2) >= k - 1
+//   P(k) i:    SA(k, k) > k, SA(i, k - 1) >= k, SA(k, k - 1) >= k, SA(i, k) >= k - 1
+//   T(k) i,j:  SA(i, k) > k, SA(j, k) > k, SA(i, j) >= k
+//   S(k) j:    SA(k, k) > k; for j < k also SA(k, k - 1) >= k, SX(k - 1, j) >= k - j, SX(k, j) >= k - 1 - j
+//   U(k) i,j:  SX(k, j) > k - j, SA(i, k) > k, SX(i, j) >= k - j
+//   R(t) i,j:  SX(t, i) > t - i, SX(t, j) > t - j, ST(i, j) >= t - i
+// Apart from the chains, every task waits only for tasks claimed before it,
+// and a chain at step k waits only for tasks of steps below k, which depend
+// on chain steps below k: once G + 1 CTAs run, nothing can deadlock and no
+// co-residency is needed.  Waits are bounded all the same: on expiry the
+// launch is abandoned (sync[2] != 0) and counters[6] of every problem raised.
+// sync[0..1] is the claim counter (64-bit); zero before the launch.
+constexpr uint32_t kDepPolls = 1u << 24;  // polls (64 ns sleeps) of one dependency wait
+constexpr int kFactorTiles = 9;           // shared 32 x 33 tiles per CTA
+
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded wait of one thread for *p >= need (p null: none): relaxed polls with
+// a short sleep, then an acquire fence, so that the CTA's later reads see what
+// the flag publishes.  False if the wait ran out or the launch was abandoned.
+__device__ __forceinline__ bool wait_flag(const unsigned* p, unsigned need, unsigned* sync,
+                                          const ProbDesc* __restrict__ descs, int nprob) {
+  if (p == nullptr) return true;
+  bool ok = true;
+  for (uint32_t it = 0; ld_relaxed(p) < need; ++it) {
+    if (it >= kDepPolls || ((it & 15u) == 15u && *(volatile unsigned*)&sync[2] != 0u)) {
+      ok = false;
+      break;
+    }
+    __nanosleep(64);
+  }
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+  if (!ok && atomicExch(&sync[2], 1u) == 0u)
+    for (int q = 0; q < nprob; ++q) atomicAdd(&descs[q].counters[6], 1ull);
+  return ok;
+}
+
+// Each thread with p != null waits; false for every thread of the CTA if any wait failed.
+__device__ __forceinline__ bool wait_tiles(const unsigned* p, unsigned need, unsigned* sync,
+                                           const ProbDesc* __restrict__ descs, int nprob) {
+  const bool ok = wait_flag(p, need, sync, descs, nprob);
+  return __syncthreads_and(ok) != 0;
+}
+
+// AND of ok over the nthreads threads of named barrier id (a multiple of 32).
+__device__ __forceinline__ bool bar_and(int id, int nthreads, bool ok) {
+  unsigned r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((unsigned)ok), "r"(id), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+
+// Chain step k: wait for the tiles it reads to have had the trailing updates
+// that other tasks apply, then load them:
+//   Y  = A_kk, W1 = A_{k+1,k}                   (updates of steps below k - 1 applied)
+//   Ls = L_{k,k-1}, Lq = L_{k-1,k-2}, Dp = inv(L_{k-1,k-1})   (written by this chain)
+//   Wp = A_{k+1,k-1}                             (updates of steps below k - 2 applied)
+//   Lp = L_{k+1,k-2}                             (from another task, two steps back)
+// Warp 1 waits, so that the release of the previous step by thread 0 can overlap.
+template <typename T>
+__device__ bool chain_load(const ProbDesc& d, int k, Tile<T>* tl, unsigned* sync, const ProbDesc* __restrict__ descs,
+                           int nprob) {
+  const int np = npad_of(d), nb = d.nblk, tid = threadIdx.x;
+  const int tx = tid % BS, ty = tid / BS;
+  const unsigned* SA = d.tflag;
+  const bool b1 = k + 1 < nb;
+  const unsigned* wp = nullptr;
+  unsigned wn = 0;
+  if (tid == 32 && k >= 2) wp = &SA[k * nb + k], wn = k - 1;
+  if (tid == 33 && b1 && k >= 2) wp = &SA[(k + 1) * nb + k], wn = k - 1;
+  if (tid == 34 && b1 && k >= 3) wp = &SA[(k + 1) * nb + k - 1], wn = k - 2;
+  if (tid == 35 && b1 && k >= 2) wp = &SA[(k + 1) * nb + k - 2], wn = k - 1;
+  if (!wait_tiles(wp, wn, sync, descs, nprob)) return false;
+  const T* F = F1of<T>(d);
+  const T* Dg = Dinvof<T>(d);
+  T r[7][4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int y = ty + 8 * s;
+    r[0][s] = F[(k * BS + y) * np + k * BS + tx];
+    r[1][s] = k >= 1 ? F[(k * BS + y) * np + (k - 1) * BS + tx] : (T)0;
+    r[2][s] = b1 ? F[((k + 1) * BS + y) * np + k * BS + tx] : (T)0;
+    r[3][s] = b1 && k >= 1 ? F[((k + 1) * BS + y) * np + (k - 1) * BS + tx] : (T)0;
+    r[4][s] = b1 && k >= 2 ? F[((k + 1) * BS + y) * np + (k - 2) * BS + tx] : (T)0;
+    r[5][s] = b1 && k >= 2 ? F[((k - 1) * BS + y) * np + (k - 2) * BS + tx] : (T)0;
+    r[6][s] = b1 && k >= 1 ? Dg[(k - 1) * BS * BS + y * BS + tx] : (T)0;
+  }
+  constexpr int dst[7] = {0, 1, 2, 3, 6, 7, 8};  // Y, Ls, W1, Wp, Lp, Lq, Dp
+#pragma unroll
+  for (int q = 0; q < 7; ++q)
+#pragma unroll
+    for (int s = 0; s < 4; ++s) tl[dst[q]][ty + 8 * s][tx] = r[q][s];
+  __syncthreads();
+  return true;
+}
+
+// Chain step k with its tiles loaded (chain_load).  A_kk takes its last
+// trailing update; then warp 0 factors the diagonal block while four other warps
+// finish L_{k+1,k-1} = (A_{k+1,k-1} - L_{k+1,k-2} L_{k-1,k-2}^T) inv(L_{k-1,k-1})^T,
+// release it, and apply the last trailing update to A_{k+1,k}; then all
+// threads invert the factor and form L_{k+1,k}.
+template <typename T>
+__device__ bool chain_step(const ProbDesc& d, int k, Tile<T>* tl, unsigned* sync, const ProbDesc* __restrict__ descs,
+                           int nprob) {
+  const int np = npad_of(d), nb = d.nblk, tid = threadIdx.x;
+  const int tx = tid % BS, ty = tid / BS;
+  unsigned* SA = d.tflag;
+  const bool b1 = k + 1 < nb;
+  T* F = F1of<T>(d);
+  Tile<T> Y = tl[0], Ls = tl[1], W1 = tl[2], Wp = tl[3], Dv = tl[4], Z = tl[5], Lp = tl[6], Lq = tl[7], Dp = tl[8];
+  if (k >= 1) {
+    T acc[4];
+    tile_product<T, true>(Ls, Ls, acc);  // L_{k,k-1} L_{k,k-1}^T
+#pragma unroll
+    for (int s = 0; s < 4; ++s) Y[ty + 8 * s][tx] -= acc[s];
+    __syncthreads();
+  }
+  // A_kk = L_u D L_u^T, so L_kk = L_u D^1/2 and inv(L_kk) = D^-1/2 inv(L_u)
+  T* rs = &Z[0][0];  // D^-1/2 (the inverse below uses rows >= 1 of Z only)
+  if (tid < 32) {
     T a[BS];
 #pragma unroll
-    for (int c = 0; c < BS; ++c) a[c] = Akk[threadIdx.x * np + c];
+    for (int c = 0; c < BS; ++c) a[c] = Y[tid][c];
+    const T dl = warp_ldl_block<T>(a, &Dv[0][0], d);
     __syncwarp();
-    warp_potrf_block<T>(a, d, k, np, q == 0, q == 0 ? nullptr : y);
-  }
-  if (q == 0) return;
-  const int i = k + q;
-  T* Aik = F1of<T>(d) + (int64_t)i * BS * np + (int64_t)k * BS;
-  for (int e = threadIdx.x; e < BS * BS; e += 256) x[e / BS][e % BS] = Aik[(e / BS) * np + (e % BS)];
-  __syncthreads();
-  const int tx = threadIdx.x % BS, ty = threadIdx.x / BS;
-  T acc[4] = {(T)0, (T)0, (T)0, (T)0};
-  for (int t = 0; t < BS; ++t) {
-    const T yv = y[tx][t];  // inv(L_kk)[tx][t]
 #pragma unroll
-    for (int s = 0; s < 4; ++s) acc[s] = fma(x[ty + 8 * s][t], yv, acc[s]);
+    for (int c = 0; c < BS; ++c) {
+      Y[tid][c] = a[c];
+      Dv[tid][c] = c == tid ? (T)1 : (T)0;
+    }
+    rs[tid] = fast_rsqrt(dl);
+  } else if ((tid < 128 || (tid >= 160 && tid < 192)) && b1 && k >= 1) {
+    // warps 1, 2, 3 and 5, 8 rows per thread (warp 4 would share a scheduler
+    // with warp 0, whose factorisation is the critical path)
+    const int wb = tid < 128 ? tid / 32 - 1 : 3, cx = tid % BS, ry0 = wb;
+    const int t2 = wb * 32 + cx;
+    T acc[8];
+    if (k >= 2) {  // A_{k+1,k-1} -= L_{k+1,k-2} L_{k-1,k-2}^T
+#pragma unroll
+      for (int s = 0; s < 8; ++s) acc[s] = (T)0;
+#pragma unroll 8
+      for (int t = 0; t < BS; ++t) {
+        const T lv = Lq[cx][t];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) acc[s] = fma(Lp[ry0 + 4 * s][t], lv, acc[s]);
+      }
+#pragma unroll
+      for (int s = 0; s < 8; ++s) Wp[ry0 + 4 * s][cx] -= acc[s];
+      bar_and(1, 128, true);
+    }
+    // L_{k+1,k-1} = A_{k+1,k-1} inv(L_{k-1,k-1})^T, into F1 and (for the next product) Lp
+#pragma unroll
+    for (int s = 0; s < 8; ++s) acc[s] = (T)0;
+#pragma unroll 8
+    for (int t = 0; t < BS; ++t) {
+      const T dv = Dp[cx][t];
+#pragma unroll
+      for (int s = 0; s < 8; ++s) acc[s] = fma(Wp[ry0 + 4 * s][t], dv, acc[s]);
+    }
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      F[((k + 1) * BS + ry0 + 4 * s) * np + (k - 1) * BS + cx] = acc[s];
+      Lp[ry0 + 4 * s][cx] = acc[s];
+    }
+    bar_and(1, 128, true);
+    if (t2 == 0) st_release(&SA[(k + 1) * nb + k - 1], (unsigned)k);
+    // A_{k+1,k} -= L_{k+1,k-1} L_{k,k-1}^T
+#pragma unroll
+    for (int s = 0; s < 8; ++s) acc[s] = (T)0;
+#pragma unroll 8
+    for (int t = 0; t < BS; ++t) {
+      const T lv = Ls[cx][t];
+#pragma unroll
+      for (int s = 0; s < 8; ++s) acc[s] = fma(Lp[ry0 + 4 * s][t], lv, acc[s]);
+    }
+#pragma unroll
+    for (int s = 0; s < 8; ++s) W1[ry0 + 4 * s][cx] -= acc[s];
   }
+  __syncthreads();
+  T rsr[4];  // D^-1/2 of the rows ty + 8 s, and of column tx
+#pragma unroll
+  for (int s = 0; s < 4; ++s) rsr[s] = rs[ty + 8 * s];
+  const T rsc = rs[tx];
+  tri_inverse_block<T>(Y, Dv, Z);  // inv(L_u); it never writes row 0 of Z
+  T* Dg = Dinvof<T>(d) + k * BS * BS;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) Dg[(ty + 8 * s) * BS + tx] = Dv[ty + 8 * s][tx] * rsr[s];
+  if (b1) {
+    T acc[4];
+    tile_product<T, true>(W1, Dv, acc);  // A_{k+1,k} inv(L_u)^T, then the column scale D^-1/2
+#pragma unroll
+    for (int s = 0; s < 4; ++s) F[((k + 1) * BS + ty + 8 * s) * np + k * BS + tx] = acc[s] * rsc;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    st_release(&SA[k * nb + k], (unsigned)k + 1u);
+    if (b1) st_release(&SA[(k + 1) * nb + k], (unsigned)k + 1u);
+  }
+  return true;
+}
+
+// P(k) for tile (i, k), i >= k + 3: the last trailing update (step k - 1) is
+// applied while the chain may still be factoring A_kk; then L_ik = A_ik inv(L_kk)^T.
+template <typename T>
+__device__ bool panel_task(const ProbDesc& d, int np, int k, int i, Tile<T> x, Tile<T> y, unsigned* sync,
+                           const ProbDesc* __restrict__ descs, int nprob) {
+  T* F = F1of<T>(d);
+  T* Aik = F + i * BS * np + k * BS;
+  const int tx = threadIdx.x % BS, ty = threadIdx.x / BS;
+  T a[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) a[s] = Aik[(ty + 8 * s) * np + tx];
+  if (k > 0) {
+    load_two<T>(x, F + i * BS * np + (k - 1) * BS, y, F + k * BS * np + (k - 1) * BS, np, np);
+    T acc[4];
+    tile_product<T, true>(x, y, acc);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) a[s] -= acc[s];
+  }
+  const int nb = d.nblk;
+  if (!wait_tiles(threadIdx.x == 0 ? &d.tflag[k * nb + k] : nullptr, (unsigned)k + 1u, sync, descs, nprob))
+    return false;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) x[ty + 8 * s][tx] = a[s];
+  load_dense<T>(y, Dinvof<T>(d) + k * BS * BS);
+  __syncthreads();
+  T acc[4];
+  tile_product<T, true>(x, y, acc);  // A_ik inv(L_kk)^T
 #pragma unroll
   for (int s = 0; s < 4; ++s) Aik[(ty + 8 * s) * np + tx] = acc[s];
+  return true;
 }
 
-__device__ __forceinline__ void tri_index(int64_t u, int& i, int& j) {
-  // u -> (i, j) with 0 <= j <= i, u = i (i + 1) / 2 + j
-  int r = (int)((sqrt(8.0 * (double)u + 1.0) - 1.0) * 0.5);
-  while ((int64_t)(r + 1) * (r + 2) / 2 <= u) ++r;
-  while ((int64_t)r * (r + 1) / 2 > u) --r;
-  i = r;
-  j = (int)(u - (int64_t)r * (r + 1) / 2);
-}
-
-// Trailing update: A_ij -= L_ik L_jk^T for k < j <= i.
+// T(k): A_ij -= L_ik L_jk^T.
 template <typename T>
-__global__ void __launch_bounds__(256) k_trail(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
-                                              int nprob, int k) {
-  __shared__ T x[BS][BS + 1], y[BS][BS + 1];
-  const int p = find_problem(off, nprob, blockIdx.x);
-  const ProbDesc& d = descs[p];
-  const int np = npad_of(d);
-  int ii, jj;
-  tri_index(blockIdx.x - off[p], ii, jj);
-  const int i = k + 1 + ii, j = k + 1 + jj;
-  const T* Lik = F1of<T>(d) + (int64_t)i * BS * np + (int64_t)k * BS;
-  const T* Ljk = F1of<T>(d) + (int64_t)j * BS * np + (int64_t)k * BS;
-  T* Aij = F1of<T>(d) + (int64_t)i * BS * np + (int64_t)j * BS;
-  for (int e = threadIdx.x; e < BS * BS; e += 256) {
-    x[e / BS][e % BS] = Lik[(e / BS) * np + (e % BS)];
-    y[e / BS][e % BS] = Ljk[(e / BS) * np + (e % BS)];
-  }
-  __syncthreads();
+__device__ void trail_task(const ProbDesc& d, int np, int k, int i, int j, Tile<T> x, Tile<T> y) {
+  T* F = F1of<T>(d);
+  T* Aij = F + i * BS * np + j * BS;
   const int tx = threadIdx.x % BS, ty = threadIdx.x / BS;
-  T acc[4] = {(T)0, (T)0, (T)0, (T)0};
-  for (int t = 0; t < BS; ++t) {
-    const T yv = y[tx][t];
+  T a[4];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) acc[s] = fma(x[ty + 8 * s][t], yv, acc[s]);
-  }
+  for (int s = 0; s < 4; ++s) a[s] = Aij[(ty + 8 * s) * np + tx];
+  load_two<T>(x, F + i * BS * np + k * BS, y, F + j * BS * np + k * BS, np, np);
+  T acc[4];
+  tile_product<T, true>(x, y, acc);
 #pragma unroll
-  for (int s = 0; s < 4; ++s) Aij[(ty + 8 * s) * np + tx] -= acc[s];
+  for (int s = 0; s < 4; ++s) Aij[(ty + 8 * s) * np + tx] = a[s] - acc[s];
 }
 
-// ------------------------------------------------------------------ L^-1 (into F2)
-// Right-looking block forward substitution of L X = I: X starts as I on the
-// diagonal blocks and 0 below; at step k block row k is final after
-// X_kj <- inv(L_kk) X_kj (j <= k), and every block X_ij (i > k, j <= k) then
-// subtracts L_ik X_kj.  Each CTA does one 32 x 32 x 32 product per launch.
+// S(k): row k of X = L^-1 (block forward substitution; its last update, from
+// step k - 1, is applied here).
 template <typename T>
-__global__ void __launch_bounds__(256) k_linv_init(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
-                                                  int nprob) {
-  const int p = find_problem(off, nprob, blockIdx.x);
-  const ProbDesc& d = descs[p];
-  const int np = npad_of(d);
-  int i, j;
-  tri_index(blockIdx.x - off[p], i, j);
-  T* out = F2of<T>(d) + (int64_t)i * BS * np + (int64_t)j * BS;
-  for (int e = threadIdx.x; e < BS * BS; e += 256) {
-    const int r = e / BS, c = e % BS;
-    out[r * np + c] = (i == j && r == c) ? (T)1 : (T)0;
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_linv_scale(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
-                                                   int nprob, int k) {
-  __shared__ T x[BS][BS + 1], y[BS][BS + 1];
-  const int p = find_problem(off, nprob, blockIdx.x);
-  const ProbDesc& d = descs[p];
-  const int np = npad_of(d);
-  const int j = (int)(blockIdx.x - off[p]);  // j <= k
-  T* Xkj = F2of<T>(d) + (int64_t)k * BS * np + (int64_t)j * BS;
-  const T* D = Dinvof<T>(d) + (int64_t)k * BS * BS;
-  for (int e = threadIdx.x; e < BS * BS; e += 256) {
-    x[e / BS][e % BS] = D[e];
-    y[e / BS][e % BS] = Xkj[(e / BS) * np + (e % BS)];
-  }
-  __syncthreads();
+__device__ void linv_row_task(const ProbDesc& d, int np, int k, int j, Tile<T> x, Tile<T> y, Tile<T> z) {
+  T* X = F2of<T>(d);
+  T* Xkj = X + k * BS * np + j * BS;
+  const T* D = Dinvof<T>(d) + k * BS * BS;
   const int tx = threadIdx.x % BS, ty = threadIdx.x / BS;
-  T acc[4] = {(T)0, (T)0, (T)0, (T)0};
-  for (int u = 0; u < BS; ++u) {
-    const T yv = y[u][tx];
+  if (j == k) {
+    T rx[4];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) acc[s] = fma(x[ty + 8 * s][u], yv, acc[s]);
+    for (int s = 0; s < 4; ++s) rx[s] = D[(ty + 8 * s) * BS + tx];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) Xkj[(ty + 8 * s) * np + tx] = rx[s];
+    return;
   }
+  T a[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) a[s] = Xkj[(ty + 8 * s) * np + tx];
+  load_dense<T>(z, D);
+  load_two<T>(x, F1of<T>(d) + k * BS * np + (k - 1) * BS, y, X + (k - 1) * BS * np + j * BS, np, np);
+  T acc[4];
+  tile_product<T, false>(x, y, acc);  // L_{k,k-1} X_{k-1,j}
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < 4; ++s) y[ty + 8 * s][tx] = a[s] - acc[s];
+  __syncthreads();
+  tile_product<T, false>(z, y, acc);  // inv(L_kk) (...)
 #pragma unroll
   for (int s = 0; s < 4; ++s) Xkj[(ty + 8 * s) * np + tx] = acc[s];
 }
 
+// U(k): X_ij -= L_ik X_kj.
 template <typename T>
-__global__ void __launch_bounds__(256) k_linv_update(const ProbDesc* __restrict__ descs,
-                                                    const int64_t* __restrict__ off, int nprob, int k) {
-  __shared__ T x[BS][BS + 1], y[BS][BS + 1];
-  const int p = find_problem(off, nprob, blockIdx.x);
-  const ProbDesc& d = descs[p];
-  const int np = npad_of(d);
-  const int64_t local = blockIdx.x - off[p];
-  const int i = k + 1 + (int)(local / (k + 1)), j = (int)(local % (k + 1));
-  const T* Lik = F1of<T>(d) + (int64_t)i * BS * np + (int64_t)k * BS;
-  const T* Xkj = F2of<T>(d) + (int64_t)k * BS * np + (int64_t)j * BS;
-  T* Xij = F2of<T>(d) + (int64_t)i * BS * np + (int64_t)j * BS;
-  for (int e = threadIdx.x; e < BS * BS; e += 256) {
-    x[e / BS][e % BS] = Lik[(e / BS) * np + (e % BS)];
-    y[e / BS][e % BS] = Xkj[(e / BS) * np + (e % BS)];
-  }
-  __syncthreads();
+__device__ void linv_update_task(const ProbDesc& d, int np, int k, int i, int j, Tile<T> x, Tile<T> y) {
+  T* X = F2of<T>(d);
+  T* Xij = X + i * BS * np + j * BS;
   const int tx = threadIdx.x % BS, ty = threadIdx.x / BS;
-  T acc[4] = {(T)0, (T)0, (T)0, (T)0};
-  for (int u = 0; u < BS; ++u) {
-    const T yv = y[u][tx];
+  T a[4];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) acc[s] = fma(x[ty + 8 * s][u], yv, acc[s]);
-  }
+  for (int s = 0; s < 4; ++s) a[s] = Xij[(ty + 8 * s) * np + tx];
+  load_two<T>(x, F1of<T>(d) + i * BS * np + k * BS, y, X + k * BS * np + j * BS, np, np);
+  T acc[4];
+  tile_product<T, false>(x, y, acc);
 #pragma unroll
-  for (int s = 0; s < 4; ++s) Xij[(ty + 8 * s) * np + tx] -= acc[s];
+  for (int s = 0; s < 4; ++s) Xij[(ty + 8 * s) * np + tx] = a[s] - acc[s];
 }
 
-// T = A^-1 = L^-T L^-1:  T_ij = sum_{t >= max(i, j)} Linv_ti^T Linv_tj  (into F1, both triangles)
+// R(t): T_ij (+)= X_ti^T X_tj; the last row also writes T_ji = T_ij^T.
 template <typename T>
-__global__ void __launch_bounds__(256) k_ainv(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
-                                             int nprob) {
-  __shared__ T x[BS][BS + 1], y[BS][BS + 1];
-  const int p = find_problem(off, nprob, blockIdx.x);
-  const ProbDesc& d = descs[p];
-  const int np = npad_of(d);
-  int i, j;
-  tri_index(blockIdx.x - off[p], i, j);  // j <= i
+__device__ void trow_task(const ProbDesc& d, int np, int t, int i, int j, Tile<T> x, Tile<T> y) {
+  T* Tm = Tof<T>(d);
+  const T* X = F2of<T>(d);
+  T* Tij = Tm + i * BS * np + j * BS;
   const int tx = threadIdx.x % BS, ty = threadIdx.x / BS;
-  T acc[4] = {(T)0, (T)0, (T)0, (T)0};
-  for (int t = i; t < d.nblk; ++t) {
-    const T* Lti = F2of<T>(d) + (int64_t)t * BS * np + (int64_t)i * BS;
-    const T* Ltj = F2of<T>(d) + (int64_t)t * BS * np + (int64_t)j * BS;
+  T a[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) a[s] = t > i ? Tij[(ty + 8 * s) * np + tx] : (T)0;
+  load_two<T>(x, X + t * BS * np + i * BS, y, X + t * BS * np + j * BS, np, np);
+#pragma unroll 8
+  for (int v = 0; v < BS; ++v) {
+    const T yv = y[v][tx];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) a[s] = fma(x[v][ty + 8 * s], yv, a[s]);
+  }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) Tij[(ty + 8 * s) * np + tx] = a[s];
+  if (t == d.nblk - 1 && i != j) {
     __syncthreads();
-    for (int e = threadIdx.x; e < BS * BS; e += 256) {
-      x[e / BS][e % BS] = Lti[(e / BS) * np + (e % BS)];
-      y[e / BS][e % BS] = Ltj[(e / BS) * np + (e % BS)];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) x[ty + 8 * s][tx] = a[s];
+    __syncthreads();
+    T* Tji = Tm + j * BS * np + i * BS;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) Tji[(ty + 8 * s) * np + tx] = x[tx][ty + 8 * s];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
+    k_factor(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ tables, int nprob, FactorTables ft,
+             unsigned* sync, int nchain) {
+  extern __shared__ __align__(16) unsigned char factor_smem[];
+  Tile<T> tl[kFactorTiles];
+#pragma unroll
+  for (int q = 0; q < kFactorTiles; ++q) tl[q] = reinterpret_cast<Tile<T>>(factor_smem) + q * BS;
+  Tile<T> x = tl[0], y = tl[1], z = tl[2];
+  __shared__ unsigned long long s_task;
+  const int K = ft.nsteps, lag = ft.lag;
+  const int nseg = 5 * K + 3 * lag;
+  const int64_t* seg_start = tables + ft.phase;  // task prefix over the segments after the chains
+  const unsigned long long ntask = (unsigned long long)nchain + (unsigned long long)seg_start[nseg];
+  const size_t n1 = (size_t)nprob + 1;
+  unsigned long long* claim = reinterpret_cast<unsigned long long*>(sync);
+  const int tid = threadIdx.x;
+  int seg = 0;
+  for (;;) {
+    __syncthreads();  // the previous task is done with the tiles and s_task
+    if (tid == 0) s_task = atomicAdd(claim, 1ull);
+    __syncthreads();
+    const unsigned long long task = s_task;
+    if (task >= ntask) return;
+    if (task < (unsigned long long)nchain) {
+      // chain: for k = 0, 1, ...: every problem of the chain with nblk > k;
+      // the next step's tiles are loaded right after each step's release
+      const int c = (int)task;
+      int k = 0, p = c;
+      auto advance = [&](int& kk, int& pp) {  // next (step, problem) of the chain; kk = K at the end
+        for (;;) {
+          pp += nchain;
+          if (pp >= nprob) {
+            pp = c;
+            if (++kk >= K) return;
+          }
+          if (kk < descs[pp].nblk) return;
+        }
+      };
+      if (k >= descs[p].nblk) advance(k, p);
+      if (k < K && !chain_load<T>(descs[p], k, tl, sync, descs, nprob)) return;
+      while (k < K) {
+        if (!chain_step<T>(descs[p], k, tl, sync, descs, nprob)) return;
+        advance(k, p);
+        if (k < K && !chain_load<T>(descs[p], k, tl, sync, descs, nprob)) return;
+      }
+      continue;
+    }
+    const int64_t u = (int64_t)(task - (unsigned long long)nchain);
+    while (u >= seg_start[seg + 1]) ++seg;
+    int kind, k;  // kind: 0 P, 1 T, 2 S, 3 U, 4 R
+    if (seg < 5 * K) {
+      k = seg / 5;
+      kind = seg % 5;
+      if (kind >= 2) k -= lag;
+    } else {
+      k = K - lag + (seg - 5 * K) / 3;
+      kind = 2 + (seg - 5 * K) % 3;
+    }
+    const int64_t* tab = kind < 2 ? tables + ft.step + (size_t)k * 2 * n1 + (size_t)kind * n1
+                                  : tables + ft.linv + (size_t)k * 3 * n1 + (size_t)(kind - 2) * n1;
+    const int64_t g = u - seg_start[seg];
+    const int p = find_problem(tab, nprob, g);
+    const ProbDesc& d = descs[p];
+    const int np = npad_of(d), nb = d.nblk;
+    const int l = (int)(g - tab[p]);
+    unsigned* SA = d.tflag;                // SA(i, j) = SA[i * nb + j]
+    unsigned* SX = d.tflag + nb * nb;      // SX(i, j) = SX[i * nb + j]
+    unsigned* ST = d.tflag + 2 * nb * nb;  // ST(i, j) = ST[i * nb + j]
+    // the task's tiles, its conditions (thread t waits for condition t) and its output state
+    int i = 0, j = 0;
+    const unsigned* wp = nullptr;
+    unsigned wn = 0;
+    unsigned* out = nullptr;
+    unsigned out_v = 0;
+    switch (kind) {
+      case 0:  // P(k), tile (i, k)
+        i = k + 3 + l;
+        if (k > 0) {
+          if (tid == 0) wp = &SA[i * nb + k - 1], wn = k;
+          if (tid == 1) wp = &SA[k * nb + k - 1], wn = k;
+          if (tid == 2) wp = &SA[i * nb + k], wn = k - 1;
+        }
+        out = &SA[i * nb + k], out_v = k + 1;
+        break;
+      case 1:  // T(k), tile (i, j), j >= k + 2
+        trail_pair(k + 1, nb - k - 2, l, i, j);
+        if (tid == 0) wp = &SA[i * nb + k], wn = k + 1;
+        if (tid == 1) wp = &SA[j * nb + k], wn = k + 1;
+        if (tid == 2) wp = &SA[i * nb + j], wn = k;
+        out = &SA[i * nb + j], out_v = k + 1;
+        break;
+      case 2:  // S(k), tile (k, j)
+        j = l;
+        if (tid == 0) wp = &SA[k * nb + k], wn = k + 1;
+        if (j < k) {
+          if (tid == 1) wp = &SA[k * nb + k - 1], wn = k;
+          if (tid == 2) wp = &SX[(k - 1) * nb + j], wn = k - j;
+          if (tid == 3) wp = &SX[k * nb + j], wn = k - 1 - j;
+        }
+        out = &SX[k * nb + j], out_v = k - j + 1;
+        break;
+      case 3:  // U(k), tile (i, j), i >= k + 2
+        i = k + 2 + l / (k + 1), j = l % (k + 1);
+        if (tid == 0) wp = &SX[k * nb + j], wn = k - j + 1;
+        if (tid == 1) wp = &SA[i * nb + k], wn = k + 1;
+        if (tid == 2) wp = &SX[i * nb + j], wn = k - j;
+        out = &SX[i * nb + j], out_v = k - j + 1;
+        break;
+      default:  // R(k), tile (i, j), j <= i <= k
+        tri_index(l, i, j);
+        if (tid == 0) wp = &SX[k * nb + i], wn = k - i + 1;
+        if (tid == 1) wp = &SX[k * nb + j], wn = k - j + 1;
+        if (tid == 2) wp = &ST[i * nb + j], wn = k - i;
+        out = &ST[i * nb + j], out_v = k - i + 1;
+        break;
+    }
+    if (!wait_tiles(wp, wn, sync, descs, nprob)) return;
+    switch (kind) {
+      case 0:
+        if (!panel_task<T>(d, np, k, i, x, y, sync, descs, nprob)) return;
+        break;
+      case 1: trail_task<T>(d, np, k, i, j, x, y); break;
+      case 2: linv_row_task<T>(d, np, k, j, x, y, z); break;
+      case 3: linv_update_task<T>(d, np, k, i, j, x, y); break;
+      default: trow_task<T>(d, np, k, i, j, x, y); break;
     }
     __syncthreads();
-    for (int u = 0; u < BS; ++u) {
-      const T yv = y[u][tx];
-#pragma unroll
-      for (int s = 0; s < 4; ++s) acc[s] = fma(x[u][ty + 8 * s], yv, acc[s]);
-    }
+    if (tid == 0) st_release(out, out_v);
   }
-  T* Tij = F1of<T>(d) + (int64_t)i * BS * np + (int64_t)j * BS;
-  T* Tji = F1of<T>(d) + (int64_t)j * BS * np + (int64_t)i * BS;
-  __syncthreads();
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    Tij[(ty + 8 * s) * np + tx] = acc[s];
-    x[ty + 8 * s][tx] = acc[s];
-  }
-  __syncthreads();
-  if (i != j)
-    for (int e = threadIdx.x; e < BS * BS; e += 256) Tji[(e / BS) * np + (e % BS)] = x[e % BS][e / BS];
 }
 
 // ------------------------------------------------------------------ block iteration (FP64)
@@ -838,7 +1241,7 @@ __global__ void __launch_bounds__(256) k_precond(const ProbDesc* __restrict__ de
     for (int e = threadIdx.x; e < kPRows * 64; e += 256) {
       const int r = e / 64, c = e % 64;
       const int i = i0 + r, j = j0 + c;
-      ts[r][c] = (i < n && j < j_end) ? F1of<T>(d)[i * np + j] : (T)0;
+      ts[r][c] = (i < n && j < j_end) ? Tof<T>(d)[i * np + j] : (T)0;
     }
     for (int e = threadIdx.x; e < 64 * kx; e += 256) {
       const int r = dkx.q(e), c = dkx.r(e);
@@ -970,32 +1373,25 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
   auto* precond_x = k_precond<T, 1>;  // A^-1 X
   auto* precond_r = k_precond<T, 0>;  // A^-1 R
   RSM_LAUNCH(k_eig_prep<T>, (total(P.pad2) + 255) / 256, 256, D, dev(P.pad2), np, shift_rel, a_iters);
-  // Blocked Cholesky on the stream; the inverse factor X = L^-1 on the second
-  // stream, step k of it as soon as block column k of L is final (after the
-  // panel of step k), so the two sequential chains overlap.
-  cudaError_t ee;
-  if ((ee = cudaEventRecord(P.fork, s)) != cudaSuccess || (ee = cudaStreamWaitEvent(P.aux, P.fork, 0)) != cudaSuccess)
-    return ee;
-  {
-    cudaStream_t s = P.aux;
-    RSM_LAUNCH(k_linv_init<T>, total(P.tri), 256, D, dev(P.tri), np);
+  // The factor, its inverse and T = A^-1 in one launch (see k_factor).
+  static int factor_ctas[2] = {0, 0};
+  const int factor_smem = kFactorTiles * BS * (BS + 1) * (int)sizeof(T);
+  int& fc = factor_ctas[sizeof(T) == 8];
+  if (fc == 0) {
+    int dev_id = 0, sms = 0, per_sm = 0;
+    cudaError_t eo = cudaFuncSetAttribute(k_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, factor_smem);
+    if (eo == cudaSuccess) eo = cudaGetDevice(&dev_id);
+    if (eo == cudaSuccess) eo = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
+    if (eo == cudaSuccess) eo = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor<T>, 256, factor_smem);
+    if (eo != cudaSuccess) return eo;
+    fc = std::max(2, sms * per_sm);
   }
-  for (int k = 0; k < P.max_nblk; ++k) {
-    const size_t o1 = P.step + (size_t)k * 3 * (np + 1), o3 = o1 + 2 * (np + 1);
-    RSM_LAUNCH(k_panel<T>, total(o1), 256, D, dev(o1), np, k);  // diagonal block + block column k
-    if ((ee = cudaEventRecord(P.fork, s)) != cudaSuccess || (ee = cudaStreamWaitEvent(P.aux, P.fork, 0)) != cudaSuccess)
-      return ee;
-    {
-      cudaStream_t s = P.aux;
-      const size_t l1 = P.linv + (size_t)k * 2 * (np + 1), l2 = l1 + (np + 1);
-      RSM_LAUNCH(k_linv_scale<T>, total(l1), 256, D, dev(l1), np, k);
-      RSM_LAUNCH(k_linv_update<T>, total(l2), 256, D, dev(l2), np, k);
-    }
-    RSM_LAUNCH(k_trail<T>, total(o3), 256, D, dev(o3), np, k);
-  }
-  if ((ee = cudaEventRecord(P.join, P.aux)) != cudaSuccess || (ee = cudaStreamWaitEvent(s, P.join, 0)) != cudaSuccess)
-    return ee;
-  RSM_LAUNCH(k_ainv<T>, total(P.tri), 256, D, dev(P.tri), np);
+  // one chain per problem while they take at most half the CTAs (so that at
+  // least as many CTAs serve the other tasks), else problems share chains
+  const int nchain = std::min(np, std::max(1, fc / 2));
+  FactorTables ft{P.step, P.linv, P.tri, P.phase, P.max_nblk, kFactorLag};
+  const int64_t ntask = nchain + P.hT[P.phase + 5 * P.max_nblk + 3 * kFactorLag];
+  RSM_LAUNCH_SMEM(k_factor<T>, std::min<int64_t>(ntask, fc), 256, factor_smem, D, P.dT, np, ft, P.sync, nchain);
   RSM_LAUNCH(k_init_X, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
   auto orthonormalise = [&]() -> cudaError_t {
     RSM_LAUNCH_SMEM(k_xtx<false>, total(P.chunk), 256, xtx_smem, D, dev(P.chunk), np, P.part, dev(P.part_off));

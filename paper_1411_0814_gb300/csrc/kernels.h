@@ -25,10 +25,18 @@ struct EigPlan {
   const int64_t* dT;
   const int64_t* hT;
   size_t pad2, step, blk, linv, tri, nk, mx, chunk, part_off, rot, row_tile;  // table positions (linv: 2 per step)
-  double* part;  // partial Gram sums of the block iteration
-  cudaStream_t aux;          // second stream for the inverse factor
-  cudaEvent_t fork, join;    // events between the two streams (no timing)
+  size_t phase;   // task prefix over the 5 max_nblk + 3 kFactorLag segments of the factor launch
+  double* part;   // partial Gram sums of the block iteration
+  unsigned* sync; // factor launch: claim counter, abort word, per-phase completion counts (zeroed)
 };
+
+// Table positions read by the factor launch.
+struct FactorTables {
+  size_t step, linv, tri, phase;
+  int nsteps;  // largest block count of the batch
+  int lag;     // steps by which the inverse-factor tasks trail the Cholesky tasks in claim order
+};
+constexpr int kFactorLag = 1;
 
 struct SolvePlan {
   const ProbDesc* descs;

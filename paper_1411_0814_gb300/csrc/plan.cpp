@@ -17,7 +17,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Sizes {
-  size_t macc, counters, colcount, stats;                    // zero region
+  size_t macc, counters, colcount, stats, tflag;             // zero region
   size_t bits, cols, rowc, gram, M, Mdf, F1, F2, Dinv, X, MX, R, small, Kmat, NB;  // data region
 };
 
@@ -28,14 +28,15 @@ Sizes sizes_of(const rsm_problem& p, const Derived& dv) {
   s.counters = align_up(8 * 8);
   s.colcount = align_up(n * 4);
   s.stats = align_up(64 * 8);
+  s.tflag = align_up((size_t)3 * dv.nblk * dv.nblk * 4);
   s.bits = align_up(n * (size_t)dv.ldb * 4);
   s.cols = align_up(I * dv.l * 4);
   s.rowc = align_up(I * 4);
   s.gram = align_up(I * dv.P_l * 8);
   s.M = align_up(n * n * 8);
   s.Mdf = align_up(n * n * 8);
-  s.F1 = align_up((size_t)dv.npad * dv.npad * 8);
-  s.F2 = s.F1;
+  s.F1 = align_up((size_t)dv.npad * dv.npad * 8 * 2);  // the factor, then T = A^-1
+  s.F2 = align_up((size_t)dv.npad * dv.npad * 8);
   s.Dinv = align_up((size_t)dv.nblk * 32 * 32 * 8);
   s.X = align_up(n * dv.kx * 8);
   s.MX = s.X;
@@ -49,7 +50,7 @@ Sizes sizes_of(const rsm_problem& p, const Derived& dv) {
   return s;
 }
 
-size_t zero_sum(const Sizes& s) { return s.macc + s.counters + s.colcount + s.stats; }
+size_t zero_sum(const Sizes& s) { return s.macc + s.counters + s.colcount + s.stats + s.tflag; }
 size_t data_sum(const Sizes& s) {
   return s.bits + s.cols + s.rowc + s.gram + s.M + s.Mdf + s.F1 + s.F2 + s.Dinv + s.X + s.MX + s.R + s.small + s.Kmat + s.NB;
 }
@@ -179,21 +180,42 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
   b.o_pad2 = prefix([&](int i) { return b.dv[i].npad * b.dv[i].npad; });
   b.pad2_total = total(b.o_pad2);
   b.o_step = T.size();
-  for (int k = 0; k < b.max_nblk; ++k) {  // per step: block column k (diagonal + below), unused, trailing update
-    prefix([&](int i) { return (int64_t)std::max(0, b.dv[i].nblk - k); });
-    prefix([&](int i) { return (int64_t)0; });
+  for (int k = 0; k < b.max_nblk; ++k) {  // per step: panel tiles i >= k + 3, trailing tiles of columns >= k + 2
+    prefix([&](int i) { return (int64_t)std::max(0, b.dv[i].nblk - k - 3); });
     prefix([&](int i) {
-      const int64_t t = std::max(0, b.dv[i].nblk - k - 1);
+      const int64_t t = std::max(0, b.dv[i].nblk - k - 2);
       return t * (t + 1) / 2;
     });
   }
   b.o_blk = prefix([&](int i) { return (int64_t)b.dv[i].nblk; });
   b.o_linv = T.size();
-  for (int k = 0; k < b.max_nblk; ++k) {
+  for (int k = 0; k < b.max_nblk; ++k) {  // per step: row k of L^-1, updates of the rows >= k + 2, row k's share of T
     prefix([&](int i) { return (int64_t)(k < b.dv[i].nblk ? k + 1 : 0); });
-    prefix([&](int i) { return (int64_t)(k < b.dv[i].nblk ? (b.dv[i].nblk - k - 1) * (k + 1) : 0); });
+    prefix([&](int i) { return (int64_t)std::max(0, b.dv[i].nblk - k - 2) * (k + 1); });
+    prefix([&](int i) { return (int64_t)(k < b.dv[i].nblk ? (int64_t)(k + 1) * (k + 2) / 2 : 0); });
   }
   b.o_tri = prefix([&](int i) { return (int64_t)b.dv[i].nblk * (b.dv[i].nblk + 1) / 2; });
+  // Task prefix over the segments of the factor launch's claim order (after
+  // its chain tasks): per step k the panel and the trailing update, then the
+  // inverse-factor tasks and the rows of T of step k - kFactorLag; then those
+  // of the last kFactorLag steps.
+  {
+    const size_t n1 = (size_t)count + 1;
+    const int K = b.max_nblk, lag = kFactorLag;
+    auto tot = [&](size_t pos) { return T[pos + count]; };
+    std::vector<int64_t> ph(1, 0);
+    auto linv_seg = [&](int kk) {
+      for (int c = 0; c < 3; ++c)
+        ph.push_back(ph.back() + (kk >= 0 && kk < K ? tot(b.o_linv + (size_t)kk * 3 * n1 + (size_t)c * n1) : 0));
+    };
+    for (int k = 0; k < K; ++k) {
+      for (int c = 0; c < 2; ++c) ph.push_back(ph.back() + tot(b.o_step + (size_t)k * 2 * n1 + (size_t)c * n1));
+      linv_seg(k - lag);
+    }
+    for (int m = 0; m < lag; ++m) linv_seg(K - lag + m);
+    b.o_phase = T.size();
+    T.insert(T.end(), ph.begin(), ph.end());
+  }
   b.o_nk = prefix([&](int i) { return ps[i].n * b.dv[i].kx; });
   b.nk_total = total(b.o_nk);
   b.o_mx = prefix([&](int i) { return (int64_t)kEigSplit * ((ps[i].n + 127) / 128); });
@@ -265,6 +287,9 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
   b.data_size.resize(count);
   size_t off = kAlign;  // batch header: the fail-list counter
   b.fail_count_off = 0;
+  b.sync_off = off;  // factor launch: claim counter, abort word
+  b.sync_bytes = align_up(4 * 4);
+  off += b.sync_bytes;
   for (int i = 0; i < count; ++i) {
     Sizes s = sizes_of(ps[i], b.dv[i]);
     b.zero_off[i] = off;
@@ -333,6 +358,8 @@ void bind_batch(Batch& b, const rsm_problem* ps, unsigned char* ws) {
     d.colcount = reinterpret_cast<int32_t*>(z);
     z += s.colcount;
     d.stats = reinterpret_cast<double*>(z);
+    z += s.stats;
+    d.tflag = reinterpret_cast<unsigned*>(z);
     unsigned char* q = ws + b.data_off[i];
     auto take = [&](size_t bytes) {
       unsigned char* r = q;

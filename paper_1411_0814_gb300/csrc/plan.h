@@ -45,7 +45,7 @@ struct Batch {
   // positions (in int64 elements) of each table inside `tables`
   size_t o_pack = 0, o_trial = 0, o_ent = 0, o_pad2 = 0, o_step = 0, o_blk = 0, o_linv = 0, o_tri = 0, o_nk = 0,
          o_mx = 0, o_chunk = 0, o_part = 0, o_rot = 0, o_rowtile = 0, o_k = 0, o_tile = 0, o_row = 0, o_res = 0,
-         o_b = 0, o_tc = 0, o_res4 = 0;
+         o_b = 0, o_tc = 0, o_res4 = 0, o_phase = 0;
   int64_t pack_blocks = 0, trials_total = 0, ent_total = 0, pad2_total = 0, nk_total = 0, part_total = 0,
           k_total = 0, tile_total = 0, row_total = 0, res_blocks = 0, b_total = 0, tc_total = 0, res4_blocks = 0;
   int64_t solve_rows = 0;  // rows of all problems that solve for U
@@ -55,6 +55,7 @@ struct Batch {
   std::vector<size_t> zero_off, data_off;
   std::vector<size_t> zero_size, data_size;
   size_t part_bytes_off = 0, res_bytes_off = 0, fail_list_off = 0, fail_count_off = 0;
+  size_t sync_off = 0, sync_bytes = 0;  // the factor launch's claim counter and phase counts (zeroed)
   int rmax = 0;
   // Row-slab schedule of the Gram: one group per distinct l that the slab
   // kernel supports (a launch per slab per group); problems of other l go

@@ -114,12 +114,10 @@ struct PinBuf {
 // workspace, a plan buffer, pinned readback space and stage events.
 struct Slot {
   cudaStream_t stream = nullptr;
-  cudaStream_t aux = nullptr;  // second stream: the inverse factor overlaps the factorisation
   bool own_stream = false;
   DevBuf ws, plan;
   PinBuf host;
   cudaEvent_t ev[10] = {};
-  cudaEvent_t fork = nullptr, join = nullptr;  // timing-free events between stream and aux
   int init(cudaStream_t external) {
     if (external) {
       stream = external;
@@ -127,18 +125,10 @@ struct Slot {
       RSM_CUDA(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
       own_stream = true;
     }
-    RSM_CUDA(cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking));
     for (auto& e : ev) RSM_CUDA(cudaEventCreate(&e));
-    RSM_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-    RSM_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
     return RSM_OK;
   }
   void destroy() {
-    if (fork) cudaEventDestroy(fork);
-    if (join) cudaEventDestroy(join);
-    fork = join = nullptr;
-    if (aux) cudaStreamDestroy(aux);
-    aux = nullptr;
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
     ws.release();
@@ -228,9 +218,8 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
   ep.rot = b.o_rot;
   ep.row_tile = b.o_rowtile;
   ep.part = reinterpret_cast<double*>(static_cast<unsigned char*>(slot.ws.ptr) + b.part_bytes_off);
-  ep.aux = slot.aux;
-  ep.fork = slot.fork;
-  ep.join = slot.join;
+  ep.phase = b.o_phase;
+  ep.sync = reinterpret_cast<unsigned*>(static_cast<unsigned char*>(slot.ws.ptr) + b.sync_off);
   if ((e = launch_eig(ep, fp64_factor, shift_rel, fp64_factor ? kEigIters64 : kEigIters32, s)) != cudaSuccess)
     return cuda_fail(e, "eig");
   RSM_CUDA(cudaEventRecord(slot.ev[6], s));
@@ -312,6 +301,7 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
   // Accept the result when the factorisation succeeded and the a-posteriori
   // eigenvector bound (residual norm over the eigen-gap) is small; otherwise
   // redo the eigen stage with the FP64 factor (and then larger shifts).
+  bool timed_out = false;  // a bounded device-side wait ran out (counters[6])
   for (int attempt = 0; attempt < 3; ++attempt) {
     bool redo = false;
     for (int i = 0; i < count; ++i) {
@@ -323,8 +313,9 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
       const bool determined = c[0] > 0 && stats[r] > kRankTol * trace;
       const double est = stats[34] / (gap > 0.0 ? gap : 1e-300);
       if (c[3] != 0 || (!fp64 && determined && !(est <= kEigErrTol))) redo = true;
+      if (c[6] != 0) timed_out = true;
     }
-    if (!redo) break;
+    if (!redo || timed_out) break;
     if (fp64)
       shift *= 100.0;
     else {
@@ -333,6 +324,9 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
     }
     for (int i = 0; i < count; ++i) RSM_CUDA(cudaMemsetAsync(b.descs[i].counters + 3, 0, 16, slot.stream));
     RSM_CUDA(cudaMemsetAsync(static_cast<unsigned char*>(slot.ws.ptr) + b.fail_count_off, 0, 8, slot.stream));
+    RSM_CUDA(cudaMemsetAsync(static_cast<unsigned char*>(slot.ws.ptr) + b.sync_off, 0, b.sync_bytes, slot.stream));
+    for (int i = 0; i < count; ++i)
+      RSM_CUDA(cudaMemsetAsync(b.descs[i].tflag, 0, (size_t)3 * b.dv[i].nblk * b.dv[i].nblk * 4, slot.stream));
     if ((st = launch_batch(b, slot, fp64, shift, false)) != RSM_OK) return st;
     if ((st = enqueue_readback(b, slot)) != RSM_OK) return st;
     RSM_CUDA(cudaStreamSynchronize(slot.stream));
@@ -358,7 +352,9 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
     const double trace = (double)c[0] * b.dv[i].nm;
     r.e_known_rms = b.dv[i].solve_u ? stats[33] : NAN;
     int status = RSM_OK;
-    if (c[0] == 0 || !(r.eig_M[ps[i].r] > kRankTol * trace))
+    if (c[6] != 0)
+      status = RSM_ERR_TIMEOUT;
+    else if (c[0] == 0 || !(r.eig_M[ps[i].r] > kRankTol * trace))
       status = RSM_ERR_UNDERDETERMINED;
     else if (c[3] != 0)
       status = RSM_ERR_UNDERDETERMINED;
