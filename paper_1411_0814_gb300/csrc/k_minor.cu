@@ -34,13 +34,15 @@ __host__ __device__ inline size_t minor_smem_per_warp(int lmax) {
 // complement eigenvectors of the FP32 basis Qf (eigenvalues on Sf's diagonal).
 // Qd (l x l, stride ls) and lam (l) are FP64 copies of the FP32 eigenvectors and
 // eigenvalues, made once per trial so the steps convert nothing.  The steps stop
-// early once every correction is below `stop` (z has unit norm): 1e-17 for an
-// FP64 or FP32-pair Gram; 1e-10 for an FP32 Gram, whose own rounding (~1e-7
-// relative) already bounds how well its minor vectors are defined.
+// early once every correction is below `stop` (z has unit norm), 1e-17, or
+// after max_steps.  An FP32 Gram takes a single step: its own rounding (~1e-7
+// relative) already bounds how well its minor vectors are defined, and one
+// step from the FP32 basis (error ~1e-7) leaves ~1e-14 (times ||G|| / gap).
 __device__ inline void newton_refine(const double* Gs, const double* Qd, const double* lam, double* Z, double* rv,
-                                     double* cv, int l, int nm, int ls, const int* is_minor, double fro, double stop) {
+                                     double* cv, int l, int nm, int ls, const int* is_minor, double fro, double stop,
+                                     int max_steps) {
   const int lane = threadIdx.x & 31;
-  for (int step = 0; step < kNewtonSteps; ++step) {
+  for (int step = 0; step < max_steps; ++step) {
     double cmax = 0.0;
     for (int j = 0; j < nm; ++j) {
       double gz = 0.0, za = 0.0;
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDe
     for (int it = lane; it < l * l; it += 32) Wd[dl.q(it) * ls + dl.r(it)] = (double)Qf[dl.q(it) * ls + dl.r(it)];
     if (lane < l) gv[lane] = (double)Sf[lane * ls + lane];
     __syncwarp();
-    newton_refine(Gs, Wd, gv, Z, rv, cv, l, nm, ls, is_minor[wid], fro, d.gram_fp32 ? 1e-10 : 1e-17);
+    newton_refine(Gs, Wd, gv, Z, rv, cv, l, nm, ls, is_minor[wid], fro, 1e-17, d.gram_fp32 ? 1 : kNewtonSteps);
   }
 
   if (d.debug_Z)
