@@ -22,9 +22,10 @@ namespace rsm {
 
 constexpr int kSlabWarps = 4;
 #ifndef RSM_SLAB_MINB
-#define RSM_SLAB_MINB 4
+#define RSM_SLAB_MINB 5  // CTAs per SM of the FP32 form; the FP64 form (45 FP64 accumulators) keeps four
 #endif
 constexpr int kRing = 1088;  // pending rows per warp: < 32 + 32 * 32
+constexpr int kMeta = 40;    // per warp: the l column offsets into Y (from 0), then into the mask (from 20)
 
 template <int MODE>
 struct SlabT;
@@ -44,7 +45,7 @@ struct SlabT<2> {  // FP32 Gram of FP32 Y
 };
 
 template <int MODE, int L>
-__global__ void __launch_bounds__(32 * kSlabWarps, RSM_SLAB_MINB) k_gram_slab(const ProbDesc* __restrict__ descs,
+__global__ void __launch_bounds__(32 * kSlabWarps, MODE == 2 ? RSM_SLAB_MINB : 4) k_gram_slab(const ProbDesc* __restrict__ descs,
                                                                const int64_t* __restrict__ task_off, int nprob,
                                                                int slab) {
   using Tr = SlabT<MODE>;
@@ -55,24 +56,26 @@ __global__ void __launch_bounds__(32 * kSlabWarps, RSM_SLAB_MINB) k_gram_slab(co
   constexpr int kWarpWords = kRedWords > kRing ? kRedWords : kRing;
   extern __shared__ __align__(16) int slab_smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int* ring = slab_smem + wid * kWarpWords;
+  int* ring = slab_smem + wid * (kWarpWords + kMeta);
   A* red = reinterpret_cast<A*>(ring);
+  uint32_t* meta = reinterpret_cast<uint32_t*>(ring + kWarpWords);
 
   const int64_t g = (int64_t)blockIdx.x * kSlabWarps + wid;
   if (g >= task_off[nprob]) return;
   const int p = find_problem(task_off, nprob, g);
   const ProbDesc& d = descs[p];
   const int64_t t = g - task_off[p];
-  // 32-bit column offsets into Y and the mask (the host checks ldy n, ldb n < 2^32)
+  // 32-bit column offsets into Y and the mask (the host checks ldy n, ldb n <
+  // 2^32), kept in shared memory (broadcast reads) rather than in 2 l
+  // registers, which leaves room for five CTAs per SM
   const typename Tr::src_t* __restrict__ Yb = static_cast<const typename Tr::src_t*>(d.Y);
   const uint32_t* __restrict__ Bb = d.bits;
-  uint32_t yofs[L], bofs[L];
-#pragma unroll
-  for (int k = 0; k < L; ++k) {
-    const uint32_t c = (uint32_t)__ldg(d.cols + t * L + k);
-    yofs[k] = c * (uint32_t)d.ldy;
-    bofs[k] = c * (uint32_t)d.ldb;
+  if (lane < L) {
+    const uint32_t c = (uint32_t)__ldg(d.cols + t * L + lane);
+    meta[lane] = c * (uint32_t)d.ldy;
+    meta[20 + lane] = c * (uint32_t)d.ldb;
   }
+  __syncwarp();
   const int64_t r0 = (int64_t)slab * d.slab_rows;
   const int64_t r1 = r0 + d.slab_rows < d.m ? r0 + d.slab_rows : d.m;
   const int64_t w_begin = r0 >> 5, w_end = (r1 + 31) >> 5;
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(32 * kSlabWarps, RSM_SLAB_MINB) k_gram_slab(co
     const uint32_t row = (uint32_t)ring[k];
     V v[L];
 #pragma unroll
-    for (int a = 0; a < L; ++a) v[a] = Tr::cvt(__ldg(Yb + (yofs[a] + row)));
+    for (int a = 0; a < L; ++a) v[a] = Tr::cvt(__ldg(Yb + (meta[a] + row)));
 #pragma unroll
     for (int a = 0; a < L; ++a)
 #pragma unroll
@@ -103,7 +106,7 @@ __global__ void __launch_bounds__(32 * kSlabWarps, RSM_SLAB_MINB) k_gram_slab(co
     const uint32_t w = (uint32_t)(w0 + lane);
     const bool in = w < (uint32_t)w_end;
 #pragma unroll
-    for (int k = 0; k < L; ++k) nextw[k] = in ? __ldg(Bb + (bofs[k] + w)) : 0u;
+    for (int k = 0; k < L; ++k) nextw[k] = in ? __ldg(Bb + (meta[20 + k] + w)) : 0u;
   };
   if (w_begin < w_end) load_words(w_begin);
   for (int64_t w0 = w_begin; w0 < w_end; w0 += 32) {
@@ -172,7 +175,7 @@ static size_t slab_smem_bytes() {
   constexpr int P = L * (L + 1) / 2;
   constexpr int kRedWords = (P * 33 * sizeof(A) + 3) / 4;
   constexpr int kWarpWords = kRedWords > kRing ? kRedWords : kRing;
-  return (size_t)kSlabWarps * kWarpWords * 4;
+  return (size_t)kSlabWarps * (kWarpWords + kMeta) * 4;
 }
 
 template <int MODE, int L>

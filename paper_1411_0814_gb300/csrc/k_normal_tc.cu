@@ -38,9 +38,6 @@ constexpr int kThreads = 128;
 constexpr int kMaxStages = 3;  // shared-memory ring: chunk c + 1 is copied in while chunk c is built
 constexpr uint32_t kWaitLimit = 1u << 26;  // polls of one mbarrier wait before giving up
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
 
 // Shared-memory matrix descriptor: start address, leading (K-direction) and
 // stride (M/N-direction) byte offsets, descriptor version 1, no swizzle.
@@ -88,17 +85,6 @@ __device__ __forceinline__ void tc_mma_tf32(uint32_t dtmem, uint64_t adesc, uint
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
-
-// Asynchronous global -> shared copies (no register staging), grouped and waited on per stage.
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_t src_bytes) {  // 0: zero fill
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
