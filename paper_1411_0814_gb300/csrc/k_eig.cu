@@ -49,34 +49,48 @@ __device__ __forceinline__ T* Tof(const ProbDesc& d) {
 }
 
 // ------------------------------------------------------------------ A = M + tau I (padded with I)
+// Four consecutive entries of one padded row per thread; npad is a multiple of
+// 32, so the 1024 entries of a CTA belong to one problem.  Also writes M as
+// FP32 (hi, lo) pairs for the products M X and L^-1 = I on the lower blocks.
 template <typename T>
 __global__ void __launch_bounds__(256) k_eig_prep(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                  int nprob, double shift_rel, int iter0) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= off[nprob]) return;
-  const int p = find_problem(off, nprob, g);
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (g0 >= off[nprob]) return;
+  const int p = find_problem(off, nprob, g0);
   const ProbDesc& d = descs[p];
-  const int64_t e = g - off[p];
-  if (e == 0) {
+  const uint32_t e0 = (uint32_t)(g0 - off[p]);
+  if (e0 == 0) {
     d.stats[kConvFlag] = 0.0;
     d.stats[kPrevRes] = 0.0;
     d.stats[kIterCount] = (double)iter0;  // the unchecked leading steps
   }
-  const int np = npad_of(d);
-  const int64_t i = e / np, j = e % np;
-  const double mean = (double)d.counters[0] * d.n_minor / (double)d.n;
-  const double tau = mean > 0.0 ? shift_rel * mean : 1.0;
-  T v;
-  if (i < d.n && j < d.n) {
-    const double mij = d.M[i * d.n + j];
-    v = (T)(mij + (i == j ? tau : 0.0));
-    const float hi = __double2float_rn(mij);  // M as an FP32 pair for the products M X
-    d.Mdf[i * d.n + j] = make_float2(hi, __double2float_rn(mij - (double)hi));
-  } else {
-    v = (i == j) ? (T)1 : (T)0;
+  const uint32_t np = (uint32_t)npad_of(d), n = (uint32_t)d.n;
+  const uint32_t i = e0 / np, j0 = e0 - i * np;
+  // tau = shift_rel * trace(M) / n, trace(M) = accepted trials * n_minor (a shift: FP32 suffices for the mean)
+  const float meanf = (float)d.counters[0] * (float)d.n_minor / (float)n;
+  const double tau = meanf > 0.f ? shift_rel * (double)meanf : 1.0;
+  T v[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t j = j0 + q;
+    if (i < n && j < n) {
+      const double mij = d.M[i * n + j];
+      v[q] = (T)(i == j ? mij + tau : mij);
+      const float hi = __double2float_rn(mij);
+      d.Mdf[i * n + j] = make_float2(hi, __double2float_rn(mij - (double)hi));
+    } else {
+      v[q] = (i == j) ? (T)1 : (T)0;
+    }
   }
-  F1of<T>(d)[e] = v;
-  if (j / BS <= i / BS) F2of<T>(d)[e] = (i == j) ? (T)1 : (T)0;  // L^-1 starts as I (lower blocks)
+  T* F1 = F1of<T>(d) + e0;
+  T* F2 = F2of<T>(d) + e0;
+  const bool lower = j0 / BS <= i / BS;  // the four entries share a 32-column block
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    F1[q] = v[q];
+    if (lower) F2[q] = (i == j0 + q) ? (T)1 : (T)0;  // L^-1 starts as I (lower blocks)
+  }
 }
 
 // ------------------------------------------------------------------ the 32 x 32 diagonal block
@@ -1372,7 +1386,7 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
   const int a_iters = sizeof(T) == 8 ? 2 : 3, a_passes = sizeof(T) == 8 ? 2 : 1;
   auto* precond_x = k_precond<T, 1>;  // A^-1 X
   auto* precond_r = k_precond<T, 0>;  // A^-1 R
-  RSM_LAUNCH(k_eig_prep<T>, (total(P.pad2) + 255) / 256, 256, D, dev(P.pad2), np, shift_rel, a_iters);
+  RSM_LAUNCH(k_eig_prep<T>, (total(P.pad2) / 4 + 255) / 256, 256, D, dev(P.pad2), np, shift_rel, a_iters);
   // The factor, its inverse and T = A^-1 in one launch (see k_factor).
   static int factor_ctas[2] = {0, 0};
   const int factor_smem = kFactorTiles * BS * (BS + 1) * (int)sizeof(T);
