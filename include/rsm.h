@@ -77,11 +77,16 @@ typedef struct rsm_config {
   uint32_t reserved;
 } rsm_config;
 
-/* Host-side fault injection bits (rsm_config.fault_inject).  They act on the
- * host only: no kernel is ever made to fault, trap or hang. */
-#define RSM_FAULT_ADMISSION 0x1u  /* every admission check reports the budget exhausted */
-#define RSM_FAULT_ALLOC 0x2u      /* the next workspace allocation reports failure */
-#define RSM_FAULT_STALL 0x4u      /* the scheduler withholds work, so waits run out (TIMEOUT) */
+/* Fault injection bits for tests (rsm_config.fault_inject).  No kernel is
+ * ever made to fault, trap or hang: the first three act on the host; the last
+ * gives one bounded device-side wait a condition that nothing meets, so that
+ * the wait runs out exactly as a lost dependency would. */
+#define RSM_FAULT_ADMISSION 0x1u    /* every admission check reports the budget exhausted */
+#define RSM_FAULT_ALLOC 0x2u        /* the next workspace allocation reports failure */
+#define RSM_FAULT_STALL 0x4u        /* the scheduler withholds work, so waits run out (TIMEOUT) */
+#define RSM_FAULT_DEVICE_WAIT 0x8u  /* the eigen stage's factor launch waits (with a short bound) for a
+                                       state word nothing sets: the launch is abandoned and the result
+                                       is RSM_ERR_TIMEOUT; the handle stays usable */
 
 typedef struct rsm_problem {
   int64_t m, n;          /* Y is m x n; the paper assumes m >= n (Section II) */

@@ -26,7 +26,7 @@ RSM_ERR_QUEUE_FULL = 10
 RSM_F64, RSM_F32 = 0, 1
 RSM_PREC_F64, RSM_PREC_F32X2, RSM_PREC_F32 = 0, 1, 2
 RSM_COLS_RANDOM, RSM_COLS_ADJACENT = 0, 1
-RSM_FAULT_ADMISSION, RSM_FAULT_ALLOC, RSM_FAULT_STALL = 0x1, 0x2, 0x4
+RSM_FAULT_ADMISSION, RSM_FAULT_ALLOC, RSM_FAULT_STALL, RSM_FAULT_DEVICE_WAIT = 0x1, 0x2, 0x4, 0x8
 
 
 class rsm_config(C.Structure):

@@ -284,8 +284,11 @@ __device__ __forceinline__ void trail_pair(int k, int t, int u, int& i, int& j) 
 // on chain steps below k: once G + 1 CTAs run, nothing can deadlock and no
 // co-residency is needed.  Waits are bounded all the same: on expiry the
 // launch is abandoned (sync[2] != 0) and counters[6] of every problem raised.
-// sync[0..1] is the claim counter (64-bit); zero before the launch.
+// sync[0..1] is the claim counter (64-bit); sync[3] stays zero (the test
+// injection RSM_FAULT_DEVICE_WAIT waits for it); all zero before the launch.
 constexpr uint32_t kDepPolls = 1u << 24;  // polls (64 ns sleeps) of one dependency wait
+constexpr uint32_t kDepPollsInjected = 1u << 12;  // the same under RSM_FAULT_DEVICE_WAIT (a few ms)
+__shared__ uint32_t s_poll_limit;  // the factor launch's bound, set by each CTA at its start
 constexpr int kFactorTiles = 9;           // shared 32 x 33 tiles per CTA
 
 __device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
@@ -304,8 +307,9 @@ __device__ __forceinline__ bool wait_flag(const unsigned* p, unsigned need, unsi
                                           const ProbDesc* __restrict__ descs, int nprob) {
   if (p == nullptr) return true;
   bool ok = true;
+  const uint32_t limit = s_poll_limit;
   for (uint32_t it = 0; ld_relaxed(p) < need; ++it) {
-    if (it >= kDepPolls || ((it & 15u) == 15u && *(volatile unsigned*)&sync[2] != 0u)) {
+    if (it >= limit || ((it & 15u) == 15u && *(volatile unsigned*)&sync[2] != 0u)) {
       ok = false;
       break;
     }
@@ -344,7 +348,7 @@ __device__ __forceinline__ bool bar_and(int id, int nthreads, bool ok) {
 // Warp 1 waits, so that the release of the previous step by thread 0 can overlap.
 template <typename T>
 __device__ bool chain_load(const ProbDesc& d, int k, Tile<T>* tl, unsigned* sync, const ProbDesc* __restrict__ descs,
-                           int nprob) {
+                           int nprob, bool inject = false) {
   const int np = npad_of(d), nb = d.nblk, tid = threadIdx.x;
   const int tx = tid % BS, ty = tid / BS;
   const unsigned* SA = d.tflag;
@@ -355,6 +359,7 @@ __device__ bool chain_load(const ProbDesc& d, int k, Tile<T>* tl, unsigned* sync
   if (tid == 33 && b1 && k >= 2) wp = &SA[(k + 1) * nb + k], wn = k - 1;
   if (tid == 34 && b1 && k >= 3) wp = &SA[(k + 1) * nb + k - 1], wn = k - 2;
   if (tid == 35 && b1 && k >= 2) wp = &SA[(k + 1) * nb + k - 2], wn = k - 1;
+  if (tid == 36 && inject) wp = &sync[3], wn = 1;  // test injection: a word nothing sets
   if (!wait_tiles(wp, wn, sync, descs, nprob)) return false;
   const T* F = F1of<T>(d);
   const T* Dg = Dinvof<T>(d);
@@ -620,6 +625,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
   for (int q = 0; q < kFactorTiles; ++q) tl[q] = reinterpret_cast<Tile<T>>(factor_smem) + q * BS;
   Tile<T> x = tl[0], y = tl[1], z = tl[2];
   __shared__ unsigned long long s_task;
+  if (threadIdx.x == 0) s_poll_limit = ft.poll_limit;
   const int K = ft.nsteps, lag = ft.lag;
   const int nseg = 5 * K + 3 * lag;
   const int64_t* seg_start = tables + ft.phase;  // task prefix over the segments after the chains
@@ -650,7 +656,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
         }
       };
       if (k >= descs[p].nblk) advance(k, p);
-      if (k < K && !chain_load<T>(descs[p], k, tl, sync, descs, nprob)) return;
+      if (k < K && !chain_load<T>(descs[p], k, tl, sync, descs, nprob, ft.fault_wait != 0 && c == 0)) return;
       while (k < K) {
         if (!chain_step<T>(descs[p], k, tl, sync, descs, nprob)) return;
         advance(k, p);
@@ -1403,7 +1409,8 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
   // one chain per problem while they take at most half the CTAs (so that at
   // least as many CTAs serve the other tasks), else problems share chains
   const int nchain = std::min(np, std::max(1, fc / 2));
-  FactorTables ft{P.step, P.linv, P.tri, P.phase, P.max_nblk, kFactorLag};
+  FactorTables ft{P.step,     P.linv,    P.tri, P.phase, P.max_nblk, kFactorLag,
+                  P.fault_wait ? kDepPollsInjected : kDepPolls, P.fault_wait ? 1 : 0};
   const int64_t ntask = nchain + P.hT[P.phase + 5 * P.max_nblk + 3 * kFactorLag];
   RSM_LAUNCH_SMEM(k_factor<T>, std::min<int64_t>(ntask, fc), 256, factor_smem, D, P.dT, np, ft, P.sync, nchain);
   RSM_LAUNCH(k_init_X, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);

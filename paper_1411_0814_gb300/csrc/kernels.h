@@ -28,6 +28,7 @@ struct EigPlan {
   size_t phase;   // task prefix over the 5 max_nblk + 3 kFactorLag segments of the factor launch
   double* part;   // partial Gram sums of the block iteration
   unsigned* sync; // factor launch: claim counter, abort word, per-phase completion counts (zeroed)
+  bool fault_wait; // test injection: the factor launch's first wait has nothing to wait for
 };
 
 // Table positions read by the factor launch.
@@ -35,6 +36,8 @@ struct FactorTables {
   size_t step, linv, tri, phase;
   int nsteps;  // largest block count of the batch
   int lag;     // steps by which the inverse-factor tasks trail the Cholesky tasks in claim order
+  unsigned poll_limit;  // polls of one dependency wait before the launch is abandoned
+  int fault_wait;       // test injection: the first chain step waits for sync[3], which nothing sets
 };
 constexpr int kFactorLag = 1;
 

@@ -118,6 +118,7 @@ struct Slot {
   DevBuf ws, plan;
   PinBuf host;
   cudaEvent_t ev[10] = {};
+  bool fault_wait = false;  // RSM_FAULT_DEVICE_WAIT for the batches this slot runs
   int init(cudaStream_t external) {
     if (external) {
       stream = external;
@@ -220,6 +221,7 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
   ep.part = reinterpret_cast<double*>(static_cast<unsigned char*>(slot.ws.ptr) + b.part_bytes_off);
   ep.phase = b.o_phase;
   ep.sync = reinterpret_cast<unsigned*>(static_cast<unsigned char*>(slot.ws.ptr) + b.sync_off);
+  ep.fault_wait = slot.fault_wait;
   if ((e = launch_eig(ep, fp64_factor, shift_rel, fp64_factor ? kEigIters64 : kEigIters32, s)) != cudaSuccess)
     return cuda_fail(e, "eig");
   RSM_CUDA(cudaEventRecord(slot.ev[6], s));
@@ -273,6 +275,7 @@ int enqueue_readback(Batch& b, Slot& slot) {
 // Prepare slot buffers, upload the plan, zero the accumulators, launch, read
 // back and fill results.  Synchronises slot.stream.
 int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_result* res) {
+  slot.fault_wait = (h->fault & RSM_FAULT_DEVICE_WAIT) != 0;
   Batch b;
   build_batch(ps, count, b);
   int st = slot.ws.reserve(b.layout.total_bytes);

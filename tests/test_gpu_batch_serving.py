@@ -15,6 +15,8 @@ same as the result of the same request run alone, within the same tolerances.
 Admission, cancellation and wait limits are driven from the host (fault
 injection bits of the handle); no kernel is ever made to fail.
 """
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -149,6 +151,27 @@ def test_serving_admission_cancel_and_wait_limit():
         results = [h.wait(t, timeout_ns=60 * 10 ** 9) for t in tickets]
         assert all(r.status == abi.RSM_OK for r in results)
         assert max(r.queue_ms for r in results) > 0.0
+
+
+def test_device_wait_runs_out_and_handle_recovers():
+    """A dependency wait of the factor launch that nothing satisfies (test
+    injection, bounded): the launch is abandoned, the result is TIMEOUT, no GPU
+    fault; the next decomposition on a clean handle is correct."""
+    p = lowrank_problem(1500, 96, 3, 0.85, 1e-4, trials=600, seed=11)
+    Y, W = to_device(p)
+    with rsm.RSM(0, fault_inject=abi.RSM_FAULT_DEVICE_WAIT) as h:
+        t0 = time.perf_counter()
+        with pytest.raises(rsm.RSMError) as e:
+            h.decompose(rsm.Problem(Y, W, p.r, trials=p.trials, seed=p.seed))
+        assert e.value.status == abi.RSM_ERR_TIMEOUT
+        assert time.perf_counter() - t0 < 30.0
+    torch.cuda.synchronize()
+    a = oracle.decompose(p.Y, p.W, p.r, p.l, p.trials, p.seed)
+    with rsm.RSM(0) as h:
+        prob = rsm.Problem(Y, W, p.r, trials=p.trials, seed=p.seed)
+        res = h.decompose(prob)
+        assert res.status == abi.RSM_OK
+        assert oracle.subspace_angle(_np(res.V), a.V) <= 1e-10
 
 
 def test_fp32_normal_equations_match_oracle():
