@@ -763,7 +763,7 @@ __global__ void __launch_bounds__(256) k_init_X(const ProbDesc* __restrict__ des
 }
 
 constexpr int kSplit = 32;   // split of the inner dimension of the product M X (R slots)
-constexpr int kPSplit = 4;   // split of the inner dimension of the preconditioner product
+constexpr int kPSplit = 16;  // split of the inner dimension of the preconditioner product (R slots 1..16)
 constexpr int kMxRows = 128;  // rows per CTA of M X (one per thread)
 constexpr int kMxSub = 64;    // columns of X staged per pass
 
@@ -1170,7 +1170,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_rr64(const ProbDesc* __restri
 // thread (row, column) computes one entry of each product from rows staged in
 // shared memory.
 constexpr int kRotRows = 8;
-constexpr int kResSlot = 7;  // R slot of the per-tile residual sums of squares (slots 1..kPSplit: preconditioner parts)
+constexpr int kResSlot = 31;  // R slot of the per-tile residual sums of squares (slots 1..kPSplit: preconditioner parts)
+static_assert(kResSlot > kPSplit && kResSlot < kSplit, "R slots of the residual sums and the preconditioner parts");
 template <bool FULL>
 __global__ void __launch_bounds__(256) k_rotate(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                int nprob) {
@@ -1237,7 +1238,7 @@ __global__ void __launch_bounds__(256) k_rotate(const ProbDesc* __restrict__ des
 // Split over the inner dimension: CTA (row tile of 16, part s) writes its
 // partial product to R slot 1 + s; k_precond_apply sums the parts in a fixed order.
 constexpr int kPRows = 16;
-template <typename T, int SRC>
+template <typename T, int SRC, bool WIDE>  // WIDE: kx > 16 (a second output column per thread)
 __global__ void __launch_bounds__(256) k_precond(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                 int nprob) {
   __shared__ T ts[kPRows][65];
@@ -1273,14 +1274,14 @@ __global__ void __launch_bounds__(256) k_precond(const ProbDesc* __restrict__ de
     for (int u = 0; u < 64; ++u) {
       const T tv = ts[tr][u];
       acc[0] = fma(tv, rs[u][tc], acc[0]);
-      acc[1] = fma(tv, rs[u][tc + 16 < kx ? tc + 16 : tc], acc[1]);
+      if (WIDE) acc[1] = fma(tv, rs[u][tc + 16 < kx ? tc + 16 : tc], acc[1]);
     }
   }
   const int i = i0 + tr;
   double* part = d.R + (1 + split) * n * kx;
   if (i < n) {
     if (tc < kx) part[i * kx + tc] = (double)acc[0];
-    if (tc + 16 < kx) part[i * kx + tc + 16] = (double)acc[1];
+    if (WIDE && tc + 16 < kx) part[i * kx + tc + 16] = (double)acc[1];
   }
 }
 
@@ -1390,8 +1391,9 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
   // orthonormalised twice (shifted CholeskyQR2); three single-pass steps with
   // the FP32 factor.
   const int a_iters = sizeof(T) == 8 ? 2 : 3, a_passes = sizeof(T) == 8 ? 2 : 1;
-  auto* precond_x = k_precond<T, 1>;  // A^-1 X
-  auto* precond_r = k_precond<T, 0>;  // A^-1 R
+  const bool wide = P.kx_max > 16;
+  auto* precond_x = wide ? k_precond<T, 1, true> : k_precond<T, 1, false>;  // A^-1 X
+  auto* precond_r = wide ? k_precond<T, 0, true> : k_precond<T, 0, false>;  // A^-1 R
   RSM_LAUNCH(k_eig_prep<T>, (total(P.pad2) / 4 + 255) / 256, 256, D, dev(P.pad2), np, shift_rel, a_iters);
   // The factor, its inverse and T = A^-1 in one launch (see k_factor).
   static int factor_ctas[2] = {0, 0};
@@ -1435,7 +1437,9 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
   for (int it = 0; it <= iters; ++it) {
     if (sizeof(T) == 8 && it > 0)
       if ((e = orthonormalise()) != cudaSuccess) return e;
-    if (P.kx_max <= 16)
+    if (P.kx_max <= 12)
+      RSM_LAUNCH(k_gemm_MX<12>, total(P.mx), kMxRows, D, dev(P.mx), np);
+    else if (P.kx_max <= 16)
       RSM_LAUNCH(k_gemm_MX<16>, total(P.mx), kMxRows, D, dev(P.mx), np);
     else
       RSM_LAUNCH(k_gemm_MX<32>, total(P.mx), kMxRows, D, dev(P.mx), np);

@@ -11,7 +11,7 @@ namespace rsm {
 
 namespace {
 constexpr int kEigSplit = 32;  // must equal kSplit in k_eig.cu
-constexpr int kPrecSplit = 4;  // must equal kPSplit in k_eig.cu
+constexpr int kPrecSplit = 16;  // must equal kPSplit in k_eig.cu
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
