@@ -241,3 +241,58 @@ def test_deterministic_rerun(handle):
     assert np.array_equal(_np(r1.M), _np(r2.M))
     assert np.array_equal(_np(r1.V), _np(r2.V))
     assert np.array_equal(_np(r1.U), _np(r2.U))
+
+
+def test_paper_scale_sampled_parity(handle):
+    """The bench workload at full size (m = 131072, n = 1024, r = 8, 20000
+    submatrices) in the form bench.py times (FP32 Y, Gram and normal equations):
+    outputs the oracle can compute one by one are compared one by one, the rest
+    through properties that hold at any size."""
+    p = config_problem("paper_131072x1024")
+    Y32 = np.asfortranarray(p.Y.astype(np.float32).astype(np.float64))  # the values the device sees
+    res = _run(handle, p, gram="f32", solve="f32", dtype=torch.float32)
+    assert res.status == oracle.STATUS_OK
+    nm = p.l - p.r
+    # a2: every column set, bit-exact
+    cols = oracle.sample_columns(p.n, p.l, p.trials, p.seed)
+    assert np.array_equal(_np(res.cols), cols)
+    counts = _np(res.row_counts)
+    assert res.accepted_trials == int(np.sum(counts >= p.l))
+    rng = np.random.default_rng(1234)
+    sample = np.sort(rng.choice(p.trials, 48, replace=False))
+    Zg = _np(res.Z)
+    worst = 0.0
+    for t in sample:
+        # a3: the selected rows, counted exactly
+        R = oracle.select_rows(p.W, cols[t])
+        assert counts[t] == R.size
+        # a4-a5: the minor subspace of this submatrix within the FP32 Gram's rounding bound
+        A = Y32[np.ix_(R, cols[t])]
+        dist = projector_distance(Zg[t], oracle.minor_vectors(A, nm))
+        bound = minor_bound(A, nm, 2.0 ** -24)
+        worst = max(worst, dist / bound)
+        assert dist <= bound, (t, dist, bound)
+    # a6: M is exactly symmetric (fixed-point sums), has trace n_minor * accepted
+    # (each Z Z^T has trace n_minor) and no negative eigenvalue beyond rounding
+    Mg = _np(res.M)
+    assert np.array_equal(Mg, Mg.T)
+    assert abs(np.trace(Mg) - nm * res.accepted_trials) <= 1e-9 * nm * res.accepted_trials
+    ev, Q = np.linalg.eigh(Mg)
+    assert ev[0] >= -1e-9 * ev[-1]
+    # a7: V-hat spans the r smallest eigenvectors of that M (a library eigensolver on
+    # the same M), within the FP64 rounding floor of the eigen-gap
+    Vg = _np(res.V)
+    assert np.allclose(Vg.T @ Vg, np.eye(p.r), atol=1e-12)
+    floor = 100 * 2.2e-16 * ev[-1] / (ev[p.r] - ev[p.r - 1])
+    ang = oracle.subspace_angle(Vg, Q[:, :p.r])
+    print(f"paper scale: angle={ang:.3e} floor={floor:.3e} worst_minor_ratio={worst:.3e}")
+    assert ang <= max(1e-10, floor)
+    # a8: sampled rows of U-hat against least squares on the same V-hat (FP32 normal equations)
+    Ug = _np(res.U)
+    for i in np.sort(rng.choice(p.m, 256, replace=False)):
+        K = np.flatnonzero(p.W[i])
+        u = np.linalg.lstsq(Vg[K], Y32[i, K], rcond=None)[0]
+        assert np.linalg.norm(Ug[i] - u) <= 1e-5 * np.linalg.norm(u) + 1e-12, i
+    # a9: e from the device against the definition evaluated on its own U-hat, V-hat
+    e = oracle.residual(Y32, p.W, Ug, Vg)
+    assert abs(res.e - e) <= 1e-5 * e
