@@ -5,19 +5,24 @@
 // Method (preconditioned inverse iteration with Rayleigh-Ritz, PINVIT):
 //   * A = M + tau I with a small shift tau = c * trace(M) / n is factored
 //     A = L L^T (blocked right-looking Cholesky, 32 x 32 blocks), then
-//     T = A^-1 = L^-T L^-1 is formed.  T is only a preconditioner.  The fast
-//     form factors in FP32 with c = 1e-3 (enough when lambda_{r+1} >> tau);
-//     the robust form factors in FP64 with c = 1e-11, which makes the step an
-//     exact shift-invert iteration and resolves clustered small eigenvalues.
-//   * A block X of kx >= r + 1 vectors is iterated in FP64:
+//     T = A^-1 = L^-T L^-1 is formed, all in one dataflow launch (k_factor).
+//     T is only a preconditioner.  The fast form factors in FP32 with
+//     c = 3e-4 (enough when lambda_{r+1} >> tau); the robust form factors in
+//     FP64 with c = 1e-11, which makes the step an exact shift-invert
+//     iteration and resolves clustered small eigenvalues.
+//   * Phase A: X <- orth(T X) a few times (subspace iteration, no product
+//     with M).
+//   * Phase B: a block X of kx >= r + 1 vectors is iterated:
 //       Rayleigh-Ritz on span(X):  S = X^T X, H = X^T M X, S = C C^T,
 //         eig(C^-1 H C^-T) = Q' diag(theta), X <- X C^-T Q'  (orthonormal Ritz basis)
 //       residual R = M X - X diag(theta)
 //       X <- X - T R
 //     Components of X along an eigenvector with eigenvalue lambda shrink by
 //     about (tau + theta) / (lambda + tau) per step, so the r smallest Ritz
-//     pairs converge quickly when lambda_{r+1} >> tau.  M X and all reductions
-//     are FP64, so the limiting accuracy is that of FP64 arithmetic on M.
+//     pairs converge quickly when lambda_{r+1} >> tau.  M X runs in FP32-pair
+//     arithmetic (about 2^-44 relative) and the reductions and the
+//     Rayleigh-Ritz step in FP64, so the limiting accuracy is close to that of
+//     FP64 arithmetic on M.
 // Every kernel is batched over the problems of the launch.
 #include "common.cuh"
 #include "jacobi.cuh"
@@ -1411,8 +1416,8 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
   // one chain per problem while they take at most half the CTAs (so that at
   // least as many CTAs serve the other tasks), else problems share chains
   const int nchain = std::min(np, std::max(1, fc / 2));
-  FactorTables ft{P.step,     P.linv,    P.tri, P.phase, P.max_nblk, kFactorLag,
-                  P.fault_wait ? kDepPollsInjected : kDepPolls, P.fault_wait ? 1 : 0};
+  FactorTables ft{P.step, P.linv, P.phase, P.max_nblk, kFactorLag, P.fault_wait ? kDepPollsInjected : kDepPolls,
+                  P.fault_wait ? 1 : 0};
   const int64_t ntask = nchain + P.hT[P.phase + 5 * P.max_nblk + 3 * kFactorLag];
   RSM_LAUNCH_SMEM(k_factor<T>, std::min<int64_t>(ntask, fc), 256, factor_smem, D, P.dT, np, ft, P.sync, nchain);
   RSM_LAUNCH(k_init_X, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);

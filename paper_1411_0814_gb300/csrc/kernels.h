@@ -24,7 +24,7 @@ struct EigPlan {
   int kx_max;  // largest block width of the batch
   const int64_t* dT;
   const int64_t* hT;
-  size_t pad2, step, blk, linv, tri, nk, mx, chunk, part_off, rot, row_tile;  // table positions (linv: 2 per step)
+  size_t pad2, step, linv, nk, mx, chunk, part_off, rot, row_tile;  // table positions (step: 2 per step, linv: 3 per step)
   size_t phase;   // task prefix over the 5 max_nblk + 3 kFactorLag segments of the factor launch
   double* part;   // partial Gram sums of the block iteration
   unsigned* sync; // factor launch: claim counter, abort word, per-phase completion counts (zeroed)
@@ -33,7 +33,7 @@ struct EigPlan {
 
 // Table positions read by the factor launch.
 struct FactorTables {
-  size_t step, linv, tri, phase;
+  size_t step, linv, phase;
   int nsteps;  // largest block count of the batch
   int lag;     // steps by which the inverse-factor tasks trail the Cholesky tasks in claim order
   unsigned poll_limit;  // polls of one dependency wait before the launch is abandoned

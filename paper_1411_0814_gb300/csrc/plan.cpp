@@ -187,14 +187,12 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
       return t * (t + 1) / 2;
     });
   }
-  b.o_blk = prefix([&](int i) { return (int64_t)b.dv[i].nblk; });
   b.o_linv = T.size();
   for (int k = 0; k < b.max_nblk; ++k) {  // per step: row k of L^-1, updates of the rows >= k + 2, row k's share of T
     prefix([&](int i) { return (int64_t)(k < b.dv[i].nblk ? k + 1 : 0); });
     prefix([&](int i) { return (int64_t)std::max(0, b.dv[i].nblk - k - 2) * (k + 1); });
     prefix([&](int i) { return (int64_t)(k < b.dv[i].nblk ? (int64_t)(k + 1) * (k + 2) / 2 : 0); });
   }
-  b.o_tri = prefix([&](int i) { return (int64_t)b.dv[i].nblk * (b.dv[i].nblk + 1) / 2; });
   // Task prefix over the segments of the factor launch's claim order (after
   // its chain tasks): per step k the panel and the trailing update, then the
   // inverse-factor tasks and the rows of T of step k - kFactorLag; then those

@@ -43,7 +43,7 @@ struct Batch {
   std::vector<ProbDesc> descs;  // host copies (device pointers filled by bind())
   std::vector<int64_t> tables;  // all int64 offset tables, concatenated
   // positions (in int64 elements) of each table inside `tables`
-  size_t o_pack = 0, o_trial = 0, o_ent = 0, o_pad2 = 0, o_step = 0, o_blk = 0, o_linv = 0, o_tri = 0, o_nk = 0,
+  size_t o_pack = 0, o_trial = 0, o_ent = 0, o_pad2 = 0, o_step = 0, o_linv = 0, o_nk = 0,
          o_mx = 0, o_chunk = 0, o_part = 0, o_rot = 0, o_rowtile = 0, o_k = 0, o_tile = 0, o_row = 0, o_res = 0,
          o_b = 0, o_tc = 0, o_res4 = 0, o_phase = 0;
   int64_t pack_blocks = 0, trials_total = 0, ent_total = 0, pad2_total = 0, nk_total = 0, part_total = 0,

@@ -209,9 +209,7 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
   ep.hT = b.tables.data();
   ep.pad2 = b.o_pad2;
   ep.step = b.o_step;
-  ep.blk = b.o_blk;
   ep.linv = b.o_linv;
-  ep.tri = b.o_tri;
   ep.nk = b.o_nk;
   ep.mx = b.o_mx;
   ep.chunk = b.o_chunk;
