@@ -30,6 +30,10 @@ Readings of points the paper leaves open (each applied below):
   * U-hat: per row, least squares over the known entries (eq. solve.barU with
     the L2 norm); a row with fewer than r known entries gets the minimum-norm
     solution and is counted.
+  * method M2 (decompose_rows): k rows drawn like the columns of M1; the
+    columns known in all of them; a trial is used iff more than r columns
+    remain; its vectors are all c - r right singular vectors beyond the r
+    largest (the c - k exact null vectors and the k - r small ones).
 """
 from __future__ import annotations
 
@@ -229,6 +233,86 @@ def decompose(Y: np.ndarray, W: np.ndarray, r: int, l: Optional[int] = None, tri
             status = STATUS_ROWS_UNDERDETERMINED
     return OracleResult(status=status, cols=cols, row_counts=row_counts, accepted=accepted, M=M,
                         evals=evals, V=V, U=U, e=e, rows_underdetermined=under, Z=Z_list)
+
+
+# ----------------------------------------------------------------- method M2 (row variant)
+
+def sample_rows(m: int, k: int, trials: int, seed: int, problem_id: int = 0) -> np.ndarray:
+    """Row sets R_t for method M2 (Section III, M2: "first randomly choose k
+    rows"): k distinct rows of [0, m) by the same Philox words and Floyd
+    mapping as the column sets of M1, sorted ascending."""
+    return sample_columns(m, k, trials, seed, problem_id, "random")
+
+
+def select_cols(W: np.ndarray, rows) -> np.ndarray:
+    """C_t for M2: the columns known in every chosen row, ascending ("then select
+    columns accordingly"; the submatrix is k x n rho^k statistically)."""
+    return np.flatnonzero(np.all(W[np.asarray(rows), :] != 0, axis=0))
+
+
+def null_vectors_rows(A: np.ndarray, r: int) -> np.ndarray:
+    """Right singular vectors of the k x c submatrix A beyond its r largest
+    singular values: the c - k exact null vectors plus the k - r of small
+    singular values (Section III: the vectors "corresponding to the null or
+    small singular values"), as the columns of a c x (c - r) matrix."""
+    _, _, Vt = np.linalg.svd(A, full_matrices=True)
+    return Vt[r:].T.copy()
+
+
+def decompose_rows(Y: np.ndarray, W: np.ndarray, r: int, k: Optional[int] = None, trials: int = 1000,
+                   seed: int = 0, problem_id: int = 0, solve_u: bool = True) -> OracleResult:
+    """The three steps of Section IV-A with M2 and the L2 norm.
+
+    Step 1: k (default r + 1) rows per trial and I = ``trials`` are given.
+    Step 2: for t = 0..I-1 draw R_t, keep the columns known in all of R_t, and,
+            if more than r columns remain (so that at least one vector beyond the
+            r largest singular values exists), take those c_t - r right singular
+            vectors.
+    Step 3: as for M1: V-hat, U-hat, e.
+    In the result, ``cols`` holds the row sets R_t and ``row_counts`` the column
+    counts c_t; ``Z[t]`` is c_t x (c_t - r) over the columns ``C[t]``.
+    """
+    m, n = Y.shape
+    k = r + 1 if k is None else k
+    if not (1 <= r < k <= m) or not (r < n <= m):
+        raise ValueError("need 1 <= r < k <= m and r < n <= m")
+    rows = sample_rows(m, k, trials, seed, problem_id)
+    col_counts = np.zeros(trials, dtype=np.int64)
+    accepted = np.zeros(trials, dtype=bool)
+    C_list, Z_list = [], []
+    for t in range(trials):
+        C = select_cols(W, rows[t])
+        col_counts[t] = C.size
+        C_list.append(C)
+        if C.size <= r:
+            Z_list.append(None)
+            continue
+        accepted[t] = True
+        A = np.asarray(Y[np.ix_(rows[t], C)], dtype=np.float64)
+        Z_list.append(null_vectors_rows(A, r))
+    M = np.zeros((n, n))
+    for t, Z in enumerate(Z_list):  # trials in ascending t, as for M1
+        if Z is None:
+            continue
+        C = C_list[t]
+        for j in range(Z.shape[1]):
+            z = Z[:, j]
+            M[np.ix_(C, C)] += np.outer(z, z)
+    V, evals = eig_smallest(M, r)
+    trace = max(float(np.trace(M)), 0.0)
+    status = STATUS_OK
+    if accepted.sum() == 0 or evals[r] <= RANK_TOL * trace:
+        status = STATUS_UNDERDETERMINED
+    U, under, e = None, 0, float("nan")
+    if solve_u and status == STATUS_OK:
+        U, under = solve_U(Y, W, V)
+        e = residual(Y, W, U, V)
+        if under:
+            status = STATUS_ROWS_UNDERDETERMINED
+    res = OracleResult(status=status, cols=rows, row_counts=col_counts, accepted=accepted, M=M,
+                       evals=evals, V=V, U=U, e=e, rows_underdetermined=under, Z=Z_list)
+    res.C = C_list
+    return res
 
 
 def subspace_angle(A: np.ndarray, B: np.ndarray) -> float:

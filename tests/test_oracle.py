@@ -385,3 +385,87 @@ def test_mutation_misaligned_solve_is_caught(monkeypatch):
     Ybar = p.U_bar @ p.V_bar.T
     known = p.W != 0
     assert np.linalg.norm((res.U @ res.V.T - Ybar)[known]) > 1e-3 * np.linalg.norm(Ybar[known])
+
+
+# ----------------------------------------------------------------- method M2 (row variant)
+
+def test_m2_row_sets_distinct_sorted_and_drawn_like_columns():
+    rows = oracle.sample_rows(5000, 9, 300, seed=7, problem_id=2)
+    assert rows.shape == (300, 9)
+    assert np.all(np.diff(rows, axis=1) > 0) and rows.min() >= 0 and rows.max() < 5000
+    # the same Philox words and Floyd mapping as the column sets of M1
+    assert np.array_equal(rows, oracle.sample_columns(5000, 9, 300, seed=7, problem_id=2))
+
+
+def test_m2_select_cols_brute_force():
+    rng = np.random.default_rng(11)
+    W = (rng.random((40, 30)) < 0.7).astype(np.uint8)
+    for rows in ([0, 5, 9], [3], [1, 2, 3, 4, 5, 6, 7], list(range(40))):
+        want = [j for j in range(30) if all(W[i, j] for i in rows)]
+        assert list(oracle.select_cols(W, rows)) == want
+
+
+def _noiseless_m2(seed, m=300, n=40, r=3, rho=0.9):
+    p = lowrank_problem(m, n, r, rho, 0.0, trials=80, seed=seed)
+    return p
+
+
+def test_m2_null_vectors_annihilated_by_ground_truth():
+    # noiseless: every kept vector lies in the null space of V_bar[C]^T (Section III)
+    p = _noiseless_m2(3)
+    res = oracle.decompose_rows(p.Y, p.W, p.r, trials=80, seed=3, solve_u=False)
+    checked = 0
+    for t in np.flatnonzero(res.accepted):
+        Z, C = res.Z[t], res.C[t]
+        assert Z.shape == (C.size, C.size - p.r)
+        assert np.allclose(Z.T @ Z, np.eye(Z.shape[1]), atol=1e-12)
+        assert np.linalg.norm(p.V_bar[C].T @ Z) <= 1e-12 * np.sqrt(C.size)
+        checked += 1
+    assert checked > 60
+
+
+def test_m2_trace_symmetry_and_exact_recovery():
+    p = _noiseless_m2(4)
+    res = oracle.decompose_rows(p.Y, p.W, p.r, trials=80, seed=4)
+    assert res.status == oracle.STATUS_OK
+    # each Z Z^T has trace c_t - r
+    want = sum(int(c) - p.r for c, a in zip(res.row_counts, res.accepted) if a)
+    assert abs(np.trace(res.M) - want) <= 1e-10 * want
+    assert np.allclose(res.M, res.M.T, atol=0)
+    assert np.linalg.eigvalsh(res.M)[0] >= -1e-10
+    assert np.linalg.norm(res.M @ p.V_bar) <= 1e-10 * np.linalg.norm(res.M)
+    assert oracle.subspace_angle(res.V, p.V_bar) <= 1e-10
+
+
+def test_m2_all_rows_single_trial_is_truncated_svd():
+    # rho = 1, k = m, I = 1: the only submatrix is Y itself, M = I - V_r V_r^T,
+    # so V-hat is the top-r right singular subspace even with noise
+    rng = np.random.default_rng(8)
+    m, n, r = 30, 12, 3
+    Y = rng.standard_normal((m, r)) @ rng.standard_normal((r, n)) + 0.3 * rng.standard_normal((m, n))
+    W = np.ones((m, n), dtype=np.uint8)
+    res = oracle.decompose_rows(np.asfortranarray(Y), np.asfortranarray(W), r, k=m, trials=1, seed=0)
+    _, s, Vt = np.linalg.svd(Y)
+    assert oracle.subspace_angle(res.V, Vt[:r].T) <= 1e-12
+    assert np.allclose(res.M, np.eye(n) - Vt[:r].T @ Vt[:r], atol=1e-12)
+    assert np.allclose(res.U, Y @ res.V, atol=1e-12)
+
+
+def test_m2_rejects_trials_with_too_few_columns():
+    p = lowrank_problem(200, 30, 4, 0.5, 0.0, trials=40, seed=9)
+    res = oracle.decompose_rows(p.Y, p.W, p.r, k=8, trials=40, seed=9, solve_u=False)
+    # 30 * 0.5^8 ~ 0.1 columns expected: nearly every trial keeps <= r columns
+    assert np.all(res.accepted == (res.row_counts > p.r))
+    assert res.accepted_trials < 5
+
+
+def test_mutation_m2_one_vector_too_many_is_caught(monkeypatch):
+    # taking the r-th singular vector too (c - r + 1 vectors) breaks the dense case
+    monkeypatch.setattr(orsm, "null_vectors_rows",
+                        lambda A, r: np.linalg.svd(A, full_matrices=True)[2][r - 1:].T.copy())
+    rng = np.random.default_rng(8)
+    m, n, r = 30, 12, 3
+    Y = rng.standard_normal((m, r)) @ rng.standard_normal((r, n)) + 0.3 * rng.standard_normal((m, n))
+    res = orsm.decompose_rows(np.asfortranarray(Y), np.ones((m, n), dtype=np.uint8), r, k=m, trials=1, seed=0)
+    _, _, Vt = np.linalg.svd(Y)
+    assert oracle.subspace_angle(res.V, Vt[:r].T) > 0.1
