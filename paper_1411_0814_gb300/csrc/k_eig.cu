@@ -24,6 +24,8 @@
 //     Rayleigh-Ritz step in FP64, so the limiting accuracy is close to that of
 //     FP64 arithmetic on M.
 // Every kernel is batched over the problems of the launch.
+#include <atomic>
+
 #include "common.cuh"
 #include "jacobi.cuh"
 #include "kernels.h"
@@ -292,6 +294,7 @@ __device__ __forceinline__ void trail_pair(int k, int t, int u, int& i, int& j) 
 // sync[0..1] is the claim counter (64-bit); sync[3] stays zero (the test
 // injection RSM_FAULT_DEVICE_WAIT waits for it); all zero before the launch.
 constexpr uint32_t kDepPolls = 1u << 24;  // polls (64 ns sleeps) of one dependency wait
+constexpr int kMaxDevices = 64;           // devices whose factor-launch width is cached
 constexpr uint32_t kDepPollsInjected = 1u << 12;  // the same under RSM_FAULT_DEVICE_WAIT (a few ms)
 __shared__ uint32_t s_poll_limit;  // the factor launch's bound, set by each CTA at its start
 constexpr int kFactorTiles = 9;           // shared 32 x 33 tiles per CTA
@@ -1400,18 +1403,24 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
   auto* precond_x = wide ? k_precond<T, 1, true> : k_precond<T, 1, false>;  // A^-1 X
   auto* precond_r = wide ? k_precond<T, 0, true> : k_precond<T, 0, false>;  // A^-1 R
   RSM_LAUNCH(k_eig_prep<T>, (total(P.pad2) / 4 + 255) / 256, 256, D, dev(P.pad2), np, shift_rel, a_iters);
-  // The factor, its inverse and T = A^-1 in one launch (see k_factor).
-  static int factor_ctas[2] = {0, 0};
+  // The factor, its inverse and T = A^-1 in one launch (see k_factor).  The
+  // attribute is set on every call (it is per device); the CTA count of a full
+  // wave is cached per device (worker threads may race to fill it with the same value).
   const int factor_smem = kFactorTiles * BS * (BS + 1) * (int)sizeof(T);
-  int& fc = factor_ctas[sizeof(T) == 8];
+  int dev_id = 0;
+  cudaError_t eo = cudaFuncSetAttribute(k_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, factor_smem);
+  if (eo == cudaSuccess) eo = cudaGetDevice(&dev_id);
+  if (eo != cudaSuccess) return eo;
+  static std::atomic<int> factor_ctas[2][kMaxDevices];
+  const int slot_id = dev_id < kMaxDevices ? dev_id : kMaxDevices - 1;
+  int fc = factor_ctas[sizeof(T) == 8][slot_id].load(std::memory_order_relaxed);
   if (fc == 0) {
-    int dev_id = 0, sms = 0, per_sm = 0;
-    cudaError_t eo = cudaFuncSetAttribute(k_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, factor_smem);
-    if (eo == cudaSuccess) eo = cudaGetDevice(&dev_id);
-    if (eo == cudaSuccess) eo = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
+    int sms = 0, per_sm = 0;
+    eo = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
     if (eo == cudaSuccess) eo = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor<T>, 256, factor_smem);
     if (eo != cudaSuccess) return eo;
     fc = std::max(2, sms * per_sm);
+    factor_ctas[sizeof(T) == 8][slot_id].store(fc, std::memory_order_relaxed);
   }
   // one chain per problem while they take at most half the CTAs (so that at
   // least as many CTAs serve the other tasks), else problems share chains
