@@ -469,3 +469,26 @@ def test_mutation_m2_one_vector_too_many_is_caught(monkeypatch):
     res = orsm.decompose_rows(np.asfortranarray(Y), np.ones((m, n), dtype=np.uint8), r, k=m, trials=1, seed=0)
     _, _, Vt = np.linalg.svd(Y)
     assert oracle.subspace_angle(res.V, Vt[:r].T) > 0.1
+
+
+def test_m2_mean_columns_kept_is_binomial():
+    # E[c_t] = n rho^k for an iid Bernoulli mask (Section III, M2: statistical size k x n rho^k)
+    p = lowrank_problem(500, 20000, 2, 0.7, 0.0, trials=300, seed=12)
+    rows = oracle.sample_rows(p.m, 4, p.trials, p.seed)
+    counts = np.array([oracle.select_cols(p.W, r).size for r in rows])
+    mean = p.n * 0.7 ** 4
+    sd = math.sqrt(p.n * 0.7 ** 4 * (1 - 0.7 ** 4)) / math.sqrt(p.trials)
+    assert abs(counts.mean() - mean) < 5 * sd + 0.01 * mean
+
+
+def test_m2_scale_and_column_permutation():
+    # scaling Y leaves V-hat unchanged; permuting the columns of Y and W permutes
+    # the rows of V-hat (the row sets do not depend on the columns)
+    p = lowrank_problem(300, 40, 3, 0.9, 1e-2, trials=80, seed=13)
+    base = oracle.decompose_rows(p.Y, p.W, p.r, trials=80, seed=13, solve_u=False)
+    scaled = oracle.decompose_rows(np.asfortranarray(3.25 * p.Y), p.W, p.r, trials=80, seed=13, solve_u=False)
+    perm = np.random.default_rng(1).permutation(p.n)
+    permuted = oracle.decompose_rows(np.asfortranarray(p.Y[:, perm]), np.asfortranarray(p.W[:, perm]), p.r,
+                                     trials=80, seed=13, solve_u=False)
+    assert oracle.subspace_angle(base.V, scaled.V) < 1e-10
+    assert oracle.subspace_angle(base.V[perm], permuted.V) < 1e-10
