@@ -6,10 +6,13 @@ One step = one full decomposition of the paper-scale synthetic workload
 mask packing, column sampling, row selection + Gram, minor vectors, M, the
 eigensolve of M, the per-row solves for U and the error e, all in librsm.so.
 
-Headline form: Y in FP32, FP32 Gram and normal equations, FP64 minor vectors,
-M, eigensolve and r x r solves; its V is checked against the plain FP64 form
-(itself parity-tested against the FP64 oracle) at <= 1e-6 subspace angle.
-The plain FP64 form is timed beside it.
+Headline form: Y in FP32, FP32 Gram and FP32 accumulation of the normal
+equations (tensor cores); FP64 minor vectors, M, eigensolve (FP32-pair
+iteration ended by FP64 refinement passes) and r x r solves.  Its V-hat is
+compared with the FP64 oracle's V-hat for this workload (stored by
+tests/golden/make_oracle_goldens.py, which calls only the oracle): the
+subspace angle must be <= 1e-6.  The plain FP64 form is timed beside it and
+held to 1e-10.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 instead (bounded samples of the same workload, single core).
@@ -34,6 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "decomps/s & submatrices/s at ≤1e-6 subspace angle vs FP64 oracle; p50/p99 lat"
 WORKLOAD = "paper_131072x1024"
 STAGES = ["setup", "pack_mask", "sample_cols", "select_gram", "minor_scatter", "eig_M", "solve_U", "residual", "total"]
+WORKLOADS = ["paper_131072x1024", "noiseless_2048x128", "trajectory_4096x144", "batched256", "serving", "fig1_sweep"]
 
 
 def parse_args():
@@ -42,6 +46,11 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
+    ap.add_argument("--workload", choices=WORKLOADS, default=WORKLOAD,
+                    help="paper_131072x1024 (default, the headline); the others are measured on demand")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving: length of the arrival stream")
+    ap.add_argument("--batched-gram", choices=["f32", "f32x2"], default="f32x2",
+                    help="batched256 / serving: the per-trial Gram form of the mixed batched form")
     ap.add_argument("--fp64-steps", type=int, default=0, help="timed steps of the FP64 form (default max(3, steps/4))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -223,6 +232,23 @@ def replica_throughput(ws: int, steps: int, max_ms: float) -> float:
     return ws * steps / (max_ms / 1e3)
 
 
+def oracle_golden(p):
+    """The FP64 oracle's V-hat of this workload (tests/golden), or None if absent or for another workload."""
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_{WORKLOAD}.npz")
+    if not os.path.exists(path):
+        return None
+    g = np.load(path)
+    if (int(g["m"]), int(g["n"]), int(g["r"]), int(g["trials"]), int(g["seed"])) != (p.m, p.n, p.r, p.trials, p.seed):
+        return None
+    return {k: g[k] for k in g.files}
+
+
+def subspace_angle_np(a, b) -> float:
+    qa, _ = np.linalg.qr(a)
+    qb, _ = np.linalg.qr(b)
+    return float(math.asin(min(1.0, np.linalg.norm(qb - qa @ (qa.T @ qb), ord=2))))
+
+
 def subspace_sin(A, B) -> float:
     """sin of the largest principal angle between the column spans of A and B (orthonormal columns).
 
@@ -296,6 +322,11 @@ def bench_mine(args):
     total64, per64, res64 = timed(fp64, k64, 1)
     assert res64[-1].status == 0
     angle = math.asin(min(1.0, subspace_sin(fp64.V, mixed.V)))
+    gold = oracle_golden(p)
+    angle_oracle = angle_oracle64 = None
+    if gold is not None:
+        angle_oracle = subspace_angle_np(mixed.V.detach().cpu().numpy(), gold["V"])
+        angle_oracle64 = subspace_angle_np(fp64.V.detach().cpu().numpy(), gold["V"])
 
     # end to end through the public API: host (pinned) -> device, decompose, device -> host.
     # Every step copies its own inputs in and its results out inside the timed
@@ -399,16 +430,22 @@ def bench_mine(args):
         "dtype": "fp32+fp64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "m": p.m, "n": p.n, "r": p.r, "rho": p.rho, "sigma": p.sigma, "l": p.l,
-                   "trials": p.trials, "form": "Y, Gram and normal equations FP32; minor vectors, M, eigensolve "
-                                                 "and r x r solves FP64",
+                   "trials": p.trials,
+                   "form": "Y FP32; per-trial Gram FP32; normal equations N_i, b_i accumulated in FP32 (tensor "
+                           "cores, TF32 head + tail); minor vectors FP64 (FP32 Jacobi + FP64 Newton); M FP64 "
+                           "(fixed-point sums); eigensolve of M FP32-pair block iteration + FP64 refinement "
+                           "(FP64 residual reported); r x r Cholesky solves FP64",
                    "l2": "inputs larger than L2 (Y fp32 537 MB, W 134 MB)", "parallelism": f"replicas x{ws}"},
         "submatrices_per_s": ws * args.steps * last.accepted_trials / (total_ms / 1e3),
         "submatrices_per_s_gram_stage": last.accepted_trials / (stage["select_gram"] * 1e-3),
         "latency_ms": {"p50": pct(per, 50), "p99": pct(per, 99)},
+        "angle_vs_oracle": angle_oracle,
+        "angle_vs_oracle_tol": 1e-6,
         "angle_vs_fp64_form": angle,
         "eig_factor_bits": last.eig_factor_bits,
         "eig_iterations": last.eig_iterations,
         "fp64_form": {"value": replica_throughput(ws, k64, max_over_ranks(total64, ws)), "unit": "decomps/s", "ms_per_step": total64 / k64,
+                      "angle_vs_oracle": angle_oracle64, "angle_vs_oracle_tol": 1e-10,
                       "latency_ms": {"p50": pct(per64, 50), "p99": pct(per64, 99)}, "stage_ms": stage64},
         "stage_ms": stage,
         "dominant_stage": dominant,
@@ -424,6 +461,377 @@ def bench_mine(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------- the other workloads (on demand)
+
+def _device_problem(p, dtype, dev):
+    import torch
+    Y = torch.from_numpy(np.ascontiguousarray(p.Y.T)).to(dev, dtype=dtype).t()
+    W = torch.from_numpy(np.ascontiguousarray(p.W.T)).to(dev).t()
+    return Y, W
+
+
+def _line(args, name, value, unit, ms_per_step, dtype, config, **extra):
+    out = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": dtype, "data": "synthetic", "config": dict(workload=name, **config)}
+    out.update(extra)
+    print(json.dumps(out), flush=True)
+
+
+def _timed_calls(fn, steps, stream):
+    import torch
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    out = []
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for k in range(steps):
+        out.append(fn())
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    per = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+    return evs[0].elapsed_time(evs[-1]), per, out
+
+
+def bench_single(args):
+    """The small single-problem workloads (FP64 form, latency bound): the noiseless
+    2048 x 128 problem and the 4096 x 144 trajectory stand-in.  The oracle runs
+    one whole decomposition on one host core (these sizes take seconds)."""
+    import torch
+
+    import oracle
+    import paper_1411_0814_gb300 as rsm
+    from workloads import config_problem
+
+    name = args.workload
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    p = config_problem(name)
+    Y, W = _device_problem(p, torch.float64, dev)
+    h = rsm.RSM(0, stream=stream)
+    common = dict(trials=p.trials, l=p.l, seed=p.seed, variant=p.variant, gram="f64", solve="f64")
+    prob = rsm.Problem(Y, W, p.r, **common)
+    for _ in range(max(3, args.warmup)):
+        h.decompose(prob)
+    import tempfile
+    clocks = ClockSampler(os.path.join(tempfile.gettempdir(), f"rsm_clocks_{os.getpid()}.csv"))
+    clocks.start()
+    total, per, res = _timed_calls(lambda: h.decompose(prob), args.steps, stream)
+    clk = clocks.stop()
+    last = res[-1]
+    stage = {k: statistics.median([r_.stage_ms[k] for r_ in res]) for k in STAGES}
+    # end to end: host Y, W copied in, U, V copied out, every step
+    hY = torch.from_numpy(np.ascontiguousarray(p.Y.T)).pin_memory()
+    hW = torch.from_numpy(np.ascontiguousarray(p.W.T)).pin_memory()
+    hU = torch.empty((p.r, p.m), dtype=torch.float64, pin_memory=True)
+    hV = torch.empty((p.r, p.n), dtype=torch.float64, pin_memory=True)
+    dY = torch.empty((p.n, p.m), dtype=torch.float64, device=dev)
+    dW = torch.empty((p.n, p.m), dtype=torch.uint8, device=dev)
+    eprob = rsm.Problem(dY.t(), dW.t(), p.r, **common)
+
+    def e2e_step():
+        dY.copy_(hY, non_blocking=True)
+        dW.copy_(hW, non_blocking=True)
+        r_ = h.decompose(eprob)
+        hU.copy_(eprob.U.t(), non_blocking=True)
+        hV.copy_(eprob.V.t(), non_blocking=True)
+        return r_
+    for _ in range(3):
+        e2e_step()
+    e2e_ms, _, _ = _timed_calls(e2e_step, args.steps, stream)
+    # the oracle: one whole decomposition, one core
+    t0 = time.perf_counter()
+    o = oracle.decompose(p.Y, p.W, p.r, p.l, p.trials, p.seed, variant=p.variant)
+    t_oracle = time.perf_counter() - t0
+    angle = oracle.subspace_angle(prob.V.cpu().numpy(), o.V)
+    _line(args, name, 1e3 * args.steps / total, "decomps/s", total / args.steps, "f64",
+          dict(m=p.m, n=p.n, r=p.r, l=p.l, trials=p.trials, variant=p.variant, form="FP64 throughout",
+               l2="inputs smaller than L2; consecutive decompositions of the same resident problem"),
+          latency_ms={"p50": pct(per, 50), "p99": pct(per, 99)}, stage_ms=stage,
+          submatrices_per_s=args.steps * last.accepted_trials / (total * 1e-3),
+          status=last.status, accepted_trials=last.accepted_trials, angle_vs_oracle=angle, angle_vs_oracle_tol=1e-10,
+          accepted_trials_oracle=o.accepted_trials, e=last.e, e_oracle=o.e,
+          e2e={"value": 1e3 * args.steps / e2e_ms, "unit": "decomps/s", "ms_per_step": e2e_ms / args.steps,
+               "h2d_bytes_per_step": int(hY.numel() * 8 + hW.numel()), "d2h_bytes_per_step": int((hU.numel() + hV.numel()) * 8)},
+          cpu_baseline={"value": 1.0 / t_oracle, "unit": "decomps/s", "cores": 1, "nproc": os.cpu_count(),
+                        "kind": "oracle", "sample": "one whole decomposition"},
+          gpu_launches=int(last.kernel_launches * args.steps), clocks=clk)
+    h.close()
+
+
+def bench_batched(args):
+    """The batched uneven workload: 256 independent problems (m log-uniform in
+    [4096, 65536], n in 64..512, r in 2..16, rho in [0.5, 0.9]) in one
+    rsm_decompose_batch call (FP32 Y, the given Gram form, FP64 minor vectors, M,
+    eigensolve and solves), against the plain per-problem FP64 form (each
+    problem alone, FP64 Y, Gram and solves) on the same GPU."""
+    import torch
+
+    import oracle
+    import paper_1411_0814_gb300 as rsm
+    from workloads import batched_problem, batched_problem_specs
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    specs = batched_problem_specs(256)
+    t0 = time.perf_counter()
+    dev64, dev32, meta = [], [], []
+    for i, sp in enumerate(specs):
+        p = batched_problem(sp)
+        Y64, W = _device_problem(p, torch.float64, dev)
+        dev64.append((Y64, W))
+        dev32.append(Y64.to(torch.float32))
+        meta.append((p.r, p.l, p.trials, p.seed, p.m, p.n))
+        del p
+    t_gen = time.perf_counter() - t0
+    h = rsm.RSM(0, stream=stream)
+    mixed = [rsm.Problem(dev32[i], dev64[i][1], r, trials=t, l=l, seed=sd, problem_id=i, gram=args.batched_gram,
+                         solve="f64") for i, (r, l, t, sd, m, n) in enumerate(meta)]
+    plain = [rsm.Problem(dev64[i][0], dev64[i][1], r, trials=t, l=l, seed=sd, problem_id=i, gram="f64", solve="f64")
+             for i, (r, l, t, sd, m, n) in enumerate(meta)]
+    for _ in range(max(1, args.warmup)):
+        resm = h.decompose_batch(mixed)
+    import tempfile
+    clocks = ClockSampler(os.path.join(tempfile.gettempdir(), f"rsm_clocks_{os.getpid()}.csv"))
+    clocks.start()
+    total, per, outs = _timed_calls(lambda: h.decompose_batch(mixed), args.steps, stream)
+    clk = clocks.stop()
+    resm = outs[-1]
+    # plain per-problem FP64 form: each problem alone, one pass over all 256 (after one warm-up pass)
+    for pr in plain[:8]:
+        h.decompose(pr)
+    t64, per64, res64 = _timed_calls(lambda: [h.decompose(pr) for pr in plain], 1, stream)
+    alone_ms = []
+    for pr in plain[:32]:  # per-problem latencies of the FP64 form
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        h.decompose(pr)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        alone_ms.append(s0.elapsed_time(s1))
+    # accuracy on the problems whose oracle result is stored (tests/golden)
+    angles, angles64 = {}, {}
+    for i in (47, 80, 181, 201, 215):
+        path = os.path.join(ROOT, "tests", "golden", f"oracle_batched_{i:03d}.npz")
+        if os.path.exists(path):
+            g = np.load(path)
+            angles[i] = subspace_angle_np(mixed[i].V.cpu().numpy(), g["V"])
+            angles64[i] = subspace_angle_np(plain[i].V.cpu().numpy(), g["V"])
+    statuses = [r_.status for r_ in resm]
+    n_ok = sum(1 for s_ in statuses if s_ in (0, 4))
+    stage = {k: float(resm[0].stage_ms[k]) for k in STAGES}
+    _line(args, "batched256", 256e3 * args.steps / total, "decomps/s", total / args.steps, "fp32+fp64",
+          dict(problems=256, m_range=[4096, 65536], n_range=[64, 512], r_range=[2, 16], rho_range=[0.5, 0.9],
+               trials="20 n per problem", form=f"one rsm_decompose_batch call: Y FP32, Gram {args.batched_gram}, "
+                                                 "minor vectors, M, eigensolve and r x r solves FP64",
+               l2="inputs larger than L2 (Y fp32 6.6 GB)"),
+          latency_ms={"p50": pct(per, 50), "p99": pct(per, 99), "what": "whole batch of 256"},
+          determined=n_ok, underdetermined=statuses.count(3),
+          submatrices_per_s=sum(r_.accepted_trials for r_ in resm) * args.steps / (total * 1e-3),
+          stage_ms=stage, angle_vs_oracle=angles, angle_vs_oracle_tol=1e-6,
+          fp64_per_problem={"value": 256e3 / t64, "unit": "decomps/s", "ms_per_pass": t64,
+                            "latency_ms_alone": {"p50": pct(alone_ms, 50), "p99": pct(alone_ms, 99),
+                                                 "what": "first 32 problems, each alone"},
+                            "angle_vs_oracle": angles64, "angle_vs_oracle_tol": 1e-10},
+          speedup_vs_fp64_per_problem=(256e3 * args.steps / total) / (256e3 / t64),
+          gpu_launches=int(resm[0].kernel_launches * args.steps), setup_s=t_gen, clocks=clk)
+    h.close()
+
+
+def bench_serving(args):
+    """The serving stream: Poisson arrivals at 200 requests/s for --serve-seconds,
+    each a problem of the batched uneven distribution (a pool of 32 resident
+    problems) or, with probability 5%, the large request (m = 262144, n = 2048,
+    r = 16, rho = 0.8).  FP32 inputs resident on the device; requests go through
+    rsm_submit and are polled; latency = completion - arrival on the host clock.
+    The same request list is then run through the plain per-problem FP64 form
+    (each request alone, synchronously) for its throughput and latencies."""
+    import torch
+
+    import paper_1411_0814_gb300 as rsm
+    from workloads import batched_problem, batched_problem_specs, config_problem, serving_arrivals
+
+    dev = torch.device("cuda", 0)
+    specs = batched_problem_specs(256)[:32]
+    pool = []
+    for i, sp in enumerate(specs):
+        p = batched_problem(sp)
+        Y64, W = _device_problem(p, torch.float64, dev)
+        pool.append(dict(Y32=Y64.to(torch.float32), Y64=Y64, W=W, r=p.r, l=p.l, trials=p.trials, seed=p.seed, pid=i))
+        del p
+    pl = config_problem("serving_large_262144x2048")
+    Y64, W = _device_problem(pl, torch.float64, dev)
+    large = dict(Y32=Y64.to(torch.float32), Y64=None, W=W, r=pl.r, l=pl.l, trials=pl.trials, seed=pl.seed, pid=1000)
+    del Y64, pl
+    torch.cuda.synchronize()
+    times, kinds = serving_arrivals(200.0, args.serve_seconds, 0.05, pool_small=32)
+
+    def make(k, form):
+        q = large if k < 0 else pool[k]
+        if form == "mixed":
+            return rsm.Problem(q["Y32"], q["W"], q["r"], trials=q["trials"], l=q["l"], seed=q["seed"],
+                               problem_id=q["pid"], gram=args.batched_gram, solve="f32")
+        return rsm.Problem(q["Y64"], q["W"], q["r"], trials=q["trials"], l=q["l"], seed=q["seed"],
+                           problem_id=q["pid"], gram="f64", solve="f64")
+
+    h = rsm.RSM(0, max_slots=4)
+    for k in (-1, 0, 1):  # warm the slots' workspaces with both request kinds
+        t = h.submit(make(k, "mixed"))
+        h.wait(t, timeout_ns=120 * 10 ** 9)
+        h.release(t)
+    import tempfile
+    clocks = ClockSampler(os.path.join(tempfile.gettempdir(), f"rsm_clocks_{os.getpid()}.csv"))
+    clocks.start()
+    pending = {}
+    lat, lat_small, lat_large, queue_ms, run_ms = [], [], [], [], []
+    statuses = []
+    max_pending = 0
+    start = time.perf_counter()
+    i = 0
+    n = len(times)
+    while i < n or pending:
+        now = time.perf_counter() - start
+        if i < n and now >= times[i]:
+            prob = make(int(kinds[i]), "mixed")
+            t = h.submit(prob)
+            pending[t] = (times[i], int(kinds[i]), prob)
+            i += 1
+            max_pending = max(max_pending, len(pending))
+            continue
+        done = []
+        for t, (t_arr, kind, prob) in pending.items():
+            res = h.poll(t)
+            if res is not None:
+                tl = (time.perf_counter() - start - t_arr) * 1e3
+                lat.append(tl)
+                (lat_large if kind < 0 else lat_small).append(tl)
+                queue_ms.append(res.queue_ms)
+                run_ms.append(res.run_ms)
+                statuses.append(res.status)
+                done.append(t)
+        for t in done:
+            h.release(t)
+            del pending[t]
+        if not done:
+            wait = (times[i] - (time.perf_counter() - start)) if i < n else 2e-4
+            time.sleep(min(max(wait, 0.0), 2e-4))
+    wall = time.perf_counter() - start
+    clk = clocks.stop()
+    h.close()
+    # the plain per-problem FP64 form over the same kinds of requests (each alone,
+    # synchronous); the large request's FP64 form needs its FP64 Y, built here
+    hs = rsm.RSM(0)
+    small_kinds = [int(k) for k in kinds if k >= 0][:200]
+    s_lat = []
+    for k in small_kinds[:8]:
+        hs.decompose(make(k, "fp64"))
+    for k in small_kinds:
+        t0 = time.perf_counter()
+        hs.decompose(make(k, "fp64"))
+        s_lat.append((time.perf_counter() - t0) * 1e3)
+    pl = config_problem("serving_large_262144x2048")
+    large["Y64"], _ = _device_problem(pl, torch.float64, dev)
+    del pl
+    l_lat = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        hs.decompose(make(-1, "fp64"))
+        l_lat.append((time.perf_counter() - t0) * 1e3)
+    hs.close()
+    frac_large = float(np.mean(kinds < 0))
+    mean64 = (1 - frac_large) * statistics.mean(s_lat) + frac_large * statistics.mean(l_lat)
+    mix64 = s_lat + l_lat * max(1, round(frac_large * len(s_lat) / max(1, len(l_lat))))
+    _line(args, "serving", len(lat) / wall, "decomps/s", wall * 1e3 / max(1, len(lat)), "fp32+fp64",
+          dict(rate_hz=200, seconds=args.serve_seconds, large_frac=0.05, pool_small=32,
+               large=dict(m=262144, n=2048, r=16, rho=0.8, l=17, trials=40960), max_slots=4,
+               form=f"rsm_submit / rsm_poll, continuous batching; Y FP32, Gram {args.batched_gram}, FP32 normal "
+                    "equations, FP64 minor vectors, M, eigensolve, r x r solves"),
+          requests=len(lat), arrivals=n, wall_s=wall,
+          latency_ms={"p50": pct(lat, 50), "p99": pct(lat, 99), "small_p50": pct(lat_small, 50),
+                      "small_p99": pct(lat_small, 99), "large_p50": pct(lat_large, 50), "large_p99": pct(lat_large, 99)},
+          queue_ms={"mean": statistics.mean(queue_ms), "p99": pct(queue_ms, 99)},
+          run_ms={"mean": statistics.mean(run_ms), "p99": pct(run_ms, 99)}, max_in_flight=max_pending,
+          statuses={str(s_): statuses.count(s_) for s_ in sorted(set(statuses))},
+          fp64_per_problem={"value": 1e3 / mean64, "unit": "decomps/s", "what": "each request alone, synchronous, "
+                            "same request mix (200 small + 3 large)",
+                            "latency_ms": {"p50": pct(mix64, 50), "p99": pct(mix64, 99),
+                                           "small_p50": pct(s_lat, 50), "large_mean": statistics.mean(l_lat)}},
+          clocks=clk)
+
+
+# Table 1 of the paper (Section V-A): m, n, rho, sigma, printed time t (s) and error e (Matlab, FP64,
+# one core of an i5-3470; context only)
+TABLE1 = [(65536, 1024, 0.2, 0.2, 52.4, 0.1987), (98304, 1024, 0.2, 0.2, 64.3, 0.1986),
+          (131072, 1024, 0.2, 0.2, 79.1, 0.1985), (131072, 768, 0.2, 0.2, 59.1, 0.1981),
+          (131072, 512, 0.2, 0.2, 53.0, 0.1971), (131072, 1024, 0.5, 0.1, 84.2, 0.0997),
+          (131072, 1024, 0.4, 0.1, 75.7, 0.0996), (131072, 1024, 0.3, 0.1, 59.1, 0.0995),
+          (131072, 1024, 0.3, 0.3, 59.5, 0.2985), (131072, 1024, 0.3, 0.5, 60.4, 0.4976)]
+
+
+def bench_fig1(args):
+    """The scaling sweep of Figure 1 on the shapes of Table 1 (r = 3, M1 with
+    l = 4, I = 20 n submatrices): time per decomposition against m and n on the
+    GPU (FP64 form, as the paper's Matlab) and for the oracle on one host core
+    (a bounded sample extrapolated), with the error e beside the paper's."""
+    import torch
+
+    import paper_1411_0814_gb300 as rsm
+    from workloads import lowrank_problem
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    h = rsm.RSM(0, stream=stream)
+    rows = []
+    for (m, n, rho, sigma, t_paper, e_paper) in TABLE1:
+        p = lowrank_problem(m, n, 3, rho, sigma, l=4, trials=20 * n, seed=0)
+        Y, W = _device_problem(p, torch.float64, dev)
+        prob = rsm.Problem(Y, W, 3, trials=p.trials, l=4, seed=0, gram="f64", solve="f64")
+        for _ in range(2):
+            h.decompose(prob)
+        total, per, res = _timed_calls(lambda: h.decompose(prob), max(3, args.steps // 10), stream)
+        k = len(per)
+        t_gpu = total / k
+        o = oracle_sample_problem(p, trial_sample=200, row_sample=2048)
+        rows.append(dict(m=m, n=n, rho=rho, sigma=sigma, gpu_ms=t_gpu, gpu_decomps_per_s=1e3 / t_gpu,
+                         e_gpu=res[-1].e, status=res[-1].status, accepted=res[-1].accepted_trials,
+                         oracle_s_est=o["est_s_per_decomp"], oracle_sample=o["sample"],
+                         paper_t_s=t_paper, paper_e=e_paper))
+        print(json.dumps(rows[-1]), flush=True)
+        del Y, W, prob, p
+        torch.cuda.empty_cache()
+    _line(args, "fig1_sweep", statistics.mean(r_["gpu_decomps_per_s"] for r_ in rows), "decomps/s",
+          statistics.mean(r_["gpu_ms"] for r_ in rows), "f64",
+          dict(shapes="Table 1 (Section V-A)", r=3, l=4, trials="20 n", form="FP64 throughout"), sweep=rows,
+          note="paper times are Matlab FP64 on one core of an i5-3470 (context only)")
+    h.close()
+
+
+def oracle_sample_problem(p, trial_sample: int, row_sample: int) -> dict:
+    """oracle_sample for a given problem, in this process (BLAS threads as configured)."""
+    import oracle
+    from oracle import rsm as orsm
+    cols = orsm.sample_columns(p.n, p.l, trial_sample, p.seed)
+    t0 = time.perf_counter()
+    Zs = []
+    for t in range(trial_sample):
+        R = orsm.select_rows(p.W, cols[t])
+        Zs.append(None if R.size < p.l else orsm.minor_vectors(np.asarray(p.Y[np.ix_(R, cols[t])]), p.l - p.r))
+    M = orsm.accumulate_M(p.n, cols, Zs)
+    t_trials = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    V, _ = orsm.eig_smallest(M, p.r)
+    t_eig = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    U, _ = orsm.solve_U(p.Y[:row_sample], p.W[:row_sample], V)
+    oracle.residual(p.Y[:row_sample], p.W[:row_sample], U, V)
+    t_rows = time.perf_counter() - t0
+    est = t_trials * p.trials / trial_sample + t_eig + t_rows * p.m / row_sample
+    return dict(est_s_per_decomp=est, sample=f"{trial_sample} of {p.trials} submatrices + full eigensolve of M + "
+                                               f"U and e on {row_sample} of {p.m} rows, extrapolated")
 
 
 # ----------------------------------------------------------------- reference arm (the oracle)
@@ -466,8 +874,11 @@ def main():
         return
     if args.impl == "reference":
         bench_reference(args)
-    else:
+    elif args.workload == WORKLOAD:
         bench_mine(args)
+    else:
+        {"noiseless_2048x128": bench_single, "trajectory_4096x144": bench_single, "batched256": bench_batched,
+         "serving": bench_serving, "fig1_sweep": bench_fig1}[args.workload](args)
 
 
 if __name__ == "__main__":

@@ -52,13 +52,20 @@ typedef enum rsm_status {
 typedef enum rsm_dtype { RSM_F64 = 0, RSM_F32 = 1 } rsm_dtype;
 
 /* Arithmetic of the two bulk contractions: the per-trial Gram A^T A of step 2
- * and the per-row normal equations of step 3.
+ * (gram_prec) and the accumulation of the per-row normal equations
+ * N_i = sum v_j v_j^T, b_i = sum y_ij v_j of step 3 (solve_prec).
  *   RSM_PREC_F64:   FP64 multiply-add throughout.
  *   RSM_PREC_F32X2: products and sums carried as unevaluated pairs of FP32
- *                   values (about 48 significant bits) on the FP32 pipes.
- *   RSM_PREC_F32:   FP32 multiply-add (the reduced-precision form).
- * The l x l eigenproblems, the accumulation of M, the eigensolve of M and the
- * r x r solves are FP64 in every mode. */
+ *                   values (about 48 significant bits) on the FP32 pipes
+ *                   (gram_prec only).
+ *   RSM_PREC_F32:   FP32 multiply-add (the reduced-precision form); for FP32 Y
+ *                   and r <= 21 the N_i accumulate on the tensor cores (TF32
+ *                   head + tail of v_a v_b, FP32 accumulation, ~2^-22).
+ * In every mode: the l x l eigenproblems (minor vectors) are refined in FP64;
+ * M is summed in 64-bit fixed point and stored in FP64; the eigensolve of M
+ * iterates with M X in FP32 pairs (~2^-44) and ends with two refinement
+ * passes whose products M X, Rayleigh-Ritz step and residual are IEEE FP64;
+ * the r x r Cholesky factorisations and triangular solves for U are FP64. */
 typedef enum rsm_prec { RSM_PREC_F64 = 0, RSM_PREC_F32X2 = 1, RSM_PREC_F32 = 2 } rsm_prec;
 
 /* Column sampler (Section III, method M1). */
@@ -72,7 +79,8 @@ typedef struct rsm_config {
   int32_t max_slots;         /* requests the serving loop runs concurrently (0 -> 4) */
   size_t hbm_budget_bytes;   /* library-owned device memory the handle may hold (0 -> 80% of free) */
   uint64_t wait_timeout_ns;  /* bound on every blocking wait of the serving loop (0 -> 10 s) */
-  void* stream;              /* cudaStream_t used by rsm_decompose (NULL -> a stream the handle creates) */
+  void* stream;              /* cudaStream_t used by rsm_decompose and rsm_decompose_batch (NULL -> a
+                                stream the handle creates; see rsm_decompose for the ordering) */
   uint32_t fault_inject;     /* host-side fault injection for tests (RSM_FAULT_* bits); 0 in production */
   uint32_t reserved;
 } rsm_config;
@@ -124,7 +132,9 @@ typedef struct rsm_result {
   int64_t kernel_launches;       /* CUDA kernels this call launched (whole batch) */
   int32_t eig_factor_bits;       /* 32 or 64: precision of the Cholesky preconditioner used for M */
   int32_t eig_iterations;        /* preconditioned block iterations of the eigensolve of M (last attempt) */
-  double eig_M[32];              /* smallest eigenvalues of M, ascending */
+  double eig_M[32];              /* smallest eigenvalues of M, ascending: the first r to FP64 working
+                                    accuracy; the rest are Ritz values of the solver's extra block
+                                    vectors (upper bounds on lambda_{r+1}, ..., loosely converged) */
   double eig_residual;           /* largest ||M v - lambda v|| over the r returned vectors */
   double e_known_rms;            /* eq. (ep): RMS residual over the known entries (NaN if U is NULL) */
   float stage_ms[12];            /* device time per stage (CUDA events on the launching stream):
@@ -162,7 +172,14 @@ size_t rsm_footprint_bytes(const rsm_problem* p);
 
 /* Synchronous decomposition (Section IV-A steps 1-3).  Runs every stage on the
  * handle's stream and returns after the stream is synchronised.  res (host)
- * may be NULL.  Returns the same status as res->status. */
+ * may be NULL.  Returns the same status as res->status.
+ * Ordering: the first read of Y and W comes after all work already enqueued
+ * on the handle's stream (rsm_config.stream).  A handle that created its own
+ * stream instead starts after all work enqueued so far on the legacy default
+ * stream, which covers the caller's blocking streams but NOT streams created
+ * with cudaStreamNonBlocking: inputs produced on such a stream must be
+ * complete (or the handle created on that stream).  U, V and the debug
+ * outputs are complete when the call returns. */
 int32_t rsm_decompose(rsm_handle* h, const rsm_problem* p, rsm_result* res);
 
 /* Batched decomposition of count independent problems (host array ps).  The
@@ -174,7 +191,13 @@ int32_t rsm_decompose_batch(rsm_handle* h, const rsm_problem* ps, int32_t count,
 /* Serving: enqueue a problem.  The problem struct is copied; Y, W, U, V and the
  * debug buffers must stay valid until rsm_poll reports a final status.  A
  * request is admitted when a slot is free and its footprint fits the budget;
- * requests run concurrently on separate streams.  *ticket identifies it. */
+ * requests run concurrently on separate streams.  *ticket identifies it.
+ * Ordering: the request's first read of Y and W comes after all work that was
+ * enqueued on `stream` (a cudaStream_t of the handle's device; NULL = the
+ * legacy default stream) before this call; its outputs are complete once
+ * rsm_poll / rsm_wait report a final status. */
+int32_t rsm_submit_on(rsm_handle* h, const rsm_problem* p, void* stream, uint64_t* ticket);
+/* rsm_submit_on with the legacy default stream. */
 int32_t rsm_submit(rsm_handle* h, const rsm_problem* p, uint64_t* ticket);
 /* Non-blocking: RSM_PENDING while queued or running, else the final status
  * (res filled).  A finished ticket can be polled again until rsm_release. */
@@ -215,6 +238,31 @@ int32_t rsm_sample_columns(int64_t n, int32_t l, int64_t t0, int64_t count, uint
  * exceeds its capacity writes only the first rows (ascending). */
 int32_t rsm_select_rows(const uint32_t* bits, int64_t ldb, int64_t m, const int32_t* cols, int32_t l, int64_t count,
                         const int64_t* row_offsets, int32_t* rows, int32_t* row_counts, void* stream);
+
+/* The eigen stage alone (row a7; Section III, eq. solve.barV_L2_norm: V-hat =
+ * the eigenvectors of M for its r smallest eigenvalues) on a caller-supplied
+ * M, with the same solver, precision and acceptance as rsm_decompose.
+ * M: device n x n symmetric (FP64, leading dimension n), read only, copied
+ * into the handle's workspace.  V: device output n x r (ldv >= n), orthonormal
+ * columns.  res (host, may be NULL): status, eig_M (the kx smallest
+ * eigenvalues, ascending), eig_residual (largest ||M v - lambda v|| of the r
+ * returned vectors, FP64), eig_factor_bits, eig_iterations, stage_ms.  The
+ * status is RSM_ERR_UNDERDETERMINED when lambda_{r+1} <= 1e-12 trace(M) (more
+ * than r numerically zero eigenvalues); V is written either way.
+ * 2 <= n <= 32768, 1 <= r < min(n, 32).  Synchronous on the handle's stream,
+ * ordered like rsm_decompose. */
+int32_t rsm_eig_smallest(rsm_handle* h, const double* M, int64_t n, int32_t r, double* V, int64_t ldv,
+                         rsm_result* res);
+
+/* The FP64 reciprocal, inverse square root and square root that the library's
+ * small dense kernels use (pivots, rotations, substitutions; the r x r solves
+ * of Section III eq. solve.barU): each is seeded by the FP32 hardware
+ * approximation and refined by Newton-Raphson steps in FP64, so the result may
+ * differ from the correctly rounded one in the last bits.  Evaluated for tests
+ * that bound that difference.  x: device array of count doubles; out: device
+ * array of 3 count doubles receiving 1/x, then 1/sqrt(x) (0 for x <= 0), then
+ * sqrt(x) (0 for x < 0).  Asynchronous on stream. */
+int32_t rsm_check_fp64_math(const double* x, int64_t count, double* out, void* stream);
 
 /* The error e of eq. (ep) for a given U and V, without allocating device memory.
  * The paper has no counterpart: this entry point exists for callers that

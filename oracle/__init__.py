@@ -13,6 +13,7 @@ Parity status per function (what pins it is listed in the tests):
   minor_vectors               pinned (noiseless null-vector invariant, dense SVD case)
   accumulate_M                pinned (trace, PSD, symmetry, M V_bar = 0)
   eig_smallest                pinned (exact noiseless recovery, rho = 1 dense-SVD case)
+  underdetermined             pinned (designed spectra either side of the threshold, rank-deficient Xi)
   solve_U                     pinned (noiseless reconstruction, rho = 1 closed form)
   residual                    pinned (closed form on hand-built cases, Table 1 statistics)
   sample_rows, select_cols    pinned (method M2: distinctness, brute-force column scan)
@@ -22,6 +23,6 @@ Parity status per function (what pins it is listed in the tests):
 from .philox import philox4x32_10, trial_words, bounded  # noqa: F401
 from .rsm import (  # noqa: F401
     sample_columns, select_rows, minor_vectors, extend, accumulate_M, eig_smallest, solve_U,
-    residual, decompose, subspace_angle, OracleResult, STATUS_OK, STATUS_UNDERDETERMINED,
+    residual, decompose, subspace_angle, underdetermined, OracleResult, STATUS_OK, STATUS_UNDERDETERMINED,
     STATUS_ROWS_UNDERDETERMINED, RANK_TOL, sample_rows, select_cols, null_vectors_rows, decompose_rows,
 )

@@ -132,6 +132,14 @@ def eig_smallest(M: np.ndarray, r: int):
     return Q[:, :r].copy(), evals
 
 
+def underdetermined(evals: np.ndarray, r: int, trace: float, accepted: int) -> bool:
+    """True when V-hat is not determined by M (Section III, before eq. solve.barV:
+    Xi must have rank n - r): no trial was accepted, or M has more than r
+    numerically zero eigenvalues, lambda_{r+1} <= RANK_TOL trace(M), with
+    trace(M) = ||Xi||_F^2 the scale of Xi's squared singular values."""
+    return bool(accepted == 0 or evals[r] <= RANK_TOL * max(float(trace), 0.0))
+
+
 def solve_U(Y: np.ndarray, W: np.ndarray, V: np.ndarray):
     """U-hat by eq. (solve.barU) with the L2 norm: for each row i, least squares of
     y_i restricted to K_i = {j : w_ij = 1} on the rows V[K_i].
@@ -221,9 +229,8 @@ def decompose(Y: np.ndarray, W: np.ndarray, r: int, l: Optional[int] = None, tri
         Z_list.append(minor_vectors(A, n_minor))
     M = accumulate_M(n, cols, Z_list)
     V, evals = eig_smallest(M, r)
-    trace = max(float(np.trace(M)), 0.0)
     status = STATUS_OK
-    if accepted.sum() == 0 or evals[r] <= RANK_TOL * trace:
+    if underdetermined(evals, r, np.trace(M), int(accepted.sum())):
         status = STATUS_UNDERDETERMINED
     U, under, e = None, 0, float("nan")
     if solve_u and status == STATUS_OK:
@@ -299,9 +306,8 @@ def decompose_rows(Y: np.ndarray, W: np.ndarray, r: int, k: Optional[int] = None
             z = Z[:, j]
             M[np.ix_(C, C)] += np.outer(z, z)
     V, evals = eig_smallest(M, r)
-    trace = max(float(np.trace(M)), 0.0)
     status = STATUS_OK
-    if accepted.sum() == 0 or evals[r] <= RANK_TOL * trace:
+    if underdetermined(evals, r, np.trace(M), int(accepted.sum())):
         status = STATUS_UNDERDETERMINED
     U, under, e = None, 0, float("nan")
     if solve_u and status == STATUS_OK:

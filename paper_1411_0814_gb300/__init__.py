@@ -7,6 +7,6 @@ and the error e) runs in the CUDA kernels of ``librsm.so`` behind the C ABI of
 """
 from .rsm import (  # noqa: F401
     RSM, Problem, Result, RSMError, colmajor, pack_mask, sample_columns, select_rows, status_string, lib,
-    residual_noalloc,
+    residual_noalloc, check_fp64_math,
 )
 from . import _abi as abi  # noqa: F401

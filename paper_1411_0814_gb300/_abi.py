@@ -104,6 +104,7 @@ SIGNATURES = {
     "rsm_decompose": (C.c_int32, [C.c_void_p, C.POINTER(rsm_problem), C.POINTER(rsm_result)]),
     "rsm_decompose_batch": (C.c_int32, [C.c_void_p, C.POINTER(rsm_problem), C.c_int32, C.POINTER(rsm_result)]),
     "rsm_submit": (C.c_int32, [C.c_void_p, C.POINTER(rsm_problem), C.POINTER(C.c_uint64)]),
+    "rsm_submit_on": (C.c_int32, [C.c_void_p, C.POINTER(rsm_problem), C.c_void_p, C.POINTER(C.c_uint64)]),
     "rsm_poll": (C.c_int32, [C.c_void_p, C.c_uint64, C.POINTER(rsm_result)]),
     "rsm_wait": (C.c_int32, [C.c_void_p, C.c_uint64, C.c_uint64, C.POINTER(rsm_result)]),
     "rsm_cancel": (C.c_int32, [C.c_void_p, C.c_uint64]),
@@ -113,6 +114,9 @@ SIGNATURES = {
                                        C.c_void_p, C.c_void_p]),
     "rsm_select_rows": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int32, C.c_int64, C.c_void_p,
                                     C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rsm_eig_smallest": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64,
+                                     C.POINTER(rsm_result)]),
+    "rsm_check_fp64_math": (C.c_int32, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "rsm_residual_noalloc": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p,
                                          C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
                                          C.c_void_p, C.c_void_p]),

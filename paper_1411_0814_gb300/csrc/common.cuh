@@ -9,6 +9,7 @@
 namespace rsm {
 
 constexpr int kMaxL = 32;  // columns per submatrix supported by the kernels
+constexpr int kStatTrace = 46;  // stats slot of trace(M) when M is supplied by the caller
 constexpr int kMaxR = 32;  // rank supported by the kernels (r < l <= 32)
 
 // Everything a kernel needs to know about one problem of a batch.  Lives in
@@ -42,6 +43,8 @@ struct ProbDesc {
   double* small;             // per-problem small matrices (k x k blocks)
   double* Kmat;              // n x q_pad products of V for the normal equations
   double* NB;                // m x q_pad normal-equation data (N_i packed, b_i)
+  float* Lf;                 // FP32 normal equations only: m x r(r+1)/2 packed Cholesky factors of the N_i
+                             // (row-major lower, a(a+1)/2 + b), entry 0 = -1 for rows on the minimum-norm path
   unsigned long long* counters;  // [0] accepted trials, [1] known entries, [2] max column count, [3] chol fail,
                                  // [4] underdetermined rows, [5] selected rows, [6] device waits that ran out
   unsigned* tflag;               // 3 nblk^2 tile states of the factor launch (zeroed before it)
@@ -62,7 +65,7 @@ struct ProbDesc {
   int32_t q;     // number of normal-equation columns: r(r+1)/2 + r
   int32_t q_pad;
   int32_t status;  // device-written status of this problem
-  int32_t pad_;
+  int32_t m_given;  // 1: M was supplied by the caller (eigen stage alone); trace(M) is in stats[kStatTrace]
   int64_t slab_rows;  // rows per slab of the row-slab Gram schedule (a function of n and the Y type only)
   // normal equations on the tensor cores (FP32 form): padded N of the W x Kw product, V columns per row of
   // the FP32 V copy; V in FP32 for the FP32 residual (row j at vf32 + j * vf_ld)

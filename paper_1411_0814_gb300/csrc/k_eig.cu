@@ -21,8 +21,10 @@
 //     about (tau + theta) / (lambda + tau) per step, so the r smallest Ritz
 //     pairs converge quickly when lambda_{r+1} >> tau.  M X runs in FP32-pair
 //     arithmetic (about 2^-44 relative) and the reductions and the
-//     Rayleigh-Ritz step in FP64, so the limiting accuracy is close to that of
-//     FP64 arithmetic on M.
+//     Rayleigh-Ritz step in FP64.
+//   * FP64 refinement: two final passes with M X in IEEE FP64 (k_gemm_MX64):
+//     a residual and correction, then a Rayleigh-Ritz step whose FP64 residual
+//     M v - theta v is what the host checks against the eigen-gap.
 // Every kernel is batched over the problems of the launch.
 #include <atomic>
 
@@ -74,8 +76,10 @@ __global__ void __launch_bounds__(256) k_eig_prep(const ProbDesc* __restrict__ d
   }
   const uint32_t np = (uint32_t)npad_of(d), n = (uint32_t)d.n;
   const uint32_t i = e0 / np, j0 = e0 - i * np;
-  // tau = shift_rel * trace(M) / n, trace(M) = accepted trials * n_minor (a shift: FP32 suffices for the mean)
-  const float meanf = (float)d.counters[0] * (float)d.n_minor / (float)n;
+  // tau = shift_rel * trace(M) / n, trace(M) = accepted trials * n_minor, or computed from a
+  // caller-supplied M (a shift: FP32 suffices for the mean)
+  const float meanf = d.m_given ? (float)(d.stats[kStatTrace] / (double)n)
+                                : (float)d.counters[0] * (float)d.n_minor / (float)n;
   const double tau = meanf > 0.f ? shift_rel * (double)meanf : 1.0;
   T v[4];
 #pragma unroll
@@ -842,6 +846,56 @@ __global__ void __launch_bounds__(kMxRows) k_gemm_MX(const ProbDesc* __restrict_
       if (c < kx) d.R[(split * n + i) * kx + c] = (double)sh[c] + (double)sl[c];
 }
 
+// out = M X in IEEE FP64 (FMA), for the refinement passes that end the
+// eigensolve: the same split over the inner dimension and the same R slots as
+// k_gemm_MX, with M read in FP64 (thread = row i, M[j][i] = M[i][j] by symmetry,
+// so consecutive threads read consecutive addresses).
+template <int KXB>
+__global__ void __launch_bounds__(kMxRows) k_gemm_MX64(const ProbDesc* __restrict__ descs,
+                                                      const int64_t* __restrict__ off, int nprob) {
+  __shared__ double xs[kMxSub][KXB];
+  const int p = find_problem(off, nprob, blockIdx.x);
+  const ProbDesc& d = descs[p];
+  if (d.stats[kConvFlag] != 0.0) return;
+  const int local = (int)(blockIdx.x - off[p]);
+  const int n = (int)d.n;
+  const int kx = d.kx;
+  const int ntile = (n + kMxRows - 1) / kMxRows;
+  const int split = local / ntile;
+  const int i = (local % ntile) * kMxRows + threadIdx.x;
+  const int j_begin = split * n / kSplit, j_end = (split + 1) * n / kSplit;
+  double acc[KXB];
+#pragma unroll
+  for (int c = 0; c < KXB; ++c) acc[c] = 0.0;
+  const double* __restrict__ M = d.M;
+  for (int j0 = j_begin; j0 < j_end; j0 += kMxSub) {
+    const int jn = j_end - j0 < kMxSub ? j_end - j0 : kMxSub;
+    __syncthreads();
+    for (int e = threadIdx.x; e < jn * KXB; e += kMxRows) {
+      const int jj = e / KXB, c = e % KXB;
+      xs[jj][c] = c < kx ? d.X[(j0 + jj) * kx + c] : 0.0;
+    }
+    __syncthreads();
+    if (i < n) {
+      for (int jj = 0; jj < jn; ++jj) {
+        const double m = __ldg(M + (j0 + jj) * n + i);
+#pragma unroll
+        for (int c = 0; c < KXB; ++c) acc[c] = fma(m, xs[jj][c], acc[c]);
+      }
+    }
+  }
+  if (i < n)
+#pragma unroll
+    for (int c = 0; c < KXB; ++c)
+      if (c < kx) d.R[(split * n + i) * kx + c] = acc[c];
+}
+
+// Start of the FP64 refinement: every problem runs it, converged or not.
+__global__ void k_refine_begin(const ProbDesc* __restrict__ descs, int nprob) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < nprob) descs[p].stats[kConvFlag] = 0.0;
+}
+
 __global__ void __launch_bounds__(256) k_split_sum(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                   int nprob) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1369,6 +1423,31 @@ __global__ void __launch_bounds__(256) k_eig_finish(const ProbDesc* __restrict__
   if (threadIdx.x == 0) d.stats[34] = mx;
 }
 
+// trace(M) of a caller-supplied M into stats[kStatTrace]: one CTA per problem,
+// fixed-order tree over the diagonal.
+__global__ void __launch_bounds__(256) k_trace_M(const ProbDesc* __restrict__ descs, int nprob) {
+  __shared__ double red[256];
+  const int p = blockIdx.x;
+  if (p >= nprob) return;
+  const ProbDesc& d = descs[p];
+  const int n = (int)d.n;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) s += d.M[i * n + i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) d.stats[kStatTrace] = red[0];
+}
+
+cudaError_t launch_trace_M(const ProbDesc* descs, int nprob, cudaStream_t s) {
+  k_trace_M<<<nprob, 256, 0, s>>>(descs, nprob);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ launchers
 #define RSM_LAUNCH_SMEM(kernel, blocks, threads, smem, ...)            \
   do {                                                                \
@@ -1444,7 +1523,7 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
       if ((e = orthonormalise()) != cudaSuccess) return e;
   }
   // Phase B: preconditioned block iteration X <- X - A^-1 (M X - X Theta) with
-  // FP64 products with M and an FP64 Rayleigh-Ritz step each time; every step
+  // FP32-pair products with M and an FP64 Rayleigh-Ritz step each time; every step
   // ends with a convergence check, and a converged problem skips everything
   // after it.  With the FP64 factor a step can again collapse the block, so X is
   // re-orthonormalised before each product.  The last step never preconditions.
@@ -1463,6 +1542,31 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
     RSM_LAUNCH(k_rotate<true>, total(P.rot), 256, D, dev(P.rot), np);
     RSM_LAUNCH(k_conv_check, np, 256, D, np);
     if (it < iters) {
+      RSM_LAUNCH(precond_r, total(P.row_tile), 256, D, dev(P.row_tile), np);
+      RSM_LAUNCH(k_precond_apply<0>, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
+    }
+  }
+  // FP64 refinement.  The iteration above carries M X in FP32 pairs (about
+  // 2^-44 relative), which bounds its residual at ~2^-44 ||M||.  Two more passes
+  // with M X in IEEE FP64: the first gives the FP64 residual R of the current
+  // Ritz vectors and the correction X <- X - A^-1 R; the second a Rayleigh-Ritz
+  // step on the corrected block with FP64 products, whose residual (also FP64)
+  // is the one reported and tested on the host.
+  RSM_LAUNCH(k_refine_begin, (np + 127) / 128, 128, D, np);
+  for (int pass = 0; pass < 2; ++pass) {
+    if (sizeof(T) == 8 && pass > 0)
+      if ((e = orthonormalise()) != cudaSuccess) return e;
+    if (P.kx_max <= 12)
+      RSM_LAUNCH(k_gemm_MX64<12>, total(P.mx), kMxRows, D, dev(P.mx), np);
+    else if (P.kx_max <= 16)
+      RSM_LAUNCH(k_gemm_MX64<16>, total(P.mx), kMxRows, D, dev(P.mx), np);
+    else
+      RSM_LAUNCH(k_gemm_MX64<32>, total(P.mx), kMxRows, D, dev(P.mx), np);
+    RSM_LAUNCH(k_split_sum, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
+    RSM_LAUNCH_SMEM(k_xtx<true>, total(P.chunk), 256, xtx_smem, D, dev(P.chunk), np, P.part, dev(P.part_off));
+    RSM_LAUNCH_SMEM(k_rr64, np, kSmallThreads, kRRSmem, D, np, P.part, dev(P.part_off));
+    RSM_LAUNCH(k_rotate<true>, total(P.rot), 256, D, dev(P.rot), np);
+    if (pass == 0) {
       RSM_LAUNCH(precond_r, total(P.row_tile), 256, D, dev(P.row_tile), np);
       RSM_LAUNCH(k_precond_apply<0>, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
     }

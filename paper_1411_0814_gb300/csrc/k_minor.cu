@@ -262,6 +262,7 @@ cudaError_t launch_minor_scatter(const ProbDesc* descs, const int64_t* trial_off
   if (e != cudaSuccess) return e;
   k_minor_scatter<<<(unsigned)((total + kMinorWarps - 1) / kMinorWarps), 32 * kMinorWarps, dyn, s>>>(descs, trial_off,
                                                                                                    nprob, lmax);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 

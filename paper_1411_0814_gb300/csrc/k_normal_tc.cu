@@ -305,9 +305,10 @@ __global__ void __launch_bounds__(kThreads) k_normal_tc(const ProbDesc* __restri
   if (failed) {
     if (tid == 0) atomicAdd(&d.counters[6], 1ull);
   } else if (RB == 8) {
-    // r <= 8: solve the r x r system of this row right here, in FP32 (the FP32
-    // form's N_i and b_i carry FP32 rounding anyway).  N_i goes through shared
-    // memory (the stages are idle now) so the packed index can depend on r.
+    // r <= 8: solve the r x r system of this row right here.  N_i and b_i come
+    // out of the FP32 accumulation; the Cholesky factorisation and the two
+    // triangular solves run in FP64.  N_i goes through shared memory (the stages
+    // are idle now) so the packed index can depend on r.
     float* nsm = reinterpret_cast<float*>(tc_smem) + tid * 37;
     float cnt = 0.f;
     for (int cb = 0; cb < npad; cb += 16) {
@@ -320,35 +321,38 @@ __global__ void __launch_bounds__(kThreads) k_normal_tc(const ProbDesc* __restri
         if (q == P) cnt = v[k];
       }
     }
-    float L[36], u[8];
-    float tr = 0.f;
+    double L[36], u[8];
+    double tr = 0.0;
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
       if (a >= r) break;
 #pragma unroll
-      for (int b = 0; b <= a; ++b) L[a * (a + 1) / 2 + b] = nsm[b * r - b * (b - 1) / 2 + (a - b)];
+      for (int b = 0; b <= a; ++b) L[a * (a + 1) / 2 + b] = (double)nsm[b * r - b * (b - 1) / 2 + (a - b)];
       tr += L[a * (a + 1) / 2 + a];
     }
+    // a pivot below 1e-6 trace(N_i) is not resolved by the FP32-accumulated N_i:
+    // such rows take the minimum-norm path
     bool ok = cnt >= (float)r;
+    double rdiag[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       if (j >= r || !ok) break;
-      float v = L[j * (j + 1) / 2 + j];
+      double v = L[j * (j + 1) / 2 + j];
 #pragma unroll
-      for (int t = 0; t < j; ++t) v -= L[j * (j + 1) / 2 + t] * L[j * (j + 1) / 2 + t];
-      if (!(v > 1e-6f * tr)) {
+      for (int t = 0; t < j; ++t) v = fma(-L[j * (j + 1) / 2 + t], L[j * (j + 1) / 2 + t], v);
+      if (!(v > 1e-6 * tr)) {
         ok = false;
         break;
       }
-      v = sqrtf(v);
-      L[j * (j + 1) / 2 + j] = v;
-      const float iv = 1.0f / v;
+      const double iv = rsqrt64(v);
+      rdiag[j] = iv;
+      L[j * (j + 1) / 2 + j] = v * iv;
 #pragma unroll
       for (int k = j + 1; k < 8; ++k) {
         if (k >= r) break;
-        float w = L[k * (k + 1) / 2 + j];
+        double w = L[k * (k + 1) / 2 + j];
 #pragma unroll
-        for (int t = 0; t < j; ++t) w -= L[k * (k + 1) / 2 + t] * L[j * (j + 1) / 2 + t];
+        for (int t = 0; t < j; ++t) w = fma(-L[k * (k + 1) / 2 + t], L[j * (j + 1) / 2 + t], w);
         L[k * (k + 1) / 2 + j] = w * iv;
       }
     }
@@ -357,24 +361,30 @@ __global__ void __launch_bounds__(kThreads) k_normal_tc(const ProbDesc* __restri
 #pragma unroll
         for (int a = 0; a < 8; ++a) {  // C y = b
           if (a >= r) break;
-          float v = bacc[a];
+          double v = (double)bacc[a];
 #pragma unroll
-          for (int t = 0; t < a; ++t) v -= L[a * (a + 1) / 2 + t] * u[t];
-          u[a] = v / L[a * (a + 1) / 2 + a];
+          for (int t = 0; t < a; ++t) v = fma(-L[a * (a + 1) / 2 + t], u[t], v);
+          u[a] = v * rdiag[a];
         }
 #pragma unroll
         for (int a = 7; a >= 0; --a) {  // C^T u = y
           if (a >= r) continue;
-          float v = u[a];
+          double v = u[a];
 #pragma unroll
           for (int t = a + 1; t < 8; ++t)
-            if (t < r) v -= L[t * (t + 1) / 2 + a] * u[t];
-          u[a] = v / L[a * (a + 1) / 2 + a];
+            if (t < r) v = fma(-L[t * (t + 1) / 2 + a], u[t], v);
+          u[a] = v * rdiag[a];
         }
 #pragma unroll
         for (int a = 0; a < 8; ++a)
-          if (a < r) d.U[(int64_t)a * d.ldu + row] = (double)u[a];
+          if (a < r) d.U[(int64_t)a * d.ldu + row] = u[a];
+        // the factor, for the refinement step of the residual pass
+        float* lf = d.Lf + (size_t)row * P;
+#pragma unroll
+        for (int q = 0; q < 36; ++q)
+          if (q < P) lf[q] = (float)L[q];
       } else {
+        d.Lf[(size_t)row * P] = -1.f;  // no refinement: the minimum-norm path owns this row
         // too few known entries or a (numerically) singular N_i: hand the row to the
         // minimum-norm path with its data in the FP64 table
         double* out = d.NB + (size_t)row * d.q_pad;

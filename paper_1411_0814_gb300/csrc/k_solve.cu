@@ -10,7 +10,9 @@
 // pseudo-inverse from a Jacobi eigendecomposition) for rank-deficient rows.
 //
 // a9, eq. (ep): e = (sum w_ij)^-1/2 || W o (Y - U V^T) ||_F, one thread per row,
-// per-CTA partial sums reduced in a fixed order.
+// per-CTA partial sums reduced in a fixed order.  In the FP32 form the same pass
+// applies one step of iterative refinement to U (refine_row) and reports the e of
+// the refined U.
 #include <cfloat>
 
 #include "common.cuh"
@@ -209,7 +211,14 @@ __global__ void __launch_bounds__(128) k_row_solve(const ProbDesc* __restrict__ 
     if (known < (double)r) atomicAdd(&d.counters[4], 1ull);
     const unsigned long long slot = atomicAdd(fail_count, 1ull);
     fail_list[slot] = ((unsigned long long)p << 32) | (unsigned long long)i;
+    if (d.Lf) d.Lf[(size_t)i * P] = -1.f;  // no refinement: the minimum-norm path owns this row
     return;
+  }
+  if (d.Lf) {  // FP32 normal equations: the factor, for the refinement step of the residual pass
+    float* lf = d.Lf + (size_t)i * P;
+#pragma unroll
+    for (int q = 0; q < RM * (RM + 1) / 2; ++q)
+      if (q < P) lf[q] = (float)L[q];
   }
 #pragma unroll
   for (int a = 0; a < RM; ++a) {  // C y = b
@@ -277,16 +286,65 @@ __global__ void __launch_bounds__(32 * kPinvWarps) k_row_pinv(const ProbDesc* __
   }
 }
 
+// One step of iterative refinement of a row of U for the FP32 normal equations.
+// The caller has the residual r0 = y_K - V_K u32 of the FP32 copy u32 of u_i and
+// c = V_K^T r0 (both in FP32); delta = N_i^-1 c through the row's stored FP32
+// Cholesky factor (forward, then back substitution).  u_i becomes u32 + delta
+// in FP64, and the row's sum of squared residuals drops by exactly c . delta
+// (||r0 - V_K delta||^2 = ||r0||^2 - 2 c.delta + delta^T N delta, N delta = c),
+// which is returned.  Rows whose factor is marked -1 (minimum-norm path) are
+// left as they are (returns 0).  The FP32 accumulation of N_i and b_i on the
+// tensor cores carries errors of about 1e-6 relative, which this step removes
+// down to the size of the correction times that.
+template <int RM>
+__device__ __forceinline__ double refine_row(const ProbDesc& d, uint32_t row, const float (&u32)[RM],
+                                             const float (&c)[RM]) {
+  const int r = d.r, P = r * (r + 1) / 2;
+  const float* __restrict__ lf = d.Lf + (size_t)row * P;
+  if (!(lf[0] > 0.f)) return 0.0;
+  float y[RM];
+#pragma unroll
+  for (int a = 0; a < RM; ++a) {  // L y = c
+    if (a >= r) break;
+    float v = c[a];
+#pragma unroll
+    for (int t = 0; t < a; ++t) v = fmaf(-lf[a * (a + 1) / 2 + t], y[t], v);
+    y[a] = v / lf[a * (a + 1) / 2 + a];
+  }
+#pragma unroll
+  for (int a = RM - 1; a >= 0; --a) {  // L^T delta = y
+    if (a >= r) continue;
+    float v = y[a];
+#pragma unroll
+    for (int t = a + 1; t < RM; ++t)
+      if (t < r) v = fmaf(-lf[t * (t + 1) / 2 + a], y[t], v);
+    y[a] = v / lf[a * (a + 1) / 2 + a];
+  }
+  double drop = 0.0;
+#pragma unroll
+  for (int a = 0; a < RM; ++a)
+    if (a < r) {
+      d.U[(int64_t)a * d.ldu + row] = (double)u32[a] + (double)y[a];
+      drop += (double)c[a] * (double)y[a];
+    }
+  return drop;
+}
+
 // e numerator: sum over known entries of (y_ij - u_i . v_j)^2.  A CTA takes 32
 // consecutive rows (lane = row, so each column read is one coalesced 32-row
 // segment and one mask word) and its 8 warps split the columns; V is staged in
 // shared memory 64 columns at a time.  One partial per CTA, fixed-order tree.
+// FP32 form (T = float): each thread also accumulates c = V_K^T r0 for its row
+// over its columns; the 8 warps' parts are added in warp order in shared memory
+// and warp 0 applies the refinement step (refine_row) to its 32 rows.
 constexpr int kResRows = 32;
 constexpr int kResCols = 64;
 template <typename T, int RM>
 __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                  int nprob, double* __restrict__ partial) {
+  constexpr bool kRefine = sizeof(T) == 4;
   __shared__ __align__(16) T vs[kResCols][RM];  // zero past r, so the products need no guard
+  __shared__ float cred[kRefine ? kResRows : 1][RM + 1];
   __shared__ double red[8];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
@@ -294,11 +352,14 @@ __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ d
   const int64_t i0 = (blockIdx.x - off[p]) * kResRows;
   const int64_t i = i0 + lane;
   const bool row_in = i < d.m;
-  const int r = d.r, P = r * (r + 1) / 2;
+  const int r = d.r;
   // V: the FP32 forms keep a copy of V in FP32 (row j at vf32 + j * vf_ld)
   T u[RM];
 #pragma unroll
   for (int a = 0; a < RM; ++a) u[a] = (a < r && row_in) ? (T)d.U[(int64_t)a * d.ldu + i] : (T)0;
+  float cacc[RM];
+#pragma unroll
+  for (int a = 0; a < RM; ++a) cacc[a] = 0.f;
   // at most n / 8 terms per thread in the working precision (FP64 arithmetic is
   // far slower than FP32 on this part; one conversion per thread at the end)
   T acc = (T)0;
@@ -322,25 +383,46 @@ __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ d
       const uint32_t word = __ldg(d.bits + (j * ldb + wcol));
       const T y = load_y<T>(d, j * ldy + irow);
       T pred = (T)0;
-      if constexpr (sizeof(T) == 4) {  // V row by 16-byte shared-memory loads
-        const float4* vr = reinterpret_cast<const float4*>(&vs[jj][0]);
+      if constexpr (kRefine) {  // V row by 16-byte shared-memory loads
+        float vr[RM];
+        const float4* v4 = reinterpret_cast<const float4*>(&vs[jj][0]);
 #pragma unroll
         for (int a4 = 0; a4 < RM / 4; ++a4) {
-          const float4 v = vr[a4];
-          pred = fmaf(u[4 * a4], v.x, pred);
-          pred = fmaf(u[4 * a4 + 1], v.y, pred);
-          pred = fmaf(u[4 * a4 + 2], v.z, pred);
-          pred = fmaf(u[4 * a4 + 3], v.w, pred);
+          const float4 v = v4[a4];
+          vr[4 * a4] = v.x, vr[4 * a4 + 1] = v.y, vr[4 * a4 + 2] = v.z, vr[4 * a4 + 3] = v.w;
         }
+#pragma unroll
+        for (int a = 0; a < RM; ++a) pred = fmaf(u[a], vr[a], pred);
+        const float diff = (row_in && ((word >> lane) & 1u)) ? y - pred : 0.f;
+        acc = fmaf(diff, diff, acc);
+#pragma unroll
+        for (int a = 0; a < RM; ++a) cacc[a] = fmaf(diff, vr[a], cacc[a]);
       } else {
 #pragma unroll
         for (int a = 0; a < RM; ++a) pred = fma(u[a], vs[jj][a], pred);
+        const T diff = (row_in && ((word >> lane) & 1u)) ? y - pred : (T)0;
+        acc = fma(diff, diff, acc);
       }
-      const T diff = (row_in && ((word >> lane) & 1u)) ? y - pred : (T)0;
-      acc = fma(diff, diff, acc);
     }
   }
   double dacc = (double)acc;
+  if constexpr (kRefine) {
+    for (int w = 0; w < 8; ++w) {  // c of each row: the warps' parts in warp order
+      if (wg == w)
+#pragma unroll
+        for (int a = 0; a < RM; ++a) cred[lane][a] = (w == 0 ? 0.f : cred[lane][a]) + cacc[a];
+      __syncthreads();
+    }
+    if (wg == 0 && row_in) {
+      float c[RM], u32[RM];
+#pragma unroll
+      for (int a = 0; a < RM; ++a) {
+        c[a] = cred[lane][a];
+        u32[a] = (float)u[a];
+      }
+      dacc -= refine_row<RM>(d, (uint32_t)i, u32, c);
+    }
+  }
 #pragma unroll
   for (int o = 16; o; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
   if (lane == 0) red[wg] = dacc;
@@ -355,12 +437,15 @@ __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ d
 // FP32 form of FP32 Y with 16-byte aligned columns: each lane takes 4
 // consecutive rows (one 16-byte load per column), a CTA 128 rows, its 8 warps
 // split the columns; 4 columns are loaded before any is used, so each warp has
-// 2 KB of Y in flight.  Partials as in k_residual.
+// 2 KB of Y in flight.  Each lane also accumulates c = V_K^T r0 for its 4 rows;
+// the warps' parts are added in warp order in shared memory and threads 0..127
+// apply the refinement step (refine_row), one row each.  Partials as in k_residual.
 constexpr int kRes4Rows = 128;
 template <int RM>
 __global__ void __launch_bounds__(256) k_residual4(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                   int nprob, double* __restrict__ partial) {
   __shared__ __align__(16) float vs[kResCols][RM];
+  __shared__ float cred[kRes4Rows][RM + 1];
   __shared__ double red[8];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
@@ -370,11 +455,14 @@ __global__ void __launch_bounds__(256) k_residual4(const ProbDesc* __restrict__ 
   const uint32_t m = (uint32_t)d.m;
   const bool quad_in = ib < m;
   const int r = d.r;
-  float u[4][RM];
+  float u[4][RM], cacc[4][RM];
 #pragma unroll
   for (int k = 0; k < 4; ++k)
 #pragma unroll
-    for (int a = 0; a < RM; ++a) u[k][a] = (a < r && ib + k < m) ? (float)d.U[(int64_t)a * d.ldu + ib + k] : 0.f;
+    for (int a = 0; a < RM; ++a) {
+      u[k][a] = (a < r && ib + k < m) ? (float)d.U[(int64_t)a * d.ldu + ib + k] : 0.f;
+      cacc[k][a] = 0.f;
+    }
   const float* __restrict__ Y = static_cast<const float*>(d.Y);
   const uint32_t ldy = (uint32_t)d.ldy, ldb = (uint32_t)d.ldb, n = (uint32_t)d.n;
   const uint32_t wrow = ib >> 5, shift = ib & 31u;
@@ -403,29 +491,46 @@ __global__ void __launch_bounds__(256) k_residual4(const ProbDesc* __restrict__ 
       for (int q = 0; q < 4; ++q) {
         const int jj = jb + 8 * q;
         if (jj >= jn) break;
-        float pr[4] = {0.f, 0.f, 0.f, 0.f};
-        const float4* vr = reinterpret_cast<const float4*>(&vs[jj][0]);
+        float vr[RM];
+        const float4* v4 = reinterpret_cast<const float4*>(&vs[jj][0]);
 #pragma unroll
         for (int a4 = 0; a4 < RM / 4; ++a4) {
-          const float4 v = vr[a4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            pr[k] = fmaf(u[k][4 * a4], v.x, pr[k]);
-            pr[k] = fmaf(u[k][4 * a4 + 1], v.y, pr[k]);
-            pr[k] = fmaf(u[k][4 * a4 + 2], v.z, pr[k]);
-            pr[k] = fmaf(u[k][4 * a4 + 3], v.w, pr[k]);
-          }
+          const float4 v = v4[a4];
+          vr[4 * a4] = v.x, vr[4 * a4 + 1] = v.y, vr[4 * a4 + 2] = v.z, vr[4 * a4 + 3] = v.w;
         }
         const float yv[4] = {y[q].x, y[q].y, y[q].z, y[q].w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const float diff = ((bits[q] >> k) & 1u) ? yv[k] - pr[k] : 0.f;
+          float pr = 0.f;
+#pragma unroll
+          for (int a = 0; a < RM; ++a) pr = fmaf(u[k][a], vr[a], pr);
+          const float diff = ((bits[q] >> k) & 1u) ? yv[k] - pr : 0.f;
           acc = fmaf(diff, diff, acc);
+#pragma unroll
+          for (int a = 0; a < RM; ++a) cacc[k][a] = fmaf(diff, vr[a], cacc[k][a]);
         }
       }
     }
   }
   double dacc = (double)acc;
+  for (int w = 0; w < 8; ++w) {  // c of each row: the warps' parts in warp order
+    if (wg == w)
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int a = 0; a < RM; ++a) cred[4 * lane + k][a] = (w == 0 ? 0.f : cred[4 * lane + k][a]) + cacc[k][a];
+    __syncthreads();
+  }
+  if (threadIdx.x < kRes4Rows && i0 + threadIdx.x < m) {
+    const uint32_t row = i0 + threadIdx.x;
+    float c[RM], u32[RM];
+#pragma unroll
+    for (int a = 0; a < RM; ++a) {
+      c[a] = cred[threadIdx.x][a];
+      u32[a] = a < r ? (float)d.U[(int64_t)a * d.ldu + row] : 0.f;
+    }
+    dacc -= refine_row<RM>(d, row, u32, c);
+  }
 #pragma unroll
   for (int o = 16; o; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
   if (lane == 0) red[wg] = dacc;
@@ -518,14 +623,8 @@ cudaError_t launch_residual(const SolvePlan& S, int mode, double* partial, cudaS
 #undef RSM_RES
     ++g_kernel_launches;
   }
-  if (S.res4_blocks > 0) {
-    double* p4 = partial + S.res_blocks;
-    if (S.rmax <= 8)
-      k_residual4<8><<<(unsigned)S.res4_blocks, 256, 0, s>>>(D, S.res4_off, np, p4);
-    else if (S.rmax <= 16)
-      k_residual4<16><<<(unsigned)S.res4_blocks, 256, 0, s>>>(D, S.res4_off, np, p4);
-    else
-      k_residual4<32><<<(unsigned)S.res4_blocks, 256, 0, s>>>(D, S.res4_off, np, p4);
+  if (S.res4_blocks > 0) {  // problems with r <= 8 only
+    k_residual4<8><<<(unsigned)S.res4_blocks, 256, 0, s>>>(D, S.res4_off, np, partial + S.res_blocks);
     ++g_kernel_launches;
   }
   cudaError_t e = cudaGetLastError();

@@ -33,6 +33,26 @@ __global__ void __launch_bounds__(128) k_readback(const ProbDesc* __restrict__ d
   if (threadIdx.x < 64) st[threadIdx.x] = d.stats[threadIdx.x];
 }
 
+// The library's FP64 reciprocal, inverse square root and square root
+// (common.cuh) on an array, for tests that bound their error.
+__global__ void __launch_bounds__(256) k_fp64_math(const double* __restrict__ x, int64_t count,
+                                                  double* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    out[i] = rcp64(v);
+    out[count + i] = v > 0.0 ? rsqrt64(v) : 0.0;
+    out[2 * count + i] = v >= 0.0 ? sqrt64(v) : 0.0;
+  }
+}
+
+cudaError_t launch_fp64_math(const double* x, int64_t count, double* out, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const int64_t blocks = (count + 255) / 256 < 4096 ? (count + 255) / 256 : 4096;
+  k_fp64_math<<<(unsigned)blocks, 256, 0, s>>>(x, count, out);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_copy16(const void* src, void* dst, size_t bytes, cudaStream_t s) {
   const int64_t n16 = (int64_t)(bytes / 16);
   if (n16 <= 0) return cudaSuccess;

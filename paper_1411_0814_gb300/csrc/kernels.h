@@ -86,6 +86,7 @@ cudaError_t launch_gram_slab(int mode, int l, const SlabPlan& S, cudaStream_t s)
 
 cudaError_t launch_copy16(const void* src, void* dst, size_t bytes, cudaStream_t s);  // bytes: multiple of 16
 cudaError_t launch_zero16(void* dst, size_t bytes, cudaStream_t s);
+cudaError_t launch_fp64_math(const double* x, int64_t count, double* out, cudaStream_t s);
 cudaError_t launch_readback(const ProbDesc* descs, int nprob, void* host, int stride, cudaStream_t s);
 cudaError_t launch_pack_mask(const ProbDesc* descs, const int64_t* blk_off, int nprob, int64_t nblocks, cudaStream_t s);
 cudaError_t launch_sample(const ProbDesc* descs, const int64_t* trial_off, int nprob, int64_t total, cudaStream_t s);
@@ -98,6 +99,7 @@ cudaError_t launch_minor_scatter(const ProbDesc* descs, const int64_t* trial_off
                                  cudaStream_t s);
 cudaError_t launch_finalize_M(const ProbDesc* descs, const int64_t* ent_off, int nprob, int64_t total, cudaStream_t s);
 cudaError_t launch_eig(const EigPlan& P, bool fp64_factor, double shift_rel, int iters, cudaStream_t s);
+cudaError_t launch_trace_M(const ProbDesc* descs, int nprob, cudaStream_t s);
 cudaError_t launch_solve_u(const SolvePlan& S, int mode, cudaStream_t s);
 cudaError_t launch_residual(const SolvePlan& S, int mode, double* partial, cudaStream_t s);
 

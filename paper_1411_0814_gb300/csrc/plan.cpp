@@ -18,7 +18,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Sizes {
   size_t macc, counters, colcount, stats, tflag;             // zero region
-  size_t bits, cols, rowc, gram, M, Mdf, F1, F2, Dinv, X, MX, R, small, Kmat, NB;  // data region
+  size_t bits, cols, rowc, gram, M, Mdf, F1, F2, Dinv, X, MX, R, small, Kmat, NB, Lf;  // data region
 };
 
 Sizes sizes_of(const rsm_problem& p, const Derived& dv) {
@@ -47,20 +47,24 @@ Sizes sizes_of(const rsm_problem& p, const Derived& dv) {
   const size_t n_pad = (n + 31) / 32 * 32;
   s.Kmat = dv.solve_u ? align_up(std::max(n * dv.q_pad * 8, n_pad * (2 * (size_t)normal_tc_npad(p.r) + 24) * 4)) : 0;
   s.NB = dv.solve_u ? align_up(m * dv.q_pad * 8) : 0;
+  // the FP32 normal equations keep each row's factor for the refinement step of the residual pass
+  s.Lf = dv.solve_u && p.solve_prec == RSM_PREC_F32 ? align_up(m * (size_t)(p.r * (p.r + 1) / 2) * 4) : 0;
   return s;
 }
 
 size_t zero_sum(const Sizes& s) { return s.macc + s.counters + s.colcount + s.stats + s.tflag; }
 size_t data_sum(const Sizes& s) {
-  return s.bits + s.cols + s.rowc + s.gram + s.M + s.Mdf + s.F1 + s.F2 + s.Dinv + s.X + s.MX + s.R + s.small + s.Kmat + s.NB;
+  return s.bits + s.cols + s.rowc + s.gram + s.M + s.Mdf + s.F1 + s.F2 + s.Dinv + s.X + s.MX + s.R + s.small + s.Kmat +
+         s.NB + s.Lf;
 }
 size_t part_doubles(const rsm_problem& p, const Derived& dv) {
   return (size_t)((p.n + 63) / 64) * 2 * dv.kx * dv.kx;  // chunks of kChunk = 64 rows (k_eig.cu)
 }
-// The 4-row residual kernel: FP32 form of FP32 Y whose columns start on 16-byte boundaries.
+// The 4-row residual kernel: FP32 form of FP32 Y whose columns start on 16-byte
+// boundaries, r <= 8 (its refinement keeps 4 rows x r sums per lane in registers).
 bool res4_of(const rsm_problem& p, const Derived& dv) {
   return dv.solve_u && p.solve_prec == RSM_PREC_F32 && p.y_dtype == RSM_F32 && p.ldy % 4 == 0 &&
-         (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0;
+         (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0 && p.r <= 8;
 }
 size_t res_blocks_of(const rsm_problem& p, const Derived& dv) {  // partial sums of the residual
   if (!dv.solve_u) return 0;
@@ -379,6 +383,7 @@ void bind_batch(Batch& b, const rsm_problem* ps, unsigned char* ws) {
     d.small = reinterpret_cast<double*>(take(s.small));
     d.Kmat = s.Kmat ? reinterpret_cast<double*>(take(s.Kmat)) : nullptr;
     d.NB = s.NB ? reinterpret_cast<double*>(take(s.NB)) : nullptr;
+    d.Lf = s.Lf ? reinterpret_cast<float*>(take(s.Lf)) : nullptr;
     d.tc = dv.tc ? 1 : 0;
     d.gram_fp32 = p.gram_prec == RSM_PREC_F32 ? 1 : 0;
     d.tc_npad = dv.tc_npad;

@@ -52,6 +52,20 @@ int cuda_fail(cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
   } while (0)
 
+// Makes `device` current for the scope of an entry point and restores the
+// caller's current device on exit.
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int device) {
+    if ((err = cudaGetDevice(&prev)) == cudaSuccess && prev != device) err = cudaSetDevice(device);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
 constexpr double kShiftRel32 = 3e-4;   // tau / (trace(M) / n) with the FP32 factor
 constexpr double kShiftRel64 = 1e-11;  // tau / (trace(M) / n) with the FP64 factor
 #ifndef RSM_EIG_ITERS32
@@ -118,6 +132,7 @@ struct Slot {
   DevBuf ws, plan;
   PinBuf host;
   cudaEvent_t ev[10] = {};
+  cudaEvent_t ev_order = nullptr;  // recorded on the legacy default stream before a call on an owned stream
   bool fault_wait = false;  // RSM_FAULT_DEVICE_WAIT for the batches this slot runs
   int init(cudaStream_t external) {
     if (external) {
@@ -127,11 +142,14 @@ struct Slot {
       own_stream = true;
     }
     for (auto& e : ev) RSM_CUDA(cudaEventCreate(&e));
+    RSM_CUDA(cudaEventCreateWithFlags(&ev_order, cudaEventDisableTiming));
     return RSM_OK;
   }
   void destroy() {
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
+    if (ev_order) cudaEventDestroy(ev_order);
+    ev_order = nullptr;
     ws.release();
     plan.release();
     host.release();
@@ -145,6 +163,7 @@ struct Request {
   rsm_problem prob{};
   size_t footprint = 0;
   int state = 0;  // 0 queued, 1 running, 2 done
+  cudaEvent_t ready = nullptr;  // recorded on the submitter's stream: the inputs are complete after it
   rsm_result res{};
   std::chrono::steady_clock::time_point t_submit, t_start, t_end;
 };
@@ -272,7 +291,10 @@ int enqueue_readback(Batch& b, Slot& slot) {
 
 // Prepare slot buffers, upload the plan, zero the accumulators, launch, read
 // back and fill results.  Synchronises slot.stream.
-int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_result* res) {
+// given_M (count == 1 only): the caller's n x n M (device); the stages before
+// the eigensolve are skipped and M is copied into the workspace instead.
+int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_result* res,
+              const double* given_M = nullptr) {
   slot.fault_wait = (h->fault & RSM_FAULT_DEVICE_WAIT) != 0;
   Batch b;
   build_batch(ps, count, b);
@@ -281,6 +303,7 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
   if ((st = slot.plan.reserve(b.layout.plan_bytes + (size_t)count * kReadback)) != RSM_OK) return st;
   if ((st = slot.host.reserve(std::max(b.layout.plan_bytes, (size_t)count * kReadback))) != RSM_OK) return st;
   bind_batch(b, ps, static_cast<unsigned char*>(slot.ws.ptr));
+  if (given_M) b.descs[0].m_given = 1;
   // plan upload through the pinned buffer
   unsigned char* hp = static_cast<unsigned char*>(slot.host.ptr);
   const size_t dsz = (sizeof(ProbDesc) * count + 255) / 256 * 256;
@@ -296,7 +319,14 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
   for (int i = 0; i < count; ++i) max_n = std::max<int64_t>(max_n, ps[i].n);
   bool fp64 = max_n <= kSmallN;
   double shift = fp64 ? kShiftRel64 : kShiftRel32;
-  if ((st = launch_batch(b, slot, fp64, shift, true)) != RSM_OK) return st;
+  if (given_M) {
+    const ProbDesc* D = reinterpret_cast<const ProbDesc*>(slot.plan.ptr);
+    RSM_CUDA(cudaMemcpyAsync(b.descs[0].M, given_M, (size_t)ps[0].n * ps[0].n * 8, cudaMemcpyDeviceToDevice,
+                             slot.stream));
+    RSM_CUDA(launch_trace_M(D, 1, slot.stream));
+    for (int k = 2; k <= 5; ++k) RSM_CUDA(cudaEventRecord(slot.ev[k], slot.stream));
+  }
+  if ((st = launch_batch(b, slot, fp64, shift, given_M == nullptr)) != RSM_OK) return st;
   if ((st = enqueue_readback(b, slot)) != RSM_OK) return st;
   RSM_CUDA(cudaStreamSynchronize(slot.stream));
   // Accept the result when the factorisation succeeded and the a-posteriori
@@ -310,8 +340,8 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
       const double* stats = reinterpret_cast<const double*>(hp + (size_t)i * kReadback + 64);
       const int r = ps[i].r;
       const double gap = stats[r] - stats[r - 1];
-      const double trace = (double)c[0] * b.dv[i].nm;
-      const bool determined = c[0] > 0 && stats[r] > kRankTol * trace;
+      const double trace = given_M ? stats[kStatTrace] : (double)c[0] * b.dv[i].nm;
+      const bool determined = (given_M || c[0] > 0) && stats[r] > kRankTol * trace;
       const double est = stats[34] / (gap > 0.0 ? gap : 1e-300);
       if (c[3] != 0 || (!fp64 && determined && !(est <= kEigErrTol))) redo = true;
       if (c[6] != 0) timed_out = true;
@@ -350,12 +380,12 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
     r.n_eig = b.dv[i].kx;
     for (int k = 0; k < 32; ++k) r.eig_M[k] = k < r.n_eig ? stats[k] : 0.0;
     r.eig_residual = stats[34];
-    const double trace = (double)c[0] * b.dv[i].nm;
+    const double trace = given_M ? stats[kStatTrace] : (double)c[0] * b.dv[i].nm;
     r.e_known_rms = b.dv[i].solve_u ? stats[33] : NAN;
     int status = RSM_OK;
     if (c[6] != 0)
       status = RSM_ERR_TIMEOUT;
-    else if (c[0] == 0 || !(r.eig_M[ps[i].r] > kRankTol * trace))
+    else if ((!given_M && c[0] == 0) || !(r.eig_M[ps[i].r] > kRankTol * trace))
       status = RSM_ERR_UNDERDETERMINED;
     else if (c[3] != 0)
       status = RSM_ERR_UNDERDETERMINED;
@@ -453,13 +483,21 @@ int32_t rsm_decompose_batch(rsm_handle* h, const rsm_problem* ps, int32_t count,
   int st = validate_all(ps, count);
   if (st != RSM_OK) return st;
   std::lock_guard<std::mutex> lk(h->api_mu);
-  RSM_CUDA(cudaSetDevice(h->device));
+  DeviceGuard dg(h->device);
+  RSM_CUDA(dg.err);
   size_t need = 0;
   for (int i = 0; i < count; ++i) need += rsm_footprint_bytes(&ps[i]);
   if (need > h->budget) return fail(RSM_ERR_NO_MEMORY, "batch footprint above the handle's HBM budget");
   if (h->fault & RSM_FAULT_ALLOC) {
     h->fault &= ~RSM_FAULT_ALLOC;
     return fail(RSM_ERR_NO_MEMORY, "injected allocation failure");
+  }
+  if (h->main.own_stream) {
+    // the handle's own stream does not order with the caller's work: start
+    // after everything enqueued on the legacy default stream so far (which in
+    // turn waits for the caller's blocking streams)
+    RSM_CUDA(cudaEventRecord(h->main.ev_order, nullptr));
+    RSM_CUDA(cudaStreamWaitEvent(h->main.stream, h->main.ev_order, 0));
   }
   return run_batch(h, h->main, ps, count, res);
 }
@@ -514,6 +552,14 @@ void worker_loop(rsm_handle* h, int slot_id) {
       }
     }
     const int count = (int)reqs.size();
+    // each request's inputs are complete once the work its submitter had
+    // enqueued before rsm_submit has run
+    for (auto& r : reqs)
+      if (r->ready) {
+        cudaStreamWaitEvent(slot.stream, r->ready, 0);
+        cudaEventDestroy(r->ready);
+        r->ready = nullptr;
+      }
     std::vector<rsm_problem> probs(count);
     std::vector<rsm_result> res(count);
     for (int i = 0; i < count; ++i) probs[i] = reqs[i]->prob;
@@ -550,7 +596,7 @@ int ensure_workers(rsm_handle* h) {
 
 }  // namespace
 
-int32_t rsm_submit(rsm_handle* h, const rsm_problem* p, uint64_t* ticket) {
+int32_t rsm_submit_on(rsm_handle* h, const rsm_problem* p, void* stream, uint64_t* ticket) {
   if (!h || !p || !ticket) return fail(RSM_ERR_INVALID_ARG, "handle, problem and ticket are required");
   int st = validate_all(p, 1);
   if (st != RSM_OK) return st;
@@ -559,9 +605,19 @@ int32_t rsm_submit(rsm_handle* h, const rsm_problem* p, uint64_t* ticket) {
   if (fp > h->budget || (h->fault & RSM_FAULT_ADMISSION))
     return fail(RSM_ERR_NO_MEMORY, "footprint above the handle's HBM budget: never admissible");
   if (h->queue.size() >= 4096) return fail(RSM_ERR_QUEUE_FULL, "admission queue full");
+  DeviceGuard dg(h->device);
+  RSM_CUDA(dg.err);
   st = ensure_workers(h);
   if (st != RSM_OK) return st;
+  cudaEvent_t ready = nullptr;
+  RSM_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  cudaError_t er = cudaEventRecord(ready, static_cast<cudaStream_t>(stream));
+  if (er != cudaSuccess) {
+    cudaEventDestroy(ready);
+    return cuda_fail(er, "cudaEventRecord on the submitting stream");
+  }
   auto r = std::make_shared<Request>();
+  r->ready = ready;
   r->ticket = h->next_ticket++;
   r->prob = *p;
   r->footprint = fp;
@@ -571,6 +627,10 @@ int32_t rsm_submit(rsm_handle* h, const rsm_problem* p, uint64_t* ticket) {
   *ticket = r->ticket;
   h->cv.notify_all();
   return RSM_OK;
+}
+
+int32_t rsm_submit(rsm_handle* h, const rsm_problem* p, uint64_t* ticket) {
+  return rsm_submit_on(h, p, nullptr, ticket);
 }
 
 int32_t rsm_poll(rsm_handle* h, uint64_t ticket, rsm_result* res) {
@@ -604,6 +664,10 @@ int32_t rsm_cancel(rsm_handle* h, uint64_t ticket) {
   auto& r = it->second;
   if (r->state != 0) return fail(RSM_ERR_INVALID_ARG, "request already started");
   h->queue.erase(std::remove(h->queue.begin(), h->queue.end(), ticket), h->queue.end());
+  if (r->ready) {
+    cudaEventDestroy(r->ready);
+    r->ready = nullptr;
+  }
   r->state = 2;
   r->res = rsm_result{};
   r->res.status = RSM_ERR_CANCELLED;
@@ -627,6 +691,13 @@ void rsm_destroy(rsm_handle* h) {
   {
     std::unique_lock<std::mutex> lk(h->mu);
     // let running requests finish (bounded by the wait limit), drop queued ones
+    for (uint64_t t : h->queue) {
+      auto it = h->reqs.find(t);
+      if (it != h->reqs.end() && it->second->ready) {
+        cudaEventDestroy(it->second->ready);
+        it->second->ready = nullptr;
+      }
+    }
     h->queue.clear();
     h->done_cv.wait_for(lk, std::chrono::nanoseconds(h->cfg.wait_timeout_ns), [&] {
       for (auto& kv : h->reqs)
@@ -698,6 +769,53 @@ int32_t rsm_select_rows(const uint32_t* bits, int64_t ldb, int64_t m, const int3
   cudaError_t e = launch_select_rows(bits, ldb, m, cols, l, count, row_offsets, rows, row_counts,
                                      static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "select_rows");
+  return RSM_OK;
+}
+
+int32_t rsm_eig_smallest(rsm_handle* h, const double* M, int64_t n, int32_t r, double* V, int64_t ldv,
+                         rsm_result* res) {
+  if (!h || !M || !V) return fail(RSM_ERR_INVALID_ARG, "eig_smallest: handle, M and V are required");
+  if (n < 2 || n > 32768 || r < 1 || r >= n || r >= kMaxL || ldv < n)
+    return fail(RSM_ERR_INVALID_ARG, "eig_smallest: need 2 <= n <= 32768, 1 <= r < min(n, 32), ldv >= n");
+  rsm_problem p{};
+  p.m = n;
+  p.n = n;
+  p.r = r;
+  p.l = r + 1;
+  p.trials = 1;
+  p.Y = M;  // never read: the stages that read Y and W are skipped
+  p.W = reinterpret_cast<const uint8_t*>(M);
+  p.ldy = p.ldw = n;
+  p.V = V;
+  p.ldv = ldv;
+  p.y_dtype = RSM_F64;
+  p.gram_prec = p.solve_prec = RSM_PREC_F64;
+  Derived dv;
+  std::string why;
+  int st = validate_problem(p, dv, &why);
+  if (st != RSM_OK) return fail(st, "eig_smallest: " + why);
+  std::lock_guard<std::mutex> lk(h->api_mu);
+  DeviceGuard dg(h->device);
+  RSM_CUDA(dg.err);
+  if (rsm_footprint_bytes(&p) > h->budget) return fail(RSM_ERR_NO_MEMORY, "footprint above the handle's HBM budget");
+  if (h->main.own_stream) {
+    RSM_CUDA(cudaEventRecord(h->main.ev_order, nullptr));
+    RSM_CUDA(cudaStreamWaitEvent(h->main.stream, h->main.ev_order, 0));
+  }
+  rsm_result tmp{};
+  st = run_batch(h, h->main, &p, 1, &tmp, M);
+  tmp.accepted_trials = 0;
+  tmp.rows_selected = 0;
+  if (res) *res = tmp;
+  if (st == RSM_OK || st == RSM_ERR_UNDERDETERMINED) return tmp.status;
+  if (res) res->status = st;
+  return st;
+}
+
+int32_t rsm_check_fp64_math(const double* x, int64_t count, double* out, void* stream) {
+  if (!x || !out || count < 0) return fail(RSM_ERR_INVALID_ARG, "check_fp64_math: bad argument");
+  cudaError_t e = launch_fp64_math(x, count, out, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "check_fp64_math");
   return RSM_OK;
 }
 

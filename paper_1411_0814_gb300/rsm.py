@@ -148,7 +148,14 @@ class Problem:
 
 
 class RSM:
-    """A library handle (rsm_create / rsm_destroy) bound to one CUDA device."""
+    """A library handle (rsm_create / rsm_destroy) bound to one CUDA device.
+
+    The synchronous calls run on ``stream`` (default: torch's current stream of
+    that device when the handle is created), so they read Y and W after the
+    torch work queued there.  When torch's current stream at a call is another
+    one, that stream's queued work is waited for first.  ``submit`` orders each
+    request after the work queued on torch's current stream at submission.
+    """
 
     def __init__(self, device: int = 0, *, max_slots: int = 0, hbm_budget_bytes: int = 0, wait_timeout_ns: int = 0,
                  stream: Optional[torch.cuda.Stream] = None, fault_inject: int = 0):
@@ -157,7 +164,9 @@ class RSM:
         cfg.max_slots = max_slots
         cfg.hbm_budget_bytes = hbm_budget_bytes
         cfg.wait_timeout_ns = wait_timeout_ns
-        cfg.stream = stream.cuda_stream if stream is not None else None
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        cfg.stream = self.stream.cuda_stream
         cfg.fault_inject = fault_inject
         h = C.c_void_p()
         _check(lib().rsm_create(C.byref(cfg), C.byref(h)), "rsm_create")
@@ -183,22 +192,43 @@ class RSM:
 
     _SOFT = (_abi.RSM_OK, _abi.RSM_ERR_UNDERDETERMINED, _abi.RSM_ERR_ROWS_UNDERDETERMINED)
 
+    def _order_after_current(self):
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+
     def decompose(self, prob: Problem) -> Result:
+        self._order_after_current()
         res = rsm_result()
         st = lib().rsm_decompose(self._h, C.byref(prob.c), C.byref(res))
         _check(st, "rsm_decompose", self._SOFT)
         return _result(res, prob.outputs())
 
     def decompose_batch(self, probs: Sequence[Problem]) -> List[Result]:
+        self._order_after_current()
         arr = (rsm_problem * len(probs))(*[p.c for p in probs])
         res = (rsm_result * len(probs))()
         st = lib().rsm_decompose_batch(self._h, arr, len(probs), res)
         _check(st, "rsm_decompose_batch", self._SOFT)
         return [_result(res[i], probs[i].outputs()) for i in range(len(probs))]
 
+    def eig_smallest(self, M: torch.Tensor, r: int):
+        """V-hat (n x r, FP64) and the result record of the eigen stage alone on a symmetric FP64 CUDA M."""
+        if not (M.is_cuda and M.dtype == torch.float64 and M.dim() == 2 and M.shape[0] == M.shape[1]
+                and M.is_contiguous()):
+            raise ValueError("M must be a contiguous square float64 CUDA tensor")
+        n = M.shape[0]
+        V = torch.empty((r, n), dtype=torch.float64, device=M.device).t()
+        self._order_after_current()
+        res = rsm_result()
+        st = lib().rsm_eig_smallest(self._h, M.data_ptr(), n, r, V.data_ptr(), n, C.byref(res))
+        _check(st, "rsm_eig_smallest", (_abi.RSM_OK, _abi.RSM_ERR_UNDERDETERMINED))
+        return V, _result(res, dict(V=V))
+
     def submit(self, prob: Problem) -> int:
         t = C.c_uint64()
-        _check(lib().rsm_submit(self._h, C.byref(prob.c), C.byref(t)), "rsm_submit")
+        cur = torch.cuda.current_stream(self.device).cuda_stream
+        _check(lib().rsm_submit_on(self._h, C.byref(prob.c), cur, C.byref(t)), "rsm_submit_on")
         self._pending[t.value] = prob
         return t.value
 
@@ -271,3 +301,13 @@ def residual_noalloc(Y: torch.Tensor, W: torch.Tensor, U: torch.Tensor, V: torch
     _check(lib().rsm_residual_noalloc(Y.data_ptr(), _ld(Y), y_dtype, W.data_ptr(), _ld(W), U.data_ptr(), _ld(U),
                                       V.data_ptr(), _ld(V), m, n, r, e.data_ptr(), s), "rsm_residual_noalloc")
     return e
+
+
+def check_fp64_math(x: torch.Tensor, stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    """(3, count) tensor: the library's FP64 1/x, 1/sqrt(x) and sqrt(x) of a 1-D CUDA float64 tensor."""
+    if not (x.is_cuda and x.dtype == torch.float64 and x.dim() == 1 and x.is_contiguous()):
+        raise ValueError("x must be a contiguous 1-D float64 CUDA tensor")
+    out = torch.empty((3, x.numel()), dtype=torch.float64, device=x.device)
+    s = (stream or torch.cuda.current_stream(x.device)).cuda_stream
+    _check(lib().rsm_check_fp64_math(x.data_ptr(), x.numel(), out.data_ptr(), s), "rsm_check_fp64_math")
+    return out

@@ -100,9 +100,9 @@ def _rounding_floor(o, r):
 
 def _check_against_oracle(res, o, p, eps, angle_tol, recon_tol, n_minor=None):
     nm = n_minor or (p.l - p.r)
+    # the oracle's own subspace must be resolved far below the tolerance
     floor = _rounding_floor(o, p.r)
-    angle_tol = max(angle_tol, floor)
-    recon_tol = max(recon_tol, 10 * floor)
+    assert floor <= 1e-12, floor
     assert res.status == o.status
     assert res.accepted_trials == o.accepted_trials
     assert np.array_equal(_np(res.cols), o.cols)
@@ -176,10 +176,18 @@ def test_f32_gram_parity(handle):
 
 
 def test_trajectory_adjacent_parity(handle):
+    """Structured mask, adjacent column windows: M is near-degenerate at the rank
+    gap (see check_near_degenerate), so the subspace is held to its FP64 floor.
+    A quarter of the rows of the full workload (m = 1024): fewer rows per window
+    make M more degenerate than at full size (floor ~1e-6 here, ~6e-8 at
+    m = 4096), so the floor is capped at 1e-5."""
+    from tests.gpu_helpers import check_near_degenerate
     p = trajectory_problem(m=1024, seed=2, trials=1440)
     o = oracle.decompose(p.Y, p.W, p.r, p.l, p.trials, p.seed, variant="adjacent")
     res = _run(handle, p)
-    _check_against_oracle(res, o, p, eps=2.2e-16, angle_tol=1e-10, recon_tol=1e-10)
+    assert np.array_equal(_np(res.cols), o.cols)
+    assert np.array_equal(_np(res.row_counts), o.row_counts)
+    check_near_degenerate(res, o, p, floor_max=1e-5)
 
 
 def test_more_minor_vectors(handle):
@@ -286,7 +294,8 @@ def test_paper_scale_sampled_parity(handle):
     floor = 100 * 2.2e-16 * ev[-1] / (ev[p.r] - ev[p.r - 1])
     ang = oracle.subspace_angle(Vg, Q[:, :p.r])
     print(f"paper scale: angle={ang:.3e} floor={floor:.3e} worst_minor_ratio={worst:.3e}")
-    assert ang <= max(1e-10, floor)
+    assert floor <= 1e-12
+    assert ang <= 1e-10
     # a8: sampled rows of U-hat against least squares on the same V-hat (FP32 normal equations)
     Ug = _np(res.U)
     for i in np.sort(rng.choice(p.m, 256, replace=False)):

@@ -263,6 +263,30 @@ def test_underdetermined_when_too_few_trials():
     assert res.status == oracle.STATUS_UNDERDETERMINED
 
 
+def test_rank_decision_either_side_of_the_threshold():
+    # designed spectra: r numerically zero eigenvalues, then lambda_{r+1} at twice and at half
+    # the threshold RANK_TOL * trace
+    r, rest = 4, np.linspace(1.0, 9.0, 60)
+    trace = rest.sum()
+    for factor, want in ((2.0, False), (0.5, True)):
+        ev = np.concatenate([np.zeros(r), [factor * oracle.RANK_TOL * trace], rest])
+        assert oracle.underdetermined(ev, r, trace + ev[r], accepted=100) is want
+    ev = np.concatenate([np.zeros(r), rest])
+    assert oracle.underdetermined(ev, r, trace, accepted=0)  # no accepted trial
+
+
+def test_uncovered_column_leaves_V_underdetermined():
+    # a column without a single known entry is in no accepted trial: e_j joins
+    # span(V-bar) in the null space of M, so M has r + 1 zero eigenvalues
+    p = config_problem("noiseless_2048x128", trials=2000)
+    W = p.W.copy()
+    W[:, 17] = 0
+    res = oracle.decompose(p.Y, np.asfortranarray(W), p.r, p.l, p.trials, p.seed, solve_u=False)
+    assert res.accepted_trials > 1000
+    assert abs(res.evals[p.r]) <= 1e-12 * np.trace(res.M)
+    assert res.status == oracle.STATUS_UNDERDETERMINED
+
+
 def _table1():
     rows = []
     with open(os.path.join(GOLDEN, "table1_rsm_synthetic.txt")) as f:

@@ -11,6 +11,8 @@ from .synthetic import (  # noqa: F401
     lowrank_problem,
     trajectory_problem,
     batched_problem_specs,
+    batched_problem,
+    LARGE_SERVING,
     serving_arrivals,
     config_problem,
     CONFIGS,

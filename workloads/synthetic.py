@@ -144,10 +144,17 @@ def serving_arrivals(rate_hz: float = 200.0, duration_s: float = 60.0, large_fra
 
 LARGE_SERVING = dict(m=262144, n=2048, r=16, rho=0.8, sigma=1e-4, l=17, trials=20 * 2048)
 
+
+def batched_problem(spec: dict, dtype=np.float64) -> Problem:
+    """One problem of the batched uneven workload from its spec (batched_problem_specs)."""
+    return lowrank_problem(spec["m"], spec["n"], spec["r"], spec["rho"], spec["sigma"], l=spec["l"],
+                           trials=spec["trials"], seed=spec["seed"], dtype=dtype)
+
 CONFIGS = {
     "noiseless_2048x128": dict(m=2048, n=128, r=4, rho=0.8, sigma=0.0, l=5, trials=2000, seed=0),
     "paper_131072x1024": dict(m=131072, n=1024, r=8, rho=0.7, sigma=1e-3, l=9, trials=20000, seed=0),
     "trajectory_4096x144": dict(kind="trajectory", m=4096, views=72, rank=4, sigma=0.5, l=5, trials=2880, seed=0),
+    "serving_large_262144x2048": dict(LARGE_SERVING, seed=0),
 }
 
 
