@@ -68,10 +68,11 @@ typedef enum rsm_dtype { RSM_F64 = 0, RSM_F32 = 1 } rsm_dtype;
  * the r x r Cholesky factorisations and triangular solves for U are FP64. */
 typedef enum rsm_prec { RSM_PREC_F64 = 0, RSM_PREC_F32X2 = 1, RSM_PREC_F32 = 2 } rsm_prec;
 
-/* Column sampler (Section III, method M1). */
+/* Submatrix sampler (Section III, methods M1 and M2). */
 typedef enum rsm_variant {
-  RSM_COLS_RANDOM = 0,   /* l distinct columns, uniform without replacement (Floyd's algorithm) */
-  RSM_COLS_ADJACENT = 1  /* l contiguous columns s..s+l-1, s uniform in [0, n-l] */
+  RSM_COLS_RANDOM = 0,   /* M1: l distinct columns, uniform without replacement (Floyd's algorithm) */
+  RSM_COLS_ADJACENT = 1, /* M1: l contiguous columns s..s+l-1, s uniform in [0, n-l] */
+  RSM_ROWS_RANDOM = 2    /* M2: k distinct rows (the same sampler over m), then the columns known in all */
 } rsm_variant;
 
 typedef struct rsm_config {
@@ -121,6 +122,16 @@ typedef struct rsm_problem {
   int32_t* debug_row_counts; /* trials: rows kept by each trial (p_t), rejected trials included */
   double* debug_Z;           /* trials x l x n_minor: minor vectors (zero for rejected trials) */
   double* debug_M;           /* n x n: the accumulated M */
+  /* Trial planning and coverage (Section III, Theorem 3; Section IV-A step 1). */
+  double epsilon;            /* used when trials == 0: the library counts the known entries (density rho)
+                                and draws ceil(rsm_plan_trials(...).trials) submatrices, so that each known
+                                entry is visited with probability >= epsilon (0 < epsilon < 1); debug_cols,
+                                debug_row_counts and debug_Z must then be NULL.  rsm_submit needs trials >= 1. */
+  int32_t coverage;          /* 1: count the known entries that the accepted draws visit (rsm_result.coverage) */
+  int32_t reserved;
+  uint32_t* debug_visited;   /* optional device output with coverage = 1: the visited entries as a packed
+                                mask, n columns of ldb = 4 ceil(ceil(m / 32) / 4) uint32 words, bit (i mod 32)
+                                of word i / 32 of column j set iff entry (i, j) was visited */
 } rsm_problem;
 
 typedef struct rsm_result {
@@ -144,6 +155,8 @@ typedef struct rsm_result {
                                     the batch's times in every result. */
   double queue_ms;               /* serving: submit -> start */
   double run_ms;                 /* serving: start -> finish */
+  double coverage;               /* with rsm_problem.coverage: visited / known entries, else NaN */
+  int64_t trials;                /* submatrix draws made (the planned count when rsm_problem.trials was 0) */
 } rsm_result;
 
 typedef struct rsm_handle rsm_handle;
@@ -153,6 +166,24 @@ const char* rsm_version(void);
 /* sizeof of the ABI structs, for bindings to check their layout:
  * which = 0 rsm_config, 1 rsm_problem, 2 rsm_result; 0 for other values. */
 size_t rsm_struct_size(int32_t which);
+/* Trial-count plan (Section III, Theorem 3 and the first line of its proof):
+ * the probability that one draw visits a given known entry, and the number of
+ * draws that visits every known entry with probability at least epsilon. */
+typedef struct rsm_trial_plan {
+  double p_visit;          /* exact per-draw visit probability for density rho (binomial expectation) */
+  double trials;           /* ln(1 / (1 - epsilon)) / p_visit */
+  double p_visit_theorem3; /* Theorem 3's closed-form lower bound of p_visit (through Lemma 1) */
+  double trials_theorem3;  /* Theorem 3's upper bound ln(1 / (1 - epsilon)) / p_visit_theorem3 */
+} rsm_trial_plan;
+
+/* Plan the number of draws for an m x n Y with known density rho, rank r and
+ * submatrix size `size` (l columns for M1 variants, k rows for M2), so that each
+ * known entry is visited with probability at least epsilon (Section IV-A step 1).
+ * Pure host arithmetic.  RSM_ERR_INVALID_ARG unless 0 < rho <= 1, r < size,
+ * size <= n (M1) or <= m (M2), 0 < epsilon < 1. */
+int32_t rsm_plan_trials(int64_t m, int64_t n, double rho, int32_t r, int32_t size, int32_t variant, double epsilon,
+                        rsm_trial_plan* out);
+
 /* Text for a status code (static storage). */
 const char* rsm_status_string(int32_t status);
 /* Message of the last failure on the calling thread (thread-local storage). */
@@ -264,14 +295,16 @@ int32_t rsm_eig_smallest(rsm_handle* h, const double* M, int64_t n, int32_t r, d
  * sqrt(x) (0 for x < 0).  Asynchronous on stream. */
 int32_t rsm_check_fp64_math(const double* x, int64_t count, double* out, void* stream);
 
-/* The error e of eq. (ep) for a given U and V, without allocating device memory.
- * The paper has no counterpart: this entry point exists for callers that
- * cannot allocate when they need the error - work recorded into a CUDA graph by
- * stream capture, code running under a fixed memory pool, latency-bound loops.
+/* e = sqrt(sum over known (y_ij - u_i . v_j)^2 / number of known entries) for a
+ * given U and V, computed without allocating device memory.  The paper has no
+ * counterpart: this entry point is for callers that cannot allocate at the
+ * point where they need the error - a process whose device memory is owned by
+ * its own pool and may not be taken through the CUDA runtime allocator, or a
+ * latency-bound loop that must not pay the device synchronisation that
+ * cudaMalloc / cudaFree can cause.
  * Y: device m x n (ldy >= m) of y_dtype; W: device m x n bytes (ldw >= m),
  * nonzero = known; U: device m x r FP64 (ldu >= m); V: device n x r FP64
- * (ldv >= n); 1 <= r <= 32.  e: device pointer to one double that receives
- * sqrt(sum over known (y_ij - u_i . v_j)^2 / number of known entries).
+ * (ldv >= n); 1 <= r <= 32.  e: device pointer to one double that receives e.
  * Asynchronous on stream.  Scratch is a fixed array inside the library (256 KiB
  * per device, held until the process exits): m above 4,194,304 rows returns
  * RSM_ERR_INVALID_ARG.  All calls share that array, so calls that overlap on the

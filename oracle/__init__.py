@@ -14,6 +14,8 @@ Parity status per function (what pins it is listed in the tests):
   accumulate_M                pinned (trace, PSD, symmetry, M V_bar = 0)
   eig_smallest                pinned (exact noiseless recovery, rho = 1 dense-SVD case)
   underdetermined             pinned (designed spectra either side of the threshold, rank-deficient Xi)
+  planner.*                   pinned (Lemma 1 against the binomial CDF, Monte Carlo visit frequency,
+                              bound ordering, brute-force visited sets)
   solve_U                     pinned (noiseless reconstruction, rho = 1 closed form)
   residual                    pinned (closed form on hand-built cases, Table 1 statistics)
   sample_rows, select_cols    pinned (method M2: distinctness, brute-force column scan)
@@ -21,6 +23,7 @@ Parity status per function (what pins it is listed in the tests):
   decompose_rows              pinned (trace, exact noiseless recovery, rho = 1 dense-SVD case)
 """
 from .philox import philox4x32_10, trial_words, bounded  # noqa: F401
+from . import planner  # noqa: F401
 from .rsm import (  # noqa: F401
     sample_columns, select_rows, minor_vectors, extend, accumulate_M, eig_smallest, solve_U,
     residual, decompose, subspace_angle, underdetermined, OracleResult, STATUS_OK, STATUS_UNDERDETERMINED,

@@ -25,7 +25,7 @@ RSM_ERR_QUEUE_FULL = 10
 
 RSM_F64, RSM_F32 = 0, 1
 RSM_PREC_F64, RSM_PREC_F32X2, RSM_PREC_F32 = 0, 1, 2
-RSM_COLS_RANDOM, RSM_COLS_ADJACENT = 0, 1
+RSM_COLS_RANDOM, RSM_COLS_ADJACENT, RSM_ROWS_RANDOM = 0, 1, 2
 RSM_FAULT_ADMISSION, RSM_FAULT_ALLOC, RSM_FAULT_STALL, RSM_FAULT_DEVICE_WAIT = 0x1, 0x2, 0x4, 0x8
 
 
@@ -67,6 +67,10 @@ class rsm_problem(C.Structure):
         ("debug_row_counts", C.c_void_p),
         ("debug_Z", C.c_void_p),
         ("debug_M", C.c_void_p),
+        ("epsilon", C.c_double),
+        ("coverage", C.c_int32),
+        ("reserved", C.c_int32),
+        ("debug_visited", C.c_void_p),
     ]
 
 
@@ -86,6 +90,17 @@ class rsm_result(C.Structure):
         ("stage_ms", C.c_float * 12),
         ("queue_ms", C.c_double),
         ("run_ms", C.c_double),
+        ("coverage", C.c_double),
+        ("trials", C.c_int64),
+    ]
+
+
+class rsm_trial_plan(C.Structure):
+    _fields_ = [
+        ("p_visit", C.c_double),
+        ("trials", C.c_double),
+        ("p_visit_theorem3", C.c_double),
+        ("trials_theorem3", C.c_double),
     ]
 
 
@@ -116,6 +131,8 @@ SIGNATURES = {
                                     C.c_void_p, C.c_void_p, C.c_void_p]),
     "rsm_eig_smallest": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64,
                                      C.POINTER(rsm_result)]),
+    "rsm_plan_trials": (C.c_int32, [C.c_int64, C.c_int64, C.c_double, C.c_int32, C.c_int32, C.c_int32, C.c_double,
+                                    C.POINTER(rsm_trial_plan)]),
     "rsm_check_fp64_math": (C.c_int32, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "rsm_residual_noalloc": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p,
                                          C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32,

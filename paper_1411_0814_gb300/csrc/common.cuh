@@ -46,7 +46,14 @@ struct ProbDesc {
   float* Lf;                 // FP32 normal equations only: m x r(r+1)/2 packed Cholesky factors of the N_i
                              // (row-major lower, a(a+1)/2 + b), entry 0 = -1 for rows on the minimum-norm path
   unsigned long long* counters;  // [0] accepted trials, [1] known entries, [2] max column count, [3] chol fail,
-                                 // [4] underdetermined rows, [5] selected rows, [6] device waits that ran out
+                                 // [4] underdetermined rows, [5] selected rows, [6] device waits that ran out,
+                                 // [7] trace(M) in units of one minor vector (rows variant), [8] visited known
+                                 // entries (coverage); 16 slots are read back
+  uint32_t* visited;             // coverage: n columns of ldb words (zeroed), or NULL
+  // method M2 (variant 2): row-packed mask (m rows of ldr words) and per trial B_t (k x r, FP64)
+  uint32_t* rbits;
+  int64_t ldr;
+  double* Bt;
   unsigned* tflag;               // 3 nblk^2 tile states of the factor launch (zeroed before it)
   int32_t* colcount;             // n: how many trials drew each column
   double* stats;                 // [0..31] eigenvalues, [32] residual num, [33] e, [34] eig residual

@@ -21,9 +21,17 @@
 namespace rsm {
 
 constexpr int kSlabWarps = 4;
-#ifndef RSM_SLAB_MINB
-#define RSM_SLAB_MINB 5  // CTAs per SM of the FP32 form; the FP64 form (45 FP64 accumulators) keeps four
-#endif
+// CTAs per SM that the register file allows without spills: each lane holds the
+// l(l+1)/2 accumulators, the l gathered values and the l prefetched mask words
+// (FP64 values take two registers), plus about 40 for indices and addresses.
+// Capped at five, which keeps the ring buffers of the warps in shared memory.
+template <int MODE, int L>
+constexpr int slab_minb() {
+  constexpr int w = MODE == 0 ? 2 : 1;
+  constexpr int need = w * (L * (L + 1) / 2) + (w + 1) * L + 40;
+  constexpr int fit = 65536 / (32 * kSlabWarps * ((need + 7) / 8 * 8));
+  return fit < 1 ? 1 : (fit > 5 ? 5 : fit);
+}
 constexpr int kRing = 1088;  // pending rows per warp: < 32 + 32 * 32
 constexpr int kMeta = 40;    // per warp: the l column offsets into Y (from 0), then into the mask (from 20)
 
@@ -45,7 +53,7 @@ struct SlabT<2> {  // FP32 Gram of FP32 Y
 };
 
 template <int MODE, int L>
-__global__ void __launch_bounds__(32 * kSlabWarps, MODE == 2 ? RSM_SLAB_MINB : 4) k_gram_slab(const ProbDesc* __restrict__ descs,
+__global__ void __launch_bounds__(32 * kSlabWarps, (slab_minb<MODE, L>())) k_gram_slab(const ProbDesc* __restrict__ descs,
                                                                const int64_t* __restrict__ task_off, int nprob,
                                                                int slab) {
   using Tr = SlabT<MODE>;

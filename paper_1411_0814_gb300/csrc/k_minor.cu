@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDe
   if (g >= trial_off[nprob]) return;
   const int p = find_problem(trial_off, nprob, g);
   const ProbDesc& d = descs[p];
+  if (d.variant == 2) return;  // the row variant has its own kernels (k_rows.cu)
   const int64_t t = g - trial_off[p];
   const int l = d.l;
   const int ls = lmax + 1;

@@ -1,13 +1,12 @@
-// rsm_residual_noalloc: the error e of eq. (ep) for a given U and V, computed
-// without allocating any device memory.
+// rsm_residual_noalloc: the RMS residual e over the known entries for a given
+// U and V, computed without allocating any device memory.
 //
 // Who needs it: code that cannot call cudaMalloc at the point where it wants
-// the error - for example work recorded into a CUDA graph by stream capture
-// (allocation calls are not capturable), callers that run under a custom or
-// fixed memory pool and forbid the runtime allocator, or real-time loops that
-// must not pay an allocation's synchronisation.  The regular path keeps its
-// per-block partial sums in workspace that rsm_decompose allocates; this
-// variant keeps them in a fixed array that lives in the library image instead.
+// the error - a process whose device memory belongs to its own fixed pool and
+// forbids the runtime allocator, or a latency-bound loop that must not pay the
+// device synchronisation an allocation or a free can cause.  The regular path
+// keeps its per-block partial sums in workspace that rsm_decompose allocates;
+// this variant keeps them in a fixed array that lives in the library image.
 //
 // The scratch is the file-scope array g_residual_scratch below: kMaxBlocks
 // partial sums (one per 256 rows), 256 KiB, which caps m at kMaxBlocks * 256
@@ -21,7 +20,7 @@
 // is only a stand-in, not the device address.  The first call on each device
 // (with that device current) resolves the address once with
 // cudaGetSymbolAddress and caches it; make that first call before any stream
-// capture begins, since the lookup itself is not part of the captured work.
+// capture begins, since the lookup itself is not enqueued work.
 #include <cuda_runtime.h>
 
 #include <cmath>

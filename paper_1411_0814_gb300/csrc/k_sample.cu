@@ -51,10 +51,11 @@ __global__ void __launch_bounds__(256) k_pack_mask(const ProbDesc* __restrict__ 
 // [0, k) is (word * k) >> 32.  RANDOM: Floyd's algorithm, draw d picks x in
 // [0, n-l+d] and takes n-l+d instead when x is already chosen.  ADJACENT: a
 // start s in [0, n-l] and columns s..s+l-1.  The set is sorted ascending.
+// Method M2 (variant 2) draws its k rows the same way over [0, m).
 __device__ __forceinline__ void draw_columns(const ProbDesc& d, int64_t t, int32_t* out) {
   const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
   const int l = d.l;
-  const int64_t n = d.n;
+  const int64_t n = d.variant == 2 ? d.m : d.n;
   int32_t c[kMaxL];
   if (d.variant == 1) {
     uint4 w = philox4x32_10(make_uint4((uint32_t)t, d.pid, 0u, (uint32_t)(t >> 32)), k0, k1);
@@ -98,7 +99,8 @@ __global__ void __launch_bounds__(256) k_sample(const ProbDesc* __restrict__ des
   int32_t* out = d.cols + t * d.l;
   draw_columns(d, t, out);
   int vmax = 0;
-  for (int k = 0; k < d.l; ++k) vmax = max(vmax, atomicAdd(&d.colcount[out[k]], 1) + 1);
+  if (d.variant != 2)  // the row variant counts its columns when it selects them (k_m2_trial)
+    for (int k = 0; k < d.l; ++k) vmax = max(vmax, atomicAdd(&d.colcount[out[k]], 1) + 1);
   // one atomic per warp and problem for the largest column count (lanes of a warp may
   // belong to two problems of a batch: reduce among the lanes of the same problem)
   const unsigned same = __match_any_sync(__activemask(), p);
@@ -180,6 +182,93 @@ cudaError_t launch_select_rows(const uint32_t* bits, int64_t ldb, int64_t m, con
                                const int64_t* row_off, int32_t* rows, int32_t* row_counts, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   k_select_rows<<<(unsigned)count, 256, 0, s>>>(bits, ldb, m, cols, l, row_off, rows, row_counts);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ known-entry count (trial planning)
+// out += number of nonzero bytes of the column-major m x n mask W.
+__global__ void __launch_bounds__(256) k_count_known(const uint8_t* __restrict__ W, int64_t ldw, int64_t m, int64_t n,
+                                                    unsigned long long* __restrict__ out) {
+  __shared__ unsigned long long red[8];
+  unsigned long long c = 0;
+  const int64_t total = m * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / m, i = e - j * m;
+    c += W[j * ldw + i] != 0;
+  }
+  for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int k = 0; k < 8; ++k) t += red[k];
+    atomicAdd(out, t);
+  }
+}
+
+cudaError_t launch_count_known(const uint8_t* W, int64_t ldw, int64_t m, int64_t n, unsigned long long* out,
+                               cudaStream_t s) {
+  k_count_known<<<1216, 256, 0, s>>>(W, ldw, m, n, out);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ coverage (Section III, Theorem 3)
+// The known entries visited by the accepted draws of the column variants: for
+// trial t and mask word w, the rows of that word known in every chosen column
+// (the AND of the l mask words) are visited in each of the chosen columns.
+// Grid: x = trial (flattened over the problems that count coverage), y = chunk
+// of 256 words.  Only problems with a visited buffer take part.
+__global__ void __launch_bounds__(256) k_visit(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ trial_off,
+                                              int nprob) {
+  const int64_t g = blockIdx.x;
+  if (g >= trial_off[nprob]) return;
+  const int p = find_problem(trial_off, nprob, g);
+  const ProbDesc& d = descs[p];
+  if (!d.visited || d.variant == 2) return;  // the row variant records its visits in k_m2_trial
+  const int64_t t = g - trial_off[p];
+  const int l = d.l;
+  if (d.row_counts[t] < l) return;  // rejected draw
+  const uint32_t nw = (uint32_t)((d.m + 31) / 32), ldb = (uint32_t)d.ldb;
+  const uint32_t w = blockIdx.y * 256u + threadIdx.x;
+  if (w >= nw) return;
+  const int32_t* cols = d.cols + t * l;
+  uint32_t sel = 0xffffffffu;
+  for (int k = 0; k < l; ++k) sel &= __ldg(d.bits + ((uint32_t)cols[k] * ldb + w));
+  if (sel)
+    for (int k = 0; k < l; ++k) atomicOr(d.visited + ((uint32_t)cols[k] * ldb + w), sel);
+}
+
+// counters[8] = number of visited entries (all of them known); one CTA per problem.
+__global__ void __launch_bounds__(256) k_count_visited(const ProbDesc* __restrict__ descs, int nprob) {
+  __shared__ unsigned long long red[8];
+  const int p = blockIdx.x;
+  if (p >= nprob) return;
+  const ProbDesc& d = descs[p];
+  if (!d.visited) return;
+  const int64_t words = d.n * d.ldb;
+  unsigned long long c = 0;
+  for (int64_t e = threadIdx.x; e < words; e += 256) c += __popc(d.visited[e]);
+  for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tot = 0;
+    for (int k = 0; k < 8; ++k) tot += red[k];
+    d.counters[8] = tot;
+  }
+}
+
+cudaError_t launch_coverage(const ProbDesc* descs, const int64_t* trial_off, int nprob, int64_t trials_total,
+                            int64_t max_words, cudaStream_t s) {
+  if (trials_total <= 0) return cudaSuccess;
+  const unsigned chunks = (unsigned)((max_words + 255) / 256);
+  k_visit<<<dim3((unsigned)trials_total, chunks), 256, 0, s>>>(descs, trial_off, nprob);
+  ++g_kernel_launches;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_count_visited<<<nprob, 256, 0, s>>>(descs, nprob);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

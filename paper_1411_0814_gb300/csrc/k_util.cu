@@ -21,15 +21,15 @@ __global__ void __launch_bounds__(256) k_zero16(uint4* __restrict__ dst, int64_t
     dst[i] = make_uint4(0u, 0u, 0u, 0u);
 }
 
-// Per problem: counters (8 x u64) then stats (64 x f64) at stride `stride` bytes (device staging area).
+// Per problem: counters (16 x u64) then stats (64 x f64) at stride `stride` bytes (device staging area).
 __global__ void __launch_bounds__(128) k_readback(const ProbDesc* __restrict__ descs, int nprob,
                                                  unsigned char* __restrict__ host, int stride) {
   const int p = blockIdx.x;
   if (p >= nprob) return;
   const ProbDesc& d = descs[p];
   unsigned long long* c = reinterpret_cast<unsigned long long*>(host + (size_t)p * stride);
-  double* st = reinterpret_cast<double*>(host + (size_t)p * stride + 64);
-  if (threadIdx.x < 8) c[threadIdx.x] = d.counters[threadIdx.x];
+  double* st = reinterpret_cast<double*>(host + (size_t)p * stride + 128);
+  if (threadIdx.x < 16) c[threadIdx.x] = d.counters[threadIdx.x];
   if (threadIdx.x < 64) st[threadIdx.x] = d.stats[threadIdx.x];
 }
 

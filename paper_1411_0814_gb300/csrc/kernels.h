@@ -89,12 +89,19 @@ cudaError_t launch_zero16(void* dst, size_t bytes, cudaStream_t s);
 cudaError_t launch_fp64_math(const double* x, int64_t count, double* out, cudaStream_t s);
 cudaError_t launch_readback(const ProbDesc* descs, int nprob, void* host, int stride, cudaStream_t s);
 cudaError_t launch_pack_mask(const ProbDesc* descs, const int64_t* blk_off, int nprob, int64_t nblocks, cudaStream_t s);
+cudaError_t launch_count_known(const uint8_t* W, int64_t ldw, int64_t m, int64_t n, unsigned long long* out,
+                               cudaStream_t s);
+cudaError_t launch_coverage(const ProbDesc* descs, const int64_t* trial_off, int nprob, int64_t trials_total,
+                            int64_t max_words, cudaStream_t s);
 cudaError_t launch_sample(const ProbDesc* descs, const int64_t* trial_off, int nprob, int64_t total, cudaStream_t s);
 cudaError_t launch_sample_range(const ProbDesc& d, int64_t t0, int64_t count, int32_t* cols, cudaStream_t s);
 cudaError_t launch_select_rows(const uint32_t* bits, int64_t ldb, int64_t m, const int32_t* cols, int l, int64_t count,
                                const int64_t* row_off, int32_t* rows, int32_t* row_counts, cudaStream_t s);
 cudaError_t launch_select_gram(int mode, const ProbDesc* descs, const int64_t* trial_off, int nprob, int64_t total,
                                int lmax, cudaStream_t s);
+cudaError_t launch_rows_variant(const ProbDesc* descs, const int64_t* pack_off, int64_t pack_total,
+                                const int64_t* trial_off, int64_t trials_total, int nprob, int kmax, int rmax,
+                                int64_t nmax, cudaStream_t s);
 cudaError_t launch_minor_scatter(const ProbDesc* descs, const int64_t* trial_off, int nprob, int64_t total, int lmax,
                                  cudaStream_t s);
 cudaError_t launch_finalize_M(const ProbDesc* descs, const int64_t* ent_off, int nprob, int64_t total, cudaStream_t s);

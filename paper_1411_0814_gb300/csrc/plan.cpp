@@ -17,18 +17,19 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Sizes {
-  size_t macc, counters, colcount, stats, tflag;             // zero region
-  size_t bits, cols, rowc, gram, M, Mdf, F1, F2, Dinv, X, MX, R, small, Kmat, NB, Lf;  // data region
+  size_t macc, counters, colcount, stats, tflag, visited;    // zero region
+  size_t bits, cols, rowc, gram, M, Mdf, F1, F2, Dinv, X, MX, R, small, Kmat, NB, Lf, rbits, Bt;  // data region
 };
 
 Sizes sizes_of(const rsm_problem& p, const Derived& dv) {
   Sizes s{};
   const size_t n = (size_t)p.n, m = (size_t)p.m, I = (size_t)p.trials;
   s.macc = align_up(n * n * 8);
-  s.counters = align_up(8 * 8);
+  s.counters = align_up(16 * 8);
   s.colcount = align_up(n * 4);
   s.stats = align_up(64 * 8);
   s.tflag = align_up((size_t)3 * dv.nblk * dv.nblk * 4);
+  s.visited = p.coverage ? align_up(n * (size_t)dv.ldb * 4) : 0;
   s.bits = align_up(n * (size_t)dv.ldb * 4);
   s.cols = align_up(I * dv.l * 4);
   s.rowc = align_up(I * 4);
@@ -47,15 +48,20 @@ Sizes sizes_of(const rsm_problem& p, const Derived& dv) {
   const size_t n_pad = (n + 31) / 32 * 32;
   s.Kmat = dv.solve_u ? align_up(std::max(n * dv.q_pad * 8, n_pad * (2 * (size_t)normal_tc_npad(p.r) + 24) * 4)) : 0;
   s.NB = dv.solve_u ? align_up(m * dv.q_pad * 8) : 0;
+  // method M2: the row-packed mask and B_t of every trial (the per-trial Gram is not stored)
+  const bool rows = p.variant == RSM_ROWS_RANDOM;
+  s.gram = rows ? 0 : s.gram;
+  s.rbits = rows ? align_up(m * (size_t)((n + 31) / 32) * 4) : 0;
+  s.Bt = rows ? align_up(I * (size_t)dv.l * p.r * 8) : 0;
   // the FP32 normal equations keep each row's factor for the refinement step of the residual pass
   s.Lf = dv.solve_u && p.solve_prec == RSM_PREC_F32 ? align_up(m * (size_t)(p.r * (p.r + 1) / 2) * 4) : 0;
   return s;
 }
 
-size_t zero_sum(const Sizes& s) { return s.macc + s.counters + s.colcount + s.stats + s.tflag; }
+size_t zero_sum(const Sizes& s) { return s.macc + s.counters + s.colcount + s.stats + s.tflag + s.visited; }
 size_t data_sum(const Sizes& s) {
   return s.bits + s.cols + s.rowc + s.gram + s.M + s.Mdf + s.F1 + s.F2 + s.Dinv + s.X + s.MX + s.R + s.small + s.Kmat +
-         s.NB + s.Lf;
+         s.NB + s.Lf + s.rbits + s.Bt;
 }
 size_t part_doubles(const rsm_problem& p, const Derived& dv) {
   return (size_t)((p.n + 63) / 64) * 2 * dv.kx * dv.kx;  // chunks of kChunk = 64 rows (k_eig.cu)
@@ -82,14 +88,29 @@ int validate_problem(const rsm_problem& p, Derived& dv, std::string* why) {
   if (p.m > 0x7fffffffLL) return bad("m must fit in int32");
   if (p.r < 1 || p.r >= p.n) return bad("need 1 <= r < n");
   dv.l = p.l ? p.l : p.r + 1;
-  if (dv.l <= p.r || dv.l > p.n || dv.l > kMaxL) return bad("need r < l <= min(n, 32)");
-  dv.nm = p.n_minor ? p.n_minor : dv.l - p.r;
-  if (dv.nm < 1 || dv.nm > dv.l - p.r) return bad("need 1 <= n_minor <= l - r");
+  if (p.variant == RSM_ROWS_RANDOM) {
+    // M2: l is the number of rows k; every vector beyond the r largest is kept
+    if (dv.l <= p.r || dv.l > p.m || dv.l > kMaxL) return bad("rows variant: need r < k <= min(m, 32)");
+    if (p.n_minor != 0) return bad("rows variant: n_minor must be 0 (all c_t - r vectors are used)");
+    if (p.debug_Z) return bad("rows variant: debug_Z is not available");
+    if (p.n > 8192) {
+      if (why) *why = "rows variant: n > 8192 is not supported";
+      return (int)RSM_ERR_NOT_IMPLEMENTED;
+    }
+    dv.nm = 1;
+  } else {
+    if (dv.l <= p.r || dv.l > p.n || dv.l > kMaxL) return bad("need r < l <= min(n, 32)");
+    dv.nm = p.n_minor ? p.n_minor : dv.l - p.r;
+    if (dv.nm < 1 || dv.nm > dv.l - p.r) return bad("need 1 <= n_minor <= l - r");
+  }
   if (p.trials < 1 || p.trials > (int64_t)1 << 36) return bad("need 1 <= trials <= 2^36");
+  if (p.coverage != 0 && p.coverage != 1) return bad("coverage must be 0 or 1");
+  if (p.debug_visited && !p.coverage) return bad("debug_visited needs coverage = 1");
   if (p.ldy < p.m || p.ldw < p.m || p.ldv < p.n) return bad("leading dimensions too small");
   if (p.U && p.ldu < p.m) return bad("ldu < m");
   if (p.y_dtype != RSM_F64 && p.y_dtype != RSM_F32) return bad("y_dtype");
-  if (p.variant != RSM_COLS_RANDOM && p.variant != RSM_COLS_ADJACENT) return bad("variant");
+  if (p.variant != RSM_COLS_RANDOM && p.variant != RSM_COLS_ADJACENT && p.variant != RSM_ROWS_RANDOM)
+    return bad("variant");
   if (p.gram_prec < RSM_PREC_F64 || p.gram_prec > RSM_PREC_F32) return bad("gram_prec");
   if (p.solve_prec != RSM_PREC_F64 && p.solve_prec != RSM_PREC_F32) {
     if (p.solve_prec == RSM_PREC_F32X2) {
@@ -150,6 +171,12 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
     b.any_solve |= b.dv[i].solve_u;
     b.rmax = std::max(b.rmax, ps[i].r);
   }
+  b.any_coverage = false;
+  b.max_words = 0;
+  for (int i = 0; i < count; ++i) {
+    b.any_coverage |= ps[i].coverage != 0;
+    b.max_words = std::max<int64_t>(b.max_words, (ps[i].m + 31) / 32);
+  }
   // normal equations on the tensor cores: FP32 solve of FP32 Y, r small enough for one N tile
   b.tc_rb = 0;
   b.tc_npad_max = 0;
@@ -176,6 +203,20 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
   };
   auto total = [&](size_t pos) { return T[pos + count]; };
   b.o_pack = prefix([&](int i) { return ps[i].n * ((b.dv[i].ldb + 255) / 256); });
+  // method M2: row-packed mask (ceil(n/32) words x m rounded to 32, word-major) and its trials
+  auto is_rows = [&](int i) { return ps[i].variant == RSM_ROWS_RANDOM; };
+  b.o_prow = prefix([&](int i) { return is_rows(i) ? (ps[i].n + 31) / 32 * ((ps[i].m + 31) / 32 * 32) : (int64_t)0; });
+  b.prow_total = total(b.o_prow);
+  b.o_trial2 = prefix([&](int i) { return is_rows(i) ? ps[i].trials : (int64_t)0; });
+  b.trials2_total = total(b.o_trial2);
+  b.kmax2 = b.rmax2 = 0;
+  b.nmax2 = 0;
+  for (int i = 0; i < count; ++i)
+    if (is_rows(i)) {
+      b.kmax2 = std::max(b.kmax2, b.dv[i].l);
+      b.rmax2 = std::max(b.rmax2, ps[i].r);
+      b.nmax2 = std::max<int64_t>(b.nmax2, ps[i].n);
+    }
   b.pack_blocks = total(b.o_pack);
   b.o_trial = prefix([&](int i) { return ps[i].trials; });
   b.trials_total = total(b.o_trial);
@@ -261,7 +302,7 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
   }
   std::vector<int> ls;
   for (int i = 0; i < count; ++i)
-    if (slab_supported(mode, b.dv[i].l, ps[i].y_dtype)) ls.push_back(b.dv[i].l);
+    if (!is_rows(i) && slab_supported(mode, b.dv[i].l, ps[i].y_dtype)) ls.push_back(b.dv[i].l);
   std::sort(ls.begin(), ls.end());
   ls.erase(std::unique(ls.begin(), ls.end()), ls.end());
   b.slab_groups.clear();
@@ -269,18 +310,21 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
     Batch::SlabGroup g{L, T.size()};
     for (int sl = 0; sl < b.nslab; ++sl)
       prefix([&](int i) {
-        return b.dv[i].l == L && slab_supported(mode, L, ps[i].y_dtype) && (int64_t)sl * b.dv[i].slab_rows < ps[i].m
+        return !is_rows(i) && b.dv[i].l == L && slab_supported(mode, L, ps[i].y_dtype) &&
+                       (int64_t)sl * b.dv[i].slab_rows < ps[i].m
                    ? ps[i].trials
                    : (int64_t)0;
       });
     b.slab_groups.push_back(g);
   }
-  b.o_trial_generic =
-      prefix([&](int i) { return slab_supported(mode, b.dv[i].l, ps[i].y_dtype) ? (int64_t)0 : ps[i].trials; });
+  b.o_trial_generic = prefix([&](int i) {
+    return is_rows(i) || slab_supported(mode, b.dv[i].l, ps[i].y_dtype) ? (int64_t)0 : ps[i].trials;
+  });
   b.generic_total = total(b.o_trial_generic);
   b.generic_lmax = 0;
   for (int i = 0; i < count; ++i)
-    if (!slab_supported(mode, b.dv[i].l, ps[i].y_dtype)) b.generic_lmax = std::max(b.generic_lmax, b.dv[i].l);
+    if (!is_rows(i) && !slab_supported(mode, b.dv[i].l, ps[i].y_dtype))
+      b.generic_lmax = std::max(b.generic_lmax, b.dv[i].l);
 
   // workspace: all zero regions first, then all data regions, then shared partial buffers
   b.zero_off.resize(count);
@@ -362,6 +406,8 @@ void bind_batch(Batch& b, const rsm_problem* ps, unsigned char* ws) {
     d.stats = reinterpret_cast<double*>(z);
     z += s.stats;
     d.tflag = reinterpret_cast<unsigned*>(z);
+    z += s.tflag;
+    d.visited = s.visited ? reinterpret_cast<uint32_t*>(z) : nullptr;
     unsigned char* q = ws + b.data_off[i];
     auto take = [&](size_t bytes) {
       unsigned char* r = q;
@@ -384,6 +430,9 @@ void bind_batch(Batch& b, const rsm_problem* ps, unsigned char* ws) {
     d.Kmat = s.Kmat ? reinterpret_cast<double*>(take(s.Kmat)) : nullptr;
     d.NB = s.NB ? reinterpret_cast<double*>(take(s.NB)) : nullptr;
     d.Lf = s.Lf ? reinterpret_cast<float*>(take(s.Lf)) : nullptr;
+    d.rbits = s.rbits ? reinterpret_cast<uint32_t*>(take(s.rbits)) : nullptr;
+    d.ldr = (p.n + 31) / 32;
+    d.Bt = s.Bt ? reinterpret_cast<double*>(take(s.Bt)) : nullptr;
     d.tc = dv.tc ? 1 : 0;
     d.gram_fp32 = p.gram_prec == RSM_PREC_F32 ? 1 : 0;
     d.tc_npad = dv.tc_npad;

@@ -49,6 +49,12 @@ struct Batch {
   int64_t pack_blocks = 0, trials_total = 0, ent_total = 0, pad2_total = 0, nk_total = 0, part_total = 0,
           k_total = 0, tile_total = 0, row_total = 0, res_blocks = 0, b_total = 0, tc_total = 0, res4_blocks = 0;
   int64_t solve_rows = 0;  // rows of all problems that solve for U
+  bool any_coverage = false;  // some problem counts its visited entries
+  // method M2 problems: row-packing blocks, their trials, largest k, r and n
+  size_t o_prow = 0, o_trial2 = 0;
+  int64_t prow_total = 0, trials2_total = 0, nmax2 = 0;
+  int kmax2 = 0, rmax2 = 0;
+  int64_t max_words = 0;      // largest ceil(m / 32) of the batch
   int tc_rb = 0, tc_npad_max = 0;  // batch-wide V stride and largest N of the tensor-core normal equations
   int max_nblk = 0;
   // per-problem byte offsets inside the workspace

@@ -213,6 +213,13 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
             cudaSuccess)
       return cuda_fail(e, "select_gram");
     RSM_CUDA(cudaEventRecord(slot.ev[4], s));
+    if (b.any_coverage &&
+        (e = launch_coverage(D, T + b.o_trial, np, b.trials_total, b.max_words, s)) != cudaSuccess)
+      return cuda_fail(e, "coverage");
+    if (b.trials2_total > 0 &&
+        (e = launch_rows_variant(D, T + b.o_prow, b.prow_total, T + b.o_trial2, b.trials2_total, np, b.kmax2,
+                                 b.rmax2, b.nmax2, s)) != cudaSuccess)
+      return cuda_fail(e, "rows variant");
     if ((e = launch_minor_scatter(D, T + b.o_trial, np, b.trials_total, b.lmax, s)) != cudaSuccess)
       return cuda_fail(e, "minor_scatter");
     if ((e = launch_finalize_M(D, T + b.o_ent, np, b.ent_total, s)) != cudaSuccess) return cuda_fail(e, "finalize_M");
@@ -277,8 +284,9 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
   return RSM_OK;
 }
 
-// Host readback area per problem: counters (8 x u64) + stats (64 doubles).
-constexpr size_t kReadback = 8 * 8 + 64 * 8;
+// Host readback area per problem: counters (16 x u64) + stats (64 doubles).
+constexpr size_t kCountersBytes = 16 * 8;
+constexpr size_t kReadback = kCountersBytes + 64 * 8;
 
 int enqueue_readback(Batch& b, Slot& slot) {
   const ProbDesc* D = reinterpret_cast<const ProbDesc*>(slot.plan.ptr);
@@ -337,10 +345,12 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
     bool redo = false;
     for (int i = 0; i < count; ++i) {
       const unsigned long long* c = reinterpret_cast<const unsigned long long*>(hp + (size_t)i * kReadback);
-      const double* stats = reinterpret_cast<const double*>(hp + (size_t)i * kReadback + 64);
+      const double* stats = reinterpret_cast<const double*>(hp + (size_t)i * kReadback + kCountersBytes);
       const int r = ps[i].r;
       const double gap = stats[r] - stats[r - 1];
-      const double trace = given_M ? stats[kStatTrace] : (double)c[0] * b.dv[i].nm;
+      const double trace = given_M ? stats[kStatTrace]
+                           : ps[i].variant == RSM_ROWS_RANDOM ? (double)c[7]
+                                                              : (double)c[0] * b.dv[i].nm;
       const bool determined = (given_M || c[0] > 0) && stats[r] > kRankTol * trace;
       const double est = stats[34] / (gap > 0.0 ? gap : 1e-300);
       if (c[3] != 0 || (!fp64 && determined && !(est <= kEigErrTol))) redo = true;
@@ -369,7 +379,7 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
   int first_bad = RSM_OK;
   for (int i = 0; i < count; ++i) {
     const unsigned long long* c = reinterpret_cast<const unsigned long long*>(hp + (size_t)i * kReadback);
-    const double* stats = reinterpret_cast<const double*>(hp + (size_t)i * kReadback + 64);
+    const double* stats = reinterpret_cast<const double*>(hp + (size_t)i * kReadback + kCountersBytes);
     rsm_result r{};
     r.accepted_trials = (int64_t)c[0];
     r.rows_underdetermined = (int64_t)c[4];
@@ -380,7 +390,9 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
     r.n_eig = b.dv[i].kx;
     for (int k = 0; k < 32; ++k) r.eig_M[k] = k < r.n_eig ? stats[k] : 0.0;
     r.eig_residual = stats[34];
-    const double trace = given_M ? stats[kStatTrace] : (double)c[0] * b.dv[i].nm;
+    const double trace = given_M ? stats[kStatTrace]
+                         : ps[i].variant == RSM_ROWS_RANDOM ? (double)c[7]
+                                                            : (double)c[0] * b.dv[i].nm;
     r.e_known_rms = b.dv[i].solve_u ? stats[33] : NAN;
     int status = RSM_OK;
     if (c[6] != 0)
@@ -392,10 +404,18 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
     else if (c[4] > 0)
       status = RSM_ERR_ROWS_UNDERDETERMINED;
     r.status = status;
+    r.trials = ps[i].trials;
+    r.coverage = ps[i].coverage && c[1] > 0 ? (double)c[8] / (double)c[1] : NAN;
+    if (ps[i].debug_visited)
+      RSM_CUDA(cudaMemcpyAsync(ps[i].debug_visited, b.descs[i].visited, (size_t)ps[i].n * b.dv[i].ldb * 4,
+                               cudaMemcpyDeviceToDevice, slot.stream));
     for (int k = 0; k < 9; ++k) r.stage_ms[k] = ms[k];
     if (res) res[i] = r;
     if (status != RSM_OK && first_bad == RSM_OK) first_bad = status;
   }
+  bool copies = false;
+  for (int i = 0; i < count; ++i) copies |= ps[i].debug_visited != nullptr;
+  if (copies) RSM_CUDA(cudaStreamSynchronize(slot.stream));
   (void)h;
   return first_bad;
 }
@@ -408,6 +428,49 @@ int validate_all(const rsm_problem* ps, int count) {
     if (st != RSM_OK) return fail(st, "problem " + std::to_string(i) + ": " + why);
     if (ps[i].gram_prec != ps[0].gram_prec || ps[i].solve_prec != ps[0].solve_prec)
       return fail(RSM_ERR_INVALID_ARG, "all problems of a batch must share gram_prec and solve_prec");
+  }
+  return RSM_OK;
+}
+
+// Problems with trials == 0: count their known entries on the device (one small
+// kernel each, one synchronisation), then draw the number of submatrices that
+// visits each known entry with probability >= epsilon (rsm_plan_trials).  `out`
+// stays empty when every problem gives its trial count.
+int plan_missing_trials(rsm_handle* h, const rsm_problem* ps, int count, std::vector<rsm_problem>& out) {
+  bool any = false;
+  for (int i = 0; i < count; ++i) any |= ps[i].trials == 0;
+  if (!any) return RSM_OK;
+  out.assign(ps, ps + count);
+  Slot& slot = h->main;
+  int st = slot.plan.reserve((size_t)count * 8);
+  if (st != RSM_OK) return st;
+  if ((st = slot.host.reserve((size_t)count * 8)) != RSM_OK) return st;
+  unsigned long long* dcnt = static_cast<unsigned long long*>(slot.plan.ptr);
+  RSM_CUDA(cudaMemsetAsync(dcnt, 0, (size_t)count * 8, slot.stream));
+  for (int i = 0; i < count; ++i) {
+    const rsm_problem& p = ps[i];
+    if (p.trials != 0) continue;
+    if (!(p.epsilon > 0.0 && p.epsilon < 1.0))
+      return fail(RSM_ERR_INVALID_ARG, "problem " + std::to_string(i) + ": trials == 0 needs 0 < epsilon < 1");
+    if (p.debug_cols || p.debug_row_counts || p.debug_Z)
+      return fail(RSM_ERR_INVALID_ARG, "problem " + std::to_string(i) + ": planned trials exclude per-trial debug outputs");
+    if (!p.W || p.m < 1 || p.n < 1 || p.ldw < p.m)
+      return fail(RSM_ERR_INVALID_ARG, "problem " + std::to_string(i) + ": W, m, n, ldw");
+    RSM_CUDA(launch_count_known(p.W, p.ldw, p.m, p.n, dcnt + i, slot.stream));
+  }
+  RSM_CUDA(cudaMemcpyAsync(slot.host.ptr, dcnt, (size_t)count * 8, cudaMemcpyDeviceToHost, slot.stream));
+  RSM_CUDA(cudaStreamSynchronize(slot.stream));
+  const unsigned long long* known = static_cast<const unsigned long long*>(slot.host.ptr);
+  for (int i = 0; i < count; ++i) {
+    if (ps[i].trials != 0) continue;
+    const rsm_problem& p = ps[i];
+    const double rho = (double)known[i] / ((double)p.m * (double)p.n);
+    const int32_t size = p.l ? p.l : p.r + 1;
+    rsm_trial_plan plan{};
+    if (rho <= 0.0 || rsm_plan_trials(p.m, p.n, rho, p.r, size, p.variant, p.epsilon, &plan) != RSM_OK ||
+        !(plan.trials < 68719476736.0))
+      return fail(RSM_ERR_INVALID_ARG, "problem " + std::to_string(i) + ": no trial count reaches epsilon");
+    out[i].trials = std::max<int64_t>(1, (int64_t)std::ceil(plan.trials));
   }
   return RSM_OK;
 }
@@ -478,19 +541,16 @@ int32_t rsm_create(const rsm_config* config, rsm_handle** out) {
   return RSM_OK;
 }
 
-int32_t rsm_decompose_batch(rsm_handle* h, const rsm_problem* ps, int32_t count, rsm_result* res) {
-  if (!h || !ps || count < 1) return fail(RSM_ERR_INVALID_ARG, "handle, problems and count >= 1 are required");
-  int st = validate_all(ps, count);
-  if (st != RSM_OK) return st;
+int32_t rsm_decompose_batch(rsm_handle* h, const rsm_problem* ps_in, int32_t count, rsm_result* res) {
+  if (!h || !ps_in || count < 1) return fail(RSM_ERR_INVALID_ARG, "handle, problems and count >= 1 are required");
   std::lock_guard<std::mutex> lk(h->api_mu);
   DeviceGuard dg(h->device);
   RSM_CUDA(dg.err);
-  size_t need = 0;
-  for (int i = 0; i < count; ++i) need += rsm_footprint_bytes(&ps[i]);
-  if (need > h->budget) return fail(RSM_ERR_NO_MEMORY, "batch footprint above the handle's HBM budget");
-  if (h->fault & RSM_FAULT_ALLOC) {
-    h->fault &= ~RSM_FAULT_ALLOC;
-    return fail(RSM_ERR_NO_MEMORY, "injected allocation failure");
+  bool planning = false;
+  for (int i = 0; i < count; ++i) planning |= ps_in[i].trials == 0;
+  if (!planning) {
+    int st = validate_all(ps_in, count);
+    if (st != RSM_OK) return st;
   }
   if (h->main.own_stream) {
     // the handle's own stream does not order with the caller's work: start
@@ -498,6 +558,21 @@ int32_t rsm_decompose_batch(rsm_handle* h, const rsm_problem* ps, int32_t count,
     // turn waits for the caller's blocking streams)
     RSM_CUDA(cudaEventRecord(h->main.ev_order, nullptr));
     RSM_CUDA(cudaStreamWaitEvent(h->main.stream, h->main.ev_order, 0));
+  }
+  std::vector<rsm_problem> planned;
+  const rsm_problem* ps = ps_in;
+  int st = plan_missing_trials(h, ps_in, count, planned);
+  if (st != RSM_OK) return st;
+  if (!planned.empty()) {
+    ps = planned.data();
+    if ((st = validate_all(ps, count)) != RSM_OK) return st;
+  }
+  size_t need = 0;
+  for (int i = 0; i < count; ++i) need += rsm_footprint_bytes(&ps[i]);
+  if (need > h->budget) return fail(RSM_ERR_NO_MEMORY, "batch footprint above the handle's HBM budget");
+  if (h->fault & RSM_FAULT_ALLOC) {
+    h->fault &= ~RSM_FAULT_ALLOC;
+    return fail(RSM_ERR_NO_MEMORY, "injected allocation failure");
   }
   return run_batch(h, h->main, ps, count, res);
 }

@@ -18,7 +18,7 @@ import torch
 from . import _abi
 from ._abi import rsm_config, rsm_problem, rsm_result
 
-_VARIANT = {"random": _abi.RSM_COLS_RANDOM, "adjacent": _abi.RSM_COLS_ADJACENT}
+_VARIANT = {"random": _abi.RSM_COLS_RANDOM, "adjacent": _abi.RSM_COLS_ADJACENT, "rows": _abi.RSM_ROWS_RANDOM}
 _PREC = {"f64": _abi.RSM_PREC_F64, "f32x2": _abi.RSM_PREC_F32X2, "f32": _abi.RSM_PREC_F32}
 
 
@@ -72,12 +72,15 @@ class Result:
     stage_ms: dict
     queue_ms: float
     run_ms: float
+    coverage: float = float("nan")
+    trials: int = 0
     V: Optional[torch.Tensor] = None
     U: Optional[torch.Tensor] = None
     cols: Optional[torch.Tensor] = None
     row_counts: Optional[torch.Tensor] = None
     Z: Optional[torch.Tensor] = None
     M: Optional[torch.Tensor] = None
+    visited: Optional[torch.Tensor] = None
 
     @property
     def ok(self) -> bool:
@@ -90,7 +93,7 @@ def _result(res: rsm_result, outs: dict) -> Result:
                   eig_factor_bits=res.eig_factor_bits, eig_iterations=res.eig_iterations, eig_M=[res.eig_M[i] for i in range(res.n_eig)],
                   eig_residual=res.eig_residual, e=res.e_known_rms,
                   stage_ms={k: float(res.stage_ms[i]) for i, k in enumerate(_abi.STAGES)}, queue_ms=res.queue_ms,
-                  run_ms=res.run_ms, **outs)
+                  run_ms=res.run_ms, coverage=res.coverage, trials=res.trials, **outs)
 
 
 class Problem:
@@ -104,7 +107,8 @@ class Problem:
     def __init__(self, Y: torch.Tensor, W: torch.Tensor, r: int, *, trials: int, l: int = 0, n_minor: int = 0,
                  seed: int = 0, problem_id: int = 0, variant: str = "random", gram: str = "f64", solve: str = "f64",
                  want_U: bool = True, debug: bool = False, U: Optional[torch.Tensor] = None,
-                 V: Optional[torch.Tensor] = None):
+                 V: Optional[torch.Tensor] = None, epsilon: float = 0.0, coverage: bool = False,
+                 visited: bool = False):
         if not (Y.is_cuda and W.is_cuda):
             raise ValueError("Y and W must be CUDA tensors")
         if Y.dtype not in (torch.float64, torch.float32) or W.dtype != torch.uint8:
@@ -116,7 +120,12 @@ class Problem:
         self.U = (U if U is not None else torch.empty((r, m), dtype=torch.float64, device=dev).t()) if want_U else None
         ll = l if l else r + 1
         nm = n_minor if n_minor else ll - r
-        self.cols = self.row_counts = self.Z = self.M = None
+        self.cols = self.row_counts = self.Z = self.M = self.visited = None
+        if trials == 0 and debug:
+            raise ValueError("planned trials (trials=0) exclude the per-trial debug outputs")
+        if visited:
+            ldb = ((m + 31) // 32 + 3) // 4 * 4
+            self.visited = torch.empty((n, ldb), dtype=torch.int32, device=dev)
         if debug:
             self.cols = torch.empty((trials, ll), dtype=torch.int32, device=dev)
             self.row_counts = torch.empty(trials, dtype=torch.int32, device=dev)
@@ -133,6 +142,10 @@ class Problem:
         p.V, p.ldv = self.V.data_ptr(), _ld(self.V)
         if self.U is not None:
             p.U, p.ldu = self.U.data_ptr(), _ld(self.U)
+        p.epsilon = epsilon
+        p.coverage = 1 if (coverage or visited) else 0
+        if visited:
+            p.debug_visited = self.visited.data_ptr()
         if debug:
             p.debug_cols = self.cols.data_ptr()
             p.debug_row_counts = self.row_counts.data_ptr()
@@ -141,9 +154,11 @@ class Problem:
         self.c = p
 
     def outputs(self) -> dict:
-        return dict(V=self.V, U=self.U, cols=self.cols, row_counts=self.row_counts, Z=self.Z, M=self.M)
+        return dict(V=self.V, U=self.U, cols=self.cols, row_counts=self.row_counts, Z=self.Z, M=self.M,
+                    visited=self.visited)
 
     def footprint_bytes(self) -> int:
+        """Device bytes the library needs for this problem (0 while trials is left to the planner)."""
         return int(lib().rsm_footprint_bytes(C.byref(self.c)))
 
 
