@@ -322,6 +322,30 @@ def oracle_golden(p):
     return {k: g[k] for k in g.files}
 
 
+def gather_probe(dev, stream) -> float:
+    """Random 4-byte loads per second from a 32 MiB L2-resident buffer (rsm_probe_gather), best of 5."""
+    import torch
+
+    import paper_1411_0814_gb300 as rsm
+    lib = rsm.lib()
+    buf = torch.rand(1 << 23, device=dev)
+    blocks, per = 152 * 16, 256
+    out = torch.empty(blocks * 256, device=dev)
+    best = None
+    for k in range(7):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = lib.rsm_probe_gather(buf.data_ptr(), buf.numel(), blocks, per, out.data_ptr(), stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if st != 0:
+            return None
+        if k >= 2:
+            rate = blocks * 256 * per / (e0.elapsed_time(e1) * 1e-3)
+            best = rate if best is None else max(best, rate)
+    return best
+
+
 def subspace_angle_np(a, b) -> float:
     qa, _ = np.linalg.qr(a)
     qb, _ = np.linalg.qr(b)
@@ -476,13 +500,26 @@ def bench_mine(args):
     trec = traffic_record("k_gram_slab_paper_131072x1024.md")
     launches = trec["launches_per_step"] if trec else 16  # row slabs of 32 MiB of FP32 Y
     traffic = trec["dram_bytes_per_launch"] if trec else None
+    # the gather ceiling: random 4-byte loads from an L2-resident 32 MiB buffer (rsm_probe_gather),
+    # measured here; the slab Gram issues one such load per gathered element plus its mask reads
+    gather = gather_probe(dev, stream)
+    mask_sectors = p.trials * p.l * ((p.m + 31) // 32) / 8  # 32 consecutive words = 4 sectors per warp load
+    gathers = last.rows_selected * p.l + mask_sectors
+    gather_rate = gathers / (sg_ms * 1e-3)
     roofline = {"kernel": "k_gram_slab<2,9> (row-slab selection + FP32 Gram)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "algorithmic_bytes_per_launch": int(alg_bytes / launches), "launches_per_step": launches,
                 "launch_ms": round(sg_ms / launches, 4), "peak_source": peaks["source"] + " (copy bandwidth)",
+                "gather_ceiling": {"achieved_loads_per_s": gather_rate, "peak_loads_per_s": gather,
+                                   "frac": gather_rate / gather if gather else None,
+                                   "loads_per_step": gathers,
+                                   "peak_source": "rsm_probe_gather, measured in this run (random 4-byte loads "
+                                                  "from a 32 MiB L2-resident buffer)"},
                 "note": "traffic (DRAM bytes per launch, ncu) is ~10x below the algorithmic bytes: the slab "
-                        "schedule serves repeated reads from L2; the kernel is bound by L2 sector reads"}
+                        "schedule serves repeated reads from L2.  Every gathered element is its own 32-byte "
+                        "sector; the GPU serves about one such L1 miss per clock per SM (gather_ceiling.peak), "
+                        "which bounds this kernel"}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -295,6 +295,15 @@ int32_t rsm_eig_smallest(rsm_handle* h, const double* M, int64_t n, int32_t r, d
  * sqrt(x) (0 for x < 0).  Asynchronous on stream. */
 int32_t rsm_check_fp64_math(const double* x, int64_t count, double* out, void* stream);
 
+/* Gather-rate probe (measurement only; the paper has no counterpart): the
+ * ceiling of the row-slab Gram's access pattern.  blocks x 256 threads each
+ * issue per_thread (a multiple of 8) 4-byte loads at pseudo-random positions of
+ * buf (device, elems floats, a power of two >= 1024; size it to stay in L2).
+ * out: device, blocks x 256 floats, written only to keep the loads alive.  Time
+ * it with events on `stream`: loads per second = blocks 256 per_thread / time. */
+int32_t rsm_probe_gather(const float* buf, int64_t elems, int64_t blocks, int32_t per_thread, float* out,
+                         void* stream);
+
 /* e = sqrt(sum over known (y_ij - u_i . v_j)^2 / number of known entries) for a
  * given U and V, computed without allocating device memory.  The paper has no
  * counterpart: this entry point is for callers that cannot allocate at the
