@@ -323,7 +323,7 @@ def oracle_golden(p):
 
 
 def gather_probe(dev, stream) -> float:
-    """Random 4-byte loads per second from a 32 MiB L2-resident buffer (rsm_probe_gather), best of 5."""
+    """L2 sectors per second read from random lines of a 32 MiB L2-resident buffer (rsm_probe_gather), best of 5."""
     import torch
 
     import paper_1411_0814_gb300 as rsm
@@ -500,26 +500,27 @@ def bench_mine(args):
     trec = traffic_record("k_gram_slab_paper_131072x1024.md")
     launches = trec["launches_per_step"] if trec else 16  # row slabs of 32 MiB of FP32 Y
     traffic = trec["dram_bytes_per_launch"] if trec else None
-    # the gather ceiling: random 4-byte loads from an L2-resident 32 MiB buffer (rsm_probe_gather),
-    # measured here; the slab Gram issues one such load per gathered element plus its mask reads
+    # the L2 sector ceiling (rsm_probe_gather, measured here) against the slab Gram's sectors: per
+    # trial and column, the 8-row sectors that hold a selected row (rows selected with probability
+    # q = p_t / m: a fraction 1 - (1 - q)^8 of the m / 8 sectors), plus the mask words (8 per sector)
     gather = gather_probe(dev, stream)
-    mask_sectors = p.trials * p.l * ((p.m + 31) // 32) / 8  # 32 consecutive words = 4 sectors per warp load
-    gathers = last.rows_selected * p.l + mask_sectors
+    q = last.rows_selected / (p.trials * p.m)
+    mask_sectors = p.trials * p.l * ((p.m + 31) // 32) / 8
+    gathers = p.trials * p.l * (p.m / 8.0) * (1.0 - (1.0 - q) ** 8) + mask_sectors
     gather_rate = gathers / (sg_ms * 1e-3)
     roofline = {"kernel": "k_gram_slab<2,9> (row-slab selection + FP32 Gram)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "algorithmic_bytes_per_launch": int(alg_bytes / launches), "launches_per_step": launches,
                 "launch_ms": round(sg_ms / launches, 4), "peak_source": peaks["source"] + " (copy bandwidth)",
-                "gather_ceiling": {"achieved_loads_per_s": gather_rate, "peak_loads_per_s": gather,
-                                   "frac": gather_rate / gather if gather else None,
-                                   "loads_per_step": gathers,
-                                   "peak_source": "rsm_probe_gather, measured in this run (random 4-byte loads "
-                                                  "from a 32 MiB L2-resident buffer)"},
+                "l2_sector_ceiling": {"achieved_sectors_per_s": gather_rate, "peak_sectors_per_s": gather,
+                                      "frac": gather_rate / gather if gather else None,
+                                      "sectors_per_step": gathers,
+                                      "peak_source": "rsm_probe_gather, measured in this run (32-byte sectors of "
+                                                     "random 128-byte lines of a 32 MiB L2-resident buffer)"},
                 "note": "traffic (DRAM bytes per launch, ncu) is ~10x below the algorithmic bytes: the slab "
-                        "schedule serves repeated reads from L2.  Every gathered element is its own 32-byte "
-                        "sector; the GPU serves about one such L1 miss per clock per SM (gather_ceiling.peak), "
-                        "which bounds this kernel"}
+                        "schedule serves repeated reads from L2.  A gathered element costs a 32-byte sector "
+                        "(rows chosen by data), so the kernel is bound by L2 sector reads: l2_sector_ceiling"}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

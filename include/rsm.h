@@ -128,7 +128,18 @@ typedef struct rsm_problem {
                                 entry is visited with probability >= epsilon (0 < epsilon < 1); debug_cols,
                                 debug_row_counts and debug_Z must then be NULL.  rsm_submit needs trials >= 1. */
   int32_t coverage;          /* 1: count the known entries that the accepted draws visit (rsm_result.coverage) */
+  int32_t norm;              /* 2 (or 0): the L2 forms of eqs. solve.barV and solve.barU; 1: their L1 forms
+                                (Section IV-A eq. solve.barV_L1_norm; column variants, r <= 8), read as
+                                min sum_j ||V^T xi_j||_2 over the null vectors (rotation-invariant) and
+                                per-row least absolute deviations, each by irls_iters steps of iteratively
+                                reweighted least squares from the L2 solution.  All problems of a batch
+                                share it. */
+  int32_t irls_iters;        /* L1 forms: reweighting steps of V-hat and of U-hat (0 -> 8) */
   int32_t reserved;
+  double irls_delta_v;       /* L1 form of V-hat: weights delta / max(||V^T xi||, delta) (0 -> 1e-4); a
+                                smaller delta is more robust to outliers but leaves the reweighted M less
+                                well conditioned */
+  double irls_delta_u;       /* L1 form of U-hat: delta = irls_delta_u * e of the L2 solution (0 -> 1e-3) */
   uint32_t* debug_visited;   /* optional device output with coverage = 1: the visited entries as a packed
                                 mask, n columns of ldb = 4 ceil(ceil(m / 32) / 4) uint32 words, bit (i mod 32)
                                 of word i / 32 of column j set iff entry (i, j) was visited */
@@ -295,12 +306,14 @@ int32_t rsm_eig_smallest(rsm_handle* h, const double* M, int64_t n, int32_t r, d
  * sqrt(x) (0 for x < 0).  Asynchronous on stream. */
 int32_t rsm_check_fp64_math(const double* x, int64_t count, double* out, void* stream);
 
-/* Gather-rate probe (measurement only; the paper has no counterpart): the
+/* L2 sector-read probe (measurement only; the paper has no counterpart): the
  * ceiling of the row-slab Gram's access pattern.  blocks x 256 threads each
- * issue per_thread (a multiple of 8) 4-byte loads at pseudo-random positions of
- * buf (device, elems floats, a power of two >= 1024; size it to stay in L2).
- * out: device, blocks x 256 floats, written only to keep the loads alive.  Time
- * it with events on `stream`: loads per second = blocks 256 per_thread / time. */
+ * issue per_thread (a multiple of 16) 4-byte loads; each group of 4 lanes reads
+ * the 4 sectors of one pseudo-random 128-byte line of buf (device, elems floats,
+ * a power of two >= 1024; size it to stay in L2), so every load is one 32-byte
+ * sector.  out: device, blocks x 256 floats, written only to keep the loads
+ * alive.  Time it with events on `stream`: sectors per second =
+ * blocks 256 per_thread / time. */
 int32_t rsm_probe_gather(const float* buf, int64_t elems, int64_t blocks, int32_t per_thread, float* out,
                          void* stream);
 

@@ -14,6 +14,8 @@ Parity status per function (what pins it is listed in the tests):
   accumulate_M                pinned (trace, PSD, symmetry, M V_bar = 0)
   eig_smallest                pinned (exact noiseless recovery, rho = 1 dense-SVD case)
   underdetermined             pinned (designed spectra either side of the threshold, rank-deficient Xi)
+  robust.*                    pinned (noiseless exact recovery, monotone IRLS objectives, robustness
+                              to gross outliers against the L2 form, fixed-point property)
   planner.*                   pinned (Lemma 1 against the binomial CDF, Monte Carlo visit frequency,
                               bound ordering, brute-force visited sets)
   solve_U                     pinned (noiseless reconstruction, rho = 1 closed form)
@@ -24,6 +26,7 @@ Parity status per function (what pins it is listed in the tests):
 """
 from .philox import philox4x32_10, trial_words, bounded  # noqa: F401
 from . import planner  # noqa: F401
+from . import robust  # noqa: F401
 from .rsm import (  # noqa: F401
     sample_columns, select_rows, minor_vectors, extend, accumulate_M, eig_smallest, solve_U,
     residual, decompose, subspace_angle, underdetermined, OracleResult, STATUS_OK, STATUS_UNDERDETERMINED,

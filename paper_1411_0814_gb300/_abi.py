@@ -69,7 +69,11 @@ class rsm_problem(C.Structure):
         ("debug_M", C.c_void_p),
         ("epsilon", C.c_double),
         ("coverage", C.c_int32),
+        ("norm", C.c_int32),
+        ("irls_iters", C.c_int32),
         ("reserved", C.c_int32),
+        ("irls_delta_v", C.c_double),
+        ("irls_delta_u", C.c_double),
         ("debug_visited", C.c_void_p),
     ]
 

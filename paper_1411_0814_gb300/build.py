@@ -17,7 +17,7 @@ OUT = os.path.join(HERE, "librsm.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["k_sample.cu", "k_gram.cu", "k_gram_slab.cu", "k_minor.cu", "k_eig.cu", "k_solve.cu",
-           "k_normal_tc.cu", "k_rows.cu", "k_probe.cu", "k_noalloc.cu", "k_util.cu", "plan.cpp", "planner.cpp", "rsm_api.cpp"]
+           "k_normal_tc.cu", "k_rows.cu", "k_robust.cu", "k_probe.cu", "k_noalloc.cu", "k_util.cu", "plan.cpp", "planner.cpp", "rsm_api.cpp"]
 
 
 def _nvcc() -> str:

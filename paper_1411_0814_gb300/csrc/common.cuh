@@ -54,6 +54,12 @@ struct ProbDesc {
   uint32_t* rbits;
   int64_t ldr;
   double* Bt;
+  // L1 forms: each trial's minor vectors (trials x l x n_minor, zero for rejected trials), the
+  // reweighting parameters; the eigen stage then reads trace(M) from stats[kStatTrace]
+  double* Zst;
+  int32_t l1;
+  int32_t irls_iters;
+  double delta_v, delta_u;
   unsigned* tflag;               // 3 nblk^2 tile states of the factor launch (zeroed before it)
   int32_t* colcount;             // n: how many trials drew each column
   double* stats;                 // [0..31] eigenvalues, [32] residual num, [33] e, [34] eig residual

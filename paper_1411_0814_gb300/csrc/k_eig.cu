@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256) k_eig_prep(const ProbDesc* __restrict__ d
   const uint32_t i = e0 / np, j0 = e0 - i * np;
   // tau = shift_rel * trace(M) / n, trace(M) = accepted trials * n_minor, or computed from a
   // caller-supplied M (a shift: FP32 suffices for the mean)
-  const float meanf = d.m_given        ? (float)(d.stats[kStatTrace] / (double)n)
+  const float meanf = d.m_given || d.l1 ? (float)(d.stats[kStatTrace] / (double)n)
                       : d.variant == 2 ? (float)d.counters[7] / (float)n
                                        : (float)d.counters[0] * (float)d.n_minor / (float)n;
   const double tau = meanf > 0.f ? shift_rel * (double)meanf : 1.0;

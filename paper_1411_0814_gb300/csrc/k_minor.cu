@@ -143,6 +143,8 @@ __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDe
   if (count < l) {  // rejected trial (fewer than l rows, i.e. not more than r)
     if (d.debug_Z)
       for (int i = lane; i < l * d.n_minor; i += 32) d.debug_Z[t * l * d.n_minor + i] = 0.0;
+    if (d.Zst)
+      for (int i = lane; i < l * d.n_minor; i += 32) d.Zst[t * l * d.n_minor + i] = 0.0;
     return;
   }
   if (lane == 0) atomicAdd(&d.counters[0], 1ull);
@@ -226,6 +228,8 @@ __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDe
 
   if (d.debug_Z)
     for (int it = lane; it < l * nm; it += 32) d.debug_Z[t * l * nm + it] = Z[it];
+  if (d.Zst)  // kept for the reweighting steps of the L1 form
+    for (int it = lane; it < l * nm; it += 32) d.Zst[t * l * nm + it] = Z[it];
 
   // scatter Z Z^T into M[C_t, C_t] in fixed point
   const int f = macc_frac_bits(d.counters[2]);

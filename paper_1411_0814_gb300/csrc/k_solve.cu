@@ -341,7 +341,7 @@ constexpr int kResRows = 32;
 constexpr int kResCols = 64;
 template <typename T, int RM>
 __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
-                                                 int nprob, double* __restrict__ partial) {
+                                                 int nprob, double* __restrict__ partial, int refine) {
   constexpr bool kRefine = sizeof(T) == 4;
   __shared__ __align__(16) T vs[kResCols][RM];  // zero past r, so the products need no guard
   __shared__ float cred[kRefine ? kResRows : 1][RM + 1];
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ d
         for (int a = 0; a < RM; ++a) cred[lane][a] = (w == 0 ? 0.f : cred[lane][a]) + cacc[a];
       __syncthreads();
     }
-    if (wg == 0 && row_in) {
+    if (wg == 0 && row_in && refine) {
       float c[RM], u32[RM];
 #pragma unroll
       for (int a = 0; a < RM; ++a) {
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ d
 constexpr int kRes4Rows = 128;
 template <int RM>
 __global__ void __launch_bounds__(256) k_residual4(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
-                                                  int nprob, double* __restrict__ partial) {
+                                                  int nprob, double* __restrict__ partial, int refine) {
   __shared__ __align__(16) float vs[kResCols][RM];
   __shared__ float cred[kRes4Rows][RM + 1];
   __shared__ double red[8];
@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(256) k_residual4(const ProbDesc* __restrict__ 
         for (int a = 0; a < RM; ++a) cred[4 * lane + k][a] = (w == 0 ? 0.f : cred[4 * lane + k][a]) + cacc[k][a];
     __syncthreads();
   }
-  if (threadIdx.x < kRes4Rows && i0 + threadIdx.x < m) {
+  if (refine && threadIdx.x < kRes4Rows && i0 + threadIdx.x < m) {
     const uint32_t row = i0 + threadIdx.x;
     float c[RM], u32[RM];
 #pragma unroll
@@ -610,11 +610,12 @@ cudaError_t launch_solve_u(const SolvePlan& S, int mode, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_residual(const SolvePlan& S, int mode, double* partial, cudaStream_t s) {
+cudaError_t launch_residual(const SolvePlan& S, int mode, double* partial, cudaStream_t s, bool refine) {
   const ProbDesc* D = S.descs;
   const int np = S.nprob;
+  const int rf = refine ? 1 : 0;
   if (S.res_blocks > 0) {
-#define RSM_RES(T, RM) k_residual<T, RM><<<(unsigned)S.res_blocks, 256, 0, s>>>(D, S.res_off, np, partial)
+#define RSM_RES(T, RM) k_residual<T, RM><<<(unsigned)S.res_blocks, 256, 0, s>>>(D, S.res_off, np, partial, rf)
     if (mode == 0) {
       if (S.rmax <= 8) RSM_RES(double, 8); else if (S.rmax <= 16) RSM_RES(double, 16); else RSM_RES(double, 32);
     } else {
@@ -624,7 +625,7 @@ cudaError_t launch_residual(const SolvePlan& S, int mode, double* partial, cudaS
     ++g_kernel_launches;
   }
   if (S.res4_blocks > 0) {  // problems with r <= 8 only
-    k_residual4<8><<<(unsigned)S.res4_blocks, 256, 0, s>>>(D, S.res4_off, np, partial + S.res_blocks);
+    k_residual4<8><<<(unsigned)S.res4_blocks, 256, 0, s>>>(D, S.res4_off, np, partial + S.res_blocks, rf);
     ++g_kernel_launches;
   }
   cudaError_t e = cudaGetLastError();

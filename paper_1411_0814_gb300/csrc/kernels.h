@@ -108,6 +108,10 @@ cudaError_t launch_finalize_M(const ProbDesc* descs, const int64_t* ent_off, int
 cudaError_t launch_eig(const EigPlan& P, bool fp64_factor, double shift_rel, int iters, cudaStream_t s);
 cudaError_t launch_trace_M(const ProbDesc* descs, int nprob, cudaStream_t s);
 cudaError_t launch_solve_u(const SolvePlan& S, int mode, cudaStream_t s);
-cudaError_t launch_residual(const SolvePlan& S, int mode, double* partial, cudaStream_t s);
+cudaError_t launch_residual(const SolvePlan& S, int mode, double* partial, cudaStream_t s, bool refine = true);
+cudaError_t launch_l1_scatter(const ProbDesc* descs, const int64_t* trial_off, int nprob, int64_t total,
+                              cudaStream_t s);
+cudaError_t launch_irls_u(const ProbDesc* descs, const int64_t* row_off, int nprob, int64_t total, int rmax,
+                          bool fp64, cudaStream_t s);
 
 }  // namespace rsm

@@ -18,7 +18,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Sizes {
   size_t macc, counters, colcount, stats, tflag, visited;    // zero region
-  size_t bits, cols, rowc, gram, M, Mdf, F1, F2, Dinv, X, MX, R, small, Kmat, NB, Lf, rbits, Bt;  // data region
+  size_t bits, cols, rowc, gram, M, Mdf, F1, F2, Dinv, X, MX, R, small, Kmat, NB, Lf, rbits, Bt, Zst;  // data region
 };
 
 Sizes sizes_of(const rsm_problem& p, const Derived& dv) {
@@ -53,6 +53,8 @@ Sizes sizes_of(const rsm_problem& p, const Derived& dv) {
   s.gram = rows ? 0 : s.gram;
   s.rbits = rows ? align_up(m * (size_t)((n + 31) / 32) * 4) : 0;
   s.Bt = rows ? align_up(I * (size_t)dv.l * p.r * 8) : 0;
+  // the L1 forms keep every trial's minor vectors for the reweighting steps
+  s.Zst = p.norm == 1 ? align_up(I * (size_t)dv.l * dv.nm * 8) : 0;
   // the FP32 normal equations keep each row's factor for the refinement step of the residual pass
   s.Lf = dv.solve_u && p.solve_prec == RSM_PREC_F32 ? align_up(m * (size_t)(p.r * (p.r + 1) / 2) * 4) : 0;
   return s;
@@ -61,7 +63,7 @@ Sizes sizes_of(const rsm_problem& p, const Derived& dv) {
 size_t zero_sum(const Sizes& s) { return s.macc + s.counters + s.colcount + s.stats + s.tflag + s.visited; }
 size_t data_sum(const Sizes& s) {
   return s.bits + s.cols + s.rowc + s.gram + s.M + s.Mdf + s.F1 + s.F2 + s.Dinv + s.X + s.MX + s.R + s.small + s.Kmat +
-         s.NB + s.Lf + s.rbits + s.Bt;
+         s.NB + s.Lf + s.rbits + s.Bt + s.Zst;
 }
 size_t part_doubles(const rsm_problem& p, const Derived& dv) {
   return (size_t)((p.n + 63) / 64) * 2 * dv.kx * dv.kx;  // chunks of kChunk = 64 rows (k_eig.cu)
@@ -105,6 +107,11 @@ int validate_problem(const rsm_problem& p, Derived& dv, std::string* why) {
   }
   if (p.trials < 1 || p.trials > (int64_t)1 << 36) return bad("need 1 <= trials <= 2^36");
   if (p.coverage != 0 && p.coverage != 1) return bad("coverage must be 0 or 1");
+  if (p.norm != 0 && p.norm != 1 && p.norm != 2) return bad("norm must be 1 (L1) or 2 (L2)");
+  if (p.norm == 1 && p.variant == RSM_ROWS_RANDOM) return bad("the L1 forms need a column variant");
+  if (p.norm == 1 && p.r > 8) return bad("the L1 forms support r <= 8");
+  if (p.irls_iters < 0 || p.irls_iters > 1000 || p.irls_delta_v < 0.0 || p.irls_delta_u < 0.0)
+    return bad("irls_iters in 0..1000, irls_delta_v and irls_delta_u >= 0");
   if (p.debug_visited && !p.coverage) return bad("debug_visited needs coverage = 1");
   if (p.ldy < p.m || p.ldw < p.m || p.ldv < p.n) return bad("leading dimensions too small");
   if (p.U && p.ldu < p.m) return bad("ldu < m");
@@ -171,6 +178,8 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
     b.any_solve |= b.dv[i].solve_u;
     b.rmax = std::max(b.rmax, ps[i].r);
   }
+  b.l1 = ps[0].norm == 1;
+  b.irls_iters = ps[0].irls_iters ? ps[0].irls_iters : 8;
   b.any_coverage = false;
   b.max_words = 0;
   for (int i = 0; i < count; ++i) {
@@ -286,6 +295,8 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
   b.solve_rows = 0;
   for (int i = 0; i < count; ++i)
     if (b.dv[i].solve_u) b.solve_rows += ps[i].m;
+  b.o_urow = prefix([&](int i) { return b.dv[i].solve_u ? (ps[i].m + 127) / 128 * 128 : (int64_t)0; });
+  b.urow_total = total(b.o_urow);
   b.o_res = prefix([&](int i) { return res4_of(ps[i], b.dv[i]) ? (int64_t)0 : (int64_t)res_blocks_of(ps[i], b.dv[i]); });
   b.res_blocks = total(b.o_res);
   b.o_res4 = prefix([&](int i) { return res4_of(ps[i], b.dv[i]) ? (int64_t)res_blocks_of(ps[i], b.dv[i]) : (int64_t)0; });
@@ -433,6 +444,11 @@ void bind_batch(Batch& b, const rsm_problem* ps, unsigned char* ws) {
     d.rbits = s.rbits ? reinterpret_cast<uint32_t*>(take(s.rbits)) : nullptr;
     d.ldr = (p.n + 31) / 32;
     d.Bt = s.Bt ? reinterpret_cast<double*>(take(s.Bt)) : nullptr;
+    d.Zst = s.Zst ? reinterpret_cast<double*>(take(s.Zst)) : nullptr;
+    d.l1 = p.norm == 1 ? 1 : 0;
+    d.irls_iters = p.irls_iters ? p.irls_iters : 8;
+    d.delta_v = p.irls_delta_v > 0.0 ? p.irls_delta_v : 1e-4;
+    d.delta_u = p.irls_delta_u > 0.0 ? p.irls_delta_u : 1e-3;
     d.tc = dv.tc ? 1 : 0;
     d.gram_fp32 = p.gram_prec == RSM_PREC_F32 ? 1 : 0;
     d.tc_npad = dv.tc_npad;

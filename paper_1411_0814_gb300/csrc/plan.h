@@ -50,6 +50,10 @@ struct Batch {
           k_total = 0, tile_total = 0, row_total = 0, res_blocks = 0, b_total = 0, tc_total = 0, res4_blocks = 0;
   int64_t solve_rows = 0;  // rows of all problems that solve for U
   bool any_coverage = false;  // some problem counts its visited entries
+  bool l1 = false;            // the L1 forms (all problems of the batch)
+  int irls_iters = 0;
+  size_t o_urow = 0;          // m per solving problem (IRLS of U)
+  int64_t urow_total = 0;
   // method M2 problems: row-packing blocks, their trials, largest k, r and n
   size_t o_prow = 0, o_trial2 = 0;
   int64_t prow_total = 0, trials2_total = 0, nmax2 = 0;

@@ -190,6 +190,17 @@ struct rsm_handle {
 
 namespace {
 
+// Zero what the factor launch needs zeroed before it runs again: the claim
+// counter and abort word, every problem's tile states and factor-failure flag.
+int reset_eig_state(Batch& b, Slot& slot) {
+  RSM_CUDA(cudaMemsetAsync(static_cast<unsigned char*>(slot.ws.ptr) + b.sync_off, 0, b.sync_bytes, slot.stream));
+  for (int i = 0; i < b.nprob; ++i) {
+    RSM_CUDA(cudaMemsetAsync(b.descs[i].counters + 3, 0, 8, slot.stream));
+    RSM_CUDA(cudaMemsetAsync(b.descs[i].tflag, 0, (size_t)3 * b.dv[i].nblk * b.dv[i].nblk * 4, slot.stream));
+  }
+  return RSM_OK;
+}
+
 // Launch every stage of one batch on slot.stream.  The workspace and plan
 // buffers of the slot must already hold the batch.  Does not synchronise.
 int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool do_front) {
@@ -223,6 +234,7 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
     if ((e = launch_minor_scatter(D, T + b.o_trial, np, b.trials_total, b.lmax, s)) != cudaSuccess)
       return cuda_fail(e, "minor_scatter");
     if ((e = launch_finalize_M(D, T + b.o_ent, np, b.ent_total, s)) != cudaSuccess) return cuda_fail(e, "finalize_M");
+    if (b.l1 && (e = launch_trace_M(D, np, s)) != cudaSuccess) return cuda_fail(e, "trace_M");
     RSM_CUDA(cudaEventRecord(slot.ev[5], s));
   }
   EigPlan ep{};
@@ -248,6 +260,23 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
   ep.fault_wait = slot.fault_wait;
   if ((e = launch_eig(ep, fp64_factor, shift_rel, fp64_factor ? kEigIters64 : kEigIters32, s)) != cudaSuccess)
     return cuda_fail(e, "eig");
+  if (b.l1) {
+    // the L1 form of V-hat: reweight the stored minor vectors by the current V,
+    // rebuild M_w and solve it again, irls_iters times (k_robust.cu)
+    for (int it = 0; it < b.irls_iters; ++it) {
+      for (int i = 0; i < np; ++i)
+        RSM_CUDA(cudaMemsetAsync(b.descs[i].macc, 0, (size_t)b.descs[i].n * b.descs[i].n * 8, s));
+      if ((e = launch_l1_scatter(D, T + b.o_trial, np, b.trials_total, s)) != cudaSuccess)
+        return cuda_fail(e, "l1_scatter");
+      if ((e = launch_finalize_M(D, T + b.o_ent, np, b.ent_total, s)) != cudaSuccess)
+        return cuda_fail(e, "finalize_M");
+      if ((e = launch_trace_M(D, np, s)) != cudaSuccess) return cuda_fail(e, "trace_M");
+      int st = reset_eig_state(b, slot);
+      if (st != RSM_OK) return st;
+      if ((e = launch_eig(ep, fp64_factor, shift_rel, fp64_factor ? kEigIters64 : kEigIters32, s)) != cudaSuccess)
+        return cuda_fail(e, "eig");
+    }
+  }
   RSM_CUDA(cudaEventRecord(slot.ev[6], s));
   if (b.any_solve) {
     SolvePlan sp{};
@@ -277,6 +306,14 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
     RSM_CUDA(cudaEventRecord(slot.ev[7], s));
     double* partial = reinterpret_cast<double*>(static_cast<unsigned char*>(slot.ws.ptr) + b.res_bytes_off);
     if ((e = launch_residual(sp, b.solve_mode, partial, s)) != cudaSuccess) return cuda_fail(e, "residual");
+    if (b.l1) {
+      // the L1 rows: reweighting steps from the L2 rows (their e sets the scale of
+      // delta), then e of the final U and V without the L2 refinement step
+      for (int it = 0; it < b.irls_iters; ++it)
+        if ((e = launch_irls_u(D, T + b.o_urow, np, b.urow_total, b.rmax, b.solve_mode == 0, s)) != cudaSuccess)
+          return cuda_fail(e, "irls_u");
+      if ((e = launch_residual(sp, b.solve_mode, partial, s, false)) != cudaSuccess) return cuda_fail(e, "residual");
+    }
   } else {
     RSM_CUDA(cudaEventRecord(slot.ev[7], s));
   }
@@ -348,7 +385,7 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
       const double* stats = reinterpret_cast<const double*>(hp + (size_t)i * kReadback + kCountersBytes);
       const int r = ps[i].r;
       const double gap = stats[r] - stats[r - 1];
-      const double trace = given_M ? stats[kStatTrace]
+      const double trace = given_M || b.l1 ? stats[kStatTrace]
                            : ps[i].variant == RSM_ROWS_RANDOM ? (double)c[7]
                                                               : (double)c[0] * b.dv[i].nm;
       const bool determined = (given_M || c[0] > 0) && stats[r] > kRankTol * trace;
@@ -390,7 +427,7 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
     r.n_eig = b.dv[i].kx;
     for (int k = 0; k < 32; ++k) r.eig_M[k] = k < r.n_eig ? stats[k] : 0.0;
     r.eig_residual = stats[34];
-    const double trace = given_M ? stats[kStatTrace]
+    const double trace = given_M || b.l1 ? stats[kStatTrace]
                          : ps[i].variant == RSM_ROWS_RANDOM ? (double)c[7]
                                                             : (double)c[0] * b.dv[i].nm;
     r.e_known_rms = b.dv[i].solve_u ? stats[33] : NAN;
@@ -428,6 +465,8 @@ int validate_all(const rsm_problem* ps, int count) {
     if (st != RSM_OK) return fail(st, "problem " + std::to_string(i) + ": " + why);
     if (ps[i].gram_prec != ps[0].gram_prec || ps[i].solve_prec != ps[0].solve_prec)
       return fail(RSM_ERR_INVALID_ARG, "all problems of a batch must share gram_prec and solve_prec");
+    if ((ps[i].norm == 1) != (ps[0].norm == 1) || ps[i].irls_iters != ps[0].irls_iters)
+      return fail(RSM_ERR_INVALID_ARG, "all problems of a batch must share norm and irls_iters");
   }
   return RSM_OK;
 }
@@ -610,7 +649,9 @@ void worker_loop(rsm_handle* h, int slot_id) {
           for (auto it = h->queue.begin(); it != h->queue.end() && (int)reqs.size() < kServeBatch;) {
             auto& r = h->reqs[*it];
             const bool same_prec = reqs.empty() || (r->prob.gram_prec == reqs[0]->prob.gram_prec &&
-                                                    r->prob.solve_prec == reqs[0]->prob.solve_prec);
+                                                    r->prob.solve_prec == reqs[0]->prob.solve_prec &&
+                                                    (r->prob.norm == 1) == (reqs[0]->prob.norm == 1) &&
+                                                    r->prob.irls_iters == reqs[0]->prob.irls_iters);
             if (same_prec && r->footprint + h->in_use <= h->budget) {
               h->in_use += r->footprint;
               r->state = 1;

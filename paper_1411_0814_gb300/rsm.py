@@ -108,7 +108,8 @@ class Problem:
                  seed: int = 0, problem_id: int = 0, variant: str = "random", gram: str = "f64", solve: str = "f64",
                  want_U: bool = True, debug: bool = False, U: Optional[torch.Tensor] = None,
                  V: Optional[torch.Tensor] = None, epsilon: float = 0.0, coverage: bool = False,
-                 visited: bool = False):
+                 visited: bool = False, norm: str = "l2", irls_iters: int = 0, irls_delta_v: float = 0.0,
+                 irls_delta_u: float = 0.0):
         if not (Y.is_cuda and W.is_cuda):
             raise ValueError("Y and W must be CUDA tensors")
         if Y.dtype not in (torch.float64, torch.float32) or W.dtype != torch.uint8:
@@ -144,6 +145,8 @@ class Problem:
             p.U, p.ldu = self.U.data_ptr(), _ld(self.U)
         p.epsilon = epsilon
         p.coverage = 1 if (coverage or visited) else 0
+        p.norm = {"l2": 2, "l1": 1}[norm]
+        p.irls_iters, p.irls_delta_v, p.irls_delta_u = irls_iters, irls_delta_v, irls_delta_u
         if visited:
             p.debug_visited = self.visited.data_ptr()
         if debug:
