@@ -322,8 +322,9 @@ def oracle_golden(p):
     return {k: g[k] for k in g.files}
 
 
-def gather_probe(dev, stream) -> float:
-    """L2 sectors per second read from random lines of a 32 MiB L2-resident buffer (rsm_probe_gather), best of 5."""
+def gather_probe(dev, stream, per_line: int) -> float:
+    """Loads per second from random 128-byte lines of a 32 MiB L2-resident buffer (rsm_probe_gather), per_line
+    distinct sectors of each line (1: the L1 line rate, 4: the L2 sector rate), best of 5."""
     import torch
 
     import paper_1411_0814_gb300 as rsm
@@ -335,7 +336,8 @@ def gather_probe(dev, stream) -> float:
     for k in range(7):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        st = lib.rsm_probe_gather(buf.data_ptr(), buf.numel(), blocks, per, out.data_ptr(), stream.cuda_stream)
+        st = lib.rsm_probe_gather(buf.data_ptr(), buf.numel(), blocks, per, per_line, out.data_ptr(),
+                                  stream.cuda_stream)
         e1.record(stream)
         torch.cuda.synchronize()
         if st != 0:
@@ -503,24 +505,38 @@ def bench_mine(args):
     # the L2 sector ceiling (rsm_probe_gather, measured here) against the slab Gram's sectors: per
     # trial and column, the 8-row sectors that hold a selected row (rows selected with probability
     # q = p_t / m: a fraction 1 - (1 - q)^8 of the m / 8 sectors), plus the mask words (8 per sector)
-    gather = gather_probe(dev, stream)
+    gather = gather_probe(dev, stream, 4)
     q = last.rows_selected / (p.trials * p.m)
     mask_sectors = p.trials * p.l * ((p.m + 31) // 32) / 8
     gathers = p.trials * p.l * (p.m / 8.0) * (1.0 - (1.0 - q) ** 8) + mask_sectors
     gather_rate = gathers / (sg_ms * 1e-3)
+    # the L1 line ceiling: a warp load of 32 sorted selected rows touches one 128-byte line per
+    # lane, except where a row lies in the same 32-row line as the previous lane's row (gap g < 32
+    # with probability (32 - g) / 32 for a gap of g rows, P(g) = q (1 - q)^(g - 1)); the mask
+    # reads are one line per warp load of 32 words
+    line_rate = gather_probe(dev, stream, 1)
+    share = sum((32 - g) / 32.0 * q * (1.0 - q) ** (g - 1) for g in range(1, 32))
+    lines = last.rows_selected * p.l * (1.0 - share) + p.trials * p.l * ((p.m + 31) // 32) / 32
+    lines_rate = lines / (sg_ms * 1e-3)
     roofline = {"kernel": "k_gram_slab<2,9> (row-slab selection + FP32 Gram)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "algorithmic_bytes_per_launch": int(alg_bytes / launches), "launches_per_step": launches,
                 "launch_ms": round(sg_ms / launches, 4), "peak_source": peaks["source"] + " (copy bandwidth)",
+                "l1_line_ceiling": {"achieved_lines_per_s": lines_rate, "peak_lines_per_s": line_rate,
+                                    "frac": lines_rate / line_rate if line_rate else None, "lines_per_step": lines,
+                                    "peak_source": "rsm_probe_gather per_line = 1, measured in this run (every "
+                                                   "4-byte load on its own random 128-byte line of a 32 MiB "
+                                                   "L2-resident buffer)"},
                 "l2_sector_ceiling": {"achieved_sectors_per_s": gather_rate, "peak_sectors_per_s": gather,
                                       "frac": gather_rate / gather if gather else None,
                                       "sectors_per_step": gathers,
-                                      "peak_source": "rsm_probe_gather, measured in this run (32-byte sectors of "
-                                                     "random 128-byte lines of a 32 MiB L2-resident buffer)"},
+                                      "peak_source": "rsm_probe_gather per_line = 4, measured in this run "
+                                                     "(four 32-byte sectors of each random 128-byte line)"},
                 "note": "traffic (DRAM bytes per launch, ncu) is ~10x below the algorithmic bytes: the slab "
-                        "schedule serves repeated reads from L2.  A gathered element costs a 32-byte sector "
-                        "(rows chosen by data), so the kernel is bound by L2 sector reads: l2_sector_ceiling"}
+                        "schedule serves repeated reads from L2.  Rows are chosen by data, so a gathered "
+                        "element costs a 128-byte line lookup in L1 and a 32-byte sector from L2; the line "
+                        "lookups bound the kernel (l1_line_ceiling)"}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

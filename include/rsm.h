@@ -306,16 +306,17 @@ int32_t rsm_eig_smallest(rsm_handle* h, const double* M, int64_t n, int32_t r, d
  * sqrt(x) (0 for x < 0).  Asynchronous on stream. */
 int32_t rsm_check_fp64_math(const double* x, int64_t count, double* out, void* stream);
 
-/* L2 sector-read probe (measurement only; the paper has no counterpart): the
- * ceiling of the row-slab Gram's access pattern.  blocks x 256 threads each
- * issue per_thread (a multiple of 16) 4-byte loads; each group of 4 lanes reads
- * the 4 sectors of one pseudo-random 128-byte line of buf (device, elems floats,
- * a power of two >= 1024; size it to stay in L2), so every load is one 32-byte
- * sector.  out: device, blocks x 256 floats, written only to keep the loads
- * alive.  Time it with events on `stream`: sectors per second =
- * blocks 256 per_thread / time. */
-int32_t rsm_probe_gather(const float* buf, int64_t elems, int64_t blocks, int32_t per_thread, float* out,
-                         void* stream);
+/* Gather probe (measurement only; the paper has no counterpart): the ceilings of
+ * the row-slab Gram's access pattern.  blocks x 256 threads each issue
+ * per_thread (a multiple of 16) 4-byte loads; each group of per_line (1 or 4)
+ * consecutive lanes reads distinct 32-byte sectors of one pseudo-random
+ * 128-byte line of buf (device, elems floats, a power of two >= 1024; size it to
+ * stay in L2).  per_line = 1: every load is its own line (the L1's per-line
+ * rate); per_line = 4: four sectors per line (the L2's sector rate).  out:
+ * device, blocks x 256 floats, written only to keep the loads alive.  Time it
+ * with events on `stream`: loads per second = blocks 256 per_thread / time. */
+int32_t rsm_probe_gather(const float* buf, int64_t elems, int64_t blocks, int32_t per_thread, int32_t per_line,
+                         float* out, void* stream);
 
 /* e = sqrt(sum over known (y_ij - u_i . v_j)^2 / number of known entries) for a
  * given U and V, computed without allocating device memory.  The paper has no

@@ -138,7 +138,8 @@ SIGNATURES = {
     "rsm_plan_trials": (C.c_int32, [C.c_int64, C.c_int64, C.c_double, C.c_int32, C.c_int32, C.c_int32, C.c_double,
                                     C.POINTER(rsm_trial_plan)]),
     "rsm_check_fp64_math": (C.c_int32, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
-    "rsm_probe_gather": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]),
+    "rsm_probe_gather": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_void_p,
+                                     C.c_void_p]),
     "rsm_residual_noalloc": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p,
                                          C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
                                          C.c_void_p, C.c_void_p]),

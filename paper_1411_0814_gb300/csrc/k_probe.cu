@@ -1,15 +1,16 @@
-// L2 sector-read probe: the ceiling of the row-slab Gram's memory pattern.
+// Gather probes: the ceilings of the row-slab Gram's memory pattern.
 //
 // The slab Gram reads 4-byte elements of rows chosen by data from a 32 MiB
-// slab of Y that stays in L2; a warp's loads fall on ~16 distinct 32-byte
-// sectors (the lanes hold sorted rows, a few sharing a sector), so the kernel
-// is bound by the rate at which L2 serves sectors.  This kernel measures that
-// rate: every group of 4 lanes reads the 4 sectors of one pseudo-random 128-byte
-// line of an L2-resident buffer (8 lines, 32 sectors per warp load), each
-// thread with kGather loads in flight (a multiplicative hash gives the lines,
-// so no index array competes for bandwidth), and adds them up so nothing is
-// optimised away.  Fully scattered requests (32 lines per warp load) reach
-// only about half of this rate: they are bound by the L1's per-line work.
+// slab of Y that stays in L2.  A warp's 32 loads fall on ~25 distinct 128-byte
+// lines (the lanes hold sorted rows ~25 apart), so two rates can bound it: the
+// L1's per-line work (tag lookup and miss handling, one per distinct line of a
+// request) and the L2's sector reads.  This kernel measures either: each group
+// of `per_line` consecutive lanes (1 or 4) reads distinct 32-byte sectors of one
+// pseudo-random 128-byte line of an L2-resident buffer, so a warp load touches
+// 32 / per_line lines and 32 sectors; each thread keeps kGather loads in flight
+// (enough to cover the L2 latency at full occupancy).  A multiplicative hash
+// gives the lines, so no index array competes for bandwidth, and the values are
+// summed so nothing is optimised away.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -23,10 +24,10 @@ constexpr int kGather = 16;  // independent loads in flight per thread
 }
 
 __global__ void __launch_bounds__(256) k_probe_gather(const float* __restrict__ buf, uint32_t mask, int per_thread,
-                                                     float* __restrict__ out) {
+                                                     int shift, float* __restrict__ out) {
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t h = (tid >> 2) * 0x9E3779B1u + 0x7F4A7C15u;  // the same line for 4 consecutive lanes
-  const uint32_t sector = (tid & 3u) * 8u;               // their 4 sectors of it (8 floats each)
+  uint32_t h = (tid >> shift) * 0x9E3779B1u + 0x7F4A7C15u;  // the same line for 2^shift consecutive lanes
+  const uint32_t sector = (tid & 3u) * 8u;                  // distinct sectors of it (8 floats each)
   const uint32_t lines = mask >> 5;                      // 128-byte lines in the buffer, minus one
   float acc = 0.f;
   for (int k = 0; k < per_thread; k += kGather) {
@@ -44,12 +45,12 @@ __global__ void __launch_bounds__(256) k_probe_gather(const float* __restrict__ 
 
 }  // namespace rsm
 
-extern "C" int32_t rsm_probe_gather(const float* buf, int64_t elems, int64_t blocks, int32_t per_thread, float* out,
-                                    void* stream) {
+extern "C" int32_t rsm_probe_gather(const float* buf, int64_t elems, int64_t blocks, int32_t per_thread,
+                                    int32_t per_line, float* out, void* stream) {
   if (!buf || !out || elems < 1024 || (elems & (elems - 1)) != 0 || elems > ((int64_t)1 << 31) || blocks < 1 ||
-      blocks > (1 << 20) || per_thread < 16 || per_thread % 16 != 0)
+      blocks > (1 << 20) || per_thread < 16 || per_thread % 16 != 0 || (per_line != 1 && per_line != 4))
     return RSM_ERR_INVALID_ARG;
-  rsm::k_probe_gather<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(buf, (uint32_t)(elems - 1),
-                                                                                       per_thread, out);
+  rsm::k_probe_gather<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      buf, (uint32_t)(elems - 1), per_thread, per_line == 4 ? 2 : 0, out);
   return cudaGetLastError() == cudaSuccess ? RSM_OK : RSM_ERR_CUDA;
 }
