@@ -230,6 +230,48 @@ int32_t rsm_decompose(rsm_handle* h, const rsm_problem* p, rsm_result* res);
  * every problem succeeded, else the first failing status. */
 int32_t rsm_decompose_batch(rsm_handle* h, const rsm_problem* ps, int32_t count, rsm_result* res);
 
+/* Gram-stage autotuning.  The Gram stage (Section IV-A steps 2-3: the rows
+ * known in all drawn columns and the Gram matrix of each submatrix) has two
+ * schedules: row slabs of Y small enough to stay in L2 while every draw reads
+ * them (the default, 32 MiB), and one warp per submatrix reading Y directly.
+ * rsm_autotune times, on the caller's problem p, the default, the slab
+ * schedule at 8, 16, 32 and 64 MiB of Y per slab with the kernel's register-
+ * derived CTAs per SM (and one fewer, where that build has more registers per
+ * thread), and the per-submatrix schedule: `reps`
+ * timed runs each (0 -> 3) after one untimed run, a 256 MiB write between runs
+ * to evict L2, the Gram stage's device time (stage_ms[3]) minimum over reps.
+ * The fastest becomes the handle's choice for every later problem with the same
+ * key (gram_prec, y_dtype, l, n, and ceil(log2 m)), in rsm_decompose, the
+ * batch and the serving calls.  The results do not depend on the choice beyond
+ * rounding: M is accumulated in fixed point, but the per-submatrix schedule
+ * sums the Gram in another order.
+ * p's V is overwritten (U and the debug outputs are not touched); trials == 0
+ * is planned as in rsm_decompose.  Runs on the handle's stream like
+ * rsm_decompose and synchronises it.  RSM_ERR_INVALID_ARG for the rows variant
+ * (it has no Gram stage) or an invalid problem; the status of a failing run
+ * otherwise.  *out (may be NULL) receives the choice and its timings. */
+typedef struct rsm_tune {
+  int32_t schedule;   /* 0: L2-resident row slabs, 1: one warp per submatrix */
+  int32_t slab_mib;   /* MiB of Y per slab (schedule 0) */
+  int32_t variant;    /* 0: register-derived CTAs per SM, 1: one fewer (schedule 0) */
+  int32_t candidates; /* choices timed */
+  double gram_ms;     /* Gram-stage time of the choice (ms) */
+  double default_ms;  /* Gram-stage time of the default (ms) */
+} rsm_tune;
+int32_t rsm_autotune(rsm_handle* h, const rsm_problem* p, int32_t reps, rsm_tune* out);
+/* 1 and *out (may be NULL) filled when the handle holds a choice for p's key,
+ * 0 when not, -RSM_ERR_INVALID_ARG for a NULL handle or problem. */
+int32_t rsm_autotune_lookup(rsm_handle* h, const rsm_problem* p, rsm_tune* out);
+/* Forget every choice (later problems take the defaults). */
+int32_t rsm_autotune_clear(rsm_handle* h);
+/* Write the handle's choices to a text file (one line per key), or add those
+ * of a file written so to the handle (an entry replaces one with the same
+ * key).  A malformed file loads nothing: RSM_ERR_INVALID_ARG, message names
+ * the line.  Choices are per device model and build: a file is a cache, not a
+ * portable setting. */
+int32_t rsm_autotune_save(rsm_handle* h, const char* path);
+int32_t rsm_autotune_load(rsm_handle* h, const char* path);
+
 /* Serving: enqueue a problem.  The problem struct is copied; Y, W, U, V and the
  * debug buffers must stay valid until rsm_poll reports a final status.  A
  * request is admitted when a slot is free and its footprint fits the budget;

@@ -108,6 +108,17 @@ class rsm_trial_plan(C.Structure):
     ]
 
 
+class rsm_tune(C.Structure):
+    _fields_ = [
+        ("schedule", C.c_int32),
+        ("slab_mib", C.c_int32),
+        ("variant", C.c_int32),
+        ("candidates", C.c_int32),
+        ("gram_ms", C.c_double),
+        ("default_ms", C.c_double),
+    ]
+
+
 STAGES = ["setup", "pack_mask", "sample_cols", "select_gram", "minor_scatter", "eig_M", "solve_U", "residual", "total"]
 
 
@@ -140,6 +151,11 @@ SIGNATURES = {
     "rsm_check_fp64_math": (C.c_int32, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "rsm_probe_gather": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_void_p,
                                      C.c_void_p]),
+    "rsm_autotune": (C.c_int32, [C.c_void_p, C.POINTER(rsm_problem), C.c_int32, C.POINTER(rsm_tune)]),
+    "rsm_autotune_lookup": (C.c_int32, [C.c_void_p, C.POINTER(rsm_problem), C.POINTER(rsm_tune)]),
+    "rsm_autotune_clear": (C.c_int32, [C.c_void_p]),
+    "rsm_autotune_save": (C.c_int32, [C.c_void_p, C.c_char_p]),
+    "rsm_autotune_load": (C.c_int32, [C.c_void_p, C.c_char_p]),
     "rsm_residual_noalloc": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p,
                                          C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
                                          C.c_void_p, C.c_void_p]),

@@ -30,9 +30,6 @@ constexpr int slab_minb() {
   constexpr int w = MODE == 0 ? 2 : 1;
   constexpr int need = w * (L * (L + 1) / 2) + (w + 1) * L + 40;
   constexpr int fit = 65536 / (32 * kSlabWarps * ((need + 7) / 8 * 8));
-#ifdef RSM_SLAB_MINB_L9  // build-time tuning of the l = 9 FP32 case (CTAs per SM)
-  if (MODE == 2 && L == 9) return RSM_SLAB_MINB_L9;
-#endif
   // l = 9 FP32 (the paper-scale case) fits five CTAs per SM at 96 registers: measured
   // 2.39 ms against 2.48 ms at four per decomposition of the 131072 x 1024 workload
   if (MODE == 2 && L == 9) return 5;
@@ -58,8 +55,12 @@ struct SlabT<2> {  // FP32 Gram of FP32 Y
   __device__ static val_t cvt(src_t x) { return x; }
 };
 
-template <int MODE, int L>
-__global__ void __launch_bounds__(32 * kSlabWarps, (slab_minb<MODE, L>())) k_gram_slab(const ProbDesc* __restrict__ descs,
+// V = 0: the CTAs per SM of slab_minb; V = 1: one fewer (more registers per
+// thread); the autotuner picks between them per problem shape.
+// OCC = 1 asks for one CTA per SM fewer than slab_minb (more registers per thread)
+template <int MODE, int L, int OCC>
+__global__ void __launch_bounds__(32 * kSlabWarps, (slab_minb<MODE, L>() - OCC > 1 ? slab_minb<MODE, L>() - OCC : 1))
+    k_gram_slab(const ProbDesc* __restrict__ descs,
                                                                const int64_t* __restrict__ task_off, int nprob,
                                                                int slab) {
   using Tr = SlabT<MODE>;
@@ -193,15 +194,23 @@ static size_t slab_smem_bytes() {
   return (size_t)kSlabWarps * (kWarpWords + kMeta) * 4;
 }
 
-template <int MODE, int L>
-static cudaError_t launch_slab_l(const SlabPlan& S, cudaStream_t s) {
+// regs != NULL: report the kernel's registers per thread instead of launching
+template <int MODE, int L, int OCC>
+static cudaError_t launch_slab_l(const SlabPlan* Sp, cudaStream_t s, int* regs) {
+  if (regs) {
+    cudaFuncAttributes a{};
+    cudaError_t e = cudaFuncGetAttributes(&a, k_gram_slab<MODE, L, OCC>);
+    *regs = e == cudaSuccess ? a.numRegs : -1;
+    return e;
+  }
+  const SlabPlan& S = *Sp;
   const size_t smem = slab_smem_bytes<MODE, L>();
-  cudaError_t e = cudaFuncSetAttribute(k_gram_slab<MODE, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_gram_slab<MODE, L, OCC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   for (int sl = 0; sl < S.nslab; ++sl) {
     const int64_t tasks = S.hT[S.task_pos + (size_t)sl * (S.nprob + 1) + S.nprob];
     if (tasks <= 0) continue;
-    k_gram_slab<MODE, L><<<(unsigned)((tasks + kSlabWarps - 1) / kSlabWarps), 32 * kSlabWarps, smem, s>>>(
+    k_gram_slab<MODE, L, OCC><<<(unsigned)((tasks + kSlabWarps - 1) / kSlabWarps), 32 * kSlabWarps, smem, s>>>(
         S.descs, S.dT + S.task_pos + (size_t)sl * (S.nprob + 1), S.nprob, sl);
     ++g_kernel_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -217,10 +226,10 @@ bool slab_supported(int mode, int l, int y_dtype) {
   return false;
 }
 
-cudaError_t launch_gram_slab(int mode, int l, const SlabPlan& S, cudaStream_t s) {
-#define RSM_SLAB_CASE(M, LL) \
-  case LL:                   \
-    return launch_slab_l<M, LL>(S, s);
+static cudaError_t slab_dispatch(int mode, int l, int variant, const SlabPlan* S, cudaStream_t s, int* regs) {
+#define RSM_SLAB_CASE(M, LL)                                                  \
+  case LL:                                                                    \
+    return variant ? launch_slab_l<M, LL, 1>(S, s, regs) : launch_slab_l<M, LL, 0>(S, s, regs);
   if (mode == 2) {
     switch (l) {
       RSM_SLAB_CASE(2, 2) RSM_SLAB_CASE(2, 3) RSM_SLAB_CASE(2, 4) RSM_SLAB_CASE(2, 5) RSM_SLAB_CASE(2, 6)
@@ -239,6 +248,16 @@ cudaError_t launch_gram_slab(int mode, int l, const SlabPlan& S, cudaStream_t s)
   }
 #undef RSM_SLAB_CASE
   return cudaErrorNotSupported;
+}
+
+cudaError_t launch_gram_slab(int mode, int l, int variant, const SlabPlan& S, cudaStream_t s) {
+  return slab_dispatch(mode, l, variant, &S, s, nullptr);
+}
+
+int gram_slab_regs(int mode, int l, int variant) {
+  int regs = -1;
+  if (slab_dispatch(mode, l, variant, nullptr, nullptr, &regs) != cudaSuccess) cudaGetLastError();
+  return regs;
 }
 
 }  // namespace rsm

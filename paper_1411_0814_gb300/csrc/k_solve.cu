@@ -434,30 +434,35 @@ __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ d
   }
 }
 
-// FP32 form of FP32 Y with 16-byte aligned columns: each lane takes 4
-// consecutive rows (one 16-byte load per column), a CTA 128 rows, its 8 warps
-// split the columns; 4 columns are loaded before any is used, so each warp has
-// 2 KB of Y in flight.  Each lane also accumulates c = V_K^T r0 for its 4 rows;
-// the warps' parts are added in warp order in shared memory and threads 0..127
-// apply the refinement step (refine_row), one row each.  Partials as in k_residual.
-constexpr int kRes4Rows = 128;
+// FP32 form of FP32 Y with 16-byte aligned columns: each lane takes 2
+// consecutive rows (one 8-byte load per column), a CTA 64 rows, and its 8
+// warps split the columns, 8 columns per pass, all loaded before any is used
+// (2 KB of Y in flight per warp).  Each lane also accumulates c = V_K^T r0 for
+// its 2 rows; the warps' parts are added in warp order in shared memory and
+// threads 0..63 apply the refinement step (refine_row), one row each.  The
+// per-lane state (2 rows x (u, c)) leaves room for three CTAs (24 warps) per
+// SM.  Partials as in k_residual.
+constexpr int kResVRows = 64;
+constexpr int kResVCols = 8;      // columns in flight per warp and pass
+constexpr int kResVStage = 512;   // columns of V staged per barrier (8 passes of each warp)
 template <int RM>
-__global__ void __launch_bounds__(256) k_residual4(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
-                                                  int nprob, double* __restrict__ partial, int refine) {
-  __shared__ __align__(16) float vs[kResCols][RM];
-  __shared__ float cred[kRes4Rows][RM + 1];
+__global__ void __launch_bounds__(256, 3) k_residual2(const ProbDesc* __restrict__ descs,
+                                                     const int64_t* __restrict__ off, int nprob,
+                                                     double* __restrict__ partial, int refine) {
+  __shared__ __align__(16) float vs[kResVStage][RM];
+  __shared__ float cred[kResVRows][RM + 1];
   __shared__ double red[8];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
   const int lane = threadIdx.x & 31, wg = threadIdx.x >> 5;
-  const uint32_t i0 = (uint32_t)(blockIdx.x - off[p]) * kRes4Rows;
-  const uint32_t ib = i0 + 4u * lane;  // first of this lane's 4 rows
+  const uint32_t i0 = (uint32_t)(blockIdx.x - off[p]) * kResVRows;
+  const uint32_t ib = i0 + 2u * lane;  // first of this lane's 2 rows
   const uint32_t m = (uint32_t)d.m;
-  const bool quad_in = ib < m;
+  const bool pair_in = ib < m;  // m is even or the second row is masked out below
   const int r = d.r;
-  float u[4][RM], cacc[4][RM];
+  float u[2][RM], cacc[2][RM];
 #pragma unroll
-  for (int k = 0; k < 4; ++k)
+  for (int k = 0; k < 2; ++k)
 #pragma unroll
     for (int a = 0; a < RM; ++a) {
       u[k][a] = (a < r && ib + k < m) ? (float)d.U[(int64_t)a * d.ldu + ib + k] : 0.f;
@@ -466,29 +471,30 @@ __global__ void __launch_bounds__(256) k_residual4(const ProbDesc* __restrict__ 
   const float* __restrict__ Y = static_cast<const float*>(d.Y);
   const uint32_t ldy = (uint32_t)d.ldy, ldb = (uint32_t)d.ldb, n = (uint32_t)d.n;
   const uint32_t wrow = ib >> 5, shift = ib & 31u;
+  const uint32_t keep = ib + 1 < m ? 3u : 1u;  // the second row exists
   float acc = 0.f;
-  for (uint32_t j0 = 0; j0 < n; j0 += kResCols) {
+  for (uint32_t j0 = 0; j0 < n; j0 += kResVStage) {
     __syncthreads();
-    for (int e = threadIdx.x; e < kResCols * RM; e += 256) {
+    for (int e = threadIdx.x; e < kResVStage * RM; e += 256) {
       const int jj = e / RM, a = e % RM;
       const uint32_t j = j0 + jj;
       vs[jj][a] = (j < n && a < r) ? d.vf32[j * d.vf_ld + a] : 0.f;
     }
     __syncthreads();
-    const int jn = n - j0 < (uint32_t)kResCols ? (int)(n - j0) : kResCols;
-    for (int jb = wg; jb < jn; jb += 32) {  // 4 columns per pass: jb, jb + 8, jb + 16, jb + 24
-      float4 y[4];
-      uint32_t bits[4];
+    const int jn = n - j0 < (uint32_t)kResVStage ? (int)(n - j0) : kResVStage;
+    for (int jb = wg; jb < jn; jb += 8 * kResVCols) {  // columns jb, jb + 8, ..., jb + 56
+      float2 y[kResVCols];
+      uint32_t bits[kResVCols];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < kResVCols; ++q) {
         const int jj = jb + 8 * q;
         const uint32_t j = j0 + jj;
-        const bool ok = jj < jn && quad_in;
-        y[q] = ok ? __ldg(reinterpret_cast<const float4*>(Y + (j * ldy + ib))) : make_float4(0.f, 0.f, 0.f, 0.f);
-        bits[q] = ok ? (__ldg(d.bits + (j * ldb + wrow)) >> shift) & 0xFu : 0u;
+        const bool ok = jj < jn && pair_in;
+        y[q] = ok ? __ldg(reinterpret_cast<const float2*>(Y + (j * ldy + ib))) : make_float2(0.f, 0.f);
+        bits[q] = ok ? (__ldg(d.bits + (j * ldb + wrow)) >> shift) & keep : 0u;
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < kResVCols; ++q) {
         const int jj = jb + 8 * q;
         if (jj >= jn) break;
         float vr[RM];
@@ -498,9 +504,9 @@ __global__ void __launch_bounds__(256) k_residual4(const ProbDesc* __restrict__ 
           const float4 v = v4[a4];
           vr[4 * a4] = v.x, vr[4 * a4 + 1] = v.y, vr[4 * a4 + 2] = v.z, vr[4 * a4 + 3] = v.w;
         }
-        const float yv[4] = {y[q].x, y[q].y, y[q].z, y[q].w};
+        const float yv[2] = {y[q].x, y[q].y};
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 2; ++k) {
           float pr = 0.f;
 #pragma unroll
           for (int a = 0; a < RM; ++a) pr = fmaf(u[k][a], vr[a], pr);
@@ -513,23 +519,25 @@ __global__ void __launch_bounds__(256) k_residual4(const ProbDesc* __restrict__ 
     }
   }
   double dacc = (double)acc;
-  for (int w = 0; w < 8; ++w) {  // c of each row: the warps' parts in warp order
-    if (wg == w)
+  if (refine) {  // uniform over the CTA
+    for (int w = 0; w < 8; ++w) {  // c of each row: the warps' parts in warp order
+      if (wg == w)
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < 2; ++k)
 #pragma unroll
-        for (int a = 0; a < RM; ++a) cred[4 * lane + k][a] = (w == 0 ? 0.f : cred[4 * lane + k][a]) + cacc[k][a];
-    __syncthreads();
-  }
-  if (refine && threadIdx.x < kRes4Rows && i0 + threadIdx.x < m) {
-    const uint32_t row = i0 + threadIdx.x;
-    float c[RM], u32[RM];
-#pragma unroll
-    for (int a = 0; a < RM; ++a) {
-      c[a] = cred[threadIdx.x][a];
-      u32[a] = a < r ? (float)d.U[(int64_t)a * d.ldu + row] : 0.f;
+          for (int a = 0; a < RM; ++a) cred[2 * lane + k][a] = (w == 0 ? 0.f : cred[2 * lane + k][a]) + cacc[k][a];
+      __syncthreads();
     }
-    dacc -= refine_row<RM>(d, row, u32, c);
+    if (threadIdx.x < kResVRows && i0 + threadIdx.x < m) {
+      const uint32_t row = i0 + threadIdx.x;
+      float c[RM], u32[RM];
+#pragma unroll
+      for (int a = 0; a < RM; ++a) {
+        c[a] = cred[threadIdx.x][a];
+        u32[a] = a < r ? (float)d.U[(int64_t)a * d.ldu + row] : 0.f;
+      }
+      dacc -= refine_row<RM>(d, row, u32, c);
+    }
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
@@ -624,13 +632,13 @@ cudaError_t launch_residual(const SolvePlan& S, int mode, double* partial, cudaS
 #undef RSM_RES
     ++g_kernel_launches;
   }
-  if (S.res4_blocks > 0) {  // problems with r <= 8 only
-    k_residual4<8><<<(unsigned)S.res4_blocks, 256, 0, s>>>(D, S.res4_off, np, partial + S.res_blocks, rf);
+  if (S.resv_blocks > 0) {  // problems with r <= 8 only
+    k_residual2<8><<<(unsigned)S.resv_blocks, 256, 0, s>>>(D, S.resv_off, np, partial + S.res_blocks, rf);
     ++g_kernel_launches;
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_residual_final<<<np, 256, 0, s>>>(D, S.res_off, S.res4_off, S.res_blocks, np, partial);
+  k_residual_final<<<np, 256, 0, s>>>(D, S.res_off, S.resv_off, S.res_blocks, np, partial);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

@@ -52,8 +52,8 @@ struct SolvePlan {
   const int64_t* row_off;    // m per problem
   int64_t res_blocks;
   const int64_t* res_off;    // ceil(m / 32) per problem (scalar residual kernel)
-  int64_t res4_blocks;
-  const int64_t* res4_off;   // ceil(m / 128) per problem (4-row residual kernel); its partials follow the others
+  int64_t resv_blocks;
+  const int64_t* resv_off;   // ceil(m / 64) per problem (2-row residual kernel); its partials follow the others
   int rmax;                  // largest r of the batch
   unsigned long long* fail_list;   // row_total entries: (problem << 32) | row
   unsigned long long* fail_count;  // zero before the launch
@@ -82,7 +82,9 @@ struct SlabPlan {
   size_t task_pos;
 };
 bool slab_supported(int mode, int l, int y_dtype);
-cudaError_t launch_gram_slab(int mode, int l, const SlabPlan& S, cudaStream_t s);
+// variant 1: the slab kernel compiled for one CTA per SM fewer (more registers per thread)
+cudaError_t launch_gram_slab(int mode, int l, int variant, const SlabPlan& S, cudaStream_t s);
+int gram_slab_regs(int mode, int l, int variant);  // registers per thread of that kernel, -1 if none
 
 cudaError_t launch_copy16(const void* src, void* dst, size_t bytes, cudaStream_t s);  // bytes: multiple of 16
 cudaError_t launch_zero16(void* dst, size_t bytes, cudaStream_t s);

@@ -68,15 +68,16 @@ size_t data_sum(const Sizes& s) {
 size_t part_doubles(const rsm_problem& p, const Derived& dv) {
   return (size_t)((p.n + 63) / 64) * 2 * dv.kx * dv.kx;  // chunks of kChunk = 64 rows (k_eig.cu)
 }
-// The 4-row residual kernel: FP32 form of FP32 Y whose columns start on 16-byte
-// boundaries, r <= 8 (its refinement keeps 4 rows x r sums per lane in registers).
-bool res4_of(const rsm_problem& p, const Derived& dv) {
+// The vectorised residual kernel (2 rows per lane): FP32 form of FP32 Y whose
+// columns start on 16-byte boundaries, r <= 8 (its refinement keeps 2 rows x r
+// sums per lane in registers).
+bool resv_of(const rsm_problem& p, const Derived& dv) {
   return dv.solve_u && p.solve_prec == RSM_PREC_F32 && p.y_dtype == RSM_F32 && p.ldy % 4 == 0 &&
-         (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0 && p.r <= 8;
+         (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0 && p.r <= 8 && p.m % 2 == 0;  // pairs of rows stay in Y
 }
 size_t res_blocks_of(const rsm_problem& p, const Derived& dv) {  // partial sums of the residual
   if (!dv.solve_u) return 0;
-  return res4_of(p, dv) ? (size_t)((p.m + 127) / 128) : (size_t)((p.m + 31) / 32);
+  return resv_of(p, dv) ? (size_t)((p.m + 63) / 64) : (size_t)((p.m + 31) / 32);
 }
 }  // namespace
 
@@ -155,15 +156,17 @@ size_t problem_footprint(const rsm_problem& p, const Derived& dv) {
          align_up(dv.solve_u ? (size_t)p.m * 8 : 0) + kAlign;
 }
 
-// Rows per slab of the row-slab Gram: 32 MiB of the problem's Y (so that a
-// slab stays resident in L2 while every trial reads it), at least 1024 rows,
-// a multiple of 32 (whole mask words).
-int64_t slab_rows_of(const rsm_problem& p) {
+// Rows per slab of the row-slab Gram: slab_mib MiB of the problem's Y (32 by
+// default, so that a slab stays resident in L2 while every trial reads it), at
+// least 1024 rows, a multiple of 32 (whole mask words).
+int64_t slab_rows_of(const rsm_problem& p, int slab_mib) {
   const int64_t row_bytes = p.n * (p.y_dtype == RSM_F64 ? 8 : 4);
-  return std::max<int64_t>(1024, ((int64_t)32 << 20) / std::max<int64_t>(1, row_bytes) / 32 * 32);
+  return std::max<int64_t>(1024, ((int64_t)slab_mib << 20) / std::max<int64_t>(1, row_bytes) / 32 * 32);
 }
 
-void build_batch(const rsm_problem* ps, int count, Batch& b) {
+void build_batch(const rsm_problem* ps, int count, Batch& b, const Tune* tunes) {
+  const Tune dflt{};
+  auto tune = [&](int i) -> const Tune& { return tunes ? tunes[i] : dflt; };
   b.nprob = count;
   b.dv.resize(count);
   b.descs.assign(count, ProbDesc{});
@@ -297,10 +300,10 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
     if (b.dv[i].solve_u) b.solve_rows += ps[i].m;
   b.o_urow = prefix([&](int i) { return b.dv[i].solve_u ? (ps[i].m + 127) / 128 * 128 : (int64_t)0; });
   b.urow_total = total(b.o_urow);
-  b.o_res = prefix([&](int i) { return res4_of(ps[i], b.dv[i]) ? (int64_t)0 : (int64_t)res_blocks_of(ps[i], b.dv[i]); });
+  b.o_res = prefix([&](int i) { return resv_of(ps[i], b.dv[i]) ? (int64_t)0 : (int64_t)res_blocks_of(ps[i], b.dv[i]); });
   b.res_blocks = total(b.o_res);
-  b.o_res4 = prefix([&](int i) { return res4_of(ps[i], b.dv[i]) ? (int64_t)res_blocks_of(ps[i], b.dv[i]) : (int64_t)0; });
-  b.res4_blocks = total(b.o_res4);
+  b.o_resv = prefix([&](int i) { return resv_of(ps[i], b.dv[i]) ? (int64_t)res_blocks_of(ps[i], b.dv[i]) : (int64_t)0; });
+  b.resv_blocks = total(b.o_resv);
 
   // Row slabs: the slab size of a problem depends on its own n and Y type only,
   // and problems are grouped by l, so a problem's Gram is summed in the same
@@ -308,34 +311,36 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
   const int mode = ps[0].gram_prec == RSM_PREC_F64 ? 0 : ps[0].gram_prec == RSM_PREC_F32X2 ? 1 : 2;
   b.nslab = 0;
   for (int i = 0; i < count; ++i) {
-    b.dv[i].slab_rows = slab_rows_of(ps[i]);
+    b.dv[i].slab_rows = slab_rows_of(ps[i], tune(i).slab_mib);
     b.nslab = std::max<int>(b.nslab, (int)((ps[i].m + b.dv[i].slab_rows - 1) / b.dv[i].slab_rows));
   }
-  std::vector<int> ls;
+  // problems on the slab schedule, grouped by (l, occupancy variant); the others (the
+  // per-submatrix schedule, or a mode the slab kernel does not read) take the generic kernel
+  auto on_slab = [&](int i) {
+    return !is_rows(i) && tune(i).schedule == 0 && slab_supported(mode, b.dv[i].l, ps[i].y_dtype);
+  };
+  std::vector<std::pair<int, int>> groups;
   for (int i = 0; i < count; ++i)
-    if (!is_rows(i) && slab_supported(mode, b.dv[i].l, ps[i].y_dtype)) ls.push_back(b.dv[i].l);
-  std::sort(ls.begin(), ls.end());
-  ls.erase(std::unique(ls.begin(), ls.end()), ls.end());
+    if (on_slab(i)) groups.emplace_back(b.dv[i].l, tune(i).variant ? 1 : 0);
+  std::sort(groups.begin(), groups.end());
+  groups.erase(std::unique(groups.begin(), groups.end()), groups.end());
   b.slab_groups.clear();
-  for (int L : ls) {
-    Batch::SlabGroup g{L, T.size()};
+  for (const auto& lv : groups) {
+    Batch::SlabGroup g{lv.first, lv.second, T.size()};
     for (int sl = 0; sl < b.nslab; ++sl)
       prefix([&](int i) {
-        return !is_rows(i) && b.dv[i].l == L && slab_supported(mode, L, ps[i].y_dtype) &&
+        return on_slab(i) && b.dv[i].l == lv.first && (tune(i).variant ? 1 : 0) == lv.second &&
                        (int64_t)sl * b.dv[i].slab_rows < ps[i].m
                    ? ps[i].trials
                    : (int64_t)0;
       });
     b.slab_groups.push_back(g);
   }
-  b.o_trial_generic = prefix([&](int i) {
-    return is_rows(i) || slab_supported(mode, b.dv[i].l, ps[i].y_dtype) ? (int64_t)0 : ps[i].trials;
-  });
+  b.o_trial_generic = prefix([&](int i) { return is_rows(i) || on_slab(i) ? (int64_t)0 : ps[i].trials; });
   b.generic_total = total(b.o_trial_generic);
   b.generic_lmax = 0;
   for (int i = 0; i < count; ++i)
-    if (!is_rows(i) && !slab_supported(mode, b.dv[i].l, ps[i].y_dtype))
-      b.generic_lmax = std::max(b.generic_lmax, b.dv[i].l);
+    if (!is_rows(i) && !on_slab(i)) b.generic_lmax = std::max(b.generic_lmax, b.dv[i].l);
 
   // workspace: all zero regions first, then all data regions, then shared partial buffers
   b.zero_off.resize(count);
@@ -363,7 +368,7 @@ void build_batch(const rsm_problem* ps, int count, Batch& b) {
   b.part_bytes_off = off;
   off += align_up((size_t)b.part_total * 8);
   b.res_bytes_off = off;
-  off += align_up((size_t)(b.res_blocks + b.res4_blocks) * 8);
+  off += align_up((size_t)(b.res_blocks + b.resv_blocks) * 8);
   b.fail_list_off = off;
   off += align_up((size_t)b.solve_rows * 8);  // any solved row may take the minimum-norm path
   b.layout.total_bytes = off;

@@ -25,6 +25,16 @@ struct Derived {
 // RSM_ERR_INVALID_ARG / RSM_ERR_NOT_IMPLEMENTED with a message in *why.
 int validate_problem(const rsm_problem& p, Derived& dv, std::string* why);
 
+// Gram-stage choices of one problem (picked by rsm_autotune; the defaults
+// otherwise): the schedule (0: L2-resident row slabs, 1: one warp per
+// submatrix), the slab size in MiB of Y, and the slab kernel's occupancy
+// variant (0: the CTAs per SM its registers allow, 1: one fewer).
+struct Tune {
+  int schedule = 0;
+  int slab_mib = 32;
+  int variant = 0;
+};
+
 // Byte layout of one batch inside a workspace buffer.
 struct BatchLayout {
   size_t zero_bytes = 0;   // [0, zero_bytes) must be zeroed before the launch
@@ -45,9 +55,9 @@ struct Batch {
   // positions (in int64 elements) of each table inside `tables`
   size_t o_pack = 0, o_trial = 0, o_ent = 0, o_pad2 = 0, o_step = 0, o_linv = 0, o_nk = 0,
          o_mx = 0, o_chunk = 0, o_part = 0, o_rot = 0, o_rowtile = 0, o_k = 0, o_tile = 0, o_row = 0, o_res = 0,
-         o_b = 0, o_tc = 0, o_res4 = 0, o_phase = 0;
+         o_b = 0, o_tc = 0, o_resv = 0, o_phase = 0;
   int64_t pack_blocks = 0, trials_total = 0, ent_total = 0, pad2_total = 0, nk_total = 0, part_total = 0,
-          k_total = 0, tile_total = 0, row_total = 0, res_blocks = 0, b_total = 0, tc_total = 0, res4_blocks = 0;
+          k_total = 0, tile_total = 0, row_total = 0, res_blocks = 0, b_total = 0, tc_total = 0, resv_blocks = 0;
   int64_t solve_rows = 0;  // rows of all problems that solve for U
   bool any_coverage = false;  // some problem counts its visited entries
   bool l1 = false;            // the L1 forms (all problems of the batch)
@@ -72,7 +82,8 @@ struct Batch {
   // through the per-trial kernel (table o_trial_generic).
   struct SlabGroup {
     int l;
-    size_t o_slab;  // nslab prefix tables over the problems of this l
+    int variant;
+    size_t o_slab;  // nslab prefix tables over the problems of this l and variant
   };
   std::vector<SlabGroup> slab_groups;
   int nslab = 0;
@@ -83,7 +94,8 @@ struct Batch {
 };
 
 // Build the batch (sizes, tables, layout).  Problems must be validated first.
-void build_batch(const rsm_problem* ps, int count, Batch& b);
+// tunes: one per problem, or NULL for the defaults.
+void build_batch(const rsm_problem* ps, int count, Batch& b, const Tune* tunes = nullptr);
 // Fill the device pointers of b.descs for a workspace at `ws`.
 void bind_batch(Batch& b, const rsm_problem* ps, unsigned char* ws);
 

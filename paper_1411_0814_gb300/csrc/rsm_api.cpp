@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -186,7 +187,23 @@ struct rsm_handle {
   uint64_t next_ticket = 1;
   bool stopping = false;
   uint32_t fault = 0;
+  // Gram-stage choices found by rsm_autotune, by problem shape (tune_key)
+  std::mutex tune_mu;
+  std::map<std::vector<int64_t>, std::pair<Tune, rsm_tune>> tuned;
 };
+
+namespace {
+
+// Problems that share this key share the Gram stage's best choices: the Gram
+// precision, the type of Y, the submatrix width l, n, and m to the next power of two.
+std::vector<int64_t> tune_key(const rsm_problem& p) {
+  const int64_t l = p.l ? p.l : p.r + 1;
+  int64_t mb = 0;
+  while (((int64_t)1 << mb) < p.m) ++mb;
+  return {p.gram_prec, p.y_dtype, l, p.n, mb};
+}
+
+}  // namespace
 
 namespace {
 
@@ -217,7 +234,7 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
     RSM_CUDA(cudaEventRecord(slot.ev[3], s));
     for (const auto& g : b.slab_groups) {
       SlabPlan sp{D, np, b.nslab, T, b.tables.data(), g.o_slab};
-      if ((e = launch_gram_slab(b.gram_mode, g.l, sp, s)) != cudaSuccess) return cuda_fail(e, "gram_slab");
+      if ((e = launch_gram_slab(b.gram_mode, g.l, g.variant, sp, s)) != cudaSuccess) return cuda_fail(e, "gram_slab");
     }
     if (b.generic_total > 0 &&
         (e = launch_select_gram(b.gram_mode, D, T + b.o_trial_generic, np, b.generic_total, b.generic_lmax, s)) !=
@@ -297,8 +314,8 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
     sp.tc_off = T + b.o_tc;
     sp.tc_rb = b.tc_rb;
     sp.tc_npad_max = b.tc_npad_max;
-    sp.res4_blocks = b.res4_blocks;
-    sp.res4_off = T + b.o_res4;
+    sp.resv_blocks = b.resv_blocks;
+    sp.resv_off = T + b.o_resv;
     sp.any_solve = b.any_solve;
     sp.fail_list = reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(slot.ws.ptr) + b.fail_list_off);
     sp.fail_count = reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(slot.ws.ptr) + b.fail_count_off);
@@ -339,10 +356,20 @@ int enqueue_readback(Batch& b, Slot& slot) {
 // given_M (count == 1 only): the caller's n x n M (device); the stages before
 // the eigensolve are skipped and M is copied into the workspace instead.
 int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_result* res,
-              const double* given_M = nullptr) {
+              const double* given_M = nullptr, const Tune* force = nullptr) {
   slot.fault_wait = (h->fault & RSM_FAULT_DEVICE_WAIT) != 0;
+  std::vector<Tune> tunes(count);
+  if (force) {
+    tunes.assign(count, *force);
+  } else {
+    std::lock_guard<std::mutex> lk(h->tune_mu);
+    for (int i = 0; i < count && !h->tuned.empty(); ++i) {
+      auto it = h->tuned.find(tune_key(ps[i]));
+      if (it != h->tuned.end()) tunes[i] = it->second.first;
+    }
+  }
   Batch b;
-  build_batch(ps, count, b);
+  build_batch(ps, count, b, tunes.data());
   int st = slot.ws.reserve(b.layout.total_bytes);
   if (st != RSM_OK) return st;
   if ((st = slot.plan.reserve(b.layout.plan_bytes + (size_t)count * kReadback)) != RSM_OK) return st;
@@ -623,6 +650,151 @@ int32_t rsm_decompose(rsm_handle* h, const rsm_problem* p, rsm_result* res) {
   if (st == RSM_OK || st == RSM_ERR_UNDERDETERMINED || st == RSM_ERR_ROWS_UNDERDETERMINED) return tmp.status;
   if (res) res->status = st;
   return st;
+}
+
+// ---------------------------------------------------------------- autotuning
+
+int32_t rsm_autotune(rsm_handle* h, const rsm_problem* p_in, int32_t reps, rsm_tune* out) {
+  if (!h || !p_in) return fail(RSM_ERR_INVALID_ARG, "handle and problem are required");
+  if (reps == 0) reps = 3;
+  if (reps < 1 || reps > 100) return fail(RSM_ERR_INVALID_ARG, "reps must be 1..100 (0 -> 3)");
+  if (p_in->variant == RSM_ROWS_RANDOM)
+    return fail(RSM_ERR_INVALID_ARG, "the rows variant has no Gram schedule to tune");
+  std::lock_guard<std::mutex> lk(h->api_mu);
+  DeviceGuard dg(h->device);
+  RSM_CUDA(dg.err);
+  if (h->main.own_stream) {
+    RSM_CUDA(cudaEventRecord(h->main.ev_order, nullptr));
+    RSM_CUDA(cudaStreamWaitEvent(h->main.stream, h->main.ev_order, 0));
+  }
+  std::vector<rsm_problem> planned;
+  int st = plan_missing_trials(h, p_in, 1, planned);
+  if (st != RSM_OK) return st;
+  rsm_problem p = planned.empty() ? *p_in : planned[0];
+  p.U = nullptr;  // the Gram stage is what is timed: stop after V
+  p.debug_cols = nullptr;
+  p.debug_row_counts = nullptr;
+  p.debug_Z = nullptr;
+  p.debug_visited = nullptr;
+  if ((st = validate_all(&p, 1)) != RSM_OK) return st;
+  const size_t need = rsm_footprint_bytes(&p);
+  if (need > h->budget) return fail(RSM_ERR_NO_MEMORY, "problem footprint above the handle's HBM budget");
+  // candidates: the default first, then every slab size and occupancy, then one warp per submatrix
+  const int mode = p.gram_prec == RSM_PREC_F64 ? 0 : p.gram_prec == RSM_PREC_F32X2 ? 1 : 2;
+  const int l = p.l ? p.l : p.r + 1;
+  // (the occupancy variant only where its build differs: more registers per thread)
+  std::vector<Tune> cand{Tune{}};
+  if (slab_supported(mode, l, p.y_dtype)) {
+    const bool occ = gram_slab_regs(mode, l, 1) != gram_slab_regs(mode, l, 0);
+    for (int mib : {8, 16, 32, 64})
+      for (int v = 0; v <= (occ ? 1 : 0); ++v)
+        if (!(mib == 32 && v == 0)) cand.push_back(Tune{0, mib, v});
+  }
+  cand.push_back(Tune{1, 32, 0});
+  // between timed runs, a write larger than L2 evicts the previous run's Y, as a
+  // stream of calls on different problems would
+  constexpr size_t kFlush = (size_t)256 << 20;
+  DevBuf flush;
+  struct Release {
+    DevBuf& b;
+    ~Release() { b.release(); }
+  } release_flush{flush};
+  const bool flushing = need + kFlush <= h->budget && flush.reserve(kFlush) == RSM_OK;
+  std::vector<double> best_ms(cand.size(), INFINITY);
+  for (size_t c = 0; c < cand.size(); ++c) {
+    for (int k = 0; k <= reps; ++k) {  // k == 0: untimed warm-up
+      if (flushing) RSM_CUDA(launch_zero16(flush.ptr, kFlush, h->main.stream));
+      rsm_result r{};
+      st = run_batch(h, h->main, &p, 1, &r, nullptr, &cand[c]);
+      if (st != RSM_OK && st != RSM_ERR_UNDERDETERMINED && st != RSM_ERR_ROWS_UNDERDETERMINED) return st;
+      if (k > 0) best_ms[c] = std::min(best_ms[c], (double)r.stage_ms[3]);
+    }
+  }
+  size_t best = 0;
+  for (size_t c = 1; c < cand.size(); ++c)
+    if (best_ms[c] < best_ms[best]) best = c;
+  rsm_tune t{};
+  t.schedule = cand[best].schedule;
+  t.slab_mib = cand[best].slab_mib;
+  t.variant = cand[best].variant;
+  t.candidates = (int32_t)cand.size();
+  t.gram_ms = best_ms[best];
+  t.default_ms = best_ms[0];
+  {
+    std::lock_guard<std::mutex> tl(h->tune_mu);
+    h->tuned[tune_key(p)] = {cand[best], t};
+  }
+  if (out) *out = t;
+  return RSM_OK;
+}
+
+int32_t rsm_autotune_lookup(rsm_handle* h, const rsm_problem* p, rsm_tune* out) {
+  if (!h || !p) return -RSM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> tl(h->tune_mu);
+  auto it = h->tuned.find(tune_key(*p));
+  if (it == h->tuned.end()) return 0;
+  if (out) *out = it->second.second;
+  return 1;
+}
+
+int32_t rsm_autotune_clear(rsm_handle* h) {
+  if (!h) return fail(RSM_ERR_INVALID_ARG, "handle is NULL");
+  std::lock_guard<std::mutex> tl(h->tune_mu);
+  h->tuned.clear();
+  return RSM_OK;
+}
+
+int32_t rsm_autotune_save(rsm_handle* h, const char* path) {
+  if (!h || !path) return fail(RSM_ERR_INVALID_ARG, "handle and path are required");
+  std::lock_guard<std::mutex> tl(h->tune_mu);
+  FILE* f = std::fopen(path, "w");
+  if (!f) return fail(RSM_ERR_INVALID_ARG, std::string("cannot write ") + path);
+  std::fprintf(f, "# rsm autotune v1: gram_prec y_dtype l n log2m schedule slab_mib variant gram_ms default_ms\n");
+  for (const auto& kv : h->tuned) {
+    const auto& k = kv.first;
+    const rsm_tune& t = kv.second.second;
+    std::fprintf(f, "%lld %lld %lld %lld %lld %d %d %d %.6g %.6g\n", (long long)k[0], (long long)k[1],
+                 (long long)k[2], (long long)k[3], (long long)k[4], t.schedule, t.slab_mib, t.variant, t.gram_ms,
+                 t.default_ms);
+  }
+  const bool ok = std::fflush(f) == 0;
+  std::fclose(f);
+  return ok ? RSM_OK : fail(RSM_ERR_INVALID_ARG, std::string("write failed: ") + path);
+}
+
+int32_t rsm_autotune_load(rsm_handle* h, const char* path) {
+  if (!h || !path) return fail(RSM_ERR_INVALID_ARG, "handle and path are required");
+  FILE* f = std::fopen(path, "r");
+  if (!f) return fail(RSM_ERR_INVALID_ARG, std::string("cannot read ") + path);
+  std::map<std::vector<int64_t>, std::pair<Tune, rsm_tune>> got;
+  char line[512];
+  int lineno = 0;
+  while (std::fgets(line, sizeof line, f)) {
+    ++lineno;
+    if (line[0] == '#' || line[0] == '\n') continue;
+    long long k[5];
+    int sc, mib, v;
+    double g, d;
+    const bool ok = std::sscanf(line, "%lld %lld %lld %lld %lld %d %d %d %lf %lf", &k[0], &k[1], &k[2], &k[3], &k[4],
+                                &sc, &mib, &v, &g, &d) == 10 &&
+                    (sc == 0 || sc == 1) && (mib == 8 || mib == 16 || mib == 32 || mib == 64) && (v == 0 || v == 1) &&
+                    k[2] >= 2 && k[3] >= 2 && k[4] >= 0 && k[4] < 63;
+    if (!ok) {
+      std::fclose(f);
+      return fail(RSM_ERR_INVALID_ARG, std::string(path) + ":" + std::to_string(lineno) + ": malformed entry");
+    }
+    rsm_tune t{};
+    t.schedule = sc;
+    t.slab_mib = mib;
+    t.variant = v;
+    t.gram_ms = g;
+    t.default_ms = d;
+    got[{k[0], k[1], k[2], k[3], k[4]}] = {Tune{sc, mib, v}, t};
+  }
+  std::fclose(f);
+  std::lock_guard<std::mutex> tl(h->tune_mu);
+  for (auto& kv : got) h->tuned[kv.first] = kv.second;
+  return RSM_OK;
 }
 
 // ---------------------------------------------------------------- serving

@@ -10,6 +10,7 @@ tensor of shape (m, n) with stride (1, ld), e.g. ``t.t().contiguous().t()``.
 from __future__ import annotations
 
 import ctypes as C
+import os
 import dataclasses
 from typing import List, Optional, Sequence
 
@@ -242,6 +243,36 @@ class RSM:
         st = lib().rsm_eig_smallest(self._h, M.data_ptr(), n, r, V.data_ptr(), n, C.byref(res))
         _check(st, "rsm_eig_smallest", (_abi.RSM_OK, _abi.RSM_ERR_UNDERDETERMINED))
         return V, _result(res, dict(V=V))
+
+    @staticmethod
+    def _tune_dict(t) -> dict:
+        return dict(schedule="slab" if t.schedule == 0 else "per_submatrix", slab_mib=t.slab_mib,
+                    variant=t.variant, candidates=t.candidates, gram_ms=t.gram_ms, default_ms=t.default_ms)
+
+    def autotune(self, prob: Problem, reps: int = 3) -> dict:
+        """Time the Gram-stage choices on `prob` and keep the fastest for problems of its shape.
+
+        Overwrites prob's V; U and the debug outputs are left alone."""
+        self._order_after_current()
+        t = _abi.rsm_tune()
+        _check(lib().rsm_autotune(self._h, C.byref(prob.c), reps, C.byref(t)), "rsm_autotune")
+        return self._tune_dict(t)
+
+    def autotune_lookup(self, prob: Problem) -> Optional[dict]:
+        t = _abi.rsm_tune()
+        got = lib().rsm_autotune_lookup(self._h, C.byref(prob.c), C.byref(t))
+        if got < 0:
+            _check(-got, "rsm_autotune_lookup")
+        return self._tune_dict(t) if got == 1 else None
+
+    def autotune_clear(self):
+        _check(lib().rsm_autotune_clear(self._h), "rsm_autotune_clear")
+
+    def autotune_save(self, path: str):
+        _check(lib().rsm_autotune_save(self._h, os.fsencode(path)), "rsm_autotune_save")
+
+    def autotune_load(self, path: str):
+        _check(lib().rsm_autotune_load(self._h, os.fsencode(path)), "rsm_autotune_load")
 
     def submit(self, prob: Problem) -> int:
         t = C.c_uint64()
