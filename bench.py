@@ -350,6 +350,62 @@ def gather_probe(dev, stream, per_line: int) -> float:
     return best
 
 
+def gpu_numa_cpus(dev):
+    """(NUMA node of the GPU's PCI function, the CPUs of that node this process may use), or (None, None)."""
+    import torch
+    try:
+        pr = torch.cuda.get_device_properties(dev)
+        bus = f"{pr.pci_domain_id:04x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+        with open(f"/sys/bus/pci/devices/{bus}/numa_node") as f:
+            node = int(f.read().strip())
+        if node < 0:
+            return None, None
+        with open(f"/sys/devices/system/node/node{node}/cpulist") as f:
+            cpus = set()
+            for part in f.read().strip().split(","):
+                a, _, b = part.partition("-")
+                cpus.update(range(int(a), int(b or a) + 1))
+        cpus &= os.sched_getaffinity(0)
+        return node, (cpus or None)
+    except Exception:
+        return None, None
+
+
+def pinned_near(dev, shape, dtype, fill=None):
+    """A pinned host tensor whose pages are first touched from the CPUs of the GPU's NUMA node
+    (the process's CPU affinity is narrowed for the allocation and the fill, then restored)."""
+    import torch
+    node, cpus = gpu_numa_cpus(dev)
+    old = os.sched_getaffinity(0)
+    try:
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+        t = torch.empty(shape, dtype=dtype, pin_memory=True)
+        if fill is not None:
+            t.copy_(fill)
+        else:
+            t.zero_()
+    finally:
+        if cpus:
+            os.sched_setaffinity(0, old)
+    return t, node
+
+
+def h2d_rate(src, dst, stream, reps=3) -> float:
+    """GB/s of one pinned host -> device copy of src into dst on `stream` (best of reps)."""
+    import torch
+    best = float("inf")
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        with torch.cuda.stream(stream):
+            dst.copy_(src, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return src.numel() * src.element_size() / (best * 1e-3) / 1e9
+
+
 def subspace_angle_np(a, b) -> float:
     qa, _ = np.linalg.qr(a)
     qb, _ = np.linalg.qr(b)
@@ -447,12 +503,10 @@ def bench_mine(args):
     # computes (two device buffer sets).
     e2e = None
     if not args.no_e2e:
-        hY = torch.empty((p.n, p.m), dtype=torch.float32, pin_memory=True)
-        hY.copy_(Y32.t())
-        hW = torch.empty((p.n, p.m), dtype=torch.uint8, pin_memory=True)
-        hW.copy_(W.t())
-        hU = torch.empty((p.r, p.m), dtype=torch.float64, pin_memory=True)
-        hV = torch.empty((p.r, p.n), dtype=torch.float64, pin_memory=True)
+        hY, numa = pinned_near(dev, (p.n, p.m), torch.float32, Y32.t())
+        hW, _ = pinned_near(dev, (p.n, p.m), torch.uint8, W.t())
+        hU, _ = pinned_near(dev, (p.r, p.m), torch.float64)
+        hV, _ = pinned_near(dev, (p.r, p.n), torch.float64)
         sets = []
         for _ in range(2):
             dY = torch.empty((p.n, p.m), dtype=torch.float32, device=dev)
@@ -483,6 +537,7 @@ def bench_mine(args):
             stream.wait_stream(cs)
 
         e2e_run(max(1, args.warmup))
+        h2d_gbs = h2d_rate(hY, sets[0][0], cs)
         barrier_sync(ws)
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record(stream)
@@ -494,8 +549,12 @@ def bench_mine(args):
         d2h = hU.numel() * 8 + hV.numel() * 8
         e2e = {"value": replica_throughput(ws, args.steps, e2e_ms), "unit": "decomps/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms / args.steps,
+               "h2d_gbs": round(h2d_gbs, 1), "h2d_ms_per_step": round(h2d / (h2d_gbs * 1e9) * 1e3, 3),
+               "host_numa_node": numa,
                "note": "pinned host Y (FP32) and W copied in, U and V copied out, every step; step k+1's "
-                       "inputs copy on a second stream while step k computes"}
+                       "inputs copy on a second stream while step k computes; h2d_gbs is one pinned copy "
+                       "of Y alone, so a step cannot be shorter than h2d_ms_per_step; the pinned buffers are "
+                       "first touched from the CPUs of the GPU's NUMA node (host_numa_node)"}
 
     # roofline of the dominant kernel: fused row selection + Gram (HBM-bound)
     stage = {k: statistics.median([r_.stage_ms[k] for r_ in res]) for k in STAGES}

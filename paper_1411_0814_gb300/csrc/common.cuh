@@ -83,6 +83,7 @@ struct ProbDesc {
   // normal equations on the tensor cores (FP32 form): padded N of the W x Kw product, V columns per row of
   // the FP32 V copy; V in FP32 for the FP32 residual (row j at vf32 + j * vf_ld)
   int32_t tc;  // 1: this problem's normal equations run on the tensor cores
+  const void* tmap;  // TMA descriptors (128 B each) of Y and of the packed mask, or NULL
   int32_t gram_fp32;  // 1: the Gram is accumulated in plain FP32
   int32_t tc_npad;
   int32_t tc_rb;

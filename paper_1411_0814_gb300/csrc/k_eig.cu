@@ -779,6 +779,7 @@ constexpr int kSplit = 32;   // split of the inner dimension of the product M X 
 constexpr int kPSplit = 16;  // split of the inner dimension of the preconditioner product (R slots 1..16)
 constexpr int kMxRows = 128;  // rows per CTA of M X (one per thread)
 constexpr int kMxSub = 64;    // columns of X staged per pass
+constexpr int kMxGroup = 16;  // loads of M issued together (L2 latency is hidden by their number, not by warps)
 
 // out = M X to about FP64 accuracy on the FP32 pipes (FP64 instructions issue
 // far slower than FP32 ones here).  M is held as FP32 pairs (hi + lo, 48
@@ -825,18 +826,27 @@ __global__ void __launch_bounds__(kMxRows) k_gemm_MX(const ProbDesc* __restrict_
     }
     __syncthreads();
     if (i < n) {
-      for (int jj = 0; jj < jn; ++jj) {
-        const float2 m = __ldg(Mdf + (j0 + jj) * n + i);
+      // the loads of a group of kMxGroup columns are all in flight before the first product
+      for (int g0 = 0; g0 < jn; g0 += kMxGroup) {
+        float2 mv[kMxGroup];
 #pragma unroll
-        for (int c = 0; c < KXB; ++c) {
-          const float2 x = xs[jj][c];
-          const float ph = __fmul_rn(m.x, x.x);
-          const float pe = __fmaf_rn(m.x, x.x, -ph);
-          const float cross = __fmaf_rn(m.x, x.y, __fmul_rn(m.y, x.x));
-          float s, er;
-          two_sum(sh[c], ph, s, er);
-          sh[c] = s;
-          sl[c] = __fadd_rn(sl[c], __fadd_rn(er, __fadd_rn(pe, cross)));
+        for (int u = 0; u < kMxGroup; ++u)
+          mv[u] = g0 + u < jn ? __ldg(Mdf + (j0 + g0 + u) * n + i) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < kMxGroup; ++u) {
+          if (g0 + u >= jn) break;
+          const float2 m = mv[u];
+#pragma unroll
+          for (int c = 0; c < KXB; ++c) {
+            const float2 x = xs[g0 + u][c];
+            const float ph = __fmul_rn(m.x, x.x);
+            const float pe = __fmaf_rn(m.x, x.x, -ph);
+            const float cross = __fmaf_rn(m.x, x.y, __fmul_rn(m.y, x.x));
+            float s, er;
+            two_sum(sh[c], ph, s, er);
+            sh[c] = s;
+            sl[c] = __fadd_rn(sl[c], __fadd_rn(er, __fadd_rn(pe, cross)));
+          }
         }
       }
     }
@@ -878,10 +888,16 @@ __global__ void __launch_bounds__(kMxRows) k_gemm_MX64(const ProbDesc* __restric
     }
     __syncthreads();
     if (i < n) {
-      for (int jj = 0; jj < jn; ++jj) {
-        const double m = __ldg(M + (j0 + jj) * n + i);
+      for (int g0 = 0; g0 < jn; g0 += kMxGroup) {
+        double mv[kMxGroup];
 #pragma unroll
-        for (int c = 0; c < KXB; ++c) acc[c] = fma(m, xs[jj][c], acc[c]);
+        for (int u = 0; u < kMxGroup; ++u) mv[u] = g0 + u < jn ? __ldg(M + (j0 + g0 + u) * n + i) : 0.0;
+#pragma unroll
+        for (int u = 0; u < kMxGroup; ++u) {
+          if (g0 + u >= jn) break;
+#pragma unroll
+          for (int c = 0; c < KXB; ++c) acc[c] = fma(mv[u], xs[g0 + u][c], acc[c]);
+        }
       }
     }
   }

@@ -105,6 +105,44 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
   for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// 2-D tiled TMA load of the box at coordinates (x, y) (x innermost) into shared memory.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(tmap), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Untiled bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// The descriptors were written to global memory through the generic proxy (by an earlier kernel).
+__device__ __forceinline__ void tensormap_acquire(const void* tmap) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap) : "memory");
+}
+
+// Barrier 1 over the 128 row threads (the copy warp does not take part); the
+// second form returns whether pred held in any of them.
+__device__ __forceinline__ void rows_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ bool rows_sync_or(bool pred) {
+  uint32_t out;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 128, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(out)
+      : "r"((uint32_t)pred)
+      : "memory");
+  return out != 0;
+}
+
 }  // namespace
 
 // Bytes of one stage: W tile, Kw hi and lo tiles, the chunk's V (RB per column), mask words.
@@ -164,6 +202,136 @@ __global__ void __launch_bounds__(256) k_build_B_tc(const ProbDesc* __restrict__
   }
 }
 
+// Epilogue of the tensor-core normal equations, threads 0..127 (thread = row
+// i0 + tid): read [N_i | |K_i|] out of tensor memory; for r <= 8 solve the r x r
+// system right here, else hand N_i, b_i and |K_i| to the FP64 table.  scratch:
+// 128 x 37 floats of shared memory that no copy or MMA still touches.
+template <int RB>
+__device__ __forceinline__ void tc_epilogue(const ProbDesc& d, int p, uint32_t tmem, unsigned char* scratch,
+                                            uint32_t row, bool row_in, const float (&bacc)[RB],
+                                            unsigned long long* __restrict__ fail_list,
+                                            unsigned long long* __restrict__ fail_count) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int r = d.r, P = r * (r + 1) / 2, npad = d.tc_npad;
+  if (RB == 8) {
+    // r <= 8: solve the r x r system of this row right here.  N_i and b_i come
+    // out of the FP32 accumulation; the Cholesky factorisation and the two
+    // triangular solves run in FP64.  N_i goes through shared memory (the stages
+    // are idle now) so the packed index can depend on r.
+    float* nsm = reinterpret_cast<float*>(scratch) + tid * 37;
+    float cnt = 0.f;
+    for (int cb = 0; cb < npad; cb += 16) {
+      float v[16];
+      tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int q = cb + k;
+        if (q < P) nsm[q] = v[k];
+        if (q == P) cnt = v[k];
+      }
+    }
+    double L[36], u[8];
+    double tr = 0.0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      if (a >= r) break;
+#pragma unroll
+      for (int b = 0; b <= a; ++b) L[a * (a + 1) / 2 + b] = (double)nsm[b * r - b * (b - 1) / 2 + (a - b)];
+      tr += L[a * (a + 1) / 2 + a];
+    }
+    // a pivot below 1e-6 trace(N_i) is not resolved by the FP32-accumulated N_i:
+    // such rows take the minimum-norm path
+    bool ok = cnt >= (float)r;
+    double rdiag[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (j >= r || !ok) break;
+      double v = L[j * (j + 1) / 2 + j];
+#pragma unroll
+      for (int t = 0; t < j; ++t) v = fma(-L[j * (j + 1) / 2 + t], L[j * (j + 1) / 2 + t], v);
+      if (!(v > 1e-6 * tr)) {
+        ok = false;
+        break;
+      }
+      const double iv = rsqrt64(v);
+      rdiag[j] = iv;
+      L[j * (j + 1) / 2 + j] = v * iv;
+#pragma unroll
+      for (int k = j + 1; k < 8; ++k) {
+        if (k >= r) break;
+        double w = L[k * (k + 1) / 2 + j];
+#pragma unroll
+        for (int t = 0; t < j; ++t) w = fma(-L[k * (k + 1) / 2 + t], L[j * (j + 1) / 2 + t], w);
+        L[k * (k + 1) / 2 + j] = w * iv;
+      }
+    }
+    if (row_in) {
+      if (ok) {
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {  // C y = b
+          if (a >= r) break;
+          double v = (double)bacc[a];
+#pragma unroll
+          for (int t = 0; t < a; ++t) v = fma(-L[a * (a + 1) / 2 + t], u[t], v);
+          u[a] = v * rdiag[a];
+        }
+#pragma unroll
+        for (int a = 7; a >= 0; --a) {  // C^T u = y
+          if (a >= r) continue;
+          double v = u[a];
+#pragma unroll
+          for (int t = a + 1; t < 8; ++t)
+            if (t < r) v = fma(-L[t * (t + 1) / 2 + a], u[t], v);
+          u[a] = v * rdiag[a];
+        }
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+          if (a < r) d.U[(int64_t)a * d.ldu + row] = u[a];
+        // the factor, for the refinement step of the residual pass
+        float* lf = d.Lf + (size_t)row * P;
+#pragma unroll
+        for (int q = 0; q < 36; ++q)
+          if (q < P) lf[q] = (float)L[q];
+      } else {
+        d.Lf[(size_t)row * P] = -1.f;  // no refinement: the minimum-norm path owns this row
+        // too few known entries or a (numerically) singular N_i: hand the row to the
+        // minimum-norm path with its data in the FP64 table
+        double* out = d.NB + (size_t)row * d.q_pad;
+        for (int q = 0; q < P; ++q) out[q] = (double)nsm[q];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+          if (a < r) out[P + a] = (double)bacc[a];
+        out[P + r] = (double)cnt;
+        if (cnt < (float)r) atomicAdd(&d.counters[4], 1ull);
+        const unsigned long long slot = atomicAdd(fail_count, 1ull);
+        fail_list[slot] = ((unsigned long long)p << 32) | (unsigned long long)row;
+      }
+    }
+  } else {
+    // tensor-memory loads are warp-wide: every lane loads, only rows < m store
+    double* out = d.NB + (size_t)(row_in ? row : 0) * d.q_pad;
+    for (int cb = 0; cb < npad; cb += 16) {
+      float v[16];
+      tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+      if (row_in) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int q = cb + k;
+          if (q < P)
+            out[q] = (double)v[k];
+          else if (q == P)
+            out[P + r] = (double)v[k];  // |K_i|
+        }
+      }
+    }
+    if (row_in) {
+#pragma unroll
+      for (int a = 0; a < RB; ++a)
+        if (a < r) out[P + a] = (double)bacc[a];
+    }
+  }
+}
+
 template <int RB>
 __global__ void __launch_bounds__(kThreads) k_normal_tc(const ProbDesc* __restrict__ descs,
                                                        const int64_t* __restrict__ off, int nprob,
@@ -175,7 +343,7 @@ __global__ void __launch_bounds__(kThreads) k_normal_tc(const ProbDesc* __restri
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int r = d.r, P = r * (r + 1) / 2, npad = d.tc_npad;
+  const int npad = d.tc_npad;
   const int ncols = tc_tmem_cols(npad);
   const uint32_t m = (uint32_t)d.m, n = (uint32_t)d.n;
   const uint32_t i0 = (uint32_t)(blockIdx.x - off[p]) * kRows;
@@ -304,122 +472,172 @@ __global__ void __launch_bounds__(kThreads) k_normal_tc(const ProbDesc* __restri
   tc_fence_after();
   if (failed) {
     if (tid == 0) atomicAdd(&d.counters[6], 1ull);
-  } else if (RB == 8) {
-    // r <= 8: solve the r x r system of this row right here.  N_i and b_i come
-    // out of the FP32 accumulation; the Cholesky factorisation and the two
-    // triangular solves run in FP64.  N_i goes through shared memory (the stages
-    // are idle now) so the packed index can depend on r.
-    float* nsm = reinterpret_cast<float*>(tc_smem) + tid * 37;
-    float cnt = 0.f;
-    for (int cb = 0; cb < npad; cb += 16) {
-      float v[16];
-      tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int q = cb + k;
-        if (q < P) nsm[q] = v[k];
-        if (q == P) cnt = v[k];
-      }
+  } else {
+    tc_epilogue<RB>(d, p, tmem, tc_smem, row, row_in, bacc, fail_list, fail_count);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// The same product with TMA: a copy warp streams each chunk's Y tile (128 rows
+// x 32 columns, tensor map over the caller's column-major Y), its mask words
+// (tensor map over the packed mask) and its B images (bulk copies) into a ring
+// of stages, each completing one mbarrier by transaction count; the 128 row
+// threads wait on it, read their row's 32 values and mask bits, accumulate b_i,
+// then write the W tile over the Y tile they have read (K-major core matrices),
+// and thread 0 issues the MMAs, whose commit frees the stage for the copy warp.
+// Stage layout: [Y tile, then W tile: 16 KB | Kw hi, lo | V (32 x RB) | mask 4 x 32 words].
+__host__ __device__ constexpr size_t tma_stage_bytes(int npad, int rb) {
+  return (size_t)kRows * kChunkK * 4 + (size_t)2 * npad * kChunkK * 4 + (size_t)kChunkK * rb * 4 + kChunkK * 4 * 4;
+}
+constexpr int kTmaThreads = kRows + 32;
+
+template <int RB>
+__global__ void __launch_bounds__(kTmaThreads) k_normal_tma(const ProbDesc* __restrict__ descs,
+                                                           const int64_t* __restrict__ off, int nprob,
+                                                           unsigned long long* __restrict__ fail_list,
+                                                           unsigned long long* __restrict__ fail_count, int nstage) {
+  extern __shared__ __align__(1024) unsigned char tma_smem_raw[];
+  __shared__ __align__(8) unsigned long long full[kMaxStages], empty[kMaxStages];
+  __shared__ uint32_t tmem_slot;
+  // TMA destinations: 128-byte aligned
+  unsigned char* smem = tma_smem_raw + ((128u - (smem_u32(tma_smem_raw) & 127u)) & 127u);
+  const int p = find_problem(off, nprob, blockIdx.x);
+  const ProbDesc& d = descs[p];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int npad = d.tc_npad;
+  const int ncols = tc_tmem_cols(npad);
+  const uint32_t m = (uint32_t)d.m, n = (uint32_t)d.n;
+  const uint32_t i0 = (uint32_t)(blockIdx.x - off[p]) * kRows;
+  const uint32_t row = i0 + (uint32_t)tid;
+  const bool row_in = tid < kRows && row < m;
+  const int nchunk = (int)((n + kChunkK - 1) / kChunkK);
+  const uint32_t a_bytes = kRows * kChunkK * 4, b_bytes = (uint32_t)npad * kChunkK * 4;
+  const uint32_t v_bytes = kChunkK * RB * 4, w_bytes = kChunkK * 4 * 4;
+  const uint32_t stage_bytes = (uint32_t)tma_stage_bytes(npad, RB);
+  const float* img = reinterpret_cast<const float*>(d.Kmat);
+  const float* vf = img + (size_t)nchunk * kChunkK * 2 * npad;
+  const unsigned char* tmaps = static_cast<const unsigned char*>(d.tmap);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int k = 0; k < nstage; ++k) {
+      mbar_init(smem_u32(&full[k]), 1);
+      mbar_init(smem_u32(&empty[k]), 1);
     }
-    double L[36], u[8];
-    double tr = 0.0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  bool failed = false;
+  float bacc[RB];
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      if (a >= r) break;
-#pragma unroll
-      for (int b = 0; b <= a; ++b) L[a * (a + 1) / 2 + b] = (double)nsm[b * r - b * (b - 1) / 2 + (a - b)];
-      tr += L[a * (a + 1) / 2 + a];
-    }
-    // a pivot below 1e-6 trace(N_i) is not resolved by the FP32-accumulated N_i:
-    // such rows take the minimum-norm path
-    bool ok = cnt >= (float)r;
-    double rdiag[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      if (j >= r || !ok) break;
-      double v = L[j * (j + 1) / 2 + j];
-#pragma unroll
-      for (int t = 0; t < j; ++t) v = fma(-L[j * (j + 1) / 2 + t], L[j * (j + 1) / 2 + t], v);
-      if (!(v > 1e-6 * tr)) {
-        ok = false;
-        break;
-      }
-      const double iv = rsqrt64(v);
-      rdiag[j] = iv;
-      L[j * (j + 1) / 2 + j] = v * iv;
-#pragma unroll
-      for (int k = j + 1; k < 8; ++k) {
-        if (k >= r) break;
-        double w = L[k * (k + 1) / 2 + j];
-#pragma unroll
-        for (int t = 0; t < j; ++t) w = fma(-L[k * (k + 1) / 2 + t], L[j * (j + 1) / 2 + t], w);
-        L[k * (k + 1) / 2 + j] = w * iv;
-      }
-    }
-    if (row_in) {
-      if (ok) {
-#pragma unroll
-        for (int a = 0; a < 8; ++a) {  // C y = b
-          if (a >= r) break;
-          double v = (double)bacc[a];
-#pragma unroll
-          for (int t = 0; t < a; ++t) v = fma(-L[a * (a + 1) / 2 + t], u[t], v);
-          u[a] = v * rdiag[a];
+  for (int a = 0; a < RB; ++a) bacc[a] = 0.f;
+
+  if (warp == kRows / 32) {
+    // copy warp: one lane issues every copy of every chunk
+    if (lane == 0) {
+      tensormap_acquire(tmaps);
+      tensormap_acquire(tmaps + 128);
+      int issued = 0;
+      for (int c = 0; c < nchunk; ++c) {
+        const int s = c % nstage;
+        // stage s was last read by the MMAs of chunk c - nstage
+        if (c >= nstage && !mbar_wait(smem_u32(&empty[s]), (uint32_t)(c / nstage - 1) & 1u)) {
+          failed = true;
+          break;
         }
-#pragma unroll
-        for (int a = 7; a >= 0; --a) {  // C^T u = y
-          if (a >= r) continue;
-          double v = u[a];
-#pragma unroll
-          for (int t = a + 1; t < 8; ++t)
-            if (t < r) v = fma(-L[t * (t + 1) / 2 + a], u[t], v);
-          u[a] = v * rdiag[a];
-        }
-#pragma unroll
-        for (int a = 0; a < 8; ++a)
-          if (a < r) d.U[(int64_t)a * d.ldu + row] = u[a];
-        // the factor, for the refinement step of the residual pass
-        float* lf = d.Lf + (size_t)row * P;
-#pragma unroll
-        for (int q = 0; q < 36; ++q)
-          if (q < P) lf[q] = (float)L[q];
-      } else {
-        d.Lf[(size_t)row * P] = -1.f;  // no refinement: the minimum-norm path owns this row
-        // too few known entries or a (numerically) singular N_i: hand the row to the
-        // minimum-norm path with its data in the FP64 table
-        double* out = d.NB + (size_t)row * d.q_pad;
-        for (int q = 0; q < P; ++q) out[q] = (double)nsm[q];
-#pragma unroll
-        for (int a = 0; a < 8; ++a)
-          if (a < r) out[P + a] = (double)bacc[a];
-        out[P + r] = (double)cnt;
-        if (cnt < (float)r) atomicAdd(&d.counters[4], 1ull);
-        const unsigned long long slot = atomicAdd(fail_count, 1ull);
-        fail_list[slot] = ((unsigned long long)p << 32) | (unsigned long long)row;
+        const uint32_t st = smem_u32(smem + (size_t)s * stage_bytes);
+        const uint32_t bar = smem_u32(&full[s]);
+        mbar_expect_tx(bar, a_bytes + 2 * b_bytes + v_bytes + w_bytes);
+        tma_load_2d(st, tmaps, (int)i0, c * kChunkK, bar);
+        bulk_load(st + a_bytes, img + (size_t)c * 2 * npad * kChunkK, 2 * b_bytes, bar);
+        bulk_load(st + a_bytes + 2 * b_bytes, vf + (size_t)c * kChunkK * RB, v_bytes, bar);
+        tma_load_2d(st + a_bytes + 2 * b_bytes + v_bytes, tmaps + 128, (int)(i0 >> 5), c * kChunkK, bar);
+        issued = c + 1;
       }
+      // nothing may still be landing when the CTA ends: wait (bounded) for the
+      // last use of every stage (already complete unless something failed)
+      for (int c = issued - 1; c >= 0 && c >= issued - nstage; --c)
+        mbar_wait(smem_u32(&full[c % nstage]), (uint32_t)(c / nstage) & 1u);
     }
   } else {
-    // tensor-memory loads are warp-wide: every lane loads, only rows < m store
-    double* out = d.NB + (size_t)(row_in ? row : 0) * d.q_pad;
-    for (int cb = 0; cb < npad; cb += 16) {
-      float v[16];
-      tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
-      if (row_in) {
+    for (int c = 0; c < nchunk; ++c) {
+      const int s = c % nstage;
+      const bool ok = mbar_wait(smem_u32(&full[s]), (uint32_t)(c / nstage) & 1u);
+      if (rows_sync_or(!ok)) {
+        failed = true;
+        break;
+      }
+      unsigned char* st = smem + (size_t)s * stage_bytes;
+      float* As = reinterpret_cast<float*>(st);
+      const float* Vs = reinterpret_cast<const float*>(st + a_bytes + 2 * b_bytes);
+      const uint32_t* Ws = reinterpret_cast<const uint32_t*>(st + a_bytes + 2 * b_bytes + v_bytes);
+      float w[kChunkK];
+      {
+        float y[kChunkK];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const int q = cb + k;
-          if (q < P)
-            out[q] = (double)v[k];
-          else if (q == P)
-            out[P + r] = (double)v[k];  // |K_i|
+        for (int jj = 0; jj < kChunkK; ++jj) {
+          y[jj] = As[jj * kRows + tid];  // the TMA box: 32 columns of 128 rows
+          w[jj] = (float)((Ws[jj * 4 + (tid >> 5)] >> lane) & 1u);
+        }
+#pragma unroll
+        for (int jj = 0; jj < kChunkK; ++jj) {
+          const float yw = w[jj] != 0.f ? y[jj] : 0.f;
+          const float4* vrow = reinterpret_cast<const float4*>(Vs + jj * RB);
+#pragma unroll
+          for (int a4 = 0; a4 < RB / 4; ++a4) {
+            const float4 v = vrow[a4];
+            bacc[4 * a4] = fmaf(yw, v.x, bacc[4 * a4]);
+            bacc[4 * a4 + 1] = fmaf(yw, v.y, bacc[4 * a4 + 1]);
+            bacc[4 * a4 + 2] = fmaf(yw, v.z, bacc[4 * a4 + 2]);
+            bacc[4 * a4 + 3] = fmaf(yw, v.w, bacc[4 * a4 + 3]);
+          }
         }
       }
-    }
-    if (row_in) {
+      rows_sync();  // every row thread has read the Y tile: overwrite it with the W tile
+      float4* arow = reinterpret_cast<float4*>(As) + (tid >> 3) * 8 + (tid & 7);
 #pragma unroll
-      for (int a = 0; a < RB; ++a)
-        if (a < r) out[P + a] = (double)bacc[a];
+      for (int kc = 0; kc < kChunkK / 4; ++kc)
+        arow[kc * (kRows * 4 / 4)] = make_float4(w[4 * kc], w[4 * kc + 1], w[4 * kc + 2], w[4 * kc + 3]);
+      proxy_fence();
+      rows_sync();
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(As), b0 = a0 + a_bytes;
+        const uint32_t a_lbo = kRows * 16, b_lbo = (uint32_t)npad * 16;
+        const uint32_t idesc = idesc_tf32(npad);
+#pragma unroll
+        for (int ks = 0; ks < kChunkK / 8; ++ks) {
+          const uint64_t ad = smem_desc(a0 + ks * 2 * a_lbo, a_lbo, 128);
+          const uint64_t bh = smem_desc(b0 + ks * 2 * b_lbo, b_lbo, 128);
+          const uint64_t bl = smem_desc(b0 + b_bytes + ks * 2 * b_lbo, b_lbo, 128);
+          tc_mma_tf32(tmem, ad, bh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+          tc_mma_tf32(tmem, ad, bl, idesc, 1u);
+        }
+        tc_commit(smem_u32(&empty[s]));
+      }
     }
+    // the last commit covers every MMA issued before it
+    if (tid == 0 && nchunk > 0 && !failed) {
+      const int c = nchunk - 1;
+      if (!mbar_wait(smem_u32(&empty[c % nstage]), (uint32_t)(c / nstage) & 1u)) failed = true;
+    }
+  }
+  failed = __syncthreads_or(failed) != 0;  // the same decision in every thread
+  tc_fence_after();
+  if (failed) {
+    if (tid == 0) atomicAdd(&d.counters[6], 1ull);
+  } else if (tid < kRows) {
+    tc_epilogue<RB>(d, p, tmem, smem, row, row_in, bacc, fail_list, fail_count);
   }
   tc_fence_before();
   __syncthreads();
@@ -441,6 +659,31 @@ cudaError_t launch_normal_tc(const SolvePlan& S, int rb_max, int npad_max, cudaS
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (S.tc_tiles <= 0) return cudaSuccess;
+  if (S.tc_tma) {
+    // three stages when two CTAs per SM fit, else two
+    const size_t st = tma_stage_bytes(npad_max, rb_max);
+    const int stages = 2 * (3 * st + 128) <= 232448 - 4096 ? 3 : 2;
+    const size_t smem = stages * st + 128;
+#define RSM_TMA(RB)                                                                                             \
+  do {                                                                                                          \
+    if ((e = cudaFuncSetAttribute(k_normal_tma<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != \
+        cudaSuccess) {                                                                                          \
+      cudaGetLastError();                                                                                       \
+      return e;                                                                                                 \
+    }                                                                                                           \
+    k_normal_tma<RB><<<(unsigned)S.tc_tiles, kTmaThreads, smem, s>>>(D, S.tc_off, np, S.fail_list, S.fail_count, \
+                                                                     stages);                                   \
+  } while (0)
+    if (rb_max <= 8)
+      RSM_TMA(8);
+    else if (rb_max <= 16)
+      RSM_TMA(16);
+    else
+      RSM_TMA(24);
+#undef RSM_TMA
+    ++g_kernel_launches;
+    return cudaGetLastError();
+  }
   // three stages when they fit in shared memory (227 KB per CTA), else two
   const int stages = 3 * tc_stage_bytes(npad_max, rb_max) <= 232448 ? 3 : 2;
   const size_t smem = stages * tc_stage_bytes(npad_max, rb_max);

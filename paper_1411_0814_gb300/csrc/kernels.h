@@ -63,6 +63,7 @@ struct SolvePlan {
   int64_t tc_tiles;
   const int64_t* tc_off;     // ceil(m / 128) per problem
   int tc_rb, tc_npad_max;
+  bool tc_tma;               // every tensor-core problem has its TMA descriptors (ProbDesc::tmap)
   bool any_solve;
 };
 bool normal_tc_supported(int r);

@@ -372,7 +372,8 @@ void build_batch(const rsm_problem* ps, int count, Batch& b, const Tune* tunes) 
   b.fail_list_off = off;
   off += align_up((size_t)b.solve_rows * 8);  // any solved row may take the minimum-norm path
   b.layout.total_bytes = off;
-  b.layout.plan_bytes = align_up(sizeof(ProbDesc) * count) + align_up(T.size() * 8);
+  b.layout.tmap_off = align_up(sizeof(ProbDesc) * count) + align_up(T.size() * 8);
+  b.layout.plan_bytes = b.layout.tmap_off + (size_t)256 * count;
   b.gram_mode = ps[0].gram_prec == RSM_PREC_F64 ? 0 : ps[0].gram_prec == RSM_PREC_F32X2 ? 1 : 2;
   b.solve_mode = ps[0].solve_prec == RSM_PREC_F64 ? 0 : 2;
 }

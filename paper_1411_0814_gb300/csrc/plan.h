@@ -39,7 +39,8 @@ struct Tune {
 struct BatchLayout {
   size_t zero_bytes = 0;   // [0, zero_bytes) must be zeroed before the launch
   size_t total_bytes = 0;  // workspace bytes
-  size_t plan_bytes = 0;   // descriptor + offset tables (uploaded to the start of the plan buffer)
+  size_t plan_bytes = 0;   // descriptor + offset tables + TMA descriptors (uploaded to the start of the plan buffer)
+  size_t tmap_off = 0;     // two 128-byte TMA descriptors per problem, from here
 };
 
 // Everything needed to launch one batch, built on the host.
@@ -49,6 +50,7 @@ struct Batch {
   int gram_mode = 0;
   int solve_mode = 0;
   bool any_solve = false;
+  bool tc_tma = false;  // the tensor-core normal equations read Y and the mask by TMA (set at upload)
   std::vector<Derived> dv;
   std::vector<ProbDesc> descs;  // host copies (device pointers filled by bind())
   std::vector<int64_t> tables;  // all int64 offset tables, concatenated

@@ -1,5 +1,7 @@
 // C ABI of librsm.so (include/rsm.h): handles, the synchronous and batched
 // decompositions, the serving loop and the stage entry points.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -314,6 +316,7 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
     sp.tc_off = T + b.o_tc;
     sp.tc_rb = b.tc_rb;
     sp.tc_npad_max = b.tc_npad_max;
+    sp.tc_tma = b.tc_tma;
     sp.resv_blocks = b.resv_blocks;
     sp.resv_off = T + b.o_resv;
     sp.any_solve = b.any_solve;
@@ -351,6 +354,49 @@ int enqueue_readback(Batch& b, Slot& slot) {
   return RSM_OK;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to
+// the driver library); NULL when the driver does not provide it.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+
+// TMA descriptors of a tensor-core problem (out: 256 bytes, 64-byte aligned):
+// its FP32 Y (m x n column-major, boxes of 128 rows x 32 columns) and its packed
+// mask (ldb words x n, boxes of 4 words x 32 columns).  False when the layout
+// does not allow it (Y or ldy not 16-byte aligned) or the encoder refuses.
+bool encode_tc_maps(const ProbDesc& d, void* out) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || d.y_dtype != RSM_F32) return false;
+  if ((reinterpret_cast<uintptr_t>(d.Y) & 15) || ((d.ldy * 4) & 15) || (reinterpret_cast<uintptr_t>(d.bits) & 15))
+    return false;
+  CUtensorMap* maps = static_cast<CUtensorMap*>(out);
+  const cuuint32_t estr[2] = {1, 1};
+  const cuuint64_t ydim[2] = {(cuuint64_t)d.m, (cuuint64_t)d.n};
+  const cuuint64_t ystride[1] = {(cuuint64_t)d.ldy * 4};
+  const cuuint32_t ybox[2] = {128, 32};
+  if (enc(&maps[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(d.Y), ydim, ystride, ybox, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  const cuuint64_t wdim[2] = {(cuuint64_t)d.ldb, (cuuint64_t)d.n};
+  const cuuint64_t wstride[1] = {(cuuint64_t)d.ldb * 4};
+  const cuuint32_t wbox[2] = {4, 32};
+  return enc(&maps[1], CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, d.bits, wdim, wstride, wbox, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Prepare slot buffers, upload the plan, zero the accumulators, launch, read
 // back and fill results.  Synchronises slot.stream.
 // given_M (count == 1 only): the caller's n x n M (device); the stages before
@@ -379,12 +425,24 @@ int run_batch(rsm_handle* h, Slot& slot, const rsm_problem* ps, int count, rsm_r
   // plan upload through the pinned buffer
   unsigned char* hp = static_cast<unsigned char*>(slot.host.ptr);
   const size_t dsz = (sizeof(ProbDesc) * count + 255) / 256 * 256;
+  // TMA descriptors of the tensor-core normal equations: all problems have them, or the batch
+  // takes the kernel without TMA
+  b.tc_tma = b.tc_total > 0;
+  for (int i = 0; i < count; ++i) {
+    ProbDesc& d = b.descs[i];
+    d.tmap = nullptr;
+    if (!d.tc) continue;
+    if (encode_tc_maps(d, hp + b.layout.tmap_off + (size_t)256 * i))
+      d.tmap = static_cast<unsigned char*>(slot.plan.ptr) + b.layout.tmap_off + (size_t)256 * i;
+    else
+      b.tc_tma = false;
+  }
   std::memcpy(hp, b.descs.data(), sizeof(ProbDesc) * count);
   std::memcpy(hp + dsz, b.tables.data(), b.tables.size() * 8);
   const int64_t launches0 = g_kernel_launches;
   RSM_CUDA(cudaEventRecord(slot.ev[0], slot.stream));
   // plan upload and zeroing by kernels, not by the copy engines (see k_util.cu)
-  RSM_CUDA(launch_copy16(hp, slot.plan.ptr, (dsz + b.tables.size() * 8 + 15) / 16 * 16, slot.stream));
+  RSM_CUDA(launch_copy16(hp, slot.plan.ptr, b.layout.plan_bytes, slot.stream));
   RSM_CUDA(launch_zero16(slot.ws.ptr, (b.layout.zero_bytes + 15) / 16 * 16, slot.stream));
   RSM_CUDA(cudaEventRecord(slot.ev[1], slot.stream));
   int64_t max_n = 0;
