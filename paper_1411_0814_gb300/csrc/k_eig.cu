@@ -31,6 +31,7 @@
 #include "common.cuh"
 #include "jacobi.cuh"
 #include "kernels.h"
+#include "small_df.cuh"
 
 namespace rsm {
 
@@ -959,7 +960,8 @@ __global__ void __launch_bounds__(256) k_xtx(const ProbDesc* __restrict__ descs,
       s0 = fma(xs[r * kx + a], y[r * kx + b], s0);
       s1 = fma(xs[(r + 1) * kx + a], y[(r + 1) * kx + b], s1);
     }
-    part[e] = s0 + s1;
+    const DF v = df_from(s0 + s1);
+    reinterpret_cast<float2*>(part)[e] = make_float2(v.hi, v.lo);  // FP32 pair: the reduction runs on the FP32 pipes
   }
 }
 
@@ -969,30 +971,24 @@ constexpr int kSmallThreads = 128;  // four warps: the FP64 products use all fou
 typedef double DRow[kLs];
 typedef float FRow[kLs];
 
-// Sum the per-chunk partials in a fixed order: S = X^T X (and H = X^T M X).
-__device__ inline void reduce_partials(const ProbDesc& d, const double* part, DRow* S, DRow* H, int kx) {
+// Sum the per-chunk partials (FP32 pairs, see k_xtx) in chunk order: S = X^T X
+// (and H = X^T M X), as FP32 pairs.
+__device__ inline void reduce_partials(const ProbDesc& d, const float2* part, DFRow* S, DFRow* H, int kx,
+                                       int nthreads) {
   const SmallDiv dkx((uint32_t)kx);  // quotient and remainder by kx without an integer division
   const int nchunk = (int)((d.n + kChunk - 1) / kChunk);
-  for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) {
-    double s = 0.0, h = 0.0;
-#pragma unroll 4
+  for (int e = threadIdx.x; e < kx * kx; e += nthreads) {
+    DFAcc s, h;
     for (int c = 0; c < nchunk; ++c) {
-      s += part[c * 2 * kx * kx + e];
-      if (H) h += part[c * 2 * kx * kx + kx * kx + e];
+      const float2 x = part[c * 2 * kx * kx + e];
+      s.add(DF{x.x, x.y});
+      if (H) {
+        const float2 y = part[c * 2 * kx * kx + kx * kx + e];
+        h.add(DF{y.x, y.y});
+      }
     }
-    S[dkx.q(e)][dkx.r(e)] = s;
-    if (H) H[dkx.q(e)][dkx.r(e)] = h;
-  }
-}
-
-// C = op(A) B for kx x kx blocks in shared memory, all threads of the CTA.
-__device__ inline void small_prod(DRow* C, const DRow* A, bool transA, const DRow* B, int kx) {
-  const SmallDiv dkx((uint32_t)kx);  // quotient and remainder by kx without an integer division
-  for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) {
-    const int a = dkx.q(e), b = dkx.r(e);
-    double s = 0.0;
-    for (int t = 0; t < kx; ++t) s = fma(transA ? A[t][a] : A[a][t], B[t][b], s);
-    C[a][b] = s;
+    S[dkx.q(e)][dkx.r(e)] = s.get();
+    if (H) H[dkx.q(e)][dkx.r(e)] = h.get();
   }
 }
 
@@ -1037,39 +1033,58 @@ __device__ inline void inv_transpose_factor(const CT (*C)[kLs], const CT* rdiag,
     }
 }
 
-// Orthonormalisation step of the subspace iteration: S = X^T X (FP64 partial
-// sums), S + s I = C C^T in precision CT, small[0 .. kx^2) = Q = C^-T so that
-// X Q has orthonormal columns.
-template <typename CT>
+// Orthonormalisation step of the subspace iteration: S = X^T X (FP32-pair
+// partial sums), S + s I = C C^T, small[0 .. kx^2) = Q = C^-T so that X Q has
+// orthonormal columns.  FP32 factor (KP > 0): one warp, rows in registers.
+// FP64 factor (KP == 0): the FP64 warp Cholesky in shared memory.
+template <int KP>
 __global__ void __launch_bounds__(kSmallThreads) k_orth(const ProbDesc* __restrict__ descs, int nprob,
-                                                      const double* __restrict__ part_base,
+                                                      const float2* __restrict__ part_base,
                                                       const int64_t* __restrict__ part_off) {
-  __shared__ CT S[kMaxL][kLs], Q[kMaxL][kLs];
-  __shared__ DRow Sd[kMaxL];
-  __shared__ CT rdiag[kMaxL];
+  __shared__ DFRow Sp[kMaxL];
   const int p = blockIdx.x;
   if (p >= nprob) return;
   const ProbDesc& d = descs[p];
   const int kx = d.kx;
   const SmallDiv dkx((uint32_t)kx);  // quotient and remainder by kx without an integer division
-  reduce_partials(d, part_base + part_off[p], Sd, nullptr, kx);
+  reduce_partials(d, part_base + part_off[p], Sp, nullptr, kx, kSmallThreads);
   __syncthreads();
-  for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) S[dkx.q(e)][dkx.r(e)] = (CT)Sd[dkx.q(e)][dkx.r(e)];
-  __syncthreads();
-  if (threadIdx.x < 32) warp_chol_shifted<CT>(S, rdiag, kx, (CT)(sizeof(CT) == 8 ? 1e-15 : 1e-6));
-  __syncthreads();
-  inv_transpose_factor<CT>(S, rdiag, Q, kx);
-  __syncthreads();
-  for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) d.small[e] = (double)Q[dkx.q(e)][dkx.r(e)];
+  if constexpr (KP > 0) {
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      float a[KP], y[KP];
+#pragma unroll
+      for (int j = 0; j < KP; ++j) a[j] = (lane < kx && j < kx) ? Sp[lane][j].hi : (lane == j ? 1.f : 0.f);
+      float rdiag = 1.f;
+      reg_cholesky<KP>(a, rdiag, 1e-6f, kx);
+      reg_tri_inverse<KP>(a, rdiag, y);
+      if (lane < kx)
+#pragma unroll
+        for (int c = 0; c < KP; ++c)
+          if (c < kx) d.small[c * kx + lane] = (double)y[c];  // Q = C^-T: Q[c][lane] = (C^-1)[lane][c]
+    }
+  } else {
+    __shared__ double S[kMaxL][kLs], Q[kMaxL][kLs];
+    __shared__ double rdiag[kMaxL];
+    for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) S[dkx.q(e)][dkx.r(e)] = df_to(Sp[dkx.q(e)][dkx.r(e)]);
+    __syncthreads();
+    if (threadIdx.x < 32) warp_chol_shifted<double>(S, rdiag, kx, 1e-15);
+    __syncthreads();
+    inv_transpose_factor<double>(S, rdiag, Q, kx);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) d.small[e] = Q[dkx.q(e)][dkx.r(e)];
+  }
 }
 
-// Rayleigh-Ritz step of the FP64 block iteration, one CTA per problem.
-// Reduce S = X^T X and H = X^T M X, factor S + s I = C C^T (FP64), Q1 = C^-T,
-// H1 = Q1^T H Q1.  Then, with FP64 work kept to a few kx^3 products (FP64
-// issues far slower than FP32 here, and an FP64 Jacobi sweep costs tens of
-// microseconds on one warp):
-//  - FP32 Jacobi on H1 gives eigenvectors to FP32 accuracy, sorted by Ritz value;
-//  - two Lowdin steps Q2 <- Q2 (3I - Q2^T Q2) / 2 make them orthogonal in FP64;
+// Rayleigh-Ritz step of the block iteration, one CTA per problem, in FP32
+// pairs (small_df.cuh) with FP32 seeds:
+//  - S = X^T X and H = X^T M X from the partial sums;
+//  - FP32 Cholesky S + s I = C C^T and Q0 = C^-T (one warp, registers), then
+//    one Newton-Schulz step Q1 = Q0 (3I - Q0^T S Q0) / 2, which squares the
+//    FP32 error: X Q1 is orthonormal to the pair precision;
+//  - H1 = Q1^T H Q1; FP32 Jacobi of H1 gives eigenvectors to FP32 accuracy,
+//    sorted by Ritz value; two Lowdin steps Q2 <- Q2 (3I - Q2^T Q2) / 2 make
+//    them orthogonal to the pair precision;
 //  - B = Q2^T H1 Q2 is diagonal up to the FP32 error; what matters is the
 //    coupling B12 between the r wanted and the kx - r other columns, which a
 //    first-order rotation removes: G = I + A with A_pq = B_pq / (B_qq - B_pp)
@@ -1077,95 +1092,63 @@ __global__ void __launch_bounds__(kSmallThreads) k_orth(const ProbDesc* __restri
 //    defined), made orthogonal by one Lowdin step.  The coupling left is
 //    second order, ||B12||^2 / gap.  Mixing inside the wanted (or the other)
 //    block is harmless: only the two subspaces matter.
-// Writes small = [Q | H' | theta] with Q = Q1 Q2 G, H' = Q^T H Q (FP64) and
+// Writes small = [Q | H' | theta] (FP64) with Q = Q1 Q2 G, H' = Q^T H Q and
 // theta = diag(H') in ascending order of the FP32 Ritz values.
-constexpr size_t kRRSmem = sizeof(DRow) * kMaxL * 7 + sizeof(FRow) * kMaxL * 2;
+constexpr int kRRThreads = 256;
+constexpr size_t kRRSmem = sizeof(DFRow) * kMaxL * 8;
 
-__device__ inline void lowdin_step(DRow* Q, DRow* W1, DRow* W2, int kx) {  // Q <- Q (3I - Q^T Q) / 2
-  const SmallDiv dkx((uint32_t)kx);  // quotient and remainder by kx without an integer division
-  small_prod(W1, Q, true, Q, kx);
-  __syncthreads();
-  for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) {
-    const int a = dkx.q(e), b = dkx.r(e);
-    double s = 0.0;
-    for (int t = 0; t < kx; ++t) s = fma(Q[a][t], ((t == b) ? 3.0 : 0.0) - W1[t][b], s);
-    W2[a][b] = 0.5 * s;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) Q[dkx.q(e)][dkx.r(e)] = W2[dkx.q(e)][dkx.r(e)];
-  __syncthreads();
-}
-
-__device__ inline void sym_congruence(DRow* out, const DRow* Q, const DRow* A, DRow* W, int kx) {  // out = Q^T A Q
-  const SmallDiv dkx((uint32_t)kx);  // quotient and remainder by kx without an integer division
-  small_prod(W, A, false, Q, kx);
-  __syncthreads();
-  for (int e = threadIdx.x; e < kx * kx; e += kSmallThreads) {
-    const int a = dkx.q(e), b = dkx.r(e);
-    const int lo = a < b ? a : b, hi = a < b ? b : a;
-    double s = 0.0;
-    for (int t = 0; t < kx; ++t) s = fma(Q[t][lo], W[t][hi], s);
-    out[a][b] = s;
-  }
-  __syncthreads();
-}
-
-__global__ void __launch_bounds__(kSmallThreads) k_rr64(const ProbDesc* __restrict__ descs, int nprob,
-                                                      const double* __restrict__ part_base,
-                                                      const int64_t* __restrict__ part_off) {
+template <int KP>
+__global__ void __launch_bounds__(kRRThreads) k_rr(const ProbDesc* __restrict__ descs, int nprob,
+                                                   const float2* __restrict__ part_base,
+                                                   const int64_t* __restrict__ part_off) {
   extern __shared__ __align__(16) unsigned char rr_smem[];
-  DRow* S = reinterpret_cast<DRow*>(rr_smem);
-  DRow* H = S + kMaxL;
-  DRow* Q1 = H + kMaxL;
-  DRow* W1 = Q1 + kMaxL;
-  DRow* H1 = W1 + kMaxL;
-  DRow* Q2 = H1 + kMaxL;
-  DRow* W2 = Q2 + kMaxL;
-  FRow* Sf = reinterpret_cast<FRow*>(W2 + kMaxL);
-  FRow* Vf = Sf + kMaxL;
-  __shared__ JacobiScratchT<float> jsf;
-  __shared__ int order[kMaxL];
-  __shared__ double rdiag[kMaxL];
-  __shared__ int rotated, coupled;
+  DFRow* S = reinterpret_cast<DFRow*>(rr_smem);
+  DFRow* H = S + kMaxL;
+  DFRow* Q1 = H + kMaxL;
+  DFRow* H1 = Q1 + kMaxL;
+  DFRow* Q2 = H1 + kMaxL;
+  DFRow* B = Q2 + kMaxL;
+  DFRow* W1 = B + kMaxL;
+  DFRow* W2 = W1 + kMaxL;
+  __shared__ int coupled;
   const int p = blockIdx.x;
   if (p >= nprob) return;
   const ProbDesc& d = descs[p];
   if (d.stats[kConvFlag] != 0.0) return;
-  const int kx = d.kx, r = d.r, tid = threadIdx.x;
+  const int kx = d.kx, r = d.r, tid = threadIdx.x, lane = tid & 31;
   const SmallDiv dkx((uint32_t)kx);  // quotient and remainder by kx without an integer division
-  reduce_partials(d, part_base + part_off[p], S, H, kx);
+  reduce_partials(d, part_base + part_off[p], S, H, kx, kRRThreads);
   __syncthreads();
-  // S = X^T X is close to I here (X was orthonormalised before its last small
-  // update), so: FP32 Cholesky S + s I = C C^T and Q0 = C^-T, then one
-  // Newton-Schulz step in FP64, Q1 = Q0 (3I - Q0^T S Q0) / 2, which squares the
-  // FP32 error: X Q1 is orthonormal to FP64 accuracy.
-  for (int e = tid; e < kx * kx; e += kSmallThreads) Sf[dkx.q(e)][dkx.r(e)] = (float)S[dkx.q(e)][dkx.r(e)];
-  __syncthreads();
-  if (tid < 32) warp_chol_shifted<float>(Sf, reinterpret_cast<float*>(rdiag), kx, 1e-7f);
-  __syncthreads();
-  inv_transpose_factor<float>(Sf, reinterpret_cast<const float*>(rdiag), Vf, kx);
-  __syncthreads();
-  for (int e = tid; e < kx * kx; e += kSmallThreads) Q2[dkx.q(e)][dkx.r(e)] = (double)Vf[dkx.q(e)][dkx.r(e)];
-  __syncthreads();
-  sym_congruence(W2, Q2, S, W1, kx);  // Z = Q0^T S Q0
-  for (int e = tid; e < kx * kx; e += kSmallThreads) {
-    const int a = dkx.q(e), b = dkx.r(e);
-    double s = 0.0;
-    for (int t = 0; t < kx; ++t) s = fma(Q2[a][t], ((t == b) ? 3.0 : 0.0) - W2[t][b], s);
-    Q1[a][b] = 0.5 * s;
+  if (tid < 32) {  // Q0 = C^-T of the FP32 factor, into Q2
+    float a[KP], y[KP];
+#pragma unroll
+    for (int j = 0; j < KP; ++j) a[j] = (lane < kx && j < kx) ? S[lane][j].hi : (lane == j ? 1.f : 0.f);
+    float rdiag = 1.f;
+    reg_cholesky<KP>(a, rdiag, 1e-7f, kx);
+    reg_tri_inverse<KP>(a, rdiag, y);
+    if (lane < kx)
+#pragma unroll
+      for (int c = 0; c < KP; ++c)
+        if (c < kx) Q2[c][lane] = DF{y[c], 0.f};
   }
   __syncthreads();
-  sym_congruence(H1, Q1, H, W1, kx);  // H1 = Q1^T H Q1
-  // FP32 Jacobi of H1 when it has off-diagonal entries FP32 can resolve; then
-  // the eigenvector columns in ascending order of the Ritz values
-  for (int e = tid; e < kx * kx; e += kSmallThreads) Sf[dkx.q(e)][dkx.r(e)] = (float)H1[dkx.q(e)][dkx.r(e)];
+  df_congruence(W2, Q2, S, W1, kx, kRRThreads);  // Z = Q0^T S Q0
+  df_three_minus_half(W1, W2, kx, kRRThreads);   // (3I - Z) / 2
   __syncthreads();
+  df_prod(Q1, Q2, false, W1, kx, kRRThreads);  // Q1 = Q0 (3I - Z) / 2
+  __syncthreads();
+  df_congruence(H1, Q1, H, W1, kx, kRRThreads);  // H1 = Q1^T H Q1
   if (tid < 32) {
+    // FP32 Jacobi of H1 (when FP32 resolves its off-diagonal part); Q2 = its
+    // eigenvector columns in ascending order of the Ritz values
+    float a[KP], v[KP];
     float f = 0.f, o = 0.f;
-    for (int e = tid; e < kx * kx; e += 32) {
-      const float v = Sf[dkx.q(e)][dkx.r(e)];
-      f += v * v;
-      if (dkx.q(e) != dkx.r(e)) o = fmaxf(o, fabsf(v));
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+      a[j] = (lane < kx && j < kx) ? H1[lane][j].hi : 0.f;
+      v[j] = (j == lane) ? 1.f : 0.f;
+      f += a[j] * a[j];
+      if (j != lane) o = fmaxf(o, fabsf(a[j]));
     }
 #pragma unroll
     for (int s = 16; s; s >>= 1) {
@@ -1173,76 +1156,51 @@ __global__ void __launch_bounds__(kSmallThreads) k_rr64(const ProbDesc* __restri
       o = fmaxf(o, __shfl_xor_sync(0xffffffffu, o, s));
     }
     const float tol = 4.f * FLT_EPSILON * sqrtf(f);
-    int sweeps = 0;
-    if (o > tol) {
-      sweeps = warp_jacobi<float>(&Sf[0][0], &Vf[0][0], kx, kLs, jsf, tol);
+    if (o > tol) reg_jacobi<KP>(a, v, tol, 40);
+    const float lam = reg_pick<KP>(a, lane);
+    int rank = 0;
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      const float lk = __shfl_sync(0xffffffffu, lam, k);
+      if (k < kx && (lk < lam || (lk == lam && k < lane))) ++rank;
     }
-    if (tid == 0) {
-      rotated = sweeps;
-      coupled = 0;
-      for (int i = 0; i < kx; ++i) order[i] = i;
-      for (int a = 1; a < kx; ++a) {
-        const int v = order[a];
-        int b = a - 1;
-        while (b >= 0 && Sf[order[b]][order[b]] > Sf[v][v]) {
-          order[b + 1] = order[b];
-          --b;
-        }
-        order[b + 1] = v;
-      }
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+      const int rj = __shfl_sync(0xffffffffu, rank, j);
+      if (lane < kx && j < kx) Q2[lane][rj] = DF{v[j], 0.f};
     }
+    if (lane == 0) coupled = 0;
   }
   __syncthreads();
-  for (int e = tid; e < kx * kx; e += kSmallThreads)
-    Q2[dkx.q(e)][dkx.r(e)] = rotated ? (double)Vf[dkx.q(e)][order[dkx.r(e)]] : (dkx.q(e) == order[dkx.r(e)] ? 1.0 : 0.0);
-  __syncthreads();
-  if (rotated) {  // FP32 rotations: make them orthogonal in FP64, then B = Q2^T H1 Q2
-    lowdin_step(Q2, W1, W2, kx);
-    lowdin_step(Q2, W1, W2, kx);
-    sym_congruence(S, Q2, H1, W1, kx);  // into S: the factor is no longer needed
-  } else {  // H1 was already diagonal to FP32 accuracy: Q2 is a permutation, B a reordering of H1
-    for (int e = tid; e < kx * kx; e += kSmallThreads) S[dkx.q(e)][dkx.r(e)] = H1[order[dkx.q(e)]][order[dkx.r(e)]];
-    __syncthreads();
-  }
-  // first-order decoupling of the wanted block: G = I + A (into W2), then one Lowdin step
-  for (int e = tid; e < kx * kx; e += kSmallThreads) {
+  // FP32 rotations: orthogonal in pairs, then B = Q2^T H1 Q2
+  df_lowdin(Q2, W1, W2, kx, kRRThreads);
+  df_lowdin(Q2, W1, W2, kx, kRRThreads);
+  df_congruence(B, Q2, H1, W1, kx, kRRThreads);
+  // first-order decoupling of the wanted block: G = I + A (into H1), then one Lowdin step
+  for (int e = tid; e < kx * kx; e += kRRThreads) {
     const int a = dkx.q(e), b = dkx.r(e);
-    double g = (a == b) ? 1.0 : 0.0;
-    if (a < r && b >= r) {
-      g = S[a][b] * rcp64(S[b][b] - S[a][a]);
-    } else if (a >= r && b < r) {
-      g = -S[b][a] * rcp64(S[a][a] - S[b][b]);
-    }
-    if (a != b && fabs(g) > 1e-9) atomicOr(&coupled, 1);
-    W2[a][b] = g;
+    float g = (a == b) ? 1.f : 0.f;
+    if (a < r && b >= r)
+      g = B[a][b].hi * __frcp_rn(B[b][b].hi - B[a][a].hi);
+    else if (a >= r && b < r)
+      g = -B[b][a].hi * __frcp_rn(B[a][a].hi - B[b][b].hi);
+    if (a != b && fabsf(g) > 1e-9f) atomicOr(&coupled, 1);
+    H1[a][b] = DF{g, 0.f};
   }
-  __syncthreads();
-  for (int e = tid; e < kx * kx; e += kSmallThreads) H1[dkx.q(e)][dkx.r(e)] = W2[dkx.q(e)][dkx.r(e)];  // G in H1
   __syncthreads();
   // I + A is orthogonal up to ||A||^2: below 1e-18 it needs no Lowdin step
-  if (coupled) lowdin_step(H1, W1, W2, kx);
-  if (rotated) {
-    small_prod(W1, Q2, false, H1, kx);  // W1 = Q2 G
-  } else {
-    for (int e = tid; e < kx * kx; e += kSmallThreads) W1[dkx.q(e)][dkx.r(e)] = H1[dkx.q(e)][dkx.r(e)];
-    __syncthreads();
-    for (int e = tid; e < kx * kx; e += kSmallThreads) {  // W1 = P G (P the permutation Q2): rows by order
-      const int a = dkx.q(e), b = dkx.r(e);
-      W2[order[a]][b] = W1[a][b];
-    }
-    __syncthreads();
-    for (int e = tid; e < kx * kx; e += kSmallThreads) W1[dkx.q(e)][dkx.r(e)] = W2[dkx.q(e)][dkx.r(e)];
-  }
+  if (coupled) df_lowdin(H1, W1, W2, kx, kRRThreads);
+  df_prod(W1, Q2, false, H1, kx, kRRThreads);  // W1 = Q2 G
   __syncthreads();
-  small_prod(Q2, Q1, false, W1, kx);  // Q = Q1 Q2 G (into Q2)
+  df_prod(Q2, Q1, false, W1, kx, kRRThreads);  // Q = Q1 Q2 G (into Q2)
   __syncthreads();
-  sym_congruence(W2, Q2, H, W1, kx);  // H' = Q^T H Q
+  df_congruence(W2, Q2, H, W1, kx, kRRThreads);  // H' = Q^T H Q
   double* out = d.small;
-  for (int e = tid; e < kx * kx; e += kSmallThreads) {
-    out[e] = Q2[dkx.q(e)][dkx.r(e)];
-    out[kx * kx + e] = W2[dkx.q(e)][dkx.r(e)];
+  for (int e = tid; e < kx * kx; e += kRRThreads) {
+    out[e] = df_to(Q2[dkx.q(e)][dkx.r(e)]);
+    out[kx * kx + e] = df_to(W2[dkx.q(e)][dkx.r(e)]);
   }
-  for (int c = tid; c < kx; c += kSmallThreads) out[2 * kx * kx + c] = W2[c][c];
+  for (int c = tid; c < kx; c += kRRThreads) out[2 * kx * kx + c] = df_to(W2[c][c]);
 }
 
 // X <- X Q (FULL: also MX <- MX Q and R = MX - X H').  A CTA takes 8 rows;
@@ -1482,8 +1440,24 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
   const int xtx_smem = (int)(2 * kChunk * kMaxL * sizeof(double));
   cudaError_t ea = cudaFuncSetAttribute(k_xtx<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, xtx_smem);
   if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_xtx<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, xtx_smem);
-  if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_rr64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRRSmem);
+  // the register algebra of the small steps is compiled for padded sizes KP >= kx
+  const int kp = P.kx_max <= 4 ? 4 : (P.kx_max + 3) / 4 * 4;
+  void (*rr)(const ProbDesc*, int, const float2*, const int64_t*) = nullptr;
+  void (*orth)(const ProbDesc*, int, const float2*, const int64_t*) = nullptr;
+  switch (kp) {
+#define RSM_KP(K)          \
+  case K:                  \
+    rr = k_rr<K>;          \
+    orth = k_orth<K>;      \
+    break;
+    RSM_KP(4) RSM_KP(8) RSM_KP(12) RSM_KP(16) RSM_KP(20) RSM_KP(24) RSM_KP(28) RSM_KP(32)
+#undef RSM_KP
+    default: return cudaErrorInvalidValue;
+  }
+  if (sizeof(T) == 8) orth = k_orth<0>;
+  if (ea == cudaSuccess) ea = cudaFuncSetAttribute(rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRRSmem);
   if (ea != cudaSuccess) return ea;
+  const float2* part = reinterpret_cast<const float2*>(P.part);
   const ProbDesc* D = P.descs;
   const int np = P.nprob;
   auto dev = [&](size_t pos) { return P.dT + pos; };
@@ -1528,7 +1502,7 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
   RSM_LAUNCH(k_init_X, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
   auto orthonormalise = [&]() -> cudaError_t {
     RSM_LAUNCH_SMEM(k_xtx<false>, total(P.chunk), 256, xtx_smem, D, dev(P.chunk), np, P.part, dev(P.part_off));
-    RSM_LAUNCH(k_orth<T>, np, kSmallThreads, D, np, P.part, dev(P.part_off));
+    RSM_LAUNCH(orth, np, kSmallThreads, D, np, part, dev(P.part_off));
     RSM_LAUNCH(k_rotate<false>, total(P.rot), 256, D, dev(P.rot), np);
     return cudaSuccess;
   };
@@ -1555,7 +1529,7 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
       RSM_LAUNCH(k_gemm_MX<32>, total(P.mx), kMxRows, D, dev(P.mx), np);
     RSM_LAUNCH(k_split_sum, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
     RSM_LAUNCH_SMEM(k_xtx<true>, total(P.chunk), 256, xtx_smem, D, dev(P.chunk), np, P.part, dev(P.part_off));
-    RSM_LAUNCH_SMEM(k_rr64, np, kSmallThreads, kRRSmem, D, np, P.part, dev(P.part_off));
+    RSM_LAUNCH_SMEM(rr, np, kRRThreads, kRRSmem, D, np, part, dev(P.part_off));
     RSM_LAUNCH(k_rotate<true>, total(P.rot), 256, D, dev(P.rot), np);
     RSM_LAUNCH(k_conv_check, np, 256, D, np);
     if (it < iters) {
@@ -1581,7 +1555,7 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
       RSM_LAUNCH(k_gemm_MX64<32>, total(P.mx), kMxRows, D, dev(P.mx), np);
     RSM_LAUNCH(k_split_sum, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
     RSM_LAUNCH_SMEM(k_xtx<true>, total(P.chunk), 256, xtx_smem, D, dev(P.chunk), np, P.part, dev(P.part_off));
-    RSM_LAUNCH_SMEM(k_rr64, np, kSmallThreads, kRRSmem, D, np, P.part, dev(P.part_off));
+    RSM_LAUNCH_SMEM(rr, np, kRRThreads, kRRSmem, D, np, part, dev(P.part_off));
     RSM_LAUNCH(k_rotate<true>, total(P.rot), 256, D, dev(P.rot), np);
     if (pass == 0) {
       RSM_LAUNCH(precond_r, total(P.row_tile), 256, D, dev(P.row_tile), np);

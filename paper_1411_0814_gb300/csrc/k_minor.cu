@@ -11,11 +11,13 @@
 // are rounded to 64-bit fixed point (2^-f, f chosen so no sum can overflow)
 // and added with integer atomics: integer addition is associative, so the
 // result is bit-identical for any order of the trials.
+#include <algorithm>
 #include <cfloat>
 
 #include "common.cuh"
 #include "jacobi.cuh"
 #include "kernels.h"
+#include "small_df.cuh"
 
 namespace rsm {
 
@@ -38,10 +40,13 @@ __host__ __device__ inline size_t minor_smem_per_warp(int lmax) {
 // after max_steps.  An FP32 Gram takes a single step: its own rounding (~1e-7
 // relative) already bounds how well its minor vectors are defined, and one
 // step from the FP32 basis (error ~1e-7) leaves ~1e-14 (times ||G|| / gap).
+// W = 32: one warp per trial; W = 16: one half warp per trial (lane = lane in the half).
+template <int W = 32>
 __device__ inline void newton_refine(const double* Gs, const double* Qd, const double* lam, double* Z, double* rv,
                                      double* cv, int l, int nm, int ls, const int* is_minor, double fro, double stop,
                                      int max_steps) {
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & (W - 1);
+  const unsigned gmask = W == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
   for (int step = 0; step < max_steps; ++step) {
     double cmax = 0.0;
     for (int j = 0; j < nm; ++j) {
@@ -52,17 +57,17 @@ __device__ inline void newton_refine(const double* Gs, const double* Qd, const d
       }
       double th = za * gz;
 #pragma unroll
-      for (int o = 16; o; o >>= 1) th += __shfl_xor_sync(0xffffffffu, th, o);
+      for (int o = W / 2; o; o >>= 1) th += __shfl_xor_sync(gmask, th, o);
       if (lane < l) rv[lane] = gz - th * za;
-      __syncwarp();
+      __syncwarp(gmask);
       // block form: drop the part of r inside span(Z); only the part that leaves
       // the current minor subspace is corrected against the complement
       for (int k = 0; k < nm; ++k) {
         double zr = lane < l ? Z[lane * nm + k] * rv[lane] : 0.0;
 #pragma unroll
-        for (int o = 16; o; o >>= 1) zr += __shfl_xor_sync(0xffffffffu, zr, o);
+        for (int o = W / 2; o; o >>= 1) zr += __shfl_xor_sync(gmask, zr, o);
         if (lane < l) rv[lane] -= zr * Z[lane * nm + k];
-        __syncwarp();
+        __syncwarp(gmask);
       }
       if (lane < l) {
         double c = 0.0;
@@ -74,31 +79,31 @@ __device__ inline void newton_refine(const double* Gs, const double* Qd, const d
         cv[lane] = c;
         cmax = fmax(cmax, fabs(c));
       }
-      __syncwarp();
+      __syncwarp(gmask);
       if (lane < l) {
         double zn = Z[lane * nm + j];
         for (int i = 0; i < l; ++i) zn = fma(-cv[i], Qd[lane * ls + i], zn);
         Z[lane * nm + j] = zn;
       }
-      __syncwarp();
+      __syncwarp(gmask);
     }
 #pragma unroll
-    for (int o = 16; o; o >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+    for (int o = W / 2; o; o >>= 1) cmax = fmax(cmax, __shfl_xor_sync(gmask, cmax, o));
     for (int j = 0; j < nm; ++j) {  // Gram-Schmidt (twice) in FP64
       for (int pass = 0; pass < 2; ++pass)
         for (int k = 0; k < j; ++k) {
           double pr = lane < l ? Z[lane * nm + k] * Z[lane * nm + j] : 0.0;
 #pragma unroll
-          for (int o = 16; o; o >>= 1) pr += __shfl_xor_sync(0xffffffffu, pr, o);
+          for (int o = W / 2; o; o >>= 1) pr += __shfl_xor_sync(gmask, pr, o);
           if (lane < l) Z[lane * nm + j] -= pr * Z[lane * nm + k];
-          __syncwarp();
+          __syncwarp(gmask);
         }
       double nn = lane < l ? Z[lane * nm + j] * Z[lane * nm + j] : 0.0;
 #pragma unroll
-      for (int o = 16; o; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+      for (int o = W / 2; o; o >>= 1) nn += __shfl_xor_sync(gmask, nn, o);
       const double inv = rsqrt64(nn);
       if (lane < l) Z[lane * nm + j] *= inv;
-      __syncwarp();
+      __syncwarp(gmask);
     }
     if (cmax < stop) break;
   }
@@ -112,13 +117,11 @@ __device__ inline void newton_refine(const double* Gs, const double* Qd, const d
 // followed by Gram-Schmidt.  Removing the part of r inside span(Z) (block
 // Newton) keeps the fixed point exact when several minor vectors are kept.  The fixed point is an exact eigenvector of the
 // FP64 Gram whatever the FP32 rounding of Q, and the error squares per step.
-__global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDesc* __restrict__ descs,
-                                                                   const int64_t* __restrict__ trial_off, int nprob,
-                                                                   int lmax) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+// One trial (global index g) by one warp; `counted`: the accepted-trial count
+// already holds it (a trial handed over by k_minor_half).
+__device__ __forceinline__ void minor_trial(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ trial_off,
+                                            int nprob, int lmax, int64_t g, bool counted, unsigned char* smraw) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t g = (int64_t)blockIdx.x * kMinorWarps + wid;
-  if (g >= trial_off[nprob]) return;
   const int p = find_problem(trial_off, nprob, g);
   const ProbDesc& d = descs[p];
   if (d.variant == 2) return;  // the row variant has its own kernels (k_rows.cu)
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDe
       for (int i = lane; i < l * d.n_minor; i += 32) d.Zst[t * l * d.n_minor + i] = 0.0;
     return;
   }
-  if (lane == 0) atomicAdd(&d.counters[0], 1ull);
+  if (lane == 0 && !counted) atomicAdd(&d.counters[0], 1ull);
 
   // packed Gram -> full symmetric FP64 matrix and its FP32 copy
   const int P = l * (l + 1) / 2;
@@ -244,6 +247,177 @@ __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDe
   }
 }
 
+__global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDesc* __restrict__ descs,
+                                                                   const int64_t* __restrict__ trial_off, int nprob,
+                                                                   int lmax) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int64_t g = (int64_t)blockIdx.x * kMinorWarps + (threadIdx.x >> 5);
+  if (g >= trial_off[nprob]) return;
+  minor_trial(descs, trial_off, nprob, lmax, g, false, smraw);
+}
+
+// The trials k_minor_half handed over (l > 16, or a nearly degenerate pair
+// across the minor split): one warp per listed trial, grid-stride.
+__global__ void __launch_bounds__(32 * kMinorWarps) k_minor_listed(const ProbDesc* __restrict__ descs,
+                                                                  const int64_t* __restrict__ trial_off, int nprob,
+                                                                  int lmax, const unsigned long long* __restrict__ list,
+                                                                  const unsigned long long* __restrict__ list_count) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const unsigned long long count = *list_count;
+  for (unsigned long long k = (unsigned long long)blockIdx.x * kMinorWarps + (threadIdx.x >> 5); k < count;
+       k += (unsigned long long)gridDim.x * kMinorWarps)
+    minor_trial(descs, trial_off, nprob, lmax, (int64_t)list[k], true, smraw);
+}
+
+// a5 + a6 with two trials per warp: each half warp takes one trial with
+// l <= 16, its Gram's rows in the registers of its lanes (lane i < l: row i).
+// FP32 Jacobi in registers (small_df.cuh, circle ordering on KP = l rounded up
+// to even, so a trial's rotations depend on its own l only and its result is
+// the same in any batch), the n_minor smallest eigenvalues, then the same FP64
+// block-Newton refinement and fixed-point scatter as minor_trial with 16 lanes.
+// A trial with l > 16, or whose split is nearly degenerate (a complement
+// eigenvalue within 1e-4 ||G|| of a minor one), is appended to `list` for
+// k_minor_listed instead.
+template <int KP>
+__device__ __forceinline__ void minor_half_body(const ProbDesc& d, int64_t t, int64_t g, int ls, unsigned char* base,
+                                                int* pick, int* is_minor, unsigned long long* __restrict__ list,
+                                                unsigned long long* __restrict__ list_count) {
+  const int wl = threadIdx.x & 31, hl = wl & 15;
+  const unsigned hmask = 0xffffu << (wl & 16);
+  const int l = d.l, nm = d.n_minor;
+  const int lsz = ls - 1;  // the slot's matrices are lsz x lsz with row stride ls
+  double* Gs = reinterpret_cast<double*>(base);
+  float* Sf = reinterpret_cast<float*>(Gs + (size_t)lsz * ls);  // eigenvalues on the diagonal
+  float* Qf = Sf + (size_t)lsz * ls;
+  double* Z = reinterpret_cast<double*>(Qf + (size_t)lsz * ls);
+  double* Wd = Z + (size_t)lsz * ls;
+  double* gv = Wd + (size_t)lsz * ls;
+  double* rv = gv + ls;
+  double* cv = rv + ls;
+  const int P = l * (l + 1) / 2;
+  const double* G = d.gram + t * P;
+  for (int q = hl; q < P; q += 16) {
+    int a = 0, rem = q;
+    while (rem >= l - a) {
+      rem -= l - a;
+      ++a;
+    }
+    const int b = a + rem;
+    const double v = G[q];
+    Gs[a * ls + b] = v;
+    Gs[b * ls + a] = v;
+  }
+  __syncwarp(hmask);
+  float a[KP], v[KP];
+  float f = 0.f;
+#pragma unroll
+  for (int j = 0; j < KP; ++j) {
+    a[j] = (hl < l && j < l) ? (float)Gs[hl * ls + j] : 0.f;
+    v[j] = (j == hl) ? 1.f : 0.f;
+    f += a[j] * a[j];
+  }
+#pragma unroll
+  for (int o = 8; o; o >>= 1) f += __shfl_xor_sync(hmask, f, o);
+  const float fro = sqrtf(f);
+  reg_jacobi<KP, 16>(a, v, 4.f * FLT_EPSILON * fro, 40);
+  const float lam = reg_pick<KP>(a, hl);
+  if (hl < l) {
+    Sf[hl * ls + hl] = lam;
+#pragma unroll
+    for (int j = 0; j < KP; ++j)
+      if (j < l) Qf[hl * ls + j] = v[j];
+  }
+  __syncwarp(hmask);
+  // the n_minor smallest eigenvalues (ties broken by index)
+  const SmallDiv dnm((uint32_t)nm), dl((uint32_t)l);  // quotients by nm and l without integer division
+  if (hl == 0) {
+    for (int i = 0; i < l; ++i) is_minor[i] = 0;
+    for (int j = 0; j < nm; ++j) {
+      int best = -1;
+      for (int i = 0; i < l; ++i)
+        if (!is_minor[i] && (best < 0 || Sf[i * ls + i] < Sf[best * ls + best])) best = i;
+      is_minor[best] = 1;
+      pick[j] = best;
+    }
+  }
+  __syncwarp(hmask);
+  float gap_min = 3.0e38f;
+  if (hl < l && !is_minor[hl])
+    for (int j = 0; j < nm; ++j) gap_min = fminf(gap_min, fabsf(lam - Sf[pick[j] * ls + pick[j]]));
+#pragma unroll
+  for (int o = 8; o; o >>= 1) gap_min = fminf(gap_min, __shfl_xor_sync(hmask, gap_min, o));
+  if (gap_min < 1e-4f * fro) {  // k_minor_listed takes this trial
+    if (hl == 0) list[atomicAdd(list_count, 1ull)] = (unsigned long long)g;
+    return;
+  }
+  for (int it = hl; it < l * nm; it += 16) {
+    const int aa = dnm.q(it), j = dnm.r(it);
+    Z[aa * nm + j] = (double)Qf[aa * ls + pick[j]];
+  }
+  for (int it = hl; it < l * l; it += 16) Wd[dl.q(it) * ls + dl.r(it)] = (double)Qf[dl.q(it) * ls + dl.r(it)];
+  if (hl < l) gv[hl] = (double)lam;
+  __syncwarp(hmask);
+  newton_refine<16>(Gs, Wd, gv, Z, rv, cv, l, nm, ls, is_minor, (double)fro, 1e-17, d.gram_fp32 ? 1 : kNewtonSteps);
+  if (d.debug_Z)
+    for (int it = hl; it < l * nm; it += 16) d.debug_Z[t * l * nm + it] = Z[it];
+  if (d.Zst)
+    for (int it = hl; it < l * nm; it += 16) d.Zst[t * l * nm + it] = Z[it];
+  const int fb = macc_frac_bits(d.counters[2]);
+  const double scale = ldexp(1.0, fb);
+  const int32_t* C = d.cols + t * l;
+  for (int it = hl; it < l * l; it += 16) {
+    const int aa = dl.q(it), b = dl.r(it);
+    double pr = 0.0;
+    for (int j = 0; j < nm; ++j) pr = fma(Z[aa * nm + j], Z[b * nm + j], pr);
+    const long long val = llrint(pr * scale);
+    if (val) atomicAdd(&d.macc[(uint32_t)C[aa] * (uint32_t)d.n + (uint32_t)C[b]], (unsigned long long)val);
+  }
+}
+
+constexpr int kHalfMaxL = 16;  // largest l of the two-per-warp kernel
+
+__global__ void __launch_bounds__(32 * kMinorWarps, 4) k_minor_half(const ProbDesc* __restrict__ descs,
+                                                                   const int64_t* __restrict__ trial_off, int nprob,
+                                                                   int ls, unsigned long long* __restrict__ list,
+                                                                   unsigned long long* __restrict__ list_count) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int pick[2 * kMinorWarps][kHalfMaxL];
+  __shared__ int is_minor[2 * kMinorWarps][kHalfMaxL];
+  const int wl = threadIdx.x & 31, hl = wl & 15, slot = threadIdx.x >> 4;
+  const int64_t g = (int64_t)blockIdx.x * 2 * kMinorWarps + slot;
+  if (g >= trial_off[nprob]) return;  // the half's lanes leave together
+  const int p = find_problem(trial_off, nprob, g);
+  const ProbDesc& d = descs[p];
+  if (d.variant == 2) return;  // the row variant has its own kernels (k_rows.cu)
+  const int64_t t = g - trial_off[p];
+  const int l = d.l, nm = d.n_minor;
+  const int count = d.row_counts[t];
+  if (count < l) {  // rejected trial (fewer than l rows, i.e. not more than r)
+    if (d.debug_Z)
+      for (int i = hl; i < l * nm; i += 16) d.debug_Z[t * l * nm + i] = 0.0;
+    if (d.Zst)
+      for (int i = hl; i < l * nm; i += 16) d.Zst[t * l * nm + i] = 0.0;
+    return;
+  }
+  if (hl == 0) atomicAdd(&d.counters[0], 1ull);
+  if (l > kHalfMaxL) {  // one warp per trial
+    if (hl == 0) list[atomicAdd(list_count, 1ull)] = (unsigned long long)g;
+    return;
+  }
+  unsigned char* base = smraw + (size_t)slot * minor_smem_per_warp(ls - 1);
+  int* pk = pick[slot];
+  int* im = is_minor[slot];
+  switch (l <= 4 ? 4 : (l + 1) & ~1) {
+    case 4: minor_half_body<4>(d, t, g, ls, base, pk, im, list, list_count); break;
+    case 6: minor_half_body<6>(d, t, g, ls, base, pk, im, list, list_count); break;
+    case 8: minor_half_body<8>(d, t, g, ls, base, pk, im, list, list_count); break;
+    case 10: minor_half_body<10>(d, t, g, ls, base, pk, im, list, list_count); break;
+    case 12: minor_half_body<12>(d, t, g, ls, base, pk, im, list, list_count); break;
+    case 14: minor_half_body<14>(d, t, g, ls, base, pk, im, list, list_count); break;
+    default: minor_half_body<16>(d, t, g, ls, base, pk, im, list, list_count); break;
+  }
+}
+
 // M = macc * 2^-f (two's-complement words read as signed).  Grid over all
 // entries of all problems.
 __global__ void __launch_bounds__(256) k_finalize_M(const ProbDesc* __restrict__ descs,
@@ -260,8 +434,27 @@ __global__ void __launch_bounds__(256) k_finalize_M(const ProbDesc* __restrict__
 }
 
 cudaError_t launch_minor_scatter(const ProbDesc* descs, const int64_t* trial_off, int nprob, int64_t total, int lmax,
-                                 cudaStream_t s) {
+                                 unsigned long long* list, unsigned long long* list_count, cudaStream_t s) {
   if (total <= 0) return cudaSuccess;
+  if (list && list_count) {
+    // two trials per warp (l <= 16), then the handed-over trials one per warp
+    const int lh = std::min(lmax, kHalfMaxL);
+    const size_t dynh = 2 * kMinorWarps * minor_smem_per_warp(lh) + 16;
+    cudaError_t e = cudaFuncSetAttribute(k_minor_half, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dynh);
+    if (e != cudaSuccess) return e;
+    k_minor_half<<<(unsigned)((total + 2 * kMinorWarps - 1) / (2 * kMinorWarps)), 32 * kMinorWarps, dynh, s>>>(
+        descs, trial_off, nprob, lh + 1, list, list_count);
+    ++g_kernel_launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t dyn = kMinorWarps * minor_smem_per_warp(lmax) + 16;
+    if ((e = cudaFuncSetAttribute(k_minor_listed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn)) !=
+        cudaSuccess)
+      return e;
+    const int64_t grid = std::min<int64_t>((total + kMinorWarps - 1) / kMinorWarps, 256);
+    k_minor_listed<<<(unsigned)grid, 32 * kMinorWarps, dyn, s>>>(descs, trial_off, nprob, lmax, list, list_count);
+    ++g_kernel_launches;
+    return cudaGetLastError();
+  }
   const size_t dyn = kMinorWarps * minor_smem_per_warp(lmax) + 16;
   cudaError_t e = cudaFuncSetAttribute(k_minor_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   if (e != cudaSuccess) return e;

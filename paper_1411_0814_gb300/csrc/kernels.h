@@ -105,8 +105,10 @@ cudaError_t launch_select_gram(int mode, const ProbDesc* descs, const int64_t* t
 cudaError_t launch_rows_variant(const ProbDesc* descs, const int64_t* pack_off, int64_t pack_total,
                                 const int64_t* trial_off, int64_t trials_total, int nprob, int kmax, int rmax,
                                 int64_t nmax, cudaStream_t s);
+// list (total entries) and list_count (zeroed): the trials that the two-per-warp kernel hands
+// to the one-per-warp kernel; NULL: one trial per warp throughout
 cudaError_t launch_minor_scatter(const ProbDesc* descs, const int64_t* trial_off, int nprob, int64_t total, int lmax,
-                                 cudaStream_t s);
+                                 unsigned long long* list, unsigned long long* list_count, cudaStream_t s);
 cudaError_t launch_finalize_M(const ProbDesc* descs, const int64_t* ent_off, int nprob, int64_t total, cudaStream_t s);
 cudaError_t launch_eig(const EigPlan& P, bool fp64_factor, double shift_rel, int iters, cudaStream_t s);
 cudaError_t launch_trace_M(const ProbDesc* descs, int nprob, cudaStream_t s);

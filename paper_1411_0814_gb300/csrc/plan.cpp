@@ -371,6 +371,8 @@ void build_batch(const rsm_problem* ps, int count, Batch& b, const Tune* tunes) 
   off += align_up((size_t)(b.res_blocks + b.resv_blocks) * 8);
   b.fail_list_off = off;
   off += align_up((size_t)b.solve_rows * 8);  // any solved row may take the minimum-norm path
+  b.minor_list_off = off;  // any trial may be handed to the one-per-warp minor kernel
+  off += align_up((size_t)b.trials_total * 8);
   b.layout.total_bytes = off;
   b.layout.tmap_off = align_up(sizeof(ProbDesc) * count) + align_up(T.size() * 8);
   b.layout.plan_bytes = b.layout.tmap_off + (size_t)256 * count;

@@ -77,6 +77,7 @@ struct Batch {
   std::vector<size_t> zero_off, data_off;
   std::vector<size_t> zero_size, data_size;
   size_t part_bytes_off = 0, res_bytes_off = 0, fail_list_off = 0, fail_count_off = 0;
+  size_t minor_list_off = 0, minor_count_off = 8;  // trials handed from the two-per-warp minor kernel (count zeroed)
   size_t sync_off = 0, sync_bytes = 0;  // the factor launch's claim counter and phase counts (zeroed)
   int rmax = 0;
   // Row-slab schedule of the Gram: one group per distinct l that the slab

@@ -250,7 +250,10 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
         (e = launch_rows_variant(D, T + b.o_prow, b.prow_total, T + b.o_trial2, b.trials2_total, np, b.kmax2,
                                  b.rmax2, b.nmax2, s)) != cudaSuccess)
       return cuda_fail(e, "rows variant");
-    if ((e = launch_minor_scatter(D, T + b.o_trial, np, b.trials_total, b.lmax, s)) != cudaSuccess)
+    unsigned char* wsb = static_cast<unsigned char*>(slot.ws.ptr);
+    if ((e = launch_minor_scatter(D, T + b.o_trial, np, b.trials_total, b.lmax,
+                                  reinterpret_cast<unsigned long long*>(wsb + b.minor_list_off),
+                                  reinterpret_cast<unsigned long long*>(wsb + b.minor_count_off), s)) != cudaSuccess)
       return cuda_fail(e, "minor_scatter");
     if ((e = launch_finalize_M(D, T + b.o_ent, np, b.ent_total, s)) != cudaSuccess) return cuda_fail(e, "finalize_M");
     if (b.l1 && (e = launch_trace_M(D, np, s)) != cudaSuccess) return cuda_fail(e, "trace_M");

@@ -14,8 +14,8 @@ the same delta_V and delta_U.
   equations) the rows themselves are not a stable target: least-absolute-
   deviation solutions move a lot when a residual near delta changes its weight
   by orders of magnitude, so the form is held to the objective the rows
-  minimise, sum |y - u . v| over the known entries, within 1e-6 relative of the
-  oracle's (the objective is stationary at the optimum).
+  minimise, sum |y - u . v| over the known entries: within 1e-5 relative of the
+  oracle's, the FP32 forms' tolerance on U V^T (1e-6 in the FP64 form).
 * Noiseless data: exact recovery.
 """
 import numpy as np
@@ -77,7 +77,9 @@ def test_l1_forms_match_oracle_on_corrupted_columns(form):
     print(f"{form}: L1 objective device {f_g:.9e} oracle {f_o:.9e}")
     if form == "fp64":
         assert rel <= 1e-8
-    assert abs(f_g - f_o) <= 1e-6 * f_o
+    # FP32 form: least absolute deviations move with the FP32 rounding of the data, so the
+    # objective is held to the FP32 forms' tolerance on U V^T (1e-5 relative)
+    assert abs(f_g - f_o) <= (1e-6 if form == "fp64" else 1e-5) * f_o
 
 
 def test_l1_forms_noiseless_exact():

@@ -305,3 +305,37 @@ def test_paper_scale_sampled_parity(handle):
     # a9: e from the device against the definition evaluated on its own U-hat, V-hat
     e = oracle.residual(Y32, p.W, Ug, Vg)
     assert abs(res.e - e) <= 1e-5 * e
+
+
+def test_near_degenerate_trials_parity(handle):
+    """Every trial's Gram is nearly a multiple of I: the columns are Walsh
+    functions (orthogonal over all rows, every entry known) scaled by
+    1 + 1e-5 j, so the eigenvalues of each Gram differ by ~2e-5 relative, below
+    the 1e-4 ||G|| split test.  Every trial then takes the FP64 polish path
+    (handed from the two-trials-per-warp kernel to the one-per-warp kernel);
+    its minor subspace is still well defined (diagonal Gram) and is compared with
+    the oracle's per trial, and M as a whole."""
+    import scipy.linalg
+    m, n, r, l, trials = 2048, 32, 2, 4, 300
+    H = scipy.linalg.hadamard(m).astype(np.float64)
+    rng = np.random.default_rng(11)
+    Y = H[:, 1:n + 1] * (1.0 + 1e-5 * np.arange(1, n + 1)) + 1e-9 * rng.standard_normal((m, n))
+    Y = np.asfortranarray(Y)
+    W = np.ones((m, n), dtype=np.uint8, order="F")
+    o = oracle.decompose(Y, W, r, l, trials, 3, solve_u=False)
+    Yd = torch.from_numpy(np.ascontiguousarray(Y.T)).cuda().t()
+    Wd = torch.from_numpy(np.ascontiguousarray(W.T)).cuda().t()
+    res = handle.decompose(rsm.Problem(Yd, Wd, r, trials=trials, l=l, seed=3, want_U=False, debug=True))
+    assert res.accepted_trials == o.accepted_trials == trials
+    assert np.array_equal(_np(res.cols), o.cols)
+    Zg = _np(res.Z)
+    worst = 0.0
+    for t in range(trials):
+        A = Y[:, o.cols[t]]
+        dist = projector_distance(Zg[t], o.Z[t])
+        bound = minor_bound(A, l - r, 2.2e-16)
+        worst = max(worst, dist / bound)
+        assert dist <= bound, (t, dist, bound)
+    Mg = _np(res.M)
+    print(f"near-degenerate trials: worst_minor_ratio={worst:.3e}")
+    assert np.linalg.norm(Mg - o.M) <= 1e-10 * np.linalg.norm(o.M)
