@@ -85,6 +85,7 @@ struct ProbDesc {
   int32_t tc;  // 1: this problem's normal equations run on the tensor cores
   const void* tmap;  // TMA descriptors (128 B each) of Y and of the packed mask, or NULL
   int32_t gram_fp32;  // 1: the Gram is accumulated in plain FP32
+  int32_t resv;       // 1: the FP32 residual pass of r <= 8 with 16-byte aligned columns of Y (even m)
   int32_t tc_npad;
   int32_t tc_rb;
   int32_t vf_ld;

@@ -24,6 +24,14 @@ namespace rsm {
 constexpr int kMinorWarps = 4;
 constexpr int kNewtonSteps = 4;
 
+// Relative gap across the minor split below which a trial takes the FP64
+// polish path instead of Newton steps from the FP32 Jacobi basis.  FP64 Gram:
+// 1e-4 (four steps reach FP64 from an FP32 basis off by u32 / 1e-4).  FP32
+// Gram: its own rounding defines the minor subspace only to ~u32 ||G|| / gap,
+// and the single Newton step from the FP32 basis leaves ~(u32 ||G|| / gap)^2,
+// below that limit for any gap above u32 ||G||; 1e-5 keeps a wide margin.
+__device__ __forceinline__ float split_tol(const ProbDesc& d) { return d.gram_fp32 ? 1e-5f : 1e-4f; }
+
 // Shared memory per warp (row stride ls = lmax + 1): G (FP64), the FP32 copy
 // and FP32 eigenvectors, Z and a second FP64 work matrix, three FP64 vectors.
 __host__ __device__ inline size_t minor_smem_per_warp(int lmax) {
@@ -187,15 +195,15 @@ __device__ __forceinline__ void minor_trial(const ProbDesc* __restrict__ descs, 
   }
   __syncwarp();
   // Newton converges from the FP32 basis when every complement eigenvalue is at
-  // least 1e-4 ||G|| away from the minor ones ((u32 ||G|| / gap)^5 < 1e-16 after
-  // 4 steps).  Otherwise (a nearly degenerate pair across the split) the trial
-  // takes the FP32 Jacobi + FP64 polish path instead.
+  // least split_tol ||G|| away from the minor ones.  Otherwise (a nearly
+  // degenerate pair across the split) the trial takes the FP32 Jacobi + FP64
+  // polish path instead.
   float gap_min = 3.0e38f;
   if (lane < l && !is_minor[wid][lane])
     for (int j = 0; j < nm; ++j) gap_min = fminf(gap_min, fabsf(Sf[lane * ls + lane] - Sf[pick[wid][j] * ls + pick[wid][j]]));
 #pragma unroll
   for (int o = 16; o; o >>= 1) gap_min = fminf(gap_min, __shfl_xor_sync(0xffffffffu, gap_min, o));
-  const bool polish = gap_min < (float)(1e-4 * fro);
+  const bool polish = gap_min < split_tol(d) * (float)fro;
   if (polish) {
     // eigen-decomposition of the FP64 Gram: eigenvalues on Gs's diagonal, vectors in Z (stride ls)
     warp_eig_mixed(Gs, Z, Sf, Qf, Wd, l, ls, js[wid], jsd[wid]);
@@ -276,7 +284,7 @@ __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_listed(const ProbDes
 // the same in any batch), the n_minor smallest eigenvalues, then the same FP64
 // block-Newton refinement and fixed-point scatter as minor_trial with 16 lanes.
 // A trial with l > 16, or whose split is nearly degenerate (a complement
-// eigenvalue within 1e-4 ||G|| of a minor one), is appended to `list` for
+// eigenvalue within split_tol ||G|| of a minor one), is appended to `list` for
 // k_minor_listed instead.
 template <int KP>
 __device__ __forceinline__ void minor_half_body(const ProbDesc& d, int64_t t, int64_t g, int ls, unsigned char* base,
@@ -346,7 +354,7 @@ __device__ __forceinline__ void minor_half_body(const ProbDesc& d, int64_t t, in
     for (int j = 0; j < nm; ++j) gap_min = fminf(gap_min, fabsf(lam - Sf[pick[j] * ls + pick[j]]));
 #pragma unroll
   for (int o = 8; o; o >>= 1) gap_min = fminf(gap_min, __shfl_xor_sync(hmask, gap_min, o));
-  if (gap_min < 1e-4f * fro) {  // k_minor_listed takes this trial
+  if (gap_min < split_tol(d) * fro) {  // k_minor_listed takes this trial
     if (hl == 0) list[atomicAdd(list_count, 1ull)] = (unsigned long long)g;
     return;
   }

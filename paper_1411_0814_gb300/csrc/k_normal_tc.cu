@@ -27,6 +27,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "refine.cuh"
 
 namespace rsm {
 
@@ -123,6 +124,10 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 // The descriptors were written to global memory through the generic proxy (by an earlier kernel).
@@ -644,6 +649,160 @@ __global__ void __launch_bounds__(kTmaThreads) k_normal_tma(const ProbDesc* __re
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
+// ------------------------------------------------------------------ a9: the residual pass, TMA-fed
+// e numerator sum_{known} (y_ij - u_i . v_j)^2 and, with `refine`, the
+// refinement step of U (refine_row) for the FP32 form with r <= 8.  A CTA
+// takes the same 128-row tile as k_normal_tma (thread = row, so c_i = V_K^T r0
+// stays in the thread): the copy warp streams each 32-column chunk's Y tile
+// and mask words (the same tensor maps) and the chunk's V rows (bulk copy of
+// the FP32 V image) into a ring of stages; the row threads wait on the stage's
+// mbarrier, accumulate, and release the stage through a second mbarrier (one
+// arrival per warp).  Per chunk the FP32 sum of squares is added into an FP64
+// running sum; the CTA's sum goes to its two slots of the 64-row partials.
+__host__ __device__ constexpr size_t res_stage_bytes(int rb) {
+  return (size_t)kRows * kChunkK * 4 + (size_t)kChunkK * rb * 4 + kChunkK * 4 * 4;
+}
+constexpr int kResStages = 4;
+
+template <int RB>
+__global__ void __launch_bounds__(kTmaThreads, 3) k_residual_tma(const ProbDesc* __restrict__ descs,
+                                                             const int64_t* __restrict__ off,
+                                                             const int64_t* __restrict__ resv_off, int nprob,
+                                                             double* __restrict__ partial, int refine) {
+  extern __shared__ __align__(1024) unsigned char res_smem_raw[];
+  __shared__ __align__(8) unsigned long long full[kResStages], empty[kResStages];
+  __shared__ double red[kRows / 32];
+  unsigned char* smem = res_smem_raw + ((128u - (smem_u32(res_smem_raw) & 127u)) & 127u);
+  const int p = find_problem(off, nprob, blockIdx.x);
+  const ProbDesc& d = descs[p];
+  if (!d.resv) return;  // a tensor-core problem without the vectorised residual (the scalar kernel has it)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t m = (uint32_t)d.m, n = (uint32_t)d.n;
+  const uint32_t tile = (uint32_t)(blockIdx.x - off[p]);
+  const uint32_t i0 = tile * kRows;
+  const uint32_t row = i0 + (uint32_t)tid;
+  const bool row_in = tid < kRows && row < m;
+  const int nchunk = (int)((n + kChunkK - 1) / kChunkK);
+  const uint32_t y_bytes = kRows * kChunkK * 4, v_bytes = kChunkK * RB * 4, w_bytes = kChunkK * 4 * 4;
+  const uint32_t stage_bytes = (uint32_t)res_stage_bytes(RB);
+  const unsigned char* tmaps = static_cast<const unsigned char*>(d.tmap);
+  if (tid == 0) {
+    for (int k = 0; k < kResStages; ++k) {
+      mbar_init(smem_u32(&full[k]), 1);
+      mbar_init(smem_u32(&empty[k]), kRows / 32);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  bool failed = false;
+  double dacc = 0.0;
+  if (warp == kRows / 32) {
+    if (lane == 0) {  // copy warp
+      tensormap_acquire(tmaps);
+      tensormap_acquire(tmaps + 128);
+      int issued = 0;
+      for (int c = 0; c < nchunk; ++c) {
+        const int s = c % kResStages;
+        if (c >= kResStages && !mbar_wait(smem_u32(&empty[s]), (uint32_t)(c / kResStages - 1) & 1u)) {
+          failed = true;
+          break;
+        }
+        const uint32_t st = smem_u32(smem + (size_t)s * stage_bytes);
+        const uint32_t bar = smem_u32(&full[s]);
+        mbar_expect_tx(bar, y_bytes + v_bytes + w_bytes);
+        tma_load_2d(st, tmaps, (int)i0, c * kChunkK, bar);
+        bulk_load(st + y_bytes, d.vf32 + (size_t)c * kChunkK * RB, v_bytes, bar);
+        tma_load_2d(st + y_bytes + v_bytes, tmaps + 128, (int)(i0 >> 5), c * kChunkK, bar);
+        issued = c + 1;
+      }
+      for (int c = issued - 1; c >= 0 && c >= issued - kResStages; --c)
+        mbar_wait(smem_u32(&full[c % kResStages]), (uint32_t)(c / kResStages) & 1u);
+    }
+  } else {
+    const int r = d.r;
+    float u[8], cacc[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      u[a] = (row_in && a < r) ? (float)d.U[(int64_t)a * d.ldu + row] : 0.f;
+      cacc[a] = 0.f;
+    }
+    for (int c = 0; c < nchunk; ++c) {
+      const int s = c % kResStages;
+      if (!mbar_wait(smem_u32(&full[s]), (uint32_t)(c / kResStages) & 1u)) {
+        failed = true;
+        break;
+      }
+      const unsigned char* st = smem + (size_t)s * stage_bytes;
+      const float* Ys = reinterpret_cast<const float*>(st);
+      const float* Vs = reinterpret_cast<const float*>(st + y_bytes);
+      const uint32_t* Ws = reinterpret_cast<const uint32_t*>(st + y_bytes + v_bytes);
+      float ch = 0.f;
+#pragma unroll 8
+      for (int jj = 0; jj < kChunkK; ++jj) {
+        const float y = Ys[jj * kRows + tid];
+        const bool known = row_in && ((Ws[jj * 4 + (tid >> 5)] >> lane) & 1u);
+        const float4 va = *reinterpret_cast<const float4*>(Vs + jj * RB);
+        const float4 vb = *reinterpret_cast<const float4*>(Vs + jj * RB + 4);
+        const float v[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+        float pr = 0.f;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) pr = fmaf(u[a], v[a], pr);
+        const float diff = known ? y - pr : 0.f;
+        ch = fmaf(diff, diff, ch);
+#pragma unroll
+        for (int a = 0; a < 8; ++a) cacc[a] = fmaf(diff, v[a], cacc[a]);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
+      dacc += (double)ch;
+    }
+    if (!failed && refine && row_in) dacc -= refine_row<8>(d, row, u, cacc);
+  }
+  failed = __syncthreads_or(failed) != 0;
+  if (failed) {
+    if (tid == 0) atomicAdd(&d.counters[6], 1ull);
+    dacc = 0.0;
+  }
+  if (tid < kRows) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+    if (lane == 0) red[warp] = dacc;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kRows / 32; ++k) t += red[k];
+    const int64_t slot = resv_off[p] + 2 * (int64_t)tile;  // the 64-row slots of this tile
+    partial[slot] = t;
+    if (slot + 1 < resv_off[p + 1]) partial[slot + 1] = 0.0;
+  }
+}
+
+cudaError_t launch_residual_tma(const SolvePlan& S, double* partial, int refine, cudaStream_t s) {
+  if (S.tc_tiles <= 0) return cudaSuccess;
+  const size_t smem = kResStages * res_stage_bytes(S.tc_rb) + 128;
+  cudaError_t e;
+#define RSM_RTMA(RB)                                                                                              \
+  do {                                                                                                            \
+    if ((e = cudaFuncSetAttribute(k_residual_tma<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != \
+        cudaSuccess) {                                                                                            \
+      cudaGetLastError();                                                                                         \
+      return e;                                                                                                   \
+    }                                                                                                             \
+    k_residual_tma<RB><<<(unsigned)S.tc_tiles, kTmaThreads, smem, s>>>(S.descs, S.tc_off, S.resv_off, S.nprob,   \
+                                                                       partial, refine);                          \
+  } while (0)
+  if (S.tc_rb <= 8)
+    RSM_RTMA(8);
+  else if (S.tc_rb <= 16)
+    RSM_RTMA(16);
+  else
+    RSM_RTMA(24);
+#undef RSM_RTMA
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
 bool normal_tc_supported(int r) { return r >= 1 && r <= 21; }
 
 int normal_tc_rb(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : 24; }
@@ -660,9 +819,10 @@ cudaError_t launch_normal_tc(const SolvePlan& S, int rb_max, int npad_max, cudaS
   }
   if (S.tc_tiles <= 0) return cudaSuccess;
   if (S.tc_tma) {
-    // three stages when two CTAs per SM fit, else two
+    // two stages, so that three CTAs fit per SM: their warps hide the FP64 epilogue
+    // of the others
     const size_t st = tma_stage_bytes(npad_max, rb_max);
-    const int stages = 2 * (3 * st + 128) <= 232448 - 4096 ? 3 : 2;
+    const int stages = 2;
     const size_t smem = stages * st + 128;
 #define RSM_TMA(RB)                                                                                             \
   do {                                                                                                          \

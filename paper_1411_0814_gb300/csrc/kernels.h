@@ -69,6 +69,9 @@ struct SolvePlan {
 bool normal_tc_supported(int r);
 int normal_tc_rb(int r);
 int normal_tc_npad(int r);
+// The residual pass (a9) with the refinement step of U for the problems with resv set, fed by
+// TMA (every tensor-core problem's descriptors present: S.tc_tma); partial holds the resv slots.
+cudaError_t launch_residual_tma(const SolvePlan& S, double* partial, int refine, cudaStream_t s);
 cudaError_t launch_normal_tc(const SolvePlan& S, int rb_max, int npad_max, cudaStream_t s);
 
 // Row-slab schedule of the fused selection + Gram (k_gram_slab.cu).  Table

@@ -458,6 +458,7 @@ void bind_batch(Batch& b, const rsm_problem* ps, unsigned char* ws) {
     d.delta_v = p.irls_delta_v > 0.0 ? p.irls_delta_v : 1e-4;
     d.delta_u = p.irls_delta_u > 0.0 ? p.irls_delta_u : 1e-3;
     d.tc = dv.tc ? 1 : 0;
+    d.resv = resv_of(p, dv) ? 1 : 0;
     d.gram_fp32 = p.gram_prec == RSM_PREC_F32 ? 1 : 0;
     d.tc_npad = dv.tc_npad;
     d.tc_rb = b.tc_rb;
