@@ -923,45 +923,83 @@ __global__ void __launch_bounds__(256) k_split_sum(const ProbDesc* __restrict__ 
   if (d.stats[kConvFlag] != 0.0) return;
   const int e = (int)(g - off[p]);
   const int nk = (int)d.n * d.kx;
-  double s = d.R[e];
-  for (int q = 1; q < kSplit; ++q) s += d.R[q * nk + e];
+  double v[kSplit];
+#pragma unroll
+  for (int q = 0; q < kSplit; ++q) v[q] = d.R[q * nk + e];  // every load in flight, then the sum in slot order
+  double s = v[0];
+#pragma unroll
+  for (int q = 1; q < kSplit; ++q) s += v[q];
   d.MX[e] = s;
 }
 
 // Partial Gram sums over chunks of kChunk rows: part[chunk] = [X^T X | X^T MX]
 // (2 kx^2 values; the second half only when WITH_H).
 constexpr int kChunk = 64;
-template <bool WITH_H>
-__global__ void __launch_bounds__(256) k_xtx(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
-                                            int nprob, double* __restrict__ part_base, const int64_t* __restrict__ part_off) {
-  extern __shared__ double xtx_smem[];
+constexpr int kXtxThreads = 320;  // 2 kx^2 = 288 outputs at kx = 12 in one round
+// Each partial is written as an FP32 pair.  PAIRS (FP32 factor): X and M X are
+// staged as FP32 pairs and the 64-term dot products run in pair arithmetic on
+// the FP32 pipes (small_df.cuh).  Otherwise (FP64 factor, an almost exact
+// shift-invert whose steps leave X with column norms spread over many orders of
+// magnitude until it is orthonormalised) the products run in FP64: X^T X then
+// needs every bit of its smallest directions.
+template <bool WITH_H, bool PAIRS>
+__global__ void __launch_bounds__(kXtxThreads) k_xtx(const ProbDesc* __restrict__ descs,
+                                                    const int64_t* __restrict__ off, int nprob,
+                                                    double* __restrict__ part_base,
+                                                    const int64_t* __restrict__ part_off) {
+  extern __shared__ DF xtx_smem[];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
   if (d.stats[kConvFlag] != 0.0) return;  // converged: the rest of the iteration is skipped
   const int chunk = (int)(blockIdx.x - off[p]);
   const int kx = d.kx;
   const SmallDiv dkx((uint32_t)kx);  // quotient and remainder by kx without an integer division
-  double* xs = xtx_smem;                  // kChunk x kx
-  double* ys = xtx_smem + kChunk * kx;    // kChunk x kx
   const int i0 = chunk * kChunk;
-  for (int e = threadIdx.x; e < kChunk * kx; e += 256) {
-    const int i = i0 + dkx.q(e);
-    xs[e] = i < d.n ? d.X[i0 * kx + e] : 0.0;
-    if (WITH_H) ys[e] = i < d.n ? d.MX[i0 * kx + e] : 0.0;
-  }
-  __syncthreads();
-  double* part = part_base + part_off[p] + chunk * 2 * kx * kx;
+  float2* part = reinterpret_cast<float2*>(part_base + part_off[p] + chunk * 2 * kx * kx);
   const int outs = (WITH_H ? 2 : 1) * kx * kx;
-  for (int e = threadIdx.x; e < outs; e += 256) {
-    const int which = e / (kx * kx), ab = e % (kx * kx), a = dkx.q(ab), b = dkx.r(ab);
-    const double* y = which == 0 ? xs : ys;
-    double s0 = 0.0, s1 = 0.0;
-    for (int r = 0; r < kChunk; r += 2) {
-      s0 = fma(xs[r * kx + a], y[r * kx + b], s0);
-      s1 = fma(xs[(r + 1) * kx + a], y[(r + 1) * kx + b], s1);
+  if constexpr (PAIRS) {
+    DF* xs = xtx_smem;                  // kChunk x kx
+    DF* ys = xtx_smem + kChunk * kx;    // kChunk x kx
+    for (int e = threadIdx.x; e < kChunk * kx; e += kXtxThreads) {
+      const int i = i0 + dkx.q(e);
+      xs[e] = i < d.n ? df_from(d.X[i0 * kx + e]) : DF{0.f, 0.f};
+      if (WITH_H) ys[e] = i < d.n ? df_from(d.MX[i0 * kx + e]) : DF{0.f, 0.f};
     }
-    const DF v = df_from(s0 + s1);
-    reinterpret_cast<float2*>(part)[e] = make_float2(v.hi, v.lo);  // FP32 pair: the reduction runs on the FP32 pipes
+    __syncthreads();
+    for (int e = threadIdx.x; e < outs; e += kXtxThreads) {
+      const int which = e / (kx * kx), ab = e % (kx * kx), a = dkx.q(ab), b = dkx.r(ab);
+      const DF* y = which == 0 ? xs : ys;
+      DFAcc s0, s1;
+      for (int r = 0; r < kChunk; r += 2) {
+        s0.add_prod(xs[r * kx + a], y[r * kx + b]);
+        s1.add_prod(xs[(r + 1) * kx + a], y[(r + 1) * kx + b]);
+      }
+      DFAcc t;
+      t.add(s0.get());
+      t.add(s1.get());
+      const DF v = t.get();
+      part[e] = make_float2(v.hi, v.lo);
+    }
+  } else {
+    double* xs = reinterpret_cast<double*>(xtx_smem);
+    double* ys = xs + kChunk * kx;
+    for (int e = threadIdx.x; e < kChunk * kx; e += kXtxThreads) {
+      const int i = i0 + dkx.q(e);
+      xs[e] = i < d.n ? d.X[i0 * kx + e] : 0.0;
+      if (WITH_H) ys[e] = i < d.n ? d.MX[i0 * kx + e] : 0.0;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < outs; e += kXtxThreads) {
+      const int which = e / (kx * kx), ab = e % (kx * kx), a = dkx.q(ab), b = dkx.r(ab);
+      const double* y = which == 0 ? xs : ys;
+      double s0 = 0.0, s1 = 0.0;
+      for (int r = 0; r < kChunk; r += 2) {
+        s0 = fma(xs[r * kx + a], y[r * kx + b], s0);
+        s1 = fma(xs[(r + 1) * kx + a], y[(r + 1) * kx + b], s1);
+      }
+      const DF v = df_from(s0 + s1);
+      part[e] = make_float2(v.hi, v.lo);
+    }
   }
 }
 
@@ -979,13 +1017,20 @@ __device__ inline void reduce_partials(const ProbDesc& d, const float2* part, DF
   const int nchunk = (int)((d.n + kChunk - 1) / kChunk);
   for (int e = threadIdx.x; e < kx * kx; e += nthreads) {
     DFAcc s, h;
-    for (int c = 0; c < nchunk; ++c) {
-      const float2 x = part[c * 2 * kx * kx + e];
-      s.add(DF{x.x, x.y});
-      if (H) {
-        const float2 y = part[c * 2 * kx * kx + kx * kx + e];
-        h.add(DF{y.x, y.y});
+    for (int c0 = 0; c0 < nchunk; c0 += 8) {  // the loads of 8 chunks in flight, then the sums in chunk order
+      float2 xv[8], yv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int c = c0 + u;
+        xv[u] = c < nchunk ? part[c * 2 * kx * kx + e] : make_float2(0.f, 0.f);
+        yv[u] = (H && c < nchunk) ? part[c * 2 * kx * kx + kx * kx + e] : make_float2(0.f, 0.f);
       }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (c0 + u < nchunk) {
+          s.add(DF{xv[u].x, xv[u].y});
+          if (H) h.add(DF{yv[u].x, yv[u].y});
+        }
     }
     S[dkx.q(e)][dkx.r(e)] = s.get();
     if (H) H[dkx.q(e)][dkx.r(e)] = h.get();
@@ -1349,7 +1394,13 @@ __device__ inline double wanted_residual_norm(const ProbDesc& d) {
   const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
   double s = 0.0;
   if (c < r)
-    for (int t = g; t < ntile; t += 8) s += pr[t * kx + c];
+    for (int t0 = g; t0 < ntile; t0 += 8 * 8) {  // 8 loads in flight, summed in tile order
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = t0 + 8 * u < ntile ? pr[(t0 + 8 * u) * kx + c] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
   red[g][c] = s;
   __syncthreads();
   double mx = 0.0;
@@ -1391,8 +1442,14 @@ __global__ void __launch_bounds__(256) k_eig_finish(const ProbDesc* __restrict__
   if (p >= nprob) return;
   const ProbDesc& d = descs[p];
   const int kx = d.kx, r = d.r;
-  for (int c = 0; c < r; ++c)
-    for (int64_t i = threadIdx.x; i < d.n; i += 256) d.V[(int64_t)c * d.ldv + i] = d.X[i * kx + c];
+  for (int64_t i = threadIdx.x; i < d.n; i += 256) {  // row i of X: its r loads in flight, then the stores
+    double x[kMaxR];
+#pragma unroll
+    for (int c = 0; c < kMaxR; ++c) x[c] = c < r ? d.X[i * kx + c] : 0.0;
+#pragma unroll
+    for (int c = 0; c < kMaxR; ++c)
+      if (c < r) d.V[(int64_t)c * d.ldv + i] = x[c];
+  }
   const double mx = wanted_residual_norm(d);
   if (threadIdx.x < kx && threadIdx.x < 32) d.stats[threadIdx.x] = d.small[2 * kx * kx + threadIdx.x];
   if (threadIdx.x == 0) d.stats[34] = mx;
@@ -1438,8 +1495,10 @@ cudaError_t launch_trace_M(const ProbDesc* descs, int nprob, cudaStream_t s) {
 template <typename T>
 static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, cudaStream_t s) {
   const int xtx_smem = (int)(2 * kChunk * kMaxL * sizeof(double));
-  cudaError_t ea = cudaFuncSetAttribute(k_xtx<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, xtx_smem);
-  if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_xtx<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, xtx_smem);
+  auto* xtx_s = k_xtx<false, sizeof(T) == 4>;  // X^T X
+  auto* xtx_h = k_xtx<true, sizeof(T) == 4>;   // X^T X and X^T M X
+  cudaError_t ea = cudaFuncSetAttribute(xtx_h, cudaFuncAttributeMaxDynamicSharedMemorySize, xtx_smem);
+  if (ea == cudaSuccess) ea = cudaFuncSetAttribute(xtx_s, cudaFuncAttributeMaxDynamicSharedMemorySize, xtx_smem);
   // the register algebra of the small steps is compiled for padded sizes KP >= kx
   const int kp = P.kx_max <= 4 ? 4 : (P.kx_max + 3) / 4 * 4;
   void (*rr)(const ProbDesc*, int, const float2*, const int64_t*) = nullptr;
@@ -1501,7 +1560,7 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
   RSM_LAUNCH_SMEM(k_factor<T>, std::min<int64_t>(ntask, fc), 256, factor_smem, D, P.dT, np, ft, P.sync, nchain);
   RSM_LAUNCH(k_init_X, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
   auto orthonormalise = [&]() -> cudaError_t {
-    RSM_LAUNCH_SMEM(k_xtx<false>, total(P.chunk), 256, xtx_smem, D, dev(P.chunk), np, P.part, dev(P.part_off));
+    RSM_LAUNCH_SMEM(xtx_s, total(P.chunk), kXtxThreads, xtx_smem, D, dev(P.chunk), np, P.part, dev(P.part_off));
     RSM_LAUNCH(orth, np, kSmallThreads, D, np, part, dev(P.part_off));
     RSM_LAUNCH(k_rotate<false>, total(P.rot), 256, D, dev(P.rot), np);
     return cudaSuccess;
@@ -1528,7 +1587,7 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
     else
       RSM_LAUNCH(k_gemm_MX<32>, total(P.mx), kMxRows, D, dev(P.mx), np);
     RSM_LAUNCH(k_split_sum, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
-    RSM_LAUNCH_SMEM(k_xtx<true>, total(P.chunk), 256, xtx_smem, D, dev(P.chunk), np, P.part, dev(P.part_off));
+    RSM_LAUNCH_SMEM(xtx_h, total(P.chunk), kXtxThreads, xtx_smem, D, dev(P.chunk), np, P.part, dev(P.part_off));
     RSM_LAUNCH_SMEM(rr, np, kRRThreads, kRRSmem, D, np, part, dev(P.part_off));
     RSM_LAUNCH(k_rotate<true>, total(P.rot), 256, D, dev(P.rot), np);
     RSM_LAUNCH(k_conv_check, np, 256, D, np);
@@ -1554,7 +1613,7 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
     else
       RSM_LAUNCH(k_gemm_MX64<32>, total(P.mx), kMxRows, D, dev(P.mx), np);
     RSM_LAUNCH(k_split_sum, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
-    RSM_LAUNCH_SMEM(k_xtx<true>, total(P.chunk), 256, xtx_smem, D, dev(P.chunk), np, P.part, dev(P.part_off));
+    RSM_LAUNCH_SMEM(xtx_h, total(P.chunk), kXtxThreads, xtx_smem, D, dev(P.chunk), np, P.part, dev(P.part_off));
     RSM_LAUNCH_SMEM(rr, np, kRRThreads, kRRSmem, D, np, part, dev(P.part_off));
     RSM_LAUNCH(k_rotate<true>, total(P.rot), 256, D, dev(P.rot), np);
     if (pass == 0) {

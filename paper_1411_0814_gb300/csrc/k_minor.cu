@@ -264,8 +264,8 @@ __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_scatter(const ProbDe
   minor_trial(descs, trial_off, nprob, lmax, g, false, smraw);
 }
 
-// The trials k_minor_half handed over (l > 16, or a nearly degenerate pair
-// across the minor split): one warp per listed trial, grid-stride.
+// The trials k_minor_half handed over (l > 16): one warp per listed trial,
+// grid-stride.
 __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_listed(const ProbDesc* __restrict__ descs,
                                                                   const int64_t* __restrict__ trial_off, int nprob,
                                                                   int lmax, const unsigned long long* __restrict__ list,
@@ -283,9 +283,45 @@ __global__ void __launch_bounds__(32 * kMinorWarps) k_minor_listed(const ProbDes
 // to even, so a trial's rotations depend on its own l only and its result is
 // the same in any batch), the n_minor smallest eigenvalues, then the same FP64
 // block-Newton refinement and fixed-point scatter as minor_trial with 16 lanes.
-// A trial with l > 16, or whose split is nearly degenerate (a complement
-// eigenvalue within split_tol ||G|| of a minor one), is appended to `list` for
-// k_minor_listed instead.
+// A trial whose split is nearly degenerate (a complement eigenvalue within
+// split_tol ||G|| of a minor one) refines that cluster as a block and splits it
+// by a small FP64 Rayleigh-Ritz step, in the same half warp; a trial with
+// l > 16 is appended to `list` for k_minor_listed.
+// Cyclic Jacobi of the small symmetric FP64 matrix C (nc x nc, row stride
+// ls) by one thread (nc is the size of a nearly degenerate cluster, usually 2):
+// eigenvalues on C's diagonal, eigenvectors into V (columns).
+__device__ inline void serial_jacobi64(double* C, double* V, int nc, int ls) {
+  for (int i = 0; i < nc; ++i)
+    for (int j = 0; j < nc; ++j) V[i * ls + j] = i == j ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 16; ++sweep) {
+    bool any = false;
+    for (int p = 0; p < nc; ++p)
+      for (int q = p + 1; q < nc; ++q) {
+        const double apq = C[p * ls + q], app = C[p * ls + p], aqq = C[q * ls + q];
+        if (apq == 0.0 || fabs(apq) <= 1e-17 * (fabs(app) + fabs(aqq))) continue;
+        any = true;
+        const double tau = (aqq - app) / (2.0 * apq);
+        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+        for (int k = 0; k < nc; ++k) {  // columns p, q
+          const double x = C[k * ls + p], y = C[k * ls + q];
+          C[k * ls + p] = c * x - s * y;
+          C[k * ls + q] = s * x + c * y;
+          const double vx = V[k * ls + p], vy = V[k * ls + q];
+          V[k * ls + p] = c * vx - s * vy;
+          V[k * ls + q] = s * vx + c * vy;
+        }
+        for (int k = 0; k < nc; ++k) {  // rows p, q
+          const double x = C[p * ls + k], y = C[q * ls + k];
+          C[p * ls + k] = c * x - s * y;
+          C[q * ls + k] = s * x + c * y;
+        }
+        C[p * ls + q] = C[q * ls + p] = 0.0;
+      }
+    if (!any) break;
+  }
+}
+
 template <int KP>
 __device__ __forceinline__ void minor_half_body(const ProbDesc& d, int64_t t, int64_t g, int ls, unsigned char* base,
                                                 int* pick, int* is_minor, unsigned long long* __restrict__ list,
@@ -354,18 +390,85 @@ __device__ __forceinline__ void minor_half_body(const ProbDesc& d, int64_t t, in
     for (int j = 0; j < nm; ++j) gap_min = fminf(gap_min, fabsf(lam - Sf[pick[j] * ls + pick[j]]));
 #pragma unroll
   for (int o = 8; o; o >>= 1) gap_min = fminf(gap_min, __shfl_xor_sync(hmask, gap_min, o));
-  if (gap_min < split_tol(d) * fro) {  // k_minor_listed takes this trial
-    if (hl == 0) list[atomicAdd(list_count, 1ull)] = (unsigned long long)g;
-    return;
+  if (gap_min < split_tol(d) * fro) {
+    // Nearly degenerate across the split: the cluster of the minor eigenvectors
+    // and the complement ones within split_tol ||G|| of them is refined as one
+    // block by the FP64 Newton steps (its gaps to the rest are wide), then a
+    // Rayleigh-Ritz step inside it (FP64, nc x nc) gives the n_minor vectors.
+    const float tol = split_tol(d) * fro;
+    if (hl == 0) {  // the cluster: is_minor marks it, pick lists it
+      int nc = 0;
+      for (int i = 0; i < l; ++i) {
+        bool in = is_minor[i] != 0;
+        for (int j = 0; j < nm && !in; ++j) in = fabsf(Sf[i * ls + i] - Sf[pick[j] * ls + pick[j]]) < tol;
+        is_minor[i] = in ? 1 : 0;
+      }
+      for (int i = 0; i < l; ++i)
+        if (is_minor[i]) pick[nc++] = i;
+      gv[ls - 1] = (double)nc;  // (the last entry of ev is beyond l)
+    }
+    __syncwarp(hmask);
+    const int nc = (int)gv[ls - 1];
+    const SmallDiv dnc((uint32_t)nc);
+    for (int it = hl; it < l * nc; it += 16) {
+      const int aa = dnc.q(it), j = dnc.r(it);
+      Z[aa * nc + j] = (double)Qf[aa * ls + pick[j]];
+    }
+    for (int it = hl; it < l * l; it += 16) Wd[dl.q(it) * ls + dl.r(it)] = (double)Qf[dl.q(it) * ls + dl.r(it)];
+    if (hl < l) gv[hl] = (double)lam;
+    __syncwarp(hmask);
+    newton_refine<16>(Gs, Wd, gv, Z, rv, cv, l, nc, ls, is_minor, (double)fro, 1e-17, kNewtonSteps);
+    // Rayleigh-Ritz inside the cluster: T = G Z (l x nc, into Wd), C = Z^T T (into the space of Sf and Qf)
+    double* T = Wd;
+    double* Cm = reinterpret_cast<double*>(Sf);  // Sf and Qf are no longer needed: lsz x ls doubles
+    double* Vc = Wd;                             // after C is formed, T's space
+    for (int it = hl; it < l * nc; it += 16) {
+      const int aa = dnc.q(it), j = dnc.r(it);
+      double acc = 0.0;
+      for (int b = 0; b < l; ++b) acc = fma(Gs[aa * ls + b], Z[b * nc + j], acc);
+      T[aa * nc + j] = acc;
+    }
+    __syncwarp(hmask);
+    for (int it = hl; it < nc * nc; it += 16) {
+      const int i = dnc.q(it), j = dnc.r(it);
+      double acc = 0.0;
+      for (int b = 0; b < l; ++b) acc = fma(Z[b * nc + i], T[b * nc + j], acc);
+      Cm[i * ls + j] = acc;
+    }
+    __syncwarp(hmask);
+    if (hl == 0) {
+      for (int i = 0; i < nc; ++i)  // symmetrise
+        for (int j = i + 1; j < nc; ++j) Cm[i * ls + j] = Cm[j * ls + i] = 0.5 * (Cm[i * ls + j] + Cm[j * ls + i]);
+      serial_jacobi64(Cm, Vc, nc, ls);
+      for (int i = 0; i < nc; ++i) is_minor[i] = 0;  // now: which cluster vectors are minor
+      for (int j = 0; j < nm; ++j) {
+        int best = -1;
+        for (int i = 0; i < nc; ++i)
+          if (!is_minor[i] && (best < 0 || Cm[i * ls + i] < Cm[best * ls + best])) best = i;
+        is_minor[best] = 1;
+        pick[j] = best;
+      }
+    }
+    __syncwarp(hmask);
+    for (int it = hl; it < l * nm; it += 16) {  // Z (l x n_minor) = Z_cluster Vc[:, picked], into C's space
+      const int aa = dnm.q(it), j = dnm.r(it);
+      double acc = 0.0;
+      for (int c = 0; c < nc; ++c) acc = fma(Z[aa * nc + c], Vc[c * ls + pick[j]], acc);
+      Cm[aa * nm + j] = acc;
+    }
+    __syncwarp(hmask);
+    for (int it = hl; it < l * nm; it += 16) Z[it] = Cm[it];
+    __syncwarp(hmask);
+  } else {
+    for (int it = hl; it < l * nm; it += 16) {
+      const int aa = dnm.q(it), j = dnm.r(it);
+      Z[aa * nm + j] = (double)Qf[aa * ls + pick[j]];
+    }
+    for (int it = hl; it < l * l; it += 16) Wd[dl.q(it) * ls + dl.r(it)] = (double)Qf[dl.q(it) * ls + dl.r(it)];
+    if (hl < l) gv[hl] = (double)lam;
+    __syncwarp(hmask);
+    newton_refine<16>(Gs, Wd, gv, Z, rv, cv, l, nm, ls, is_minor, (double)fro, 1e-17, d.gram_fp32 ? 1 : kNewtonSteps);
   }
-  for (int it = hl; it < l * nm; it += 16) {
-    const int aa = dnm.q(it), j = dnm.r(it);
-    Z[aa * nm + j] = (double)Qf[aa * ls + pick[j]];
-  }
-  for (int it = hl; it < l * l; it += 16) Wd[dl.q(it) * ls + dl.r(it)] = (double)Qf[dl.q(it) * ls + dl.r(it)];
-  if (hl < l) gv[hl] = (double)lam;
-  __syncwarp(hmask);
-  newton_refine<16>(Gs, Wd, gv, Z, rv, cv, l, nm, ls, is_minor, (double)fro, 1e-17, d.gram_fp32 ? 1 : kNewtonSteps);
   if (d.debug_Z)
     for (int it = hl; it < l * nm; it += 16) d.debug_Z[t * l * nm + it] = Z[it];
   if (d.Zst)
@@ -458,7 +561,8 @@ cudaError_t launch_minor_scatter(const ProbDesc* descs, const int64_t* trial_off
     if ((e = cudaFuncSetAttribute(k_minor_listed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn)) !=
         cudaSuccess)
       return e;
-    const int64_t grid = std::min<int64_t>((total + kMinorWarps - 1) / kMinorWarps, 256);
+    // grid-stride over the list with enough CTAs to fill the GPU when every trial is listed
+    const int64_t grid = std::min<int64_t>((total + kMinorWarps - 1) / kMinorWarps, 1024);
     k_minor_listed<<<(unsigned)grid, 32 * kMinorWarps, dyn, s>>>(descs, trial_off, nprob, lmax, list, list_count);
     ++g_kernel_launches;
     return cudaGetLastError();

@@ -130,12 +130,16 @@ __device__ inline void df_lowdin(DFRow* Q, DFRow* W1, DFRow* W2, int kx, int nth
 // Lane i < KP holds row i of a KP x KP matrix in a[0 .. KP).
 
 // a[idx] for a runtime idx without dynamic register indexing.
-template <int KP>
-__device__ __forceinline__ float reg_pick(const float (&a)[KP], int idx) {
-  float v = 0.f;
+template <typename T, int KP>
+__device__ __forceinline__ T reg_pick(const T (&a)[KP], int idx) {
+  T v = 0;
 #pragma unroll
   for (int j = 0; j < KP; ++j) v = (j == idx) ? a[j] : v;
   return v;
+}
+template <int KP>
+__device__ __forceinline__ float reg_pick(const float (&a)[KP], int idx) {
+  return reg_pick<float, KP>(a, idx);
 }
 
 // In place: a (symmetric, rows per lane, the shift s * trace of its leading
@@ -217,60 +221,82 @@ __host__ __device__ constexpr int circle_prev(int y) {
 // Rows and columns of padding (index >= the true size) must be zero off the
 // diagonal: their pairs are never rotated.  W = 32: the whole warp holds one
 // matrix; W = 16: each half warp holds its own (lane = lane within the half),
-// and the halves sweep independently.  Returns the sweeps that rotated.
-template <int KP, int W = 32>
-__device__ __forceinline__ int reg_jacobi(float (&a)[KP], float (&v)[KP], float tol, int max_sweeps) {
+// and the halves sweep independently.  T = float (hardware reciprocal and
+// square roots) or double (the Newton-Raphson forms of common.cuh).  Returns the
+// sweeps that rotated.
+template <typename T>
+__device__ __forceinline__ T jac_rcp(T x);
+template <>
+__device__ __forceinline__ float jac_rcp<float>(float x) { return __frcp_rn(x); }
+template <>
+__device__ __forceinline__ double jac_rcp<double>(double x) { return rcp64(x); }
+template <typename T>
+__device__ __forceinline__ T jac_sqrt(T x);
+template <>
+__device__ __forceinline__ float jac_sqrt<float>(float x) { return sqrtf(x); }
+template <>
+__device__ __forceinline__ double jac_sqrt<double>(double x) { return sqrt64(x); }
+template <typename T>
+__device__ __forceinline__ T jac_rsqrt(T x);
+template <>
+__device__ __forceinline__ float jac_rsqrt<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ __forceinline__ double jac_rsqrt<double>(double x) { return rsqrt64(x); }
+
+template <typename T, int KP, int W = 32>
+__device__ __forceinline__ int reg_jacobi_t(T (&a)[KP], T (&v)[KP], T tol, int max_sweeps) {
   static_assert(KP % 2 == 0 && KP >= 2 && KP <= W && (W == 16 || W == 32), "KP: even, 2..W");
   const int wl = threadIdx.x & 31;
   const int lane = wl & (W - 1), base = wl - lane;
   const unsigned mask = W == 32 ? 0xffffffffu : (0xffffu << base);
-  const float eps2 = FLT_EPSILON * FLT_EPSILON;
+  const T eps = sizeof(T) == 4 ? (T)FLT_EPSILON : (T)DBL_EPSILON;
+  const T eps2 = eps * eps;
   const int src = base + (lane < KP ? circle_prev<KP>(lane) : lane);
   int rotated = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     bool any = false;
     for (int round = 0; round < KP - 1; ++round) {
       const bool even = (lane & 1) == 0;
-      const float own = reg_pick<KP>(a, lane);
-      const float off = reg_pick<KP>(a, lane ^ 1);
-      const float other = __shfl_xor_sync(mask, own, 1);
-      const float apq = __shfl_sync(mask, off, wl & ~1);  // the even lane's a_pq for both
-      const float app = even ? own : other, aqq = even ? other : own;
-      float c = 1.f, s = 0.f;
-      if (lane < KP && fabsf(apq) > tol && apq * apq > eps2 * fabsf(app * aqq)) {
-        const float tau = (aqq - app) * __frcp_rn(2.f * apq);
-        const float t = (tau >= 0.f ? 1.f : -1.f) * __frcp_rn(fabsf(tau) + sqrtf(1.f + tau * tau));
-        c = rsqrtf(1.f + t * t);
+      const T own = reg_pick<T, KP>(a, lane);
+      const T off = reg_pick<T, KP>(a, lane ^ 1);
+      const T other = __shfl_xor_sync(mask, own, 1);
+      const T apq = __shfl_sync(mask, off, wl & ~1);  // the even lane's a_pq for both
+      const T app = even ? own : other, aqq = even ? other : own;
+      T c = 1, s = 0;
+      if (lane < KP && fabs(apq) > tol && apq * apq > eps2 * fabs(app * aqq)) {
+        const T tau = (aqq - app) * jac_rcp<T>(2 * apq);
+        const T t = (tau >= 0 ? (T)1 : (T)-1) * jac_rcp<T>(fabs(tau) + jac_sqrt<T>(1 + tau * tau));
+        c = jac_rsqrt<T>(1 + t * t);
         s = t * c;
       }
-      const bool rot = s != 0.f;
+      const bool rot = s != (T)0;
       any |= __any_sync(mask, rot);
       // columns: every pair (2k, 2k + 1) with the rotation of lane 2k
 #pragma unroll
       for (int k = 0; k < KP / 2; ++k) {
-        const float ck = __shfl_sync(mask, c, base + 2 * k), sk = __shfl_sync(mask, s, base + 2 * k);
-        const float x = a[2 * k], y = a[2 * k + 1];
+        const T ck = __shfl_sync(mask, c, base + 2 * k), sk = __shfl_sync(mask, s, base + 2 * k);
+        const T x = a[2 * k], y = a[2 * k + 1];
         a[2 * k] = ck * x - sk * y;
         a[2 * k + 1] = sk * x + ck * y;
-        const float vx = v[2 * k], vy = v[2 * k + 1];
+        const T vx = v[2 * k], vy = v[2 * k + 1];
         v[2 * k] = ck * vx - sk * vy;
         v[2 * k + 1] = sk * vx + ck * vy;
       }
       // rows: this lane's row with its partner's
 #pragma unroll
       for (int j = 0; j < KP; ++j) {
-        const float o = __shfl_xor_sync(mask, a[j], 1);
+        const T o = __shfl_xor_sync(mask, a[j], 1);
         a[j] = even ? (c * a[j] - s * o) : (s * o + c * a[j]);
       }
       if (rot) {  // the annihilated entry, exactly
 #pragma unroll
         for (int j = 0; j < KP; ++j)
-          if (j == (lane ^ 1)) a[j] = 0.f;
+          if (j == (lane ^ 1)) a[j] = 0;
       }
       // the circle permutation: rows from lane circle_prev(lane), columns (of a and v) by moves
 #pragma unroll
       for (int j = 0; j < KP; ++j) a[j] = __shfl_sync(mask, a[j], src);
-      float ta[KP], tv[KP];
+      T ta[KP], tv[KP];
 #pragma unroll
       for (int j = 0; j < KP; ++j) {
         ta[circle_next<KP>(j)] = a[j];
@@ -286,6 +312,11 @@ __device__ __forceinline__ int reg_jacobi(float (&a)[KP], float (&v)[KP], float 
     ++rotated;
   }
   return rotated;
+}
+
+template <int KP, int W = 32>
+__device__ __forceinline__ int reg_jacobi(float (&a)[KP], float (&v)[KP], float tol, int max_sweeps) {
+  return reg_jacobi_t<float, KP, W>(a, v, tol, max_sweeps);
 }
 
 }  // namespace rsm
