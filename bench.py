@@ -566,9 +566,14 @@ def bench_mine(args):
     sg_ms = stage["select_gram"]
     peaks = measured_peaks()
     achieved = alg_bytes / (sg_ms * 1e-3) / 1e9
+    # one launch per row slab: 32 MiB of FP32 Y by default, or the autotuner's slab size
+    slab_mib = tune["slab_mib"] if tune is not None and tune["schedule"] == "slab" else 32
+    slab_rows = max(1024, ((slab_mib << 20) // (p.n * 4)) // 32 * 32)
+    launches = -(-p.m // slab_rows)
+    # DRAM bytes per launch from the committed ncu summary (taken at its own slab size; the slab
+    # launches read Y once between them, so the bytes per launch scale with the rows per launch)
     trec = traffic_record("k_gram_slab_paper_131072x1024.md")
-    launches = trec["launches_per_step"] if trec else 16  # row slabs of 32 MiB of FP32 Y
-    traffic = trec["dram_bytes_per_launch"] if trec else None
+    traffic = (int(trec["dram_bytes_per_launch"] * trec["launches_per_step"] / launches) if trec else None)
     # the L2 sector ceiling (rsm_probe_gather, measured here) against the slab Gram's sectors: per
     # trial and column, the 8-row sectors that hold a selected row (rows selected with probability
     # q = p_t / m: a fraction 1 - (1 - q)^8 of the m / 8 sectors), plus the mask words (8 per sector)
@@ -585,7 +590,7 @@ def bench_mine(args):
     share = sum((32 - g) / 32.0 * q * (1.0 - q) ** (g - 1) for g in range(1, 32))
     lines = last.rows_selected * p.l * (1.0 - share) + p.trials * p.l * ((p.m + 31) // 32) / 32
     lines_rate = lines / (sg_ms * 1e-3)
-    roofline = {"kernel": "k_gram_slab<2,9> (row-slab selection + FP32 Gram)", "bound": "hbm",
+    roofline = {"kernel": "k_gram_slab<2,9,0> (row-slab selection + FP32 Gram)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "algorithmic_bytes_per_launch": int(alg_bytes / launches), "launches_per_step": launches,

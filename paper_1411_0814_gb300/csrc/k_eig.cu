@@ -791,7 +791,7 @@ constexpr int kMxGroup = 16;  // loads of M issued together (L2 latency is hidde
 // about 2^-44 relative accuracy; the lo*lo term (2^-48) is dropped.
 // Thread = row i (M is symmetric, so M[j][i] is read: consecutive threads read
 // consecutive addresses); split s covers columns j in [s n / kSplit, (s+1) n / kSplit);
-// the parts go to R slots and k_split_sum adds them in FP64 in a fixed order.
+// the parts go to R slots and sum_mx_slots adds them in FP64 in a fixed order.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   const float bb = __fsub_rn(s, a);
@@ -914,29 +914,27 @@ __global__ void k_refine_begin(const ProbDesc* __restrict__ descs, int nprob) {
   if (p < nprob) descs[p].stats[kConvFlag] = 0.0;
 }
 
-__global__ void __launch_bounds__(256) k_split_sum(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
-                                                  int nprob) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= off[nprob]) return;
-  const int p = find_problem(off, nprob, g);
-  const ProbDesc& d = descs[p];
-  if (d.stats[kConvFlag] != 0.0) return;
-  const int e = (int)(g - off[p]);
+
+// Partial Gram sums over chunks of kChunk rows: part[chunk] = [X^T X | X^T MX]
+// (2 kx^2 values; the second half only when WITH_H).
+// M X entry e (row-major n x kx): the kSplit partial products of k_gemm_MX in
+// slot order (every load in flight first); stored into MX for the later steps.
+__device__ __forceinline__ double sum_mx_slots(const ProbDesc& d, int e) {
   const int nk = (int)d.n * d.kx;
   double v[kSplit];
 #pragma unroll
-  for (int q = 0; q < kSplit; ++q) v[q] = d.R[q * nk + e];  // every load in flight, then the sum in slot order
+  for (int q = 0; q < kSplit; ++q) v[q] = d.R[q * nk + e];
   double s = v[0];
 #pragma unroll
   for (int q = 1; q < kSplit; ++q) s += v[q];
   d.MX[e] = s;
+  return s;
 }
 
-// Partial Gram sums over chunks of kChunk rows: part[chunk] = [X^T X | X^T MX]
-// (2 kx^2 values; the second half only when WITH_H).
 constexpr int kChunk = 64;
 constexpr int kXtxThreads = 320;  // 2 kx^2 = 288 outputs at kx = 12 in one round
-// Each partial is written as an FP32 pair.  PAIRS (FP32 factor): X and M X are
+// With H, M X is first formed from its kSplit slots (sum_mx_slots).  Each
+// partial is written as an FP32 pair.  PAIRS (FP32 factor): X and M X are
 // staged as FP32 pairs and the 64-term dot products run in pair arithmetic on
 // the FP32 pipes (small_df.cuh).  Otherwise (FP64 factor, an almost exact
 // shift-invert whose steps leave X with column norms spread over many orders of
@@ -963,7 +961,7 @@ __global__ void __launch_bounds__(kXtxThreads) k_xtx(const ProbDesc* __restrict_
     for (int e = threadIdx.x; e < kChunk * kx; e += kXtxThreads) {
       const int i = i0 + dkx.q(e);
       xs[e] = i < d.n ? df_from(d.X[i0 * kx + e]) : DF{0.f, 0.f};
-      if (WITH_H) ys[e] = i < d.n ? df_from(d.MX[i0 * kx + e]) : DF{0.f, 0.f};
+      if (WITH_H) ys[e] = i < d.n ? df_from(sum_mx_slots(d, i0 * kx + e)) : DF{0.f, 0.f};
     }
     __syncthreads();
     for (int e = threadIdx.x; e < outs; e += kXtxThreads) {
@@ -986,7 +984,7 @@ __global__ void __launch_bounds__(kXtxThreads) k_xtx(const ProbDesc* __restrict_
     for (int e = threadIdx.x; e < kChunk * kx; e += kXtxThreads) {
       const int i = i0 + dkx.q(e);
       xs[e] = i < d.n ? d.X[i0 * kx + e] : 0.0;
-      if (WITH_H) ys[e] = i < d.n ? d.MX[i0 * kx + e] : 0.0;
+      if (WITH_H) ys[e] = i < d.n ? sum_mx_slots(d, i0 * kx + e) : 0.0;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < outs; e += kXtxThreads) {
@@ -1254,7 +1252,57 @@ __global__ void __launch_bounds__(kRRThreads) k_rr(const ProbDesc* __restrict__ 
 constexpr int kRotRows = 8;
 constexpr int kResSlot = 31;  // R slot of the per-tile residual sums of squares (slots 1..kPSplit: preconditioner parts)
 static_assert(kResSlot > kPSplit && kResSlot < kSplit, "R slots of the residual sums and the preconditioner parts");
-template <bool FULL>
+// Largest residual column norm ||R_j|| over the r wanted columns, from the
+// per-tile sums of squares of k_rotate (summed in a fixed order).  256 threads:
+// 8 groups split the tiles, lane = column.
+__device__ inline double wanted_residual_norm(const ProbDesc& d) {
+  __shared__ double red[8][32];
+  const int kx = d.kx, r = d.r;
+  const int ntile = (int)((d.n + kRotRows - 1) / kRotRows);
+  const double* pr = d.R + (int64_t)kResSlot * d.n * kx;
+  const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
+  double s = 0.0;
+  if (c < r)
+    for (int t0 = g; t0 < ntile; t0 += 8 * 8) {  // 8 loads in flight, summed in tile order
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = t0 + 8 * u < ntile ? __ldcg(pr + (t0 + 8 * u) * kx + c) : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
+  red[g][c] = s;
+  __syncthreads();
+  double mx = 0.0;
+  if (threadIdx.x < 32) {
+    double tot = 0.0;
+    for (int k = 0; k < 8; ++k) tot += red[k][c];
+    mx = c < r ? sqrt64(tot) : 0.0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  return mx;  // valid in thread 0
+}
+
+// After a Rayleigh-Ritz step: the largest wanted residual norm against the gap
+// theta_{r+1} - theta_r; sets the flag that skips the remaining iterations.
+// Run by the last CTA of k_rotate<true, true> to finish.
+__device__ __forceinline__ void conv_check(const ProbDesc& d) {
+  const int kx = d.kx, r = d.r;
+  const double mx = wanted_residual_norm(d);
+  if (threadIdx.x == 0) {
+    const double* th = d.small + 2 * kx * kx;
+    const double gap = r < kx ? th[r] - th[r - 1] : 0.0;
+    const double prev = d.stats[kPrevRes];
+    // converged: below the target, or no longer falling (at the FP64 rounding
+    // floor of M X - X Theta) while already below kStallTol * gap
+    const bool stalled = prev > 0.0 && mx > 0.5 * prev && mx <= kStallTol * gap;
+    if (gap > 0.0 && (mx <= kConvTol * gap || stalled)) d.stats[kConvFlag] = 1.0;
+    d.stats[kPrevRes] = mx;
+    d.stats[kIterCount] += 1.0;
+  }
+}
+
+template <bool FULL, bool CHECK>
 __global__ void __launch_bounds__(256) k_rotate(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                int nprob) {
   __shared__ double q[2 * kMaxL * kMaxL];
@@ -1311,6 +1359,23 @@ __global__ void __launch_bounds__(256) k_rotate(const ProbDesc* __restrict__ des
       double t = 0.0;
       for (int r = 0; r < kRotRows; ++r) t += rsq[r][threadIdx.x];
       d.R[(int64_t)kResSlot * d.n * kx + (blockIdx.x - off[p]) * kx + threadIdx.x] = t;
+    }
+  }
+  if (CHECK) {
+    // the last CTA of the problem to finish runs the convergence check (counters[9]
+    // counts the finished tiles and is reset for the next step)
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned long long ntile = (unsigned long long)((d.n + kRotRows - 1) / kRotRows);
+      last = atomicAdd(&d.counters[9], 1ull) == ntile - 1;
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      conv_check(d);
+      if (threadIdx.x == 0) d.counters[9] = 0ull;
     }
   }
 }
@@ -1378,62 +1443,13 @@ __global__ void __launch_bounds__(256) k_precond_apply(const ProbDesc* __restric
   if (d.stats[kConvFlag] != 0.0) return;
   const int e = (int)(g - off[p]);
   const int nk = (int)d.n * d.kx;
+  double v[kPSplit];
+#pragma unroll
+  for (int q = 0; q < kPSplit; ++q) v[q] = d.R[(1 + q) * nk + e];  // every load in flight, summed in order
   double s = 0.0;
-  for (int q = 0; q < kPSplit; ++q) s += d.R[(1 + q) * nk + e];
+#pragma unroll
+  for (int q = 0; q < kPSplit; ++q) s += v[q];
   d.X[e] = MODE == 0 ? d.X[e] - s : s;
-}
-
-// Largest residual column norm ||R_j|| over the r wanted columns, from the
-// per-tile sums of squares of k_rotate (summed in a fixed order).  256 threads:
-// 8 groups split the tiles, lane = column.
-__device__ inline double wanted_residual_norm(const ProbDesc& d) {
-  __shared__ double red[8][32];
-  const int kx = d.kx, r = d.r;
-  const int ntile = (int)((d.n + kRotRows - 1) / kRotRows);
-  const double* pr = d.R + (int64_t)kResSlot * d.n * kx;
-  const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
-  double s = 0.0;
-  if (c < r)
-    for (int t0 = g; t0 < ntile; t0 += 8 * 8) {  // 8 loads in flight, summed in tile order
-      double v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = t0 + 8 * u < ntile ? pr[(t0 + 8 * u) * kx + c] : 0.0;
-#pragma unroll
-      for (int u = 0; u < 8; ++u) s += v[u];
-    }
-  red[g][c] = s;
-  __syncthreads();
-  double mx = 0.0;
-  if (threadIdx.x < 32) {
-    double tot = 0.0;
-    for (int k = 0; k < 8; ++k) tot += red[k][c];
-    mx = c < r ? sqrt64(tot) : 0.0;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  }
-  return mx;  // valid in thread 0
-}
-
-// After a Rayleigh-Ritz step: the largest wanted residual norm against the gap
-// theta_{r+1} - theta_r; sets the flag that skips the remaining iterations.
-__global__ void __launch_bounds__(256) k_conv_check(const ProbDesc* __restrict__ descs, int nprob) {
-  const int p = blockIdx.x;
-  if (p >= nprob) return;
-  const ProbDesc& d = descs[p];
-  if (d.stats[kConvFlag] != 0.0) return;
-  const int kx = d.kx, r = d.r;
-  const double mx = wanted_residual_norm(d);
-  if (threadIdx.x == 0) {
-    const double* th = d.small + 2 * kx * kx;
-    const double gap = r < kx ? th[r] - th[r - 1] : 0.0;
-    const double prev = d.stats[kPrevRes];
-    // converged: below the target, or no longer falling (at the FP64 rounding
-    // floor of M X - X Theta) while already below kStallTol * gap
-    const bool stalled = prev > 0.0 && mx > 0.5 * prev && mx <= kStallTol * gap;
-    if (gap > 0.0 && (mx <= kConvTol * gap || stalled)) d.stats[kConvFlag] = 1.0;
-    d.stats[kPrevRes] = mx;
-    d.stats[kIterCount] += 1.0;
-  }
 }
 
 // V = first r columns of X (n x r column-major, ldv); Ritz values; residual norm.
@@ -1495,6 +1511,9 @@ cudaError_t launch_trace_M(const ProbDesc* descs, int nprob, cudaStream_t s) {
 template <typename T>
 static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, cudaStream_t s) {
   const int xtx_smem = (int)(2 * kChunk * kMaxL * sizeof(double));
+  auto* rot_x = k_rotate<false, false>;     // X <- X Q
+  auto* rot_full = k_rotate<true, false>;   // also M X and R
+  auto* rot_check = k_rotate<true, true>;   // ... and the convergence check by the last CTA
   auto* xtx_s = k_xtx<false, sizeof(T) == 4>;  // X^T X
   auto* xtx_h = k_xtx<true, sizeof(T) == 4>;   // X^T X and X^T M X
   cudaError_t ea = cudaFuncSetAttribute(xtx_h, cudaFuncAttributeMaxDynamicSharedMemorySize, xtx_smem);
@@ -1562,7 +1581,7 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
   auto orthonormalise = [&]() -> cudaError_t {
     RSM_LAUNCH_SMEM(xtx_s, total(P.chunk), kXtxThreads, xtx_smem, D, dev(P.chunk), np, P.part, dev(P.part_off));
     RSM_LAUNCH(orth, np, kSmallThreads, D, np, part, dev(P.part_off));
-    RSM_LAUNCH(k_rotate<false>, total(P.rot), 256, D, dev(P.rot), np);
+    RSM_LAUNCH(rot_x, total(P.rot), 256, D, dev(P.rot), np);
     return cudaSuccess;
   };
   cudaError_t e;
@@ -1586,11 +1605,9 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
       RSM_LAUNCH(k_gemm_MX<16>, total(P.mx), kMxRows, D, dev(P.mx), np);
     else
       RSM_LAUNCH(k_gemm_MX<32>, total(P.mx), kMxRows, D, dev(P.mx), np);
-    RSM_LAUNCH(k_split_sum, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
     RSM_LAUNCH_SMEM(xtx_h, total(P.chunk), kXtxThreads, xtx_smem, D, dev(P.chunk), np, P.part, dev(P.part_off));
     RSM_LAUNCH_SMEM(rr, np, kRRThreads, kRRSmem, D, np, part, dev(P.part_off));
-    RSM_LAUNCH(k_rotate<true>, total(P.rot), 256, D, dev(P.rot), np);
-    RSM_LAUNCH(k_conv_check, np, 256, D, np);
+    RSM_LAUNCH(rot_check, total(P.rot), 256, D, dev(P.rot), np);
     if (it < iters) {
       RSM_LAUNCH(precond_r, total(P.row_tile), 256, D, dev(P.row_tile), np);
       RSM_LAUNCH(k_precond_apply<0>, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
@@ -1612,10 +1629,9 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
       RSM_LAUNCH(k_gemm_MX64<16>, total(P.mx), kMxRows, D, dev(P.mx), np);
     else
       RSM_LAUNCH(k_gemm_MX64<32>, total(P.mx), kMxRows, D, dev(P.mx), np);
-    RSM_LAUNCH(k_split_sum, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
     RSM_LAUNCH_SMEM(xtx_h, total(P.chunk), kXtxThreads, xtx_smem, D, dev(P.chunk), np, P.part, dev(P.part_off));
     RSM_LAUNCH_SMEM(rr, np, kRRThreads, kRRSmem, D, np, part, dev(P.part_off));
-    RSM_LAUNCH(k_rotate<true>, total(P.rot), 256, D, dev(P.rot), np);
+    RSM_LAUNCH(rot_full, total(P.rot), 256, D, dev(P.rot), np);
     if (pass == 0) {
       RSM_LAUNCH(precond_r, total(P.row_tile), 256, D, dev(P.row_tile), np);
       RSM_LAUNCH(k_precond_apply<0>, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);

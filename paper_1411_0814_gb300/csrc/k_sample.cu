@@ -26,22 +26,31 @@ __global__ void __launch_bounds__(256) k_pack_mask(const ProbDesc* __restrict__ 
       const uint4* q = reinterpret_cast<const uint4*>(col + r0);
       uint4 a = __ldg(q), b = __ldg(q + 1);
       uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+      // per 4 bytes: 0x01 in each nonzero byte, then the multiply by 0x01020408 moves byte i's bit
+      // to bit 24 + i with no other product term reaching bits 24..27
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
-#pragma unroll
-        for (int by = 0; by < 4; ++by)
-          if ((v[k] >> (8 * by)) & 0xffu) word |= 1u << (4 * k + by);
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t ones = __vcmpne4(v[k], 0u) & 0x01010101u;
+        word |= ((ones * 0x01020408u) >> 24) << (4 * k);
+      }
     } else {
       for (int k = 0; k < 32; ++k)
         if (r0 + k < d.m && col[r0 + k]) word |= 1u << k;
     }
     d.bits[c * d.ldb + w] = word;
   }
-  // known-entry count of the problem (eq. def.rho numerator), exact integer sum
+  // known-entry count of the problem (eq. def.rho numerator), exact integer sum: one atomic per CTA
+  __shared__ unsigned wcnt[8];
   unsigned cnt = __popc(word);
 #pragma unroll
   for (int o = 16; o; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
-  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&d.counters[1], (unsigned long long)cnt);
+  if ((threadIdx.x & 31) == 0) wcnt[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int k = 0; k < 8; ++k) t += wcnt[k];
+    if (t) atomicAdd(&d.counters[1], t);
+  }
 }
 
 // ------------------------------------------------------------------ a2 sample_cols
