@@ -301,10 +301,10 @@ def decompose_rows(Y: np.ndarray, W: np.ndarray, r: int, k: Optional[int] = None
     for t, Z in enumerate(Z_list):  # trials in ascending t, as for M1
         if Z is None:
             continue
+        # the trial's block of Xi Xi^T (eq. M): its c_t - r null vectors are the
+        # columns of Z, so their outer products sum to Z Z^T on C_t x C_t
         C = C_list[t]
-        for j in range(Z.shape[1]):
-            z = Z[:, j]
-            M[np.ix_(C, C)] += np.outer(z, z)
+        M[np.ix_(C, C)] += Z @ Z.T
     V, evals = eig_smallest(M, r)
     status = STATUS_OK
     if underdetermined(evals, r, np.trace(M), int(accepted.sum())):
