@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace rsm {
 
 constexpr int kMaxL = 32;  // columns per submatrix supported by the kernels
@@ -151,6 +153,34 @@ __device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_
 }
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, uint32_t src_bytes) {  // 0: zero fill
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream serialisation attribute may be scheduled as soon as every CTA of its
+// predecessor on the stream has exited, before that grid's completion and
+// memory flush; pdl_enter() (griddepcontrol.wait; a no-op for a normal launch)
+// blocks until the predecessor has completed and its memory is visible.  It is
+// the first statement of every kernel launched that way, before any access to
+// memory.  No kernel signals its dependents early (launch_dependents): measured
+// on the eigen stage's chain of small launches, the early-scheduled CTAs of the
+// next launch made the chain slower, not faster.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Host side: launch `kernel` with programmatic stream serialisation (see
+// pdl_enter, which the kernel must call first).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_chained(void (*kernel)(KArgs...), unsigned blocks, unsigned threads, size_t smem,
+                                  cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>

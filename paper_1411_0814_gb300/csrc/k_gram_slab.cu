@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(32 * kSlabWarps, (slab_minb<MODE, L>() - OCC >
     k_gram_slab(const ProbDesc* __restrict__ descs,
                                                                const int64_t* __restrict__ task_off, int nprob,
                                                                int slab) {
+  pdl_enter();
   using Tr = SlabT<MODE>;
   using A = typename Tr::acc_t;
   using V = typename Tr::val_t;
@@ -210,8 +211,8 @@ static cudaError_t launch_slab_l(const SlabPlan* Sp, cudaStream_t s, int* regs) 
   for (int sl = 0; sl < S.nslab; ++sl) {
     const int64_t tasks = S.hT[S.task_pos + (size_t)sl * (S.nprob + 1) + S.nprob];
     if (tasks <= 0) continue;
-    k_gram_slab<MODE, L, OCC><<<(unsigned)((tasks + kSlabWarps - 1) / kSlabWarps), 32 * kSlabWarps, smem, s>>>(
-        S.descs, S.dT + S.task_pos + (size_t)sl * (S.nprob + 1), S.nprob, sl);
+    (void)launch_chained(k_gram_slab<MODE, L, OCC>, (unsigned)((tasks + kSlabWarps - 1) / kSlabWarps), 32 * kSlabWarps,
+                         smem, s, S.descs, S.dT + S.task_pos + (size_t)sl * (S.nprob + 1), S.nprob, sl);
     ++g_kernel_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

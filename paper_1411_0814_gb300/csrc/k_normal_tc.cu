@@ -168,6 +168,7 @@ __host__ __device__ inline int tc_tmem_cols(int npad) {
 // bytes; then V in FP32 (n_pad x RB).  Kw column q < P: v_a v_b (pair q), q = P: 1.
 __global__ void __launch_bounds__(256) k_build_B_tc(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                    int nprob) {
+  pdl_enter();
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= off[nprob]) return;
   const int p = find_problem(off, nprob, g);
@@ -342,6 +343,7 @@ __global__ void __launch_bounds__(kThreads) k_normal_tc(const ProbDesc* __restri
                                                        const int64_t* __restrict__ off, int nprob,
                                                        unsigned long long* __restrict__ fail_list,
                                                        unsigned long long* __restrict__ fail_count, int nstage) {
+  pdl_enter();
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   __shared__ __align__(8) unsigned long long bars[kMaxStages];
   __shared__ uint32_t tmem_slot;
@@ -503,6 +505,7 @@ __global__ void __launch_bounds__(kTmaThreads) k_normal_tma(const ProbDesc* __re
                                                            const int64_t* __restrict__ off, int nprob,
                                                            unsigned long long* __restrict__ fail_list,
                                                            unsigned long long* __restrict__ fail_count, int nstage) {
+  pdl_enter();
   extern __shared__ __align__(1024) unsigned char tma_smem_raw[];
   __shared__ __align__(8) unsigned long long full[kMaxStages], empty[kMaxStages];
   __shared__ uint32_t tmem_slot;
@@ -669,6 +672,7 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_residual_tma(const ProbDesc*
                                                              const int64_t* __restrict__ off,
                                                              const int64_t* __restrict__ resv_off, int nprob,
                                                              double* __restrict__ partial, int refine) {
+  pdl_enter();
   extern __shared__ __align__(1024) unsigned char res_smem_raw[];
   __shared__ __align__(8) unsigned long long full[kResStages], empty[kResStages];
   __shared__ double red[kRows / 32];
@@ -789,8 +793,8 @@ cudaError_t launch_residual_tma(const SolvePlan& S, double* partial, int refine,
       cudaGetLastError();                                                                                         \
       return e;                                                                                                   \
     }                                                                                                             \
-    k_residual_tma<RB><<<(unsigned)S.tc_tiles, kTmaThreads, smem, s>>>(S.descs, S.tc_off, S.resv_off, S.nprob,   \
-                                                                       partial, refine);                          \
+    (void)launch_chained(k_residual_tma<RB>, (unsigned)S.tc_tiles, kTmaThreads, smem, s, S.descs, S.tc_off,        \
+                         S.resv_off, S.nprob, partial, refine);                                               \
   } while (0)
   if (S.tc_rb <= 8)
     RSM_RTMA(8);
@@ -813,7 +817,7 @@ cudaError_t launch_normal_tc(const SolvePlan& S, int rb_max, int npad_max, cudaS
   const int np = S.nprob;
   cudaError_t e;
   if (S.b_total > 0) {
-    k_build_B_tc<<<(unsigned)((S.b_total + 255) / 256), 256, 0, s>>>(D, S.b_off, np);
+    (void)launch_chained(k_build_B_tc, (unsigned)((S.b_total + 255) / 256), 256, 0, s, D, S.b_off, np);
     ++g_kernel_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -831,8 +835,8 @@ cudaError_t launch_normal_tc(const SolvePlan& S, int rb_max, int npad_max, cudaS
       cudaGetLastError();                                                                                       \
       return e;                                                                                                 \
     }                                                                                                           \
-    k_normal_tma<RB><<<(unsigned)S.tc_tiles, kTmaThreads, smem, s>>>(D, S.tc_off, np, S.fail_list, S.fail_count, \
-                                                                     stages);                                   \
+    (void)launch_chained(k_normal_tma<RB>, (unsigned)S.tc_tiles, kTmaThreads, smem, s, D, S.tc_off, np,         \
+                         S.fail_list, S.fail_count, stages);                                                  \
   } while (0)
     if (rb_max <= 8)
       RSM_TMA(8);
@@ -854,8 +858,8 @@ cudaError_t launch_normal_tc(const SolvePlan& S, int rb_max, int npad_max, cudaS
       cudaGetLastError();                                                                                      \
       return e;                                                                                                \
     }                                                                                                          \
-    k_normal_tc<RB><<<(unsigned)S.tc_tiles, kThreads, smem, s>>>(D, S.tc_off, np, S.fail_list, S.fail_count,   \
-                                                                 stages);                                      \
+    (void)launch_chained(k_normal_tc<RB>, (unsigned)S.tc_tiles, kThreads, smem, s, D, S.tc_off, np, S.fail_list, \
+                         S.fail_count, stages);                                                                \
   } while (0)
   if (rb_max <= 8)
     RSM_TC(8);

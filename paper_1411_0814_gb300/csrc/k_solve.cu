@@ -35,6 +35,7 @@ __device__ __forceinline__ void pair_of(int q, int r, int& a, int& b) {
 template <typename TK>
 __global__ void __launch_bounds__(256) k_build_K(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                 int nprob) {
+  pdl_enter();
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= off[nprob]) return;
   const int p = find_problem(off, nprob, g);
@@ -77,6 +78,7 @@ constexpr int kJT = 16;  // inner chunk
 template <int MODE>
 __global__ void __launch_bounds__(256) k_normal(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                int nprob) {
+  pdl_enter();
   using T = typename std::conditional<MODE == 0, double, float>::type;
   __shared__ T ys[kJT][kNT], ws[kJT][kNT], ks[kJT][kQT];
   const int p = find_problem(off, nprob, blockIdx.x);
@@ -164,6 +166,7 @@ template <int RM>
 __global__ void __launch_bounds__(128) k_row_solve(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                   int nprob, unsigned long long* __restrict__ fail_list,
                                                   unsigned long long* __restrict__ fail_count) {
+  pdl_enter();
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= off[nprob]) return;
   const int p = find_problem(off, nprob, g);
@@ -248,6 +251,7 @@ constexpr int kPinvWarps = 2;
 __global__ void __launch_bounds__(32 * kPinvWarps) k_row_pinv(const ProbDesc* __restrict__ descs,
                                                              const unsigned long long* __restrict__ fail_list,
                                                              const unsigned long long* __restrict__ fail_count) {
+  pdl_enter();
   __shared__ double S[kPinvWarps][kMaxR][kMaxR + 1], Q[kPinvWarps][kMaxR][kMaxR + 1];
   __shared__ JacobiScratch js[kPinvWarps];
   const double tol_scale = 4.0 * DBL_EPSILON;
@@ -300,6 +304,7 @@ constexpr int kResCols = 64;
 template <typename T, int RM>
 __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ off,
                                                  int nprob, double* __restrict__ partial, int refine) {
+  pdl_enter();
   constexpr bool kRefine = sizeof(T) == 4;
   __shared__ __align__(16) T vs[kResCols][RM];  // zero past r, so the products need no guard
   __shared__ float cred[kRefine ? kResRows : 1][RM + 1];
@@ -407,6 +412,7 @@ template <int RM>
 __global__ void __launch_bounds__(256, 3) k_residual2(const ProbDesc* __restrict__ descs,
                                                      const int64_t* __restrict__ off, int nprob,
                                                      double* __restrict__ partial, int refine) {
+  pdl_enter();
   __shared__ __align__(16) float vs[kResVStage][RM];
   __shared__ float cred[kResVRows][RM + 1];
   __shared__ double red[8];
@@ -511,6 +517,7 @@ __global__ void __launch_bounds__(256, 3) k_residual2(const ProbDesc* __restrict
 __global__ void __launch_bounds__(256) k_residual_final(const ProbDesc* __restrict__ descs,
                                                        const int64_t* __restrict__ off, const int64_t* __restrict__ off4,
                                                        int64_t base4, int nprob, const double* __restrict__ partial) {
+  pdl_enter();
   __shared__ double red[256];
   const int p = blockIdx.x;
   if (p >= nprob) return;
@@ -537,9 +544,9 @@ cudaError_t launch_solve_u(const SolvePlan& S, int mode, cudaStream_t s) {
   cudaError_t e;
   if (S.k_total > 0) {
     if (mode == 0)
-      k_build_K<double><<<(unsigned)((S.k_total + 255) / 256), 256, 0, s>>>(D, S.k_off, np);
+      (void)launch_chained(k_build_K<double>, (unsigned)((S.k_total + 255) / 256), 256, 0, s, D, S.k_off, np);
     else
-      k_build_K<float><<<(unsigned)((S.k_total + 255) / 256), 256, 0, s>>>(D, S.k_off, np);
+      (void)launch_chained(k_build_K<float>, (unsigned)((S.k_total + 255) / 256), 256, 0, s, D, S.k_off, np);
     ++g_kernel_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -548,9 +555,9 @@ cudaError_t launch_solve_u(const SolvePlan& S, int mode, cudaStream_t s) {
   }
   if (S.tile_off_host_total > 0) {
     if (mode == 0) {
-      k_normal<0><<<(unsigned)S.tile_off_host_total, 256, 0, s>>>(D, S.tile_off, np);
+      (void)launch_chained(k_normal<0>, (unsigned)S.tile_off_host_total, 256, 0, s, D, S.tile_off, np);
     } else {
-      k_normal<2><<<(unsigned)S.tile_off_host_total, 256, 0, s>>>(D, S.tile_off, np);
+      (void)launch_chained(k_normal<2>, (unsigned)S.tile_off_host_total, 256, 0, s, D, S.tile_off, np);
     }
     ++g_kernel_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -558,19 +565,19 @@ cudaError_t launch_solve_u(const SolvePlan& S, int mode, cudaStream_t s) {
   if (S.row_total > 0) {
     const unsigned blocks = (unsigned)((S.row_total + 127) / 128);
     if (S.rmax <= 4) {
-      k_row_solve<4><<<blocks, 128, 0, s>>>(D, S.row_off, np, S.fail_list, S.fail_count);
+      (void)launch_chained(k_row_solve<4>, blocks, 128, 0, s, D, S.row_off, np, S.fail_list, S.fail_count);
     } else if (S.rmax <= 8) {
-      k_row_solve<8><<<blocks, 128, 0, s>>>(D, S.row_off, np, S.fail_list, S.fail_count);
+      (void)launch_chained(k_row_solve<8>, blocks, 128, 0, s, D, S.row_off, np, S.fail_list, S.fail_count);
     } else if (S.rmax <= 16) {
-      k_row_solve<16><<<blocks, 128, 0, s>>>(D, S.row_off, np, S.fail_list, S.fail_count);
+      (void)launch_chained(k_row_solve<16>, blocks, 128, 0, s, D, S.row_off, np, S.fail_list, S.fail_count);
     } else {
-      k_row_solve<32><<<blocks, 128, 0, s>>>(D, S.row_off, np, S.fail_list, S.fail_count);
+      (void)launch_chained(k_row_solve<32>, blocks, 128, 0, s, D, S.row_off, np, S.fail_list, S.fail_count);
     }
     ++g_kernel_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (S.any_solve) {  // rows that any of the solvers handed to the minimum-norm path
-    k_row_pinv<<<152, 32 * kPinvWarps, 0, s>>>(D, S.fail_list, S.fail_count);
+    (void)launch_chained(k_row_pinv, 152, 32 * kPinvWarps, 0, s, D, S.fail_list, S.fail_count);
     ++g_kernel_launches;
   }
   return cudaGetLastError();
@@ -581,7 +588,8 @@ cudaError_t launch_residual(const SolvePlan& S, int mode, double* partial, cudaS
   const int np = S.nprob;
   const int rf = refine ? 1 : 0;
   if (S.res_blocks > 0) {
-#define RSM_RES(T, RM) k_residual<T, RM><<<(unsigned)S.res_blocks, 256, 0, s>>>(D, S.res_off, np, partial, rf)
+#define RSM_RES(T, RM) \
+  (void)launch_chained(k_residual<T, RM>, (unsigned)S.res_blocks, 256, 0, s, D, S.res_off, np, partial, rf)
     if (mode == 0) {
       if (S.rmax <= 8) RSM_RES(double, 8); else if (S.rmax <= 16) RSM_RES(double, 16); else RSM_RES(double, 32);
     } else {
@@ -595,13 +603,14 @@ cudaError_t launch_residual(const SolvePlan& S, int mode, double* partial, cudaS
       cudaError_t et = launch_residual_tma(S, partial + S.res_blocks, rf, s);
       if (et != cudaSuccess) return et;
     } else {
-      k_residual2<8><<<(unsigned)S.resv_blocks, 256, 0, s>>>(D, S.resv_off, np, partial + S.res_blocks, rf);
+      (void)launch_chained(k_residual2<8>, (unsigned)S.resv_blocks, 256, 0, s, D, S.resv_off, np, partial + S.res_blocks,
+                           rf);
       ++g_kernel_launches;
     }
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_residual_final<<<np, 256, 0, s>>>(D, S.res_off, S.resv_off, S.res_blocks, np, partial);
+  (void)launch_chained(k_residual_final, np, 256, 0, s, D, S.res_off, S.resv_off, S.res_blocks, np, partial);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
