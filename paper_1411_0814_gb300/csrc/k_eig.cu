@@ -435,52 +435,61 @@ __device__ bool chain_step(const ProbDesc& d, int k, Tile<T>* tl, unsigned* sync
       Dv[tid][c] = c == tid ? (T)1 : (T)0;
     }
     rs[tid] = fast_rsqrt(dl);
-  } else if ((tid < 128 || (tid >= 160 && tid < 192)) && b1 && k >= 1) {
-    // warps 1, 2, 3 and 5, 8 rows per thread (warp 4 would share a scheduler
-    // with warp 0, whose factorisation is the critical path)
-    const int wb = tid < 128 ? tid / 32 - 1 : 3, cx = tid % BS, ry0 = wb;
-    const int t2 = wb * 32 + cx;
-    T acc[8];
+  } else if ((tid < 128 || tid >= 160) && b1 && k >= 1) {
+    // warps 1, 2, 3, 5, 6 and 7 (warp 4 would share a scheduler with warp 0,
+    // whose factorisation is the critical path): thread = column cx, rows wb +
+    // 6 s.  Six warps rather than four: these three products took longer than
+    // warp 0's factorisation (3.8 against 2.0 us per step at four warps).
+    constexpr int NW = 6, NR = (BS + NW - 1) / NW;
+    const int wb = tid < 128 ? tid / 32 - 1 : tid / 32 - 2, cx = tid % BS;
+    auto in = [&](int s) { return s < NR - 1 || wb + NW * s < BS; };  // row wb + 6 s exists
+    T acc[NR];
     if (k >= 2) {  // A_{k+1,k-1} -= L_{k+1,k-2} L_{k-1,k-2}^T
 #pragma unroll
-      for (int s = 0; s < 8; ++s) acc[s] = (T)0;
+      for (int s = 0; s < NR; ++s) acc[s] = (T)0;
 #pragma unroll 8
       for (int t = 0; t < BS; ++t) {
         const T lv = Lq[cx][t];
 #pragma unroll
-        for (int s = 0; s < 8; ++s) acc[s] = fma(Lp[ry0 + 4 * s][t], lv, acc[s]);
+        for (int s = 0; s < NR; ++s)
+          if (in(s)) acc[s] = fma(Lp[wb + NW * s][t], lv, acc[s]);
       }
 #pragma unroll
-      for (int s = 0; s < 8; ++s) Wp[ry0 + 4 * s][cx] -= acc[s];
-      bar_and(1, 128, true);
+      for (int s = 0; s < NR; ++s)
+        if (in(s)) Wp[wb + NW * s][cx] -= acc[s];
+      bar_and(1, 32 * NW, true);
     }
     // L_{k+1,k-1} = A_{k+1,k-1} inv(L_{k-1,k-1})^T, into F1 and (for the next product) Lp
 #pragma unroll
-    for (int s = 0; s < 8; ++s) acc[s] = (T)0;
+    for (int s = 0; s < NR; ++s) acc[s] = (T)0;
 #pragma unroll 8
     for (int t = 0; t < BS; ++t) {
       const T dv = Dp[cx][t];
 #pragma unroll
-      for (int s = 0; s < 8; ++s) acc[s] = fma(Wp[ry0 + 4 * s][t], dv, acc[s]);
+      for (int s = 0; s < NR; ++s)
+        if (in(s)) acc[s] = fma(Wp[wb + NW * s][t], dv, acc[s]);
     }
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-      F[((k + 1) * BS + ry0 + 4 * s) * np + (k - 1) * BS + cx] = acc[s];
-      Lp[ry0 + 4 * s][cx] = acc[s];
-    }
-    bar_and(1, 128, true);
-    if (t2 == 0) st_release(&SA[(k + 1) * nb + k - 1], (unsigned)k);
+    for (int s = 0; s < NR; ++s)
+      if (in(s)) {
+        F[((k + 1) * BS + wb + NW * s) * np + (k - 1) * BS + cx] = acc[s];
+        Lp[wb + NW * s][cx] = acc[s];
+      }
+    bar_and(1, 32 * NW, true);
+    if (wb == 0 && cx == 0) st_release(&SA[(k + 1) * nb + k - 1], (unsigned)k);
     // A_{k+1,k} -= L_{k+1,k-1} L_{k,k-1}^T
 #pragma unroll
-    for (int s = 0; s < 8; ++s) acc[s] = (T)0;
+    for (int s = 0; s < NR; ++s) acc[s] = (T)0;
 #pragma unroll 8
     for (int t = 0; t < BS; ++t) {
       const T lv = Ls[cx][t];
 #pragma unroll
-      for (int s = 0; s < 8; ++s) acc[s] = fma(Lp[ry0 + 4 * s][t], lv, acc[s]);
+      for (int s = 0; s < NR; ++s)
+        if (in(s)) acc[s] = fma(Lp[wb + NW * s][t], lv, acc[s]);
     }
 #pragma unroll
-    for (int s = 0; s < 8; ++s) W1[ry0 + 4 * s][cx] -= acc[s];
+    for (int s = 0; s < NR; ++s)
+      if (in(s)) W1[wb + NW * s][cx] -= acc[s];
   }
   __syncthreads();
   T rsr[4];  // D^-1/2 of the rows ty + 8 s, and of column tx

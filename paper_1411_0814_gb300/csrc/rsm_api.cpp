@@ -72,12 +72,17 @@ struct DeviceGuard {
 constexpr double kShiftRel32 = 3e-4;   // tau / (trace(M) / n) with the FP32 factor
 constexpr double kShiftRel64 = 1e-11;  // tau / (trace(M) / n) with the FP64 factor
 #ifndef RSM_EIG_ITERS32
-#define RSM_EIG_ITERS32 5
+#define RSM_EIG_ITERS32 3
 #endif
 #ifndef RSM_EIG_ITERS64
 #define RSM_EIG_ITERS64 6
 #endif
-constexpr int kEigIters32 = RSM_EIG_ITERS32;  // most preconditioned steps with the FP32 factor (stops when converged)
+// most preconditioned steps with the FP32 factor (stops when converged; the
+// paper-scale problem and the batched problems stop after two with the
+// predicted-step rule, and every step left costs its launches even when they
+// return at once: ~8 us alone, ~0.3 ms in a batch of 64 problems); a problem
+// not converged by then takes the FP64 factor
+constexpr int kEigIters32 = RSM_EIG_ITERS32;
 constexpr int kEigIters64 = RSM_EIG_ITERS64;  // most steps with the FP64 factor (near-exact shift-invert)
 constexpr int64_t kSmallN = 256;       // at or below this n the FP64 factor is cheap: use it directly
 constexpr double kEigErrTol = 1e-11;   // a-posteriori bound that accepts the FP32-factor result
