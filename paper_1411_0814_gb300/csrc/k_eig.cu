@@ -405,6 +405,8 @@ __device__ bool chain_load(const ProbDesc& d, int k, Tile<T>* tl, unsigned* sync
 // finish L_{k+1,k-1} = (A_{k+1,k-1} - L_{k+1,k-2} L_{k-1,k-2}^T) inv(L_{k-1,k-1})^T,
 // release it, and apply the last trailing update to A_{k+1,k}; then all
 // threads invert the factor and form L_{k+1,k}.
+constexpr int kPanelWarps = 6, kPanelRows = (BS + kPanelWarps - 1) / kPanelWarps;  // the chain's panel warps, rows per thread
+constexpr int kPanelBar = 32 * (kPanelWarps + 1);  // named barrier 1: the panel warps and warp 4
 template <typename T>
 __device__ bool chain_step(const ProbDesc& d, int k, Tile<T>* tl, unsigned* sync, const ProbDesc* __restrict__ descs,
                            int nprob) {
@@ -440,56 +442,61 @@ __device__ bool chain_step(const ProbDesc& d, int k, Tile<T>* tl, unsigned* sync
     // whose factorisation is the critical path): thread = column cx, rows wb +
     // 6 s.  Six warps rather than four: these three products took longer than
     // warp 0's factorisation (3.8 against 2.0 us per step at four warps).
-    constexpr int NW = 6, NR = (BS + NW - 1) / NW;
+    // Their barriers include warp 4, which publishes L_{k+1,k-1}.
     const int wb = tid < 128 ? tid / 32 - 1 : tid / 32 - 2, cx = tid % BS;
-    auto in = [&](int s) { return s < NR - 1 || wb + NW * s < BS; };  // row wb + 6 s exists
-    T acc[NR];
+    auto in = [&](int s) { return s < kPanelRows - 1 || wb + kPanelWarps * s < BS; };  // row wb + 6 s exists
+    T acc[kPanelRows];
     if (k >= 2) {  // A_{k+1,k-1} -= L_{k+1,k-2} L_{k-1,k-2}^T
 #pragma unroll
-      for (int s = 0; s < NR; ++s) acc[s] = (T)0;
+      for (int s = 0; s < kPanelRows; ++s) acc[s] = (T)0;
 #pragma unroll 8
       for (int t = 0; t < BS; ++t) {
         const T lv = Lq[cx][t];
 #pragma unroll
-        for (int s = 0; s < NR; ++s)
-          if (in(s)) acc[s] = fma(Lp[wb + NW * s][t], lv, acc[s]);
+        for (int s = 0; s < kPanelRows; ++s)
+          if (in(s)) acc[s] = fma(Lp[wb + kPanelWarps * s][t], lv, acc[s]);
       }
 #pragma unroll
-      for (int s = 0; s < NR; ++s)
-        if (in(s)) Wp[wb + NW * s][cx] -= acc[s];
-      bar_and(1, 32 * NW, true);
+      for (int s = 0; s < kPanelRows; ++s)
+        if (in(s)) Wp[wb + kPanelWarps * s][cx] -= acc[s];
+      bar_and(1, kPanelBar, true);
     }
     // L_{k+1,k-1} = A_{k+1,k-1} inv(L_{k-1,k-1})^T, into F1 and (for the next product) Lp
 #pragma unroll
-    for (int s = 0; s < NR; ++s) acc[s] = (T)0;
+    for (int s = 0; s < kPanelRows; ++s) acc[s] = (T)0;
 #pragma unroll 8
     for (int t = 0; t < BS; ++t) {
       const T dv = Dp[cx][t];
 #pragma unroll
-      for (int s = 0; s < NR; ++s)
-        if (in(s)) acc[s] = fma(Wp[wb + NW * s][t], dv, acc[s]);
+      for (int s = 0; s < kPanelRows; ++s)
+        if (in(s)) acc[s] = fma(Wp[wb + kPanelWarps * s][t], dv, acc[s]);
     }
 #pragma unroll
-    for (int s = 0; s < NR; ++s)
+    for (int s = 0; s < kPanelRows; ++s)
       if (in(s)) {
-        F[((k + 1) * BS + wb + NW * s) * np + (k - 1) * BS + cx] = acc[s];
-        Lp[wb + NW * s][cx] = acc[s];
+        F[((k + 1) * BS + wb + kPanelWarps * s) * np + (k - 1) * BS + cx] = acc[s];
+        Lp[wb + kPanelWarps * s][cx] = acc[s];
       }
-    bar_and(1, 32 * NW, true);
-    if (wb == 0 && cx == 0) st_release(&SA[(k + 1) * nb + k - 1], (unsigned)k);
+    bar_and(1, kPanelBar, true);
     // A_{k+1,k} -= L_{k+1,k-1} L_{k,k-1}^T
 #pragma unroll
-    for (int s = 0; s < NR; ++s) acc[s] = (T)0;
+    for (int s = 0; s < kPanelRows; ++s) acc[s] = (T)0;
 #pragma unroll 8
     for (int t = 0; t < BS; ++t) {
       const T lv = Ls[cx][t];
 #pragma unroll
-      for (int s = 0; s < NR; ++s)
-        if (in(s)) acc[s] = fma(Lp[wb + NW * s][t], lv, acc[s]);
+      for (int s = 0; s < kPanelRows; ++s)
+        if (in(s)) acc[s] = fma(Lp[wb + kPanelWarps * s][t], lv, acc[s]);
     }
 #pragma unroll
-    for (int s = 0; s < NR; ++s)
-      if (in(s)) W1[wb + NW * s][cx] -= acc[s];
+    for (int s = 0; s < kPanelRows; ++s)
+      if (in(s)) W1[wb + kPanelWarps * s][cx] -= acc[s];
+  } else if (b1 && k >= 1) {
+    // warp 4: once L_{k+1,k-1} is in F1, its release (a GPU-scope fence) is
+    // issued here, so that it does not hold up a warp with a product left to do
+    if (k >= 2) bar_and(1, kPanelBar, true);
+    bar_and(1, kPanelBar, true);
+    if (tid == 128) st_release(&SA[(k + 1) * nb + k - 1], (unsigned)k);
   }
   __syncthreads();
   T rsr[4];  // D^-1/2 of the rows ty + 8 s, and of column tx
@@ -1172,7 +1179,7 @@ __global__ void __launch_bounds__(kRRThreads) k_rr(const ProbDesc* __restrict__ 
   DFRow* B = Q2 + kMaxL;
   DFRow* W1 = B + kMaxL;
   DFRow* W2 = W1 + kMaxL;
-  __shared__ int coupled;
+  __shared__ int coupled, rotated;
   const int p = blockIdx.x;
   if (p >= nprob) return;
   const ProbDesc& d = descs[p];
@@ -1231,12 +1238,18 @@ __global__ void __launch_bounds__(kRRThreads) k_rr(const ProbDesc* __restrict__ 
       const int rj = __shfl_sync(0xffffffffu, rank, j);
       if (lane < kx && j < kx) Q2[lane][rj] = DF{v[j], 0.f};
     }
-    if (lane == 0) coupled = 0;
+    if (lane == 0) {
+      coupled = 0;
+      rotated = o > tol;
+    }
   }
   __syncthreads();
-  // FP32 rotations: orthogonal in pairs, then B = Q2^T H1 Q2
-  df_lowdin(Q2, W1, W2, kx, kRRThreads);
-  df_lowdin(Q2, W1, W2, kx, kRRThreads);
+  // FP32 rotations: orthogonal in pairs, then B = Q2^T H1 Q2.  Without a Jacobi
+  // rotation Q2 is a permutation, for which the Lowdin step is exactly the identity.
+  if (rotated) {
+    df_lowdin(Q2, W1, W2, kx, kRRThreads);
+    df_lowdin(Q2, W1, W2, kx, kRRThreads);
+  }
   df_congruence(B, Q2, H1, W1, kx, kRRThreads);
   // first-order decoupling of the wanted block: G = I + A (into H1), then one Lowdin step
   for (int e = tid; e < kx * kx; e += kRRThreads) {
