@@ -37,7 +37,11 @@
 namespace rsm {
 
 constexpr int BS = 32;  // block size of the FP32 factorisation
-constexpr int kConvFlag = 40;   // stats[40] != 0: the block iteration of this problem has converged
+// stats[40]: 0 while the block iteration of this problem runs; 1 once it has
+// converged (every later kernel of the iteration returns at once); 2 when it
+// stops after one more correction X <- X - A^-1 R (the preconditioner kernels of
+// that step still run; the next convergence check sets 1)
+constexpr int kConvFlag = 40;
 constexpr double kConvTol = 1e-12;  // converged when max ||R_j|| <= kConvTol * (theta_{r+1} - theta_r)
 constexpr double kStallTol = 1e-10;  // ... or when it stops falling (rounding floor) below kStallTol * gap
 constexpr int kPrevRes = 41;         // stats[41]: max ||R_j|| at the previous check
@@ -1331,7 +1335,10 @@ __device__ __forceinline__ void conv_check(const ProbDesc& d) {
     // (at the rounding floor of M X - X Theta) while already below kStallTol * gap
     const bool predicted = prev > 0.0 && mx < prev && mx * (mx / prev) <= kConvTol * gap;
     const bool stalled = prev > 0.0 && mx > 0.5 * prev && mx <= kStallTol * gap;
-    if (gap > 0.0 && (mx <= kConvTol * gap || predicted || stalled)) d.stats[kConvFlag] = 1.0;
+    if (gap > 0.0 && (mx <= kConvTol * gap || stalled))
+      d.stats[kConvFlag] = 1.0;
+    else if (gap > 0.0 && predicted)
+      d.stats[kConvFlag] = 2.0;
     d.stats[kPrevRes] = mx;
     d.stats[kIterCount] += 1.0;
   }
@@ -1346,7 +1353,12 @@ __global__ void __launch_bounds__(256) k_rotate(const ProbDesc* __restrict__ des
   __shared__ double rsq[FULL ? kRotRows : 1][kMaxL];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
-  if (d.stats[kConvFlag] != 0.0) return;  // converged: the rest of the iteration is skipped
+  const double flag = d.stats[kConvFlag];
+  if (flag != 0.0) {  // converged: the rest of the iteration is skipped
+    // the step after a predicted stop has taken its correction: skip from now on
+    if (CHECK && flag == 2.0 && blockIdx.x == off[p] && threadIdx.x == 0) d.stats[kConvFlag] = 1.0;
+    return;
+  }
   const int kx = d.kx;
   const SmallDiv dkx((uint32_t)kx);  // quotient and remainder by kx without an integer division
   const int i0 = (int)(blockIdx.x - off[p]) * kRotRows;
@@ -1429,7 +1441,7 @@ __global__ void __launch_bounds__(256) k_precond(const ProbDesc* __restrict__ de
   __shared__ T rs[64][kMaxL + 1];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
-  if (d.stats[kConvFlag] != 0.0) return;  // converged: the rest of the iteration is skipped
+  if (d.stats[kConvFlag] == 1.0) return;  // converged (a predicted stop still takes this step)
   const int n = (int)d.n, np = npad_of(d);
   const int kx = d.kx;
   const SmallDiv dkx((uint32_t)kx);  // quotient and remainder by kx without an integer division
@@ -1478,7 +1490,7 @@ __global__ void __launch_bounds__(256) k_precond_apply(const ProbDesc* __restric
   if (g >= off[nprob]) return;
   const int p = find_problem(off, nprob, g);
   const ProbDesc& d = descs[p];
-  if (d.stats[kConvFlag] != 0.0) return;
+  if (d.stats[kConvFlag] == 1.0) return;  // converged (a predicted stop still takes this step)
   const int e = (int)(g - off[p]);
   const int nk = (int)d.n * d.kx;
   double v[kPSplit];
@@ -1637,10 +1649,11 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
       if ((e = orthonormalise()) != cudaSuccess) return e;
   }
   // Phase B: preconditioned block iteration X <- X - A^-1 (M X - X Theta) with
-  // FP32-pair products with M and an FP64 Rayleigh-Ritz step each time; every step
+  // FP32-pair products with M and a Rayleigh-Ritz step each time; every step
   // ends with a convergence check, and a converged problem skips everything
-  // after it.  With the FP64 factor a step can again collapse the block, so X is
-  // re-orthonormalised before each product.  The last step never preconditions.
+  // after it (a predicted stop after the correction of that step).  With the
+  // FP64 factor a step can again collapse the block, so X is re-orthonormalised
+  // before each product.
   for (int it = 0; it <= iters; ++it) {
     if (sizeof(T) == 8 && it > 0)
       if ((e = orthonormalise()) != cudaSuccess) return e;
@@ -1653,19 +1666,21 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
     RSM_LAUNCH_SMEM(xtx_h, total(P.chunk), kXtxThreads, xtx_smem, D, dev(P.chunk), np, P.part, dev(P.part_off));
     RSM_LAUNCH_SMEM(rr, np, kRRThreads, kRRSmem, D, np, part, dev(P.part_off));
     RSM_LAUNCH(rot_check, total(P.rot), 256, D, dev(P.rot), np);
-    if (it < iters) {
-      RSM_LAUNCH(precond_r, total(P.row_tile), 256, D, dev(P.row_tile), np);
-      RSM_LAUNCH(k_precond_apply<0>, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
-    }
+    RSM_LAUNCH(precond_r, total(P.row_tile), 256, D, dev(P.row_tile), np);
+    RSM_LAUNCH(k_precond_apply<0>, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
   }
   // FP64 refinement.  The iteration above carries M X in FP32 pairs (about
-  // 2^-44 relative), which bounds its residual at ~2^-44 ||M||.  Two more passes
-  // with M X in IEEE FP64: the first gives the FP64 residual R of the current
-  // Ritz vectors and the correction X <- X - A^-1 R; the second a Rayleigh-Ritz
-  // step on the corrected block with FP64 products, whose residual (also FP64)
-  // is the one reported and tested on the host.
+  // 2^-44 relative), which bounds its residual at ~2^-44 ||M||.  Then passes
+  // with M X in IEEE FP64, ending in a Rayleigh-Ritz step whose residual (also
+  // FP64) is the one reported and tested on the host.  With the FP32 factor one
+  // pass: the block iteration's last correction (a predicted stop) already
+  // brings the block to the FP32-pair floor, which the FP64 residual then
+  // certifies.  With the FP64 factor two: the first gives the FP64 residual R
+  // of the Ritz vectors and the correction X <- X - A^-1 R, the second the
+  // Rayleigh-Ritz step on the re-orthonormalised, corrected block.
   RSM_LAUNCH(k_refine_begin, (np + 127) / 128, 128, D, np);
-  for (int pass = 0; pass < 2; ++pass) {
+  const int passes = sizeof(T) == 8 ? 2 : 1;
+  for (int pass = 0; pass < passes; ++pass) {
     if (sizeof(T) == 8 && pass > 0)
       if ((e = orthonormalise()) != cudaSuccess) return e;
     if (P.kx_max <= 12)
@@ -1677,7 +1692,7 @@ static cudaError_t launch_eig_t(const EigPlan& P, double shift_rel, int iters, c
     RSM_LAUNCH_SMEM(xtx_h, total(P.chunk), kXtxThreads, xtx_smem, D, dev(P.chunk), np, P.part, dev(P.part_off));
     RSM_LAUNCH_SMEM(rr, np, kRRThreads, kRRSmem, D, np, part, dev(P.part_off));
     RSM_LAUNCH(rot_full, total(P.rot), 256, D, dev(P.rot), np);
-    if (pass == 0) {
+    if (pass + 1 < passes) {
       RSM_LAUNCH(precond_r, total(P.row_tile), 256, D, dev(P.row_tile), np);
       RSM_LAUNCH(k_precond_apply<0>, (total(P.nk) + 255) / 256, 256, D, dev(P.nk), np);
     }
