@@ -8,7 +8,7 @@ eigensolve of M, the per-row solves for U and the error e, all in librsm.so.
 
 Headline form: Y in FP32, FP32 Gram and FP32 accumulation of the normal
 equations (tensor cores); FP64 minor vectors, M, eigensolve (FP32-pair
-iteration ended by FP64 refinement passes) and r x r solves.  Its V-hat is
+iteration ended by an FP64 refinement pass) and r x r solves.  Its V-hat is
 compared with the FP64 oracle's V-hat for this workload (stored by
 tests/golden/make_oracle_goldens.py, which calls only the oracle): the
 subspace angle must be <= 1e-6.  The plain FP64 form is timed beside it and

@@ -63,8 +63,9 @@ typedef enum rsm_dtype { RSM_F64 = 0, RSM_F32 = 1 } rsm_dtype;
  *                   head + tail of v_a v_b, FP32 accumulation, ~2^-22).
  * In every mode: the l x l eigenproblems (minor vectors) are refined in FP64;
  * M is summed in 64-bit fixed point and stored in FP64; the eigensolve of M
- * iterates with M X in FP32 pairs (~2^-44) and ends with two refinement
- * passes whose products M X, Rayleigh-Ritz step and residual are IEEE FP64;
+ * iterates with M X in FP32 pairs (~2^-44) and ends with a refinement pass
+ * (two with the FP64 factor) whose products M X, Rayleigh-Ritz step and
+ * residual are IEEE FP64;
  * the r x r Cholesky factorisations and triangular solves for U are FP64. */
 typedef enum rsm_prec { RSM_PREC_F64 = 0, RSM_PREC_F32X2 = 1, RSM_PREC_F32 = 2 } rsm_prec;
 
