@@ -679,7 +679,9 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_residual_tma(const ProbDesc*
   unsigned char* smem = res_smem_raw + ((128u - (smem_u32(res_smem_raw) & 127u)) & 127u);
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
-  if (!d.resv) return;  // a tensor-core problem without the vectorised residual (the scalar kernel has it)
+  // a tensor-core problem without the vectorised residual (the scalar kernel has
+  // it), or with r > 8 (the 2-row kernel at RM = 16 has it)
+  if (!d.resv || d.r > 8) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t m = (uint32_t)d.m, n = (uint32_t)d.n;
   const uint32_t tile = (uint32_t)(blockIdx.x - off[p]);

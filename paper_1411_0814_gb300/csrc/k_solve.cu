@@ -408,16 +408,21 @@ __global__ void __launch_bounds__(256) k_residual(const ProbDesc* __restrict__ d
 constexpr int kResVRows = 64;
 constexpr int kResVCols = 8;      // columns in flight per warp and pass
 constexpr int kResVStage = 512;   // columns of V staged per barrier (8 passes of each warp)
+// RM = 16 (8 < r <= 16): the same with two CTAs per SM (its per-lane state is
+// twice as large).  A CTA returns at once for a problem with r outside [rlo,
+// rhi], which the other instantiation (or the TMA-fed pass) takes.
 template <int RM>
-__global__ void __launch_bounds__(256, 3) k_residual2(const ProbDesc* __restrict__ descs,
-                                                     const int64_t* __restrict__ off, int nprob,
-                                                     double* __restrict__ partial, int refine) {
+__global__ void __launch_bounds__(256, RM <= 8 ? 3 : 2) k_residual2(const ProbDesc* __restrict__ descs,
+                                                                  const int64_t* __restrict__ off, int nprob,
+                                                                  double* __restrict__ partial, int refine, int rlo,
+                                                                  int rhi) {
   pdl_enter();
   __shared__ __align__(16) float vs[kResVStage][RM];
   __shared__ float cred[kResVRows][RM + 1];
   __shared__ double red[8];
   const int p = find_problem(off, nprob, blockIdx.x);
   const ProbDesc& d = descs[p];
+  if (d.r < rlo || d.r > rhi) return;
   const int lane = threadIdx.x & 31, wg = threadIdx.x >> 5;
   const uint32_t i0 = (uint32_t)(blockIdx.x - off[p]) * kResVRows;
   const uint32_t ib = i0 + 2u * lane;  // first of this lane's 2 rows
@@ -598,13 +603,18 @@ cudaError_t launch_residual(const SolvePlan& S, int mode, double* partial, cudaS
 #undef RSM_RES
     ++g_kernel_launches;
   }
-  if (S.resv_blocks > 0) {  // problems with r <= 8 only
+  if (S.resv_blocks > 0) {  // r <= 8: the TMA-fed pass or the 2-row kernel; 8 < r <= 16: the 2-row kernel at RM = 16
     if (S.tc_tma) {
       cudaError_t et = launch_residual_tma(S, partial + S.res_blocks, rf, s);
       if (et != cudaSuccess) return et;
     } else {
       (void)launch_chained(k_residual2<8>, (unsigned)S.resv_blocks, 256, 0, s, D, S.resv_off, np, partial + S.res_blocks,
-                           rf);
+                           rf, 1, 8);
+      ++g_kernel_launches;
+    }
+    if (S.resv_rmax > 8) {
+      (void)launch_chained(k_residual2<16>, (unsigned)S.resv_blocks, 256, 0, s, D, S.resv_off, np,
+                           partial + S.res_blocks, rf, 9, 16);
       ++g_kernel_launches;
     }
   }

@@ -54,6 +54,7 @@ struct SolvePlan {
   const int64_t* res_off;    // ceil(m / 32) per problem (scalar residual kernel)
   int64_t resv_blocks;
   const int64_t* resv_off;   // ceil(m / 64) per problem (2-row residual kernel); its partials follow the others
+  int resv_rmax;             // largest r among those problems (<= 8: TMA-fed or 2-row kernel; else also RM = 16)
   int rmax;                  // largest r of the batch
   unsigned long long* fail_list;   // row_total entries: (problem << 32) | row
   unsigned long long* fail_count;  // zero before the launch

@@ -68,12 +68,12 @@ size_t data_sum(const Sizes& s) {
 size_t part_doubles(const rsm_problem& p, const Derived& dv) {
   return (size_t)((p.n + 63) / 64) * 2 * dv.kx * dv.kx;  // chunks of kChunk = 64 rows (k_eig.cu)
 }
-// The vectorised residual kernel (2 rows per lane): FP32 form of FP32 Y whose
-// columns start on 16-byte boundaries, r <= 8 (its refinement keeps 2 rows x r
-// sums per lane in registers).
+// The vectorised residual kernels (2 rows per lane, or the TMA-fed pass for r <=
+// 8): FP32 form of FP32 Y whose columns start on 16-byte boundaries, r <= 16
+// (the refinement keeps 2 rows x r sums per lane in registers).
 bool resv_of(const rsm_problem& p, const Derived& dv) {
   return dv.solve_u && p.solve_prec == RSM_PREC_F32 && p.y_dtype == RSM_F32 && p.ldy % 4 == 0 &&
-         (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0 && p.r <= 8 && p.m % 2 == 0;  // pairs of rows stay in Y
+         (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0 && p.r <= 16 && p.m % 2 == 0;  // pairs of rows stay in Y
 }
 size_t res_blocks_of(const rsm_problem& p, const Derived& dv) {  // partial sums of the residual
   if (!dv.solve_u) return 0;
@@ -304,6 +304,9 @@ void build_batch(const rsm_problem* ps, int count, Batch& b, const Tune* tunes) 
   b.res_blocks = total(b.o_res);
   b.o_resv = prefix([&](int i) { return resv_of(ps[i], b.dv[i]) ? (int64_t)res_blocks_of(ps[i], b.dv[i]) : (int64_t)0; });
   b.resv_blocks = total(b.o_resv);
+  b.resv_rmax = 0;
+  for (int i = 0; i < count; ++i)
+    if (resv_of(ps[i], b.dv[i])) b.resv_rmax = std::max(b.resv_rmax, ps[i].r);
 
   // Row slabs: the slab size of a problem depends on its own n and Y type only,
   // and problems are grouped by l, so a problem's Gram is summed in the same

@@ -60,6 +60,7 @@ struct Batch {
          o_b = 0, o_tc = 0, o_resv = 0, o_phase = 0;
   int64_t pack_blocks = 0, trials_total = 0, ent_total = 0, pad2_total = 0, nk_total = 0, part_total = 0,
           k_total = 0, tile_total = 0, row_total = 0, res_blocks = 0, b_total = 0, tc_total = 0, resv_blocks = 0;
+  int resv_rmax = 0;  // largest r of the problems with the vectorised residual
   int64_t solve_rows = 0;  // rows of all problems that solve for U
   bool any_coverage = false;  // some problem counts its visited entries
   bool l1 = false;            // the L1 forms (all problems of the batch)

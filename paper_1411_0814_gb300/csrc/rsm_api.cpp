@@ -326,6 +326,7 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
     sp.tc_npad_max = b.tc_npad_max;
     sp.tc_tma = b.tc_tma;
     sp.resv_blocks = b.resv_blocks;
+    sp.resv_rmax = b.resv_rmax;
     sp.resv_off = T + b.o_resv;
     sp.any_solve = b.any_solve;
     sp.fail_list = reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(slot.ws.ptr) + b.fail_list_off);
