@@ -161,7 +161,8 @@ typedef struct rsm_result {
   double eig_residual;           /* largest ||M v - lambda v|| over the r returned vectors */
   double e_known_rms;            /* eq. (ep): RMS residual over the known entries (NaN if U is NULL) */
   float stage_ms[12];            /* device time per stage (CUDA events on the launching stream):
-                                    0 setup (plan upload, zeroing), 1 pack_mask, 2 sample_cols,
+                                    0 setup (plan upload, zeroing), 1 pack_mask and sample_cols
+                                    (one launch), 2 empty (0),
                                     3 select+Gram, 4 minor vectors + scatter into M, 5 eigensolve of M,
                                     6 solve U, 7 residual e, 8 total; 9-11 reserved.  A batch reports
                                     the batch's times in every result. */

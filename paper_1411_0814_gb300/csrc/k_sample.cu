@@ -10,11 +10,11 @@ namespace rsm {
 // packed once into bit words: bit (i mod 32) of word i/32 of column c is
 // W[i, c] != 0.  One thread per output word; a CTA covers 256 consecutive words
 // of one column.  Blocks are flattened over the problems of the batch.
-__global__ void __launch_bounds__(256) k_pack_mask(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ blk_off,
-                                                   int nprob) {
-  const int p = find_problem(blk_off, nprob, blockIdx.x);
+__device__ __forceinline__ void pack_mask_block(const ProbDesc* __restrict__ descs,
+                                                const int64_t* __restrict__ blk_off, int nprob, int64_t block) {
+  const int p = find_problem(blk_off, nprob, block);
   const ProbDesc& d = descs[p];
-  const int64_t local = blockIdx.x - blk_off[p];
+  const int64_t local = block - blk_off[p];
   const int64_t chunks = (d.ldb + 255) / 256;
   const int64_t c = local / chunks;
   const int64_t w = (local % chunks) * 256 + threadIdx.x;
@@ -51,6 +51,11 @@ __global__ void __launch_bounds__(256) k_pack_mask(const ProbDesc* __restrict__ 
     for (int k = 0; k < 8; ++k) t += wcnt[k];
     if (t) atomicAdd(&d.counters[1], t);
   }
+}
+
+__global__ void __launch_bounds__(256) k_pack_mask(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ blk_off,
+                                                   int nprob) {
+  pack_mask_block(descs, blk_off, nprob, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ a2 sample_cols
@@ -98,9 +103,9 @@ __device__ __forceinline__ void draw_columns(const ProbDesc& d, int64_t t, int32
 // One thread per trial, flattened over the problems of the batch.  Also counts
 // how many trials drew each column (an upper bound of every entry of M, used to
 // size the fixed-point accumulator).
-__global__ void __launch_bounds__(256) k_sample(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ trial_off,
-                                                int nprob) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void sample_block(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ trial_off,
+                                             int nprob, int64_t block) {
+  const int64_t g = block * blockDim.x + threadIdx.x;
   if (g >= trial_off[nprob]) return;
   const int p = find_problem(trial_off, nprob, g);
   const ProbDesc& d = descs[p];
@@ -117,6 +122,22 @@ __global__ void __launch_bounds__(256) k_sample(const ProbDesc* __restrict__ des
   if ((threadIdx.x & 31) == __ffs(same) - 1) atomicMax(&d.counters[2], (unsigned long long)wmax);
   if (d.debug_cols)
     for (int k = 0; k < d.l; ++k) d.debug_cols[t * d.l + k] = out[k];
+}
+
+__global__ void __launch_bounds__(256) k_sample(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ trial_off,
+                                                int nprob) {
+  sample_block(descs, trial_off, nprob, blockIdx.x);
+}
+
+// Stages a1 and a2 in one launch: they are independent, so the sampler's blocks
+// (first, a short latency-bound tail of Philox draws) run beside the packing's
+// HBM-bound blocks instead of after them.
+__global__ void __launch_bounds__(256) k_front(const ProbDesc* __restrict__ descs, const int64_t* __restrict__ blk_off,
+                                               const int64_t* __restrict__ trial_off, int nprob, int64_t sample_blocks) {
+  if ((int64_t)blockIdx.x < sample_blocks)
+    sample_block(descs, trial_off, nprob, blockIdx.x);
+  else
+    pack_mask_block(descs, blk_off, nprob, (int64_t)blockIdx.x - sample_blocks);
 }
 
 // Stand-alone sampler for the stage entry point: trials t0 .. t0+count-1 of one problem.
@@ -169,6 +190,15 @@ __global__ void __launch_bounds__(256) k_select_rows(const uint32_t* __restrict_
 cudaError_t launch_pack_mask(const ProbDesc* descs, const int64_t* blk_off, int nprob, int64_t nblocks, cudaStream_t s) {
   if (nblocks <= 0) return cudaSuccess;
   k_pack_mask<<<(unsigned)nblocks, 256, 0, s>>>(descs, blk_off, nprob);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_front(const ProbDesc* descs, const int64_t* blk_off, int64_t pack_blocks, const int64_t* trial_off,
+                         int64_t trials, int nprob, cudaStream_t s) {
+  const int64_t sb = (trials + 255) / 256;
+  if (sb + pack_blocks <= 0) return cudaSuccess;
+  k_front<<<(unsigned)(sb + pack_blocks), 256, 0, s>>>(descs, blk_off, trial_off, nprob, sb);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

@@ -101,6 +101,9 @@ cudaError_t launch_count_known(const uint8_t* W, int64_t ldw, int64_t m, int64_t
 cudaError_t launch_coverage(const ProbDesc* descs, const int64_t* trial_off, int nprob, int64_t trials_total,
                             int64_t max_words, cudaStream_t s);
 cudaError_t launch_sample(const ProbDesc* descs, const int64_t* trial_off, int nprob, int64_t total, cudaStream_t s);
+// a1 and a2 in one launch (the sampler's blocks first)
+cudaError_t launch_front(const ProbDesc* descs, const int64_t* blk_off, int64_t pack_blocks, const int64_t* trial_off,
+                         int64_t trials, int nprob, cudaStream_t s);
 cudaError_t launch_sample_range(const ProbDesc& d, int64_t t0, int64_t count, int32_t* cols, cudaStream_t s);
 cudaError_t launch_select_rows(const uint32_t* bits, int64_t ldb, int64_t m, const int32_t* cols, int l, int64_t count,
                                const int64_t* row_off, int32_t* rows, int32_t* row_counts, cudaStream_t s);

@@ -235,9 +235,11 @@ int launch_batch(Batch& b, Slot& slot, bool fp64_factor, double shift_rel, bool 
   const int np = b.nprob;
   cudaError_t e;
   if (do_front) {
-    if ((e = launch_pack_mask(D, T + b.o_pack, np, b.pack_blocks, s)) != cudaSuccess) return cuda_fail(e, "pack_mask");
+    // mask packing and column sampling in one launch: the pack_mask stage time
+    // covers both and the sample_cols stage is empty
+    if ((e = launch_front(D, T + b.o_pack, b.pack_blocks, T + b.o_trial, b.trials_total, np, s)) != cudaSuccess)
+      return cuda_fail(e, "pack_mask + sample");
     RSM_CUDA(cudaEventRecord(slot.ev[2], s));
-    if ((e = launch_sample(D, T + b.o_trial, np, b.trials_total, s)) != cudaSuccess) return cuda_fail(e, "sample");
     RSM_CUDA(cudaEventRecord(slot.ev[3], s));
     for (const auto& g : b.slab_groups) {
       SlabPlan sp{D, np, b.nslab, T, b.tables.data(), g.o_slab};
