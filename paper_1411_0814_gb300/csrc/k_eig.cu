@@ -19,12 +19,15 @@
 //       X <- X - T R
 //     Components of X along an eigenvector with eigenvalue lambda shrink by
 //     about (tau + theta) / (lambda + tau) per step, so the r smallest Ritz
-//     pairs converge quickly when lambda_{r+1} >> tau.  M X runs in FP32-pair
-//     arithmetic (about 2^-44 relative) and the reductions and the
-//     Rayleigh-Ritz step in FP64.
-//   * FP64 refinement: two final passes with M X in IEEE FP64 (k_gemm_MX64):
-//     a residual and correction, then a Rayleigh-Ritz step whose FP64 residual
-//     M v - theta v is what the host checks against the eigen-gap.
+//     pairs converge quickly when lambda_{r+1} >> tau.  M X, the reductions and
+//     the Rayleigh-Ritz step run in FP32-pair arithmetic (about 2^-44
+//     relative; FP64 reductions with the FP64 factor).  The iteration stops
+//     at a residual target, or after the correction of a step that is
+//     predicted to reach it.
+//   * FP64 refinement: a final pass with M X in IEEE FP64 (k_gemm_MX64), a
+//     Rayleigh-Ritz step whose FP64 residual M v - theta v is what the host
+//     checks against the eigen-gap (with the FP64 factor a residual and
+//     correction pass first).
 // Every kernel is batched over the problems of the launch.
 #include <atomic>
 #include <utility>
